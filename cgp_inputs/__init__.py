@@ -1,0 +1,295 @@
+"""Seeded synthetic inputs for the coarse-grid-projection (CGP) step.
+
+This module is shared by the CUDA path's tests/bench and by the CPU oracle. It
+holds only problem *data*: coarse meshes drawn from a counter-based generator,
+boundary classification, boundary values and initial fields. None of the
+method's arithmetic (refinement, element matrices, solves, mapping) is here.
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014), used in counter form: draw ``k``
+of stream ``seed`` is ``mix(seed + (k + 1) * 0x9E3779B97F4A7C15)``.
+
+Workloads (the paper's Sect. 3 flows, reshaped to seeded synthetic meshes):
+
+* lid-driven cavity on the unit square (jittered random-diagonal grid);
+* backward-facing-step channel [0,30]x[0,2] minus the step [0,1]x[0,1]
+  (the paper's Sect. 3.2 geometry scaled by 2, parabolic inflow, open outflow);
+* Taylor-Green vortex on the unit square with exact Dirichlet data
+  (the paper's Eqs. 34-36; the paper's holed square is replaced by the plain
+  square so the jittered-grid generator can be reused).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Callable
+
+import numpy as np
+
+GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, idx: np.ndarray) -> np.ndarray:
+    """SplitMix64 output number ``idx`` (0-based) of the stream started at ``seed``."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (idx + np.uint64(1)) * GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, idx: np.ndarray) -> np.ndarray:
+    """Uniform doubles in [0, 1) from the top 53 bits of SplitMix64."""
+    return (splitmix64(seed, idx) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+# --------------------------------------------------------------------------------------
+# Coarse meshes
+# --------------------------------------------------------------------------------------
+
+@dataclass
+class CoarseMesh:
+    """A coarse P1 triangle mesh: node coordinates and counter-clockwise triangles."""
+    xy: np.ndarray          # float64 [n_nodes, 2]
+    tri: np.ndarray         # int32   [n_tris, 3], counter-clockwise
+    name: str = ""
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.xy.shape[0])
+
+    @property
+    def n_tris(self) -> int:
+        return int(self.tri.shape[0])
+
+
+def jittered_grid(x0: float, x1: float, y0: float, y1: float, nx: int, ny: int, seed: int,
+                  removed_cell: Callable[[np.ndarray, np.ndarray], np.ndarray] | None = None,
+                  jitter: float = 0.2) -> CoarseMesh:
+    """Grid of ``nx`` x ``ny`` cells, each split by a seed-random diagonal, interior nodes jittered.
+
+    Draw layout of the SplitMix64 stream ``seed``: draw ``c`` (cell ``c = j*nx + i`` of the full
+    bounding grid) picks the diagonal by its top bit; draws ``nx*ny + 2k`` and ``nx*ny + 2k + 1``
+    jitter node ``k = j*(nx+1) + i`` in x and y by ``U[-jitter*h, +jitter*h]``. Nodes on the
+    domain boundary (the boundary of the kept cells) are not moved. Cells for which
+    ``removed_cell(i, j)`` is true are cut out; nodes that no kept cell touches are dropped and the
+    rest renumbered in row-major order.
+    """
+    hx = (x1 - x0) / nx
+    hy = (y1 - y0) / ny
+    ii, jj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")  # [ny, nx]
+    keep = np.ones((ny, nx), dtype=bool)
+    if removed_cell is not None:
+        keep = ~removed_cell(ii, jj)
+    n_cells = nx * ny
+    diag = (splitmix64(seed, np.arange(n_cells)) >> np.uint64(63)).astype(np.int64).reshape(ny, nx)
+
+    # node usage and boundary detection: a node is on the boundary if its 4 surrounding cells are
+    # not all kept (cells outside the bounding box count as removed)
+    kp = np.zeros((ny + 2, nx + 2), dtype=bool)
+    kp[1:-1, 1:-1] = keep
+    # node (i, j) touches cells (i-1..i, j-1..j) -> padded indices (i..i+1, j..j+1)
+    c00 = kp[0:ny + 1, 0:nx + 1]
+    c10 = kp[0:ny + 1, 1:nx + 2]
+    c01 = kp[1:ny + 2, 0:nx + 1]
+    c11 = kp[1:ny + 2, 1:nx + 2]
+    used = c00 | c10 | c01 | c11
+    interior = c00 & c10 & c01 & c11
+
+    nI, nJ = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), indexing="xy")
+    # (x1-x0)*i/nx rather than i*hx so that grid lines such as x = 1 land exactly
+    x = x0 + (x1 - x0) * nI / nx
+    y = y0 + (y1 - y0) * nJ / ny
+    k = (nJ * (nx + 1) + nI).astype(np.int64)
+    jx = (2.0 * uniform01(seed, n_cells + 2 * k) - 1.0) * jitter * hx
+    jy = (2.0 * uniform01(seed, n_cells + 2 * k + 1) - 1.0) * jitter * hy
+    x = np.where(interior, x + jx, x)
+    y = np.where(interior, y + jy, y)
+
+    new_id = -np.ones((ny + 1) * (nx + 1), dtype=np.int64)
+    used_flat = used.ravel()
+    new_id[used_flat] = np.arange(int(used_flat.sum()))
+    xy = np.stack([x.ravel()[used_flat], y.ravel()[used_flat]], axis=1)
+
+    tris = []
+    cj, ci = np.nonzero(keep)
+    a = cj * (nx + 1) + ci
+    b = a + 1
+    c = a + (nx + 1) + 1
+    d = a + (nx + 1)
+    dg = diag[cj, ci]
+    # diagonal a-c: (a,b,c), (a,c,d); diagonal b-d: (a,b,d), (b,c,d); both counter-clockwise
+    t1 = np.where(dg[:, None] == 0, np.stack([a, b, c], 1), np.stack([a, b, d], 1))
+    t2 = np.where(dg[:, None] == 0, np.stack([a, c, d], 1), np.stack([b, c, d], 1))
+    tri = np.empty((2 * len(a), 3), dtype=np.int64)
+    tri[0::2] = t1
+    tri[1::2] = t2
+    tris = new_id[tri]
+    assert (tris >= 0).all()
+    return CoarseMesh(xy=np.ascontiguousarray(xy, dtype=np.float64),
+                      tri=np.ascontiguousarray(tris, dtype=np.int32))
+
+
+def cavity_mesh(n_side: int = 33, seed: int = 1000) -> CoarseMesh:
+    """Unit-square cavity mesh with ``n_side`` x ``n_side`` grid nodes."""
+    m = jittered_grid(0.0, 1.0, 0.0, 1.0, n_side - 1, n_side - 1, seed)
+    m.name = f"cavity{n_side}"
+    return m
+
+
+def bfs_mesh(cells_per_unit: int = 33, seed: int = 1001) -> CoarseMesh:
+    """Backward-facing-step channel [0,30]x[0,2] minus the step [0,1]x[0,1]."""
+    n = cells_per_unit
+    nx, ny = 30 * n, 2 * n
+    m = jittered_grid(0.0, 30.0, 0.0, 2.0, nx, ny, seed,
+                      removed_cell=lambda i, j: (i < n) & (j < n))
+    m.name = f"bfs{n}"
+    return m
+
+
+# --------------------------------------------------------------------------------------
+# Boundary conditions and problem definitions
+# --------------------------------------------------------------------------------------
+
+BC_U = 1   # bit 0: x-velocity Dirichlet
+BC_V = 2   # bit 1: y-velocity Dirichlet
+
+
+@dataclass
+class Problem:
+    """A flow problem: physical constants and boundary data as functions of node positions.
+
+    ``vel_bc(xy, on_boundary, t)`` returns ``(mask uint8[N], g float64[N,2])``: bit 0 / bit 1 of
+    ``mask`` mark nodes where u / v is prescribed, ``g`` holds the prescribed values (zero where
+    not prescribed). ``p_bc(xy, on_boundary)`` returns a uint8[N] mask of pressure nodes held at
+    p = 0 (the open boundary of the paper's Eq. 14, plus one pinned node for enclosed flows).
+    ``u0(xy, mask, g)`` is the initial velocity.
+    """
+    name: str
+    rho: float
+    mu: float
+    dt: float
+    levels: int
+    vel_bc: Callable
+    p_bc: Callable
+    u0: Callable
+    time_dependent_bc: bool = False
+    extra: dict = field(default_factory=dict)
+
+
+def _zero_u0(xy, mask, g):
+    u = np.zeros((xy.shape[0], 2))
+    u[mask & BC_U != 0, 0] = g[mask & BC_U != 0, 0]
+    u[mask & BC_V != 0, 1] = g[mask & BC_V != 0, 1]
+    return u
+
+
+def cavity_problem(re: float = 100.0, dt: float = 0.01, levels: int = 1) -> Problem:
+    """Lid-driven cavity: lid y=1 moves with u=1, other walls no-slip; corners take u=0.
+
+    The enclosed pressure problem is pinned at the node nearest (0, 0)."""
+
+    def vel_bc(xy, onb, t):
+        mask = np.where(onb, BC_U | BC_V, 0).astype(np.uint8)
+        g = np.zeros((xy.shape[0], 2))
+        lid = onb & (xy[:, 1] == 1.0) & (xy[:, 0] > 0.0) & (xy[:, 0] < 1.0)
+        g[lid, 0] = 1.0
+        return mask, g
+
+    def p_bc(xy, onb):
+        m = np.zeros(xy.shape[0], dtype=np.uint8)
+        m[int(np.argmin(xy[:, 0] ** 2 + xy[:, 1] ** 2))] = 1
+        return m
+
+    return Problem("cavity", 1.0, 1.0 / re, dt, levels, vel_bc, p_bc, _zero_u0)
+
+
+def bfs_problem(re: float = 400.0, dt: float = 0.005, levels: int = 1) -> Problem:
+    """Backward-facing step (the paper's Sect. 3.2 geometry scaled by 2).
+
+    Inflow on x=0, 1<=y<=2: u = 6(y-1)(2-y) (mean 1), v = 0. Walls no-slip. Outflow x=30 natural
+    for the velocity and p = 0 for the pressure (Eq. 14). Re = rho*H*mean/mu with H = 2.
+    """
+
+    def vel_bc(xy, onb, t):
+        x, y = xy[:, 0], xy[:, 1]
+        outflow = onb & (x == 30.0) & (y > 0.0) & (y < 2.0)
+        dir_ = onb & ~outflow
+        mask = np.where(dir_, BC_U | BC_V, 0).astype(np.uint8)
+        g = np.zeros((xy.shape[0], 2))
+        inflow = onb & (x == 0.0) & (y > 1.0) & (y < 2.0)
+        g[inflow, 0] = 6.0 * (y[inflow] - 1.0) * (2.0 - y[inflow])
+        return mask, g
+
+    def p_bc(xy, onb):
+        return (onb & (xy[:, 0] == 30.0)).astype(np.uint8)
+
+    return Problem("bfs", 1.0, 2.0 / re, dt, levels, vel_bc, p_bc, _zero_u0)
+
+
+def taylor_green_velocity(xy: np.ndarray, t: float, mu: float) -> np.ndarray:
+    """Taylor-Green velocity of the paper's Eqs. 34-35 (rho = 1)."""
+    x, y = xy[:, 0], xy[:, 1]
+    d = math.exp(-8.0 * math.pi ** 2 * mu * t)
+    return np.stack([-np.cos(2 * np.pi * x) * np.sin(2 * np.pi * y) * d,
+                     np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) * d], axis=1)
+
+
+def taylor_green_pressure(xy: np.ndarray, t: float, mu: float) -> np.ndarray:
+    """Taylor-Green pressure of the paper's Eq. 36 (rho = 1)."""
+    x, y = xy[:, 0], xy[:, 1]
+    return -(np.cos(4 * np.pi * x) + np.cos(4 * np.pi * y)) / 4.0 * math.exp(-16.0 * math.pi ** 2 * mu * t)
+
+
+def taylor_green_problem(mu: float = 0.01, dt: float = 0.01, levels: int = 1) -> Problem:
+    """Taylor-Green vortex on the unit square with exact Dirichlet velocity on the whole boundary.
+
+    All-Dirichlet velocity gives a pure-Neumann pressure problem (Eq. 13), pinned at the node
+    nearest (0, 0); pressures are compared modulo a constant."""
+
+    def vel_bc(xy, onb, t):
+        mask = np.where(onb, BC_U | BC_V, 0).astype(np.uint8)
+        g = np.where(onb[:, None], taylor_green_velocity(xy, t, mu), 0.0)
+        return mask, g
+
+    def p_bc(xy, onb):
+        m = np.zeros(xy.shape[0], dtype=np.uint8)
+        m[int(np.argmin(xy[:, 0] ** 2 + xy[:, 1] ** 2))] = 1
+        return m
+
+    def u0(xy, mask, g):
+        return taylor_green_velocity(xy, 0.0, mu)
+
+    return Problem("taylor_green", 1.0, mu, dt, levels, vel_bc, p_bc, u0, time_dependent_bc=True)
+
+
+# --------------------------------------------------------------------------------------
+# Named workloads
+# --------------------------------------------------------------------------------------
+
+def workload(name: str):
+    """Return ``(CoarseMesh, Problem, n_steps)`` for a named workload.
+
+    ``cavity33``: 33x33-node cavity, Re=100, dt=0.01, one refinement, 100 steps (seed 1000).
+    ``bfs33``: backward-facing step, h=1/33 (65,308 coarse nodes), Re=400, dt=0.005, one
+    refinement, 500 steps (seed 1001).
+    ``cavity129``: 129x129-node cavity, Re=100, dt=0.005, one refinement (seed 1004).
+    ``cavityN`` for other N: an N x N-node cavity (seed 1000), Re=100, dt=0.01.
+    """
+    if name == "cavity33":
+        return cavity_mesh(33, 1000), cavity_problem(100.0, 0.01, 1), 100
+    if name == "bfs33":
+        return bfs_mesh(33, 1001), bfs_problem(400.0, 0.005, 1), 500
+    if name == "cavity129":
+        return cavity_mesh(129, 1004), cavity_problem(100.0, 0.005, 1), 200
+    if name.startswith("bfs"):
+        n = int(name[3:])
+        return bfs_mesh(n, 1001), bfs_problem(400.0, 0.005, 1), 500
+    if name.startswith("cavity"):
+        n = int(name[6:])
+        return cavity_mesh(n, 1000), cavity_problem(100.0, 0.01, 1), 100
+    raise KeyError(name)

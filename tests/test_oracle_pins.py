@@ -1,0 +1,327 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+None of these tests compares the oracle with itself: each checks a hand-integrated value, a
+closed-form solution, an invariant of the continuous operators, a brute-force recomputation by
+quadrature and point location on a tiny mesh, or a convergence rate the paper states.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import cgp_inputs as ci
+from oracle import cgp, fem, refine
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------------------
+# Element matrices (Eqs. 16-18)
+# ----------------------------------------------------------------------------------------
+
+def _load_reference_triangle():
+    mats = {}
+    with open(os.path.join(GOLDEN, "p1_reference_triangle.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, i, j, num, den = line.split()
+            mats.setdefault(name, np.zeros((3, 3)))[int(i), int(j)] = int(num) / int(den)
+    return mats
+
+
+def test_element_matrices_reference_triangle():
+    """Hand-integrated element matrices on the right triangle (0,0),(1,0),(0,1)."""
+    gold = _load_reference_triangle()
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0]])
+    tri = np.array([[0, 1, 2]])
+    area, gx, gy = fem.triangle_geometry(xy, tri)
+    assert area[0] == 0.5
+    np.testing.assert_allclose(fem.element_mass(area)[0], gold["M"], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(fem.element_stiffness(area, gx, gy)[0], gold["K"], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(fem.element_div(area, gx)[0], gold["Dx"], rtol=0, atol=1e-15)
+    np.testing.assert_allclose(fem.element_div(area, gy)[0], gold["Dy"], rtol=0, atol=1e-15)
+    u_el = np.array([[[0.0, 0.0], [1.0, 0.0], [0.0, 0.0]]])          # u = (x, 0)
+    np.testing.assert_allclose(fem.element_convection(area, gx, gy, u_el)[0], gold["Nx"], rtol=0, atol=1e-15)
+
+
+@pytest.fixture(scope="module")
+def jmesh():
+    m = ci.cavity_mesh(17, 77)
+    return fem.P1Operators(m.xy, m.tri), refine.boundary_nodes(m.tri.astype(np.int64), m.n_nodes)
+
+
+def test_mass_sums_to_area(jmesh):
+    ops, _ = jmesh
+    assert abs(ops.M.sum() - 1.0) < 1e-13           # sum phi_i = 1 on the unit square
+
+
+def test_stiffness_annihilates_linear_fields(jmesh):
+    ops, onb = jmesh
+    x, y = ops.xy[:, 0], ops.xy[:, 1]
+    assert np.abs(ops.K @ np.ones(ops.n)).max() < 1e-12
+    r = ops.K @ (2.0 * x - 3.0 * y + 1.0)
+    assert np.abs(r[~onb]).max() < 1e-12            # -Laplacian of a linear field vanishes inside
+
+
+def test_divergence_of_coordinate_fields(jmesh):
+    """int phi_i d_x x = int phi_i = lumped mass; d_x y = 0."""
+    ops, _ = jmesh
+    x, y = ops.xy[:, 0], ops.xy[:, 1]
+    lumped = np.asarray(ops.M.sum(axis=1)).ravel()
+    np.testing.assert_allclose(ops.Dx @ x, lumped, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(ops.Dy @ y, lumped, rtol=0, atol=1e-15)
+    assert np.abs(ops.Dx @ y).max() < 1e-15 and np.abs(ops.Dy @ x).max() < 1e-15
+
+
+def test_convection_constant_velocity(jmesh):
+    """N(c) f = (c . grad f) int phi_i for constant c and linear f; N annihilates constants."""
+    ops, _ = jmesh
+    x, y = ops.xy[:, 0], ops.xy[:, 1]
+    c = np.array([0.7, -1.3])
+    N = ops.convection(np.tile(c, (ops.n, 1)))
+    lumped = np.asarray(ops.M.sum(axis=1)).ravel()
+    f = 2.0 * x + 5.0 * y
+    np.testing.assert_allclose(N @ f, (c[0] * 2.0 + c[1] * 5.0) * lumped, rtol=0, atol=1e-14)
+    assert np.abs(N @ np.ones(ops.n)).max() < 1e-14
+
+
+def test_convection_skew_for_divergence_free_velocity(jmesh):
+    """For div u = 0: N_ij + N_ji = boundary integral only, so it vanishes if i or j is interior."""
+    ops, onb = jmesh
+    x, y = ops.xy[:, 0], ops.xy[:, 1]
+    u = np.stack([0.3 + 2.0 * y, 1.1 - 0.5 * x], axis=1)             # linear, divergence-free
+    N = ops.convection(u).toarray()
+    S = N + N.T
+    inner = ~onb
+    assert np.abs(S[inner, :]).max() < 1e-14
+    assert np.abs(S[:, inner]).max() < 1e-14
+    assert np.abs(N[inner][:, inner]).max() > 1e-3                  # N itself is not zero
+
+
+def test_poisson_second_order_convergence():
+    """-Lap p = f with p = cos(pi x) cos(pi y), natural BC, P1 error O(h^2) (slope >= 1.85)."""
+    errs, hs = [], []
+    for n in (9, 17, 33, 65):
+        m = ci.cavity_mesh(n, 5)
+        ops = fem.P1Operators(m.xy, m.tri)
+        x, y = ops.xy[:, 0], ops.xy[:, 1]
+        pe = np.cos(np.pi * x) * np.cos(np.pi * y)
+        f = 2.0 * np.pi ** 2 * pe
+        K = ops.K.tolil()
+        b = ops.M @ f
+        b -= K[:, 0].toarray().ravel() * pe[0]
+        K[0, :] = 0.0
+        K[:, 0] = 0.0
+        K[0, 0] = 1.0
+        b[0] = pe[0]
+        import scipy.sparse.linalg as spla
+        p = spla.spsolve(K.tocsc(), b)
+        e = p - pe
+        e -= (ops.M @ e).sum() / ops.M.sum()                         # compare modulo a constant
+        errs.append(math.sqrt(e @ (ops.M @ e)))
+        hs.append(1.0 / (n - 1))
+    slopes = np.diff(np.log(errs)) / np.diff(np.log(hs))
+    assert (slopes > 1.85).all(), slopes
+
+
+def test_poisson_patch_test():
+    """A linear pressure with Dirichlet data on the whole boundary is reproduced exactly."""
+    m = ci.cavity_mesh(9, 3)
+    ops = fem.P1Operators(m.xy, m.tri)
+    onb = refine.boundary_nodes(m.tri.astype(np.int64), m.n_nodes)
+    pl = 1.5 * ops.xy[:, 0] - 0.25 * ops.xy[:, 1] + 3.0
+    K = ops.K.toarray()
+    free = ~onb
+    p = pl.copy()
+    p[free] = np.linalg.solve(K[np.ix_(free, free)], -K[np.ix_(free, onb)] @ pl[onb])
+    np.testing.assert_allclose(p, pl, rtol=0, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------------------
+# Refinement and mapping (Sect. 2.2, Remark 2.2, Eqs. 29-30)
+# ----------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mesh", [ci.cavity_mesh(9, 11), ci.bfs_mesh(3, 12)], ids=["cavity", "bfs"])
+@pytest.mark.parametrize("levels", [1, 2, 3])
+def test_refinement_topology(mesh, levels):
+    h = refine.build_hierarchy(mesh.xy, mesh.tri, levels)
+    for k in range(levels):
+        c, f = h.levels[k], h.levels[k + 1]
+        ec, _ = refine.edges_first_visit(c.tri, c.xy.shape[0])
+        ef, eof = refine.edges_first_visit(f.tri, f.xy.shape[0])
+        assert f.tri.shape[0] == 4 * c.tri.shape[0]                   # N = 4^{-l} M (Sect. 2.2)
+        assert f.xy.shape[0] == c.xy.shape[0] + ec.shape[0]
+        assert f.xy.shape[0] - ef.shape[0] + f.tri.shape[0] == 1      # Euler, simply connected
+        cnt = np.bincount(eof.ravel())
+        assert cnt.max() == 2                                         # conforming
+        area_c, _, _ = fem.triangle_geometry(c.xy, c.tri)
+        area_f, _, _ = fem.triangle_geometry(f.xy, f.tri)
+        assert area_f.min() > 0                                       # children counter-clockwise
+        assert abs(area_f.sum() - area_c.sum()) < 1e-12 * area_c.sum()
+        np.testing.assert_allclose(area_f.reshape(-1, 4).sum(1), area_c, rtol=1e-13)
+
+
+def test_restrict_prolong_identity_and_linear_exactness():
+    m = ci.cavity_mesh(9, 13)
+    h = refine.build_hierarchy(m.xy, m.tri, 3)
+    rng = np.random.default_rng(0)
+    pc = rng.standard_normal(m.n_nodes)
+    assert np.array_equal(refine.restrict(h, refine.prolong(h, pc)), pc)      # R P = I bitwise
+    lin = lambda xy: 3.0 * xy[:, 0] - 2.0 * xy[:, 1] + 0.5
+    np.testing.assert_allclose(refine.prolong(h, lin(h.coarse.xy)), lin(h.fine.xy), rtol=0, atol=1e-14)
+    # work counts of Remark 2.2: O(N_c) for R, sum of N_{k+1} for P
+    assert h.su.shape[0] == m.n_nodes
+    assert sum(s.shape[0] for s in h.sp) == sum(l.xy.shape[0] for l in h.levels[1:])
+
+
+def _shape_coeffs(p):
+    """Coefficients C so that [1, x, y] @ C[:, i] = phi_i, by inverting the vertex system."""
+    V = np.column_stack([np.ones(3), p[:, 0], p[:, 1]])
+    return np.linalg.inv(V), 0.5 * np.linalg.det(V)
+
+
+def _interp_matrix(coarse_xy, coarse_tri, pts):
+    """Dense P1 interpolation from the coarse mesh to ``pts`` by brute-force point location."""
+    P = np.zeros((pts.shape[0], coarse_xy.shape[0]))
+    for a, q in enumerate(pts):
+        for t in coarse_tri:
+            C, _ = _shape_coeffs(coarse_xy[t])
+            lam = np.array([1.0, q[0], q[1]]) @ C
+            if lam.min() > -1e-12:
+                P[a, t] = lam
+                break
+        else:
+            raise AssertionError("point outside mesh")
+    return P
+
+
+def test_prolongation_table_equals_coarse_interpolation():
+    """Eq. 29's midpoint average equals evaluating the coarse shape functions psi (nested spaces)."""
+    m = ci.cavity_mesh(5, 21)
+    h = refine.build_hierarchy(m.xy, m.tri, 2)
+    P = _interp_matrix(m.xy, m.tri.astype(np.int64), h.fine.xy)
+    pc = np.random.default_rng(1).standard_normal(m.n_nodes)
+    np.testing.assert_allclose(refine.prolong(h, pc), P @ pc, rtol=0, atol=1e-13)
+
+
+# ----------------------------------------------------------------------------------------
+# The whole step against a brute-force dense recomputation (Eqs. 19-23)
+# ----------------------------------------------------------------------------------------
+
+def _dense_ops(xy, tri, u=None):
+    """Dense M, K, Dx, Dy (and N(u)) by 3-point edge-midpoint quadrature (exact to degree 2)."""
+    n = xy.shape[0]
+    M, K, Dx, Dy, N = (np.zeros((n, n)) for _ in range(5))
+    for t in tri:
+        p = xy[t]
+        C, area = _shape_coeffs(p)
+        grad = C[1:, :]                                              # [2, 3]: d/dx, d/dy of phi_i
+        qs = 0.5 * (p + p[[1, 2, 0]])
+        for q in qs:
+            phi = np.array([1.0, q[0], q[1]]) @ C
+            w = area / 3.0
+            M[np.ix_(t, t)] += w * np.outer(phi, phi)
+            Dx[np.ix_(t, t)] += w * np.outer(phi, grad[0])
+            Dy[np.ix_(t, t)] += w * np.outer(phi, grad[1])
+            if u is not None:
+                uq = phi @ u[t]
+                N[np.ix_(t, t)] += w * np.outer(phi, uq @ grad)
+        K[np.ix_(t, t)] += area * grad.T @ grad
+    return M, K, Dx, Dy, N
+
+
+def _dense_cgp_step(prob, coarse, fine_xy, fine_tri, onb_f, onb_c, u_n, t_next):
+    rho, mu, dt = prob.rho, prob.mu, prob.dt
+    M, K, Dx, Dy, N = _dense_ops(fine_xy, fine_tri, u_n)
+    _, Kc, Dxc, Dyc, _ = _dense_ops(coarse.xy, coarse.tri.astype(np.int64))
+    # restriction by matching coordinates, prolongation by coarse interpolation
+    R = np.zeros((coarse.n_nodes, fine_xy.shape[0]))
+    for eta, q in enumerate(coarse.xy):
+        R[eta, np.flatnonzero((fine_xy == q).all(axis=1))[0]] = 1.0
+    P = _interp_matrix(coarse.xy, coarse.tri.astype(np.int64), fine_xy)
+    mask, g = prob.vel_bc(fine_xy, onb_f, t_next)
+    A = rho * M + dt * (rho * N + mu * K)
+    b = rho * M @ u_n
+    ut = np.zeros_like(u_n)
+    for c in range(2):
+        d = (mask & (1 << c)) != 0
+        Ac, bc = A.copy(), b[:, c].copy()
+        Ac[d, :] = 0.0
+        Ac[d, d] = 1.0
+        bc[d] = g[d, c]
+        ut[:, c] = np.linalg.solve(Ac, bc)
+    uc = R @ ut
+    bcoarse = -(rho / dt) * (Dxc @ uc[:, 0] + Dyc @ uc[:, 1])
+    pm = prob.p_bc(coarse.xy, onb_c).astype(bool)
+    Kb = Kc.copy()
+    Kb[pm, :] = 0.0
+    Kb[:, pm] = 0.0
+    Kb[pm, pm] = 1.0
+    bcoarse[pm] = 0.0
+    pc = np.linalg.solve(Kb, bcoarse)
+    pf = P @ pc
+    w = np.linalg.solve(M, np.stack([Dx @ pf, Dy @ pf], 1))
+    u = ut - dt / rho * w
+    for c in range(2):
+        d = (mask & (1 << c)) != 0
+        u[d, c] = g[d, c]
+    return dict(ut=ut, b_c=bcoarse, p_c=pc, p_f=pf, gp=w, u=u)
+
+
+@pytest.mark.parametrize("case,levels", [("cavity", 1), ("cavity", 0), ("tg", 2), ("bfs", 1)])
+def test_step_matches_bruteforce_dense(case, levels):
+    if case == "cavity":
+        coarse, prob = ci.cavity_mesh(5, 31), ci.cavity_problem(100.0, 0.01, levels)
+    elif case == "tg":
+        coarse, prob = ci.cavity_mesh(4, 32), ci.taylor_green_problem(0.01, 0.01, levels)
+    else:
+        coarse, prob = ci.bfs_mesh(2, 33), ci.bfs_problem(400.0, 0.005, levels)
+    orc = cgp.CGPOracle(coarse.xy, coarse.tri, prob.rho, prob.mu, prob.dt, levels, prob.vel_bc, prob.p_bc)
+    rng = np.random.default_rng(7)
+    u_n = 0.5 * rng.standard_normal((orc.n_fine, 2))                # exercise N with a rough field
+    t_next = 0.37
+    got = orc.step(u_n, t_next)
+    ref = _dense_cgp_step(prob, coarse, orc.fine.xy, orc.fine.tri, orc.onb_f, orc.onb_c, u_n, t_next)
+    for k, v in ref.items():
+        a = getattr(got, k)
+        err = np.linalg.norm(a - v) / max(np.linalg.norm(v), 1e-300)
+        assert err < 1e-11, (k, err)
+
+
+def test_enclosed_flow_rhs_is_compatible():
+    """sum_i (D u~)_i = closed-contour integral of u~ . n = 0 for the cavity (tangential lid)."""
+    coarse, prob = ci.workload("cavity33")[:2]
+    res, orc = cgp.run(coarse, prob, 3, return_oracle=True)
+    uc = refine.restrict(orc.h, res.ut)
+    d = orc.coarse.Dx @ uc[:, 0] + orc.coarse.Dy @ uc[:, 1]
+    assert abs(d.sum()) < 1e-13 * np.abs(d).sum()
+
+
+# ----------------------------------------------------------------------------------------
+# Taylor-Green (Eqs. 34-36): first order in time, and CGP close to the standard scheme
+# ----------------------------------------------------------------------------------------
+
+def _tg_error(coarse, dt, t_end, levels):
+    prob = ci.taylor_green_problem(0.01, dt, levels)
+    n = int(round(t_end / dt))
+    res, orc = cgp.run(coarse, prob, n, return_oracle=True)
+    ue = ci.taylor_green_velocity(orc.fine.xy, n * dt, 0.01)
+    return np.linalg.norm(res.u - ue) / np.linalg.norm(ue), res, orc
+
+
+def test_taylor_green_first_order_in_time():
+    """Non-incremental pressure correction is first order in time (Sect. 1, ref. [1]; Remark 3.1)."""
+    coarse = ci.cavity_mesh(33, 41)
+    e = [_tg_error(coarse, dt, 0.2, 1)[0] for dt in (0.04, 0.02, 0.01)]
+    rates = np.log2(np.array(e[:-1]) / np.array(e[1:]))
+    assert ((rates > 0.75) & (rates < 1.25)).all(), (e, rates)
+
+
+def test_taylor_green_cgp_close_to_standard():
+    """One level of CGP on a 65x65-node fine mesh stays within 15 % of the standard scheme's
+    velocity error (Table 1: the l = 1 velocity error grows only mildly over l = 0)."""
+    e0, _, _ = _tg_error(ci.cavity_mesh(65, 42), 0.01, 0.1, 0)
+    e1, _, _ = _tg_error(ci.cavity_mesh(33, 42), 0.01, 0.1, 1)
+    assert e1 < 1.15 * e0, (e0, e1)
