@@ -1,0 +1,292 @@
+"""Benchmark of the CGP time step on one GB300 (or N independent replicas under torchrun).
+
+Workload: the backward-facing-step channel [0,30]x[0,2] minus [0,1]^2, jittered random-diagonal
+coarse mesh with h = 1/33 (65,308 coarse / 259,117 fine nodes, one 1:4 refinement), Re = 400,
+dt = 0.005, rtol = 1e-8 for every solve (the paper's Sect. 2.3 tolerance). A "step" is one whole
+cgp_step (Eqs. 19-23). The state is warmed up for W steps from rest, then K steps are timed one
+by one with CUDA events on the launching stream; between timed steps a 512 MB buffer is written
+to flush L2 (outside the timed region).
+
+Prints one JSON line: steps/s (value), coarse Poisson solves/s, the roofline of the dominant
+kernel (the persistent coarse CG), the end-to-end rate through cgp_step_host with host buffers,
+and the oracle timed on the host cores (cpu_baseline). ``--impl reference`` times the CPU oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import cgp_inputs as ci  # noqa: E402
+
+WORKLOAD = "bfs33"
+METRIC = "time steps/sec & coarse Poisson solves/sec at 1e-8 rel. residual; SpMV HBM GB/s vs peak"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(n_steps: int):
+    """Time the CPU oracle on the same workload: setup once, then ``n_steps`` steps from rest."""
+    from oracle import cgp as ocgp
+    coarse, prob, _ = ci.workload(WORKLOAD)
+    t0 = time.perf_counter()
+    orc = ocgp.CGPOracle(coarse.xy, coarse.tri, prob.rho, prob.mu, prob.dt, prob.levels, prob.vel_bc, prob.p_bc)
+    t_setup = time.perf_counter() - t0
+    mask, g = orc.dirichlet(0.0)
+    u = prob.u0(orc.fine.xy, mask, g)
+    times = []
+    for k in range(n_steps):
+        t0 = time.perf_counter()
+        r = orc.step(u, (k + 1) * prob.dt)
+        times.append(time.perf_counter() - t0)
+        u = r.u
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([1] + [int(i.get("num_threads", 1)) for i in threadpool_info()])
+    except Exception:
+        cores = 1
+    return times, t_setup, cores
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    times, t_setup, cores = oracle_sample(max(1, min(args.steps, 10)))
+    ms = 1000.0 * statistics.mean(times)
+    v = 1000.0 / ms
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": 0, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: backward-facing step 65,308/259,117 nodes, Re=400, dt=0.005",
+                       "levels": 1, "rtol": "direct LU"},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{len(times)} oracle steps from rest after a {t_setup:.1f}s setup"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    from paper_1610_06993_gb300 import cgp as L
+    from paper_1610_06993_gb300.flow import Flow
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if not os.path.exists(L.LIB_PATH):
+        raise RuntimeError("libcgp.so is not built; run python -c 'import __graft_entry__ as g; g.build()'")
+    coarse, prob, _ = ci.workload(WORKLOAD)
+    prec = L.CGP_MIXED if args.precision == "mixed" else L.CGP_FP64
+    f = Flow(coarse, prob, precision=prec, rtol=args.rtol, device=f"cuda:{local}",
+             block_threads=args.threads, spmv_lanes=args.lanes)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+    bc = torch.empty_like(f.pc)
+    ut = torch.empty_like(f.u)
+
+    def step_parts(ev):
+        """One cgp_step through its stage entry points, with events around the Poisson solve."""
+        L.cgp_assemble(f.ctx, f.u, stream)
+        L.cgp_momentum_solve(f.ctx, f.u, ut, stream)
+        L.cgp_restrict(f.ctx, ut, bc, stream)
+        ev[0].record(stream)
+        L.cgp_poisson_solve(f.ctx, bc, f.pc, stream)
+        ev[1].record(stream)
+        L.cgp_prolong_correct(f.ctx, f.pc, ut, f.u, None, None, stream)
+
+    for _ in range(args.warmup):
+        L.cgp_step(f.ctx, f.u, f.pc, stream)
+    L.cgp_get_stats(f.ctx, stream, check=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+
+    step_ms, poi_ms, poi_iters, poi_outer, mom_iters, mass_iters = [], [], [], [], [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            e[2].record(stream)
+            step_parts(e)
+            e[3].record(stream)
+            st = L.cgp_get_stats(f.ctx, stream, check=True)
+            step_ms.append(e[2].elapsed_time(e[3]))
+            poi_ms.append(e[0].elapsed_time(e[1]))
+            poi_iters.append(st.poisson_iters)
+            poi_outer.append(st.poisson_outer)
+            mom_iters.append(st.momentum_iters)
+            mass_iters.append(st.mass_iters)
+    torch.cuda.synchronize()
+    ms = statistics.mean(step_ms)
+    if ws > 1:
+        t = torch.tensor([ms], device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    uh = torch.empty(f.u.shape, dtype=torch.float64, pin_memory=True)
+    ph = torch.empty(f.pc.shape, dtype=torch.float64, pin_memory=True)
+    uh.copy_(f.u)
+    ph.copy_(f.pc)
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        t0 = time.perf_counter()
+        L.cgp_step_host(f.ctx, uh, ph, stream)
+        e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    L.cgp_get_stats(f.ctx, stream, check=True)
+    h2d = (2 * f.info.n_fine + f.info.n_coarse) * 8
+
+    # roofline of the dominant kernel: the persistent coarse CG, algorithmic bytes per launch
+    nnz, n = f.info.nnz_coarse, f.info.n_coarse
+    it = statistics.mean(poi_iters)
+    outer = statistics.mean(poi_outer)
+    if prec == L.CGP_FP64:
+        per_iter = 12 * nnz + 60 * n
+    else:
+        per_iter = 8 * nnz + 32 * n
+    per_pass = 12 * nnz + 20 * n + 8 * n       # FP64 true residual (+ x update) per refinement pass
+    alg_bytes = it * per_iter + (outer + 1) * per_pass
+    pms = statistics.mean(poi_ms)
+    achieved = alg_bytes / (pms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        times, t_setup, cores = oracle_sample(args.cpu_steps)
+        cpu = {"value": 1.0 / statistics.mean(times), "unit": "steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{len(times)} oracle steps of the same workload from rest (setup {t_setup:.1f}s excluded)"}
+
+    launches_per_step = 7 + f.info.levels
+    line = {
+        "metric": METRIC, "value": ws * 1000.0 / ms, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == L.CGP_FP64 else "f32+f64-ir", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: backward-facing step, coarse 65,308 / fine 259,117 nodes, "
+                               f"l=1, Re=400, dt=0.005", "rtol": args.rtol, "precision": args.precision,
+                   "l2": "flushed between timed steps (512 MB write)", "parallelism": "replicas" if ws > 1 else "1gpu",
+                   "block_threads": f.info.block_threads, "grid_blocks": f.info.grid_blocks,
+                   "spmv_lanes": f.info.spmv_lanes},
+        "coarse_solves_per_s": 1000.0 / pms,
+        "poisson_ms": pms, "poisson_iters": it, "poisson_outer": outer,
+        "momentum_iters": statistics.mean(mom_iters), "mass_iters": statistics.mean(mass_iters),
+        "roofline": {"kernel": "k_cg (persistent coarse CG)", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "alg_bytes_per_launch": alg_bytes, "note": "coarse matrix + vectors (~9 MB) are L2-resident"},
+        "e2e": {"value": 1000.0 / statistics.mean(e2e_ms), "unit": "steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": h2d},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    f.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * cgp.h -- C ABI of the GB300 (sm_103a) coarse-grid-projection (CGP) pressure-correction library.
+ *
+ * The library advances the incompressible Navier-Stokes equations by the IFE-CGP scheme of
+ * Kashefi & Staples, "A Finite-Element Coarse-Grid Projection Method" (Sect. 2.2, Eqs. 19-23):
+ * a semi-implicit P1 momentum solve on a fine triangle mesh, injection of the intermediate
+ * velocity onto the coarse mesh, a coarse pressure Poisson solve, prolongation of the pressure
+ * through parent/child tables (Eq. 29) and a consistent-mass velocity correction.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: CGP_OK (0) or one of the CGP_ERR_* codes below; cgp_status_str() names it.
+ * - Pointers named *_host are host memory; pointers named *_dev are device memory on the device
+ *   that was current when the context was created. All of them are owned by the caller; the
+ *   library copies what it keeps and never frees caller memory.
+ * - Layouts: node fields are float64, contiguous; velocity-like fields are interleaved
+ *   [n][2] = (x, y) pairs; triangles are int32 [t][3] counter-clockwise.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Calls that
+ *   take a stream are asynchronous and stream-ordered: they enqueue kernels and return; errors
+ *   found on the device (no convergence, NaN, a device wait that ran out) are recorded in the
+ *   context's device status and read back by cgp_get_stats().
+ * - Ordering: the fine mesh numbering is fixed by the refinement rule of cgp_mesh_create().
+ * - A context is not thread-safe; use one context per host thread or serialise calls.
+ */
+#ifndef CGP_H
+#define CGP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define CGP_OK                 0
+#define CGP_ERR_ARG            1  /* a NULL pointer, a size out of range or an unknown option      */
+#define CGP_ERR_MESH           2  /* bad orientation, index out of range, non-manifold edge        */
+#define CGP_ERR_CUDA           3  /* a CUDA runtime call failed                                    */
+#define CGP_ERR_NOT_CONVERGED  4  /* a solve hit max_iter; its result is still written             */
+#define CGP_ERR_NAN            5  /* a non-finite residual or inner product                        */
+#define CGP_ERR_TIMEOUT        6  /* a bounded device-side wait gave up (grid barrier)             */
+#define CGP_ERR_NOMEM          7  /* device or host allocation failed                              */
+#define CGP_ERR_STATE          8  /* call out of order (e.g. a step before cgp_set_bc)             */
+
+/* ---- precision modes --------------------------------------------------------------------- */
+#define CGP_FP64   0  /* every Krylov iteration in FP64                                            */
+#define CGP_MIXED  1  /* FP32 inner Krylov iterations inside FP64 iterative refinement for the     */
+                      /* momentum and Poisson solves; true residuals, refinement updates and the   */
+                      /* mass-matrix velocity correction stay FP64                                  */
+
+/* ---- boundary masks ------------------------------------------------------------------------ */
+#define CGP_BC_U   1  /* bit 0 of a fine-node velocity mask: x-velocity prescribed (Eqs. 3, 10)   */
+#define CGP_BC_V   2  /* bit 1: y-velocity prescribed                                             */
+
+typedef struct cgp_ctx_s* cgp_ctx;
+
+/* Physical and solver parameters. rho, mu, dt: density, dynamic viscosity and time step of the
+ * semi-implicit BDF1 scheme (Eqs. 5-8). levels: number l of 1:4 refinements from the pressure
+ * (coarse) mesh to the velocity (fine) mesh (Sect. 2.2); l = 0 is the standard scheme.
+ * rtol: every solve stops when ||b - A x||_2 <= rtol ||b||_2 for each right-hand side (the
+ * paper's Sect. 2.3 uses 1e-8). inner_rtol: CGP_MIXED only, the FP32 inner solve's reduction of
+ * the FP64 residual per refinement pass (0 = default 1e-4). max_iter: cap on the total number of
+ * Krylov iterations of one solve. max_outer: cap on refinement passes (0 = default 30).
+ * spmv_lanes: lanes per CSR row in the SpMV inner loops (0 = let cgp_autotune()/default decide;
+ * otherwise 1, 2, 4, 8, 16 or 32). block_threads: threads per block of the persistent kernels
+ * (0 = default 512). */
+typedef struct {
+    double rho, mu, dt;
+    int levels;
+    int precision;
+    double rtol;
+    double inner_rtol;
+    int max_iter;
+    int max_outer;
+    int spmv_lanes;
+    int block_threads;
+} cgp_params;
+
+/* A coarse mesh: n_nodes points xy_host[n][2] and n_tris counter-clockwise triangles
+ * tri_host[t][3] (0-based). The coarse mesh is the pressure mesh V_{4-k} of Sect. 2.2. */
+typedef struct {
+    int n_nodes, n_tris;
+    const double* xy_host;
+    const int* tri_host;
+} cgp_mesh_desc;
+
+/* Sizes of a context. n_fine/n_coarse: velocity/pressure nodes; nnz_*: CSR entries of the P1
+ * pattern (node i couples to itself and its edge neighbours); n_colours: element colours of the
+ * fine mesh used by the assembly; grid_blocks: blocks of the persistent solver kernels. */
+typedef struct {
+    int n_fine, n_coarse, tris_fine, tris_coarse, nnz_fine, nnz_coarse, levels;
+    int n_colours, grid_blocks, block_threads, spmv_lanes;
+} cgp_info;
+
+/* Per-solve statistics of the most recent step (read back by cgp_get_stats, which synchronises
+ * the stream). iters: total inner Krylov iterations; outer: refinement passes; rel_res: final
+ * FP64 true relative residual ||b - A x|| / ||b|| (max over the right-hand sides); status: the
+ * CGP_* code of that solve. */
+typedef struct {
+    int momentum_iters, momentum_outer, momentum_status;
+    int poisson_iters, poisson_outer, poisson_status;
+    int mass_iters, mass_status;
+    int barrier_status;
+    double momentum_rel_res, poisson_rel_res, mass_rel_res;
+} cgp_stats;
+
+/* Fill *p with the defaults: rho = 1, mu = 0.01, dt = 0.01, levels = 1, CGP_FP64, rtol = 1e-8,
+ * inner_rtol = 1e-4, max_iter = 20000, max_outer = 30, spmv_lanes = 0, block_threads = 0. */
+void cgp_default_params(cgp_params* p);
+
+/* Preprocessing (the paper's C_pre, Sect. 2.4): validates the coarse mesh, refines it
+ * prm->levels times by conforming 1:4 splits (Sect. 2.2) with the numbering
+ *   parents keep 0..N_k-1; one midpoint per edge, appended in order of first visit
+ *   (triangles in order, local edges (a,b), (b,c), (c,a)); triangle t = (a,b,c) becomes
+ *   4t: (a,m_ab,m_ca), 4t+1: (m_ab,b,m_bc), 4t+2: (m_ca,m_bc,c), 4t+3: (m_ab,m_bc,m_ca),
+ * builds the s^p tables of Eq. 29 and the s^u table of Eq. 30, the CSR patterns, the element
+ * colouring, uploads them and assembles the constant P1 matrices (Eqs. 16-18) on the device.
+ * Host arrays are copied. On success *out owns device memory until cgp_mesh_destroy().
+ * Errors: CGP_ERR_ARG (NULL, n <= 0, levels outside 0..4), CGP_ERR_MESH (index out of range,
+ * non-positive area, an edge shared by more than two triangles), CGP_ERR_CUDA, CGP_ERR_NOMEM. */
+int cgp_mesh_create(const cgp_mesh_desc* coarse, const cgp_params* prm, cgp_ctx* out);
+
+/* Host-only preprocessing query (no device calls): refine the coarse mesh `levels` times with
+ * the same rule as cgp_mesh_create() (Sect. 2.2) and report the fine mesh. Call once with NULL
+ * outputs to learn *n_fine / *n_tris_fine, then again with buffers: xy_host [n_fine][2],
+ * tri_host [n_tris_fine][3], sp_host [n_fine][2] (the s^p pairs of Eq. 29 from level l-1 to
+ * level l; for levels = 0 the identity pairs), colour_host [n_tris_fine] (the element colour of
+ * the fine assembly). Any output may be NULL. Errors: CGP_ERR_ARG, CGP_ERR_MESH. */
+int cgp_refine(const cgp_mesh_desc* coarse, int levels, int* n_fine, int* n_tris_fine, double* xy_host,
+               int* tri_host, int* sp_host, int* colour_host);
+
+/* Sizes and launch shapes of the context. */
+int cgp_mesh_info(cgp_ctx ctx, cgp_info* info);
+
+/* Copy the fine (velocity) mesh out: xy_host[n_fine][2], tri_host[tris_fine][3] and
+ * on_boundary_host[n_fine] (1 where the node lies on an edge with a single triangle). Any of
+ * the three may be NULL. The coarse mesh is the caller's input. */
+int cgp_fine_mesh(cgp_ctx ctx, double* xy_host, int* tri_host, unsigned char* on_boundary_host);
+
+/* Boundary classes. vel_mask_host[n_fine]: CGP_BC_U / CGP_BC_V bits of velocity-Dirichlet
+ * nodes (Eqs. 3, 10); nodes without bits are natural (Eq. 11; nothing is assembled there).
+ * p_mask_host[n_coarse]: 1 where the coarse pressure is held at 0 (Eq. 14 on the open boundary,
+ * plus one pinned node for enclosed flows whose pure-Neumann problem of Eq. 13 is singular);
+ * those rows and columns are eliminated symmetrically. g_host[n_fine][2]: prescribed velocity
+ * values (read only where a bit is set). Synchronous. Errors: CGP_ERR_ARG. */
+int cgp_set_bc(cgp_ctx ctx, const unsigned char* vel_mask_host, const unsigned char* p_mask_host,
+               const double* g_host);
+
+/* Replace the prescribed velocity values (e.g. time-dependent data at t^{n+1}) from a device
+ * array g_dev[n_fine][2]; stream-ordered copy. */
+int cgp_set_dirichlet_values(cgp_ctx ctx, const double* g_dev, void* stream);
+
+/* Step 1 set-up, Eq. 19: A = rho M + dt (rho N(u^n) + mu K) written into the fixed fine CSR
+ * pattern by a colour-scheduled element loop (no atomics, deterministic), the Jacobi diagonal
+ * per component, and the right-hand side b = rho M u^n with Dirichlet rows set to the prescribed
+ * values. u_dev: [n_fine][2] velocity u^n. */
+int cgp_assemble(cgp_ctx ctx, const double* u_dev, void* stream);
+
+/* Step 1, Eq. 19: solve A u~ = b (per component, Dirichlet rows replaced by identity rows) by
+ * Jacobi-preconditioned BiCGStab on both components at once (CGP_MIXED: FP32 BiCGStab inside FP64
+ * iterative refinement). Requires cgp_assemble() on the same u^n first. u_dev is the initial guess
+ * (u^n); ut_dev: [n_fine][2] output u~^{n+1}. ut_dev may equal u_dev. */
+int cgp_momentum_solve(cgp_ctx ctx, const double* u_dev, double* ut_dev, void* stream);
+
+/* Steps 2-3 right-hand side, Eqs. 20-21 with Eq. 30: u~_c = u~_f[xi] (injection), then
+ * b_c = -(rho/dt) (Dx_c u~_c,x + Dy_c u~_c,y) with D_ij = int psi_i d phi_j on the coarse mesh,
+ * zero at p-masked nodes. ut_dev: [n_fine][2]; bc_dev: [n_coarse] output. */
+int cgp_restrict(cgp_ctx ctx, const double* ut_dev, double* bc_dev, void* stream);
+
+/* Step 3, Eq. 21: solve K_c p_c = b_c (K_c = coarse stiffness, +(-Laplacian), after symmetric
+ * elimination of masked nodes) by Jacobi-preconditioned conjugate gradients in a single
+ * persistent kernel (CGP_MIXED: FP32 CG inside FP64 iterative refinement). pc_dev [n_coarse] is
+ * the initial guess on entry (warm start) and the solution on exit. */
+int cgp_poisson_solve(cgp_ctx ctx, const double* bc_dev, double* pc_dev, void* stream);
+
+/* Steps 4-5, Eqs. 22-23 with Eq. 29: p_f = P p_c level by level, g = G p_f (G_ij = int phi_i
+ * d psi_j), w = M^{-1} g by FP64 Jacobi-CG on the consistent mass matrix, then
+ * u = u~ - (dt/rho) w and Dirichlet nodes reset to their prescribed values.
+ * pc_dev [n_coarse], ut_dev [n_fine][2] inputs; u_dev [n_fine][2] output (may equal ut_dev);
+ * pf_dev [n_fine] and gp_dev [n_fine][2] optional outputs (NULL to skip): p_f and w. */
+int cgp_prolong_correct(cgp_ctx ctx, const double* pc_dev, const double* ut_dev, double* u_dev,
+                        double* pf_dev, double* gp_dev, void* stream);
+
+/* One whole time step (Eqs. 19-23): assemble, momentum, restrict, Poisson (warm-started from
+ * pc_dev), prolong-correct. u_dev [n_fine][2] holds u^n on entry and u^{n+1} on exit; pc_dev
+ * [n_coarse] holds p_c^n on entry and p_c^{n+1} on exit. Stream-ordered, no host sync. */
+int cgp_step(cgp_ctx ctx, double* u_dev, double* pc_dev, void* stream);
+
+/* The same step on host buffers: copies u_host [n_fine][2] and pc_host [n_coarse] to the
+ * context's device staging buffers, runs cgp_step, copies both back and synchronises the
+ * stream. For best copy speed the host buffers should be page-locked. */
+int cgp_step_host(cgp_ctx ctx, double* u_host, double* pc_host, void* stream);
+
+/* Synchronise the stream and read the statistics of the latest solves. Returns the first
+ * non-OK status among them (CGP_ERR_NOT_CONVERGED, CGP_ERR_NAN, CGP_ERR_TIMEOUT) or CGP_OK. */
+int cgp_get_stats(cgp_ctx ctx, void* stream, cgp_stats* st);
+
+/* Time the SpMV lane counts {1, 2, 4, 8} on the fine and coarse matrices and keep the fastest
+ * for the solver kernels (a project-written autotuner, not in the paper). Synchronous. */
+int cgp_autotune(cgp_ctx ctx, void* stream);
+
+/* Free everything the context owns. NULL is accepted. */
+int cgp_mesh_destroy(cgp_ctx ctx);
+
+/* Name of a status code (static string). */
+const char* cgp_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CGP_H */

@@ -1,0 +1,245 @@
+"""Thin ctypes binding of ``libcgp.so`` (the C ABI declared in ``include/cgp.h``).
+
+Every function here only marshals arguments: torch tensors become device pointers, numpy arrays
+become host pointers, and the CUDA library does all the work. There is no CPU fallback: if the
+library has not been built, importing the functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcgp.so")
+
+CGP_OK = 0
+CGP_ERR_ARG = 1
+CGP_ERR_MESH = 2
+CGP_ERR_CUDA = 3
+CGP_ERR_NOT_CONVERGED = 4
+CGP_ERR_NAN = 5
+CGP_ERR_TIMEOUT = 6
+CGP_ERR_NOMEM = 7
+CGP_ERR_STATE = 8
+CGP_FP64 = 0
+CGP_MIXED = 1
+CGP_BC_U = 1
+CGP_BC_V = 2
+
+
+class cgp_params(C.Structure):
+    _fields_ = [("rho", C.c_double), ("mu", C.c_double), ("dt", C.c_double), ("levels", C.c_int),
+                ("precision", C.c_int), ("rtol", C.c_double), ("inner_rtol", C.c_double),
+                ("max_iter", C.c_int), ("max_outer", C.c_int), ("spmv_lanes", C.c_int),
+                ("block_threads", C.c_int)]
+
+
+class cgp_mesh_desc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int), ("n_tris", C.c_int), ("xy_host", C.POINTER(C.c_double)),
+                ("tri_host", C.POINTER(C.c_int))]
+
+
+class cgp_info(C.Structure):
+    _fields_ = [(k, C.c_int) for k in ("n_fine", "n_coarse", "tris_fine", "tris_coarse", "nnz_fine",
+                                       "nnz_coarse", "levels", "n_colours", "grid_blocks",
+                                       "block_threads", "spmv_lanes")]
+
+
+class cgp_stats(C.Structure):
+    _fields_ = [(k, C.c_int) for k in ("momentum_iters", "momentum_outer", "momentum_status",
+                                       "poisson_iters", "poisson_outer", "poisson_status", "mass_iters",
+                                       "mass_status", "barrier_status")] + \
+               [(k, C.c_double) for k in ("momentum_rel_res", "poisson_rel_res", "mass_rel_res")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_VP = C.c_void_p
+_SIGNATURES = {
+    "cgp_default_params": (None, [C.POINTER(cgp_params)]),
+    "cgp_mesh_create": (C.c_int, [C.POINTER(cgp_mesh_desc), C.POINTER(cgp_params), C.POINTER(_VP)]),
+    "cgp_refine": (C.c_int, [C.POINTER(cgp_mesh_desc), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                             _VP, _VP, _VP, _VP]),
+    "cgp_mesh_info": (C.c_int, [_VP, C.POINTER(cgp_info)]),
+    "cgp_fine_mesh": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "cgp_set_bc": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "cgp_set_dirichlet_values": (C.c_int, [_VP, _VP, _VP]),
+    "cgp_assemble": (C.c_int, [_VP, _VP, _VP]),
+    "cgp_momentum_solve": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "cgp_restrict": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "cgp_poisson_solve": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "cgp_prolong_correct": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "cgp_step": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "cgp_step_host": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "cgp_get_stats": (C.c_int, [_VP, _VP, C.POINTER(cgp_stats)]),
+    "cgp_autotune": (C.c_int, [_VP, _VP]),
+    "cgp_mesh_destroy": (C.c_int, [_VP]),
+    "cgp_status_str": (C.c_char_p, [C.c_int]),
+}
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load ``libcgp.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CGP CUDA library not built: {LIB_PATH} is missing "
+                               "(run `python -m paper_1610_06993_gb300.build`)")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class CGPError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {load().cgp_status_str(code).decode()}")
+
+
+def _check(code: int, where: str) -> int:
+    if code != CGP_OK:
+        raise CGPError(code, where)
+    return code
+
+
+def _ptr(t) -> int | None:
+    """Device pointer of a torch tensor, host pointer of a numpy array, or None."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous()
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def default_params(**kw) -> cgp_params:
+    p = cgp_params()
+    load().cgp_default_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+# ---- the C entry points, same names, argument marshalling only -----------------------------
+
+def cgp_mesh_create(xy: np.ndarray, tri: np.ndarray, params: cgp_params) -> int:
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    d = cgp_mesh_desc(int(xy.shape[0]), int(tri.shape[0]), xy.ctypes.data_as(C.POINTER(C.c_double)),
+                      tri.ctypes.data_as(C.POINTER(C.c_int)))
+    h = _VP()
+    _check(load().cgp_mesh_create(C.byref(d), C.byref(params), C.byref(h)), "cgp_mesh_create")
+    return h.value
+
+
+def cgp_refine(xy: np.ndarray, tri: np.ndarray, levels: int):
+    """Host-only refinement query. Returns ``(xy_f, tri_f, sp, colour)``."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    d = cgp_mesh_desc(int(xy.shape[0]), int(tri.shape[0]), xy.ctypes.data_as(C.POINTER(C.c_double)),
+                      tri.ctypes.data_as(C.POINTER(C.c_int)))
+    nf, tf = C.c_int(), C.c_int()
+    _check(load().cgp_refine(C.byref(d), levels, C.byref(nf), C.byref(tf), None, None, None, None), "cgp_refine")
+    xf = np.empty((nf.value, 2), dtype=np.float64)
+    tr = np.empty((tf.value, 3), dtype=np.int32)
+    sp = np.empty((nf.value, 2), dtype=np.int32)
+    col = np.empty(tf.value, dtype=np.int32)
+    _check(load().cgp_refine(C.byref(d), levels, C.byref(nf), C.byref(tf), xf.ctypes.data, tr.ctypes.data,
+                             sp.ctypes.data, col.ctypes.data), "cgp_refine")
+    return xf, tr, sp, col
+
+
+def cgp_mesh_info(ctx: int) -> cgp_info:
+    info = cgp_info()
+    _check(load().cgp_mesh_info(ctx, C.byref(info)), "cgp_mesh_info")
+    return info
+
+
+def cgp_fine_mesh(ctx: int):
+    info = cgp_mesh_info(ctx)
+    xy = np.empty((info.n_fine, 2), dtype=np.float64)
+    tri = np.empty((info.tris_fine, 3), dtype=np.int32)
+    onb = np.empty(info.n_fine, dtype=np.uint8)
+    _check(load().cgp_fine_mesh(ctx, xy.ctypes.data, tri.ctypes.data, onb.ctypes.data), "cgp_fine_mesh")
+    return xy, tri, onb.astype(bool)
+
+
+def cgp_set_bc(ctx: int, vel_mask: np.ndarray, p_mask: np.ndarray, g: np.ndarray) -> None:
+    vm = np.ascontiguousarray(vel_mask, dtype=np.uint8)
+    pm = np.ascontiguousarray(p_mask, dtype=np.uint8)
+    gg = np.ascontiguousarray(g, dtype=np.float64)
+    _check(load().cgp_set_bc(ctx, vm.ctypes.data, pm.ctypes.data, gg.ctypes.data), "cgp_set_bc")
+
+
+def cgp_set_dirichlet_values(ctx: int, g_dev, stream=None) -> None:
+    _check(load().cgp_set_dirichlet_values(ctx, _ptr(g_dev), _stream(stream)), "cgp_set_dirichlet_values")
+
+
+def cgp_assemble(ctx: int, u_dev, stream=None) -> None:
+    _check(load().cgp_assemble(ctx, _ptr(u_dev), _stream(stream)), "cgp_assemble")
+
+
+def cgp_momentum_solve(ctx: int, u_dev, ut_dev, stream=None) -> None:
+    _check(load().cgp_momentum_solve(ctx, _ptr(u_dev), _ptr(ut_dev), _stream(stream)), "cgp_momentum_solve")
+
+
+def cgp_restrict(ctx: int, ut_dev, bc_dev, stream=None) -> None:
+    _check(load().cgp_restrict(ctx, _ptr(ut_dev), _ptr(bc_dev), _stream(stream)), "cgp_restrict")
+
+
+def cgp_poisson_solve(ctx: int, bc_dev, pc_dev, stream=None) -> None:
+    _check(load().cgp_poisson_solve(ctx, _ptr(bc_dev), _ptr(pc_dev), _stream(stream)), "cgp_poisson_solve")
+
+
+def cgp_prolong_correct(ctx: int, pc_dev, ut_dev, u_dev, pf_dev=None, gp_dev=None, stream=None) -> None:
+    _check(load().cgp_prolong_correct(ctx, _ptr(pc_dev), _ptr(ut_dev), _ptr(u_dev), _ptr(pf_dev), _ptr(gp_dev),
+                                      _stream(stream)), "cgp_prolong_correct")
+
+
+def cgp_step(ctx: int, u_dev, pc_dev, stream=None) -> None:
+    _check(load().cgp_step(ctx, _ptr(u_dev), _ptr(pc_dev), _stream(stream)), "cgp_step")
+
+
+def cgp_step_host(ctx: int, u_host, pc_host, stream=None) -> None:
+    """``u_host``/``pc_host``: contiguous float64 host buffers (numpy arrays or pinned CPU tensors)."""
+    _check(load().cgp_step_host(ctx, _ptr(u_host), _ptr(pc_host), _stream(stream)), "cgp_step_host")
+
+
+def cgp_get_stats(ctx: int, stream=None, check: bool = False) -> cgp_stats:
+    st = cgp_stats()
+    code = load().cgp_get_stats(ctx, _stream(stream), C.byref(st))
+    if code in (CGP_ERR_ARG, CGP_ERR_CUDA) or (check and code != CGP_OK):
+        raise CGPError(code, "cgp_get_stats")
+    st.code = code
+    return st
+
+
+def cgp_autotune(ctx: int, stream=None) -> None:
+    _check(load().cgp_autotune(ctx, _stream(stream)), "cgp_autotune")
+
+
+def cgp_mesh_destroy(ctx: int) -> None:
+    _check(load().cgp_mesh_destroy(ctx), "cgp_mesh_destroy")
+
+
+def cgp_status_str(code: int) -> str:
+    return load().cgp_status_str(code).decode()

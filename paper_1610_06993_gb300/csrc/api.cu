@@ -1,0 +1,443 @@
+// C ABI of the CGP library: context lifecycle and the per-step entry points (see cgp.h).
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "ctx.h"
+
+namespace cgp {
+int persistent_blocks_per_sm(int threads);
+}
+
+using namespace cgp;
+
+#define CK(call)                                         \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) {                         \
+            return e_ == cudaErrorMemoryAllocation ? CGP_ERR_NOMEM : CGP_ERR_CUDA; \
+        }                                                \
+    } while (0)
+
+namespace {
+
+template <typename T>
+int dalloc(cgp_ctx_s* c, T** p, size_t count) {
+    void* q = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? CGP_ERR_NOMEM : CGP_ERR_CUDA;
+    c->allocs.push_back(q);
+    *p = (T*)q;
+    return CGP_OK;
+}
+
+template <typename T>
+int upload(cgp_ctx_s* c, T** p, const std::vector<T>& v) {
+    int s = dalloc(c, p, v.size());
+    if (s) return s;
+    if (!v.empty()) CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return CGP_OK;
+}
+
+#define TRY(x)                 \
+    do {                       \
+        int s_ = (x);          \
+        if (s_ != CGP_OK) return s_; \
+    } while (0)
+
+int upload_csr(cgp_ctx_s* c, const HostCsr& h, DevCsr& d) {
+    d.n = h.n;
+    d.nnz = h.nnz;
+    TRY(upload(c, &d.rp, h.rp));
+    TRY(upload(c, &d.ci, h.ci));
+    TRY(upload(c, &d.diag, h.diag));
+    return CGP_OK;
+}
+
+int upload_elems(cgp_ctx_s* c, const HostLevel& L, const HostElems& h, DevElems& d) {
+    d.t = L.t;
+    d.ncol = (int)h.colptr.size() - 1;
+    d.colptr = h.colptr;
+    TRY(upload(c, &d.colptr_dev, h.colptr));
+    TRY(upload(c, &d.tri, L.tri));
+    TRY(upload(c, &d.slot, h.slot));
+    TRY(upload(c, &d.perm, h.perm));
+    TRY(dalloc(c, &d.geo, 8 * (size_t)L.t));
+    return CGP_OK;
+}
+
+Shape make_shape(int n, int threads, int lanes, int num_sms, int bps) {
+    Shape s;
+    s.threads = threads;
+    s.lanes = lanes;
+    const int want = (n + threads - 1) / threads;
+    const int cap = std::min(num_sms, bps * num_sms);
+    s.blocks = std::max(1, std::min(want, cap));
+    return s;
+}
+
+int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
+    c->prm = *prm;
+    cgp_params& P = c->prm;
+    if (!(P.rho > 0.0) || !(P.mu >= 0.0) || !(P.dt > 0.0) || !(P.rtol > 0.0)) return CGP_ERR_ARG;
+    if (P.precision != CGP_FP64 && P.precision != CGP_MIXED) return CGP_ERR_ARG;
+    if (P.inner_rtol <= 0.0) P.inner_rtol = 1e-4;
+    if (P.max_iter <= 0) P.max_iter = 20000;
+    if (P.max_outer <= 0) P.max_outer = 30;
+    if (P.block_threads == 0) P.block_threads = 512;
+    if (P.block_threads < 64 || P.block_threads > 1024 || (P.block_threads & 31)) return CGP_ERR_ARG;
+    if (P.spmv_lanes != 0 && (P.spmv_lanes < 1 || P.spmv_lanes > 32 || (P.spmv_lanes & (P.spmv_lanes - 1))))
+        return CGP_ERR_ARG;
+    TRY(build_host_mesh(d, P.levels, c->hm));
+    HostMesh& H = c->hm;
+    c->levels = P.levels;
+    c->nc = H.lv[0].n;
+    c->nf = H.lv[P.levels].n;
+    CK(cudaGetDevice(&c->device));
+    CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+
+    const HostLevel& Lf = H.lv[P.levels];
+    const HostLevel& Lc = H.lv[0];
+    TRY(upload_csr(c, H.fine, c->F));
+    TRY(upload_csr(c, H.coarse, c->C));
+    TRY(upload_elems(c, Lf, H.ef, c->EF));
+    TRY(upload_elems(c, Lc, H.ec, c->EC));
+    TRY(upload(c, &c->xy_f, Lf.xy));
+    TRY(upload(c, &c->xy_c, Lc.xy));
+    // coarse columns mapped to fine indices through s^u (Eq. 30), for the fused injection
+    std::vector<int> cif(H.coarse.nnz);
+    for (int k = 0; k < H.coarse.nnz; ++k) cif[k] = H.su[H.coarse.ci[k]];
+    TRY(upload(c, &c->cif_su, cif));
+    c->lv_n.clear();
+    for (auto& L : H.lv) c->lv_n.push_back(L.n);
+    for (int k = 0; k < P.levels; ++k) {
+        int2* sp = nullptr;
+        TRY(dalloc(c, &sp, (size_t)H.lv[k + 1].n));
+        CK(cudaMemcpy(sp, H.sp[k].data(), sizeof(int) * H.sp[k].size(), cudaMemcpyHostToDevice));
+        c->sp.push_back(sp);
+        double* buf = nullptr;
+        TRY(dalloc(c, &buf, (size_t)H.lv[k + 1].n));
+        c->pl.push_back(buf);
+    }
+    const size_t nf = c->nf, nc = c->nc, nnzf = H.fine.nnz, nnzc = H.coarse.nnz;
+    TRY(dalloc(c, &c->M, nnzf));
+    TRY(dalloc(c, &c->A0, nnzf));
+    TRY(dalloc(c, &c->A, nnzf));
+    TRY(dalloc(c, &c->A32, nnzf));
+    TRY(dalloc(c, &c->Gxy, 2 * nnzf));
+    TRY(dalloc(c, &c->dinvM, nf));
+    TRY(dalloc(c, &c->dinvA, 2 * nf));
+    TRY(dalloc(c, &c->dinvA32, 2 * nf));
+    TRY(dalloc(c, &c->b_mom, 2 * nf));
+    TRY(dalloc(c, &c->Kc_raw, nnzc));
+    TRY(dalloc(c, &c->Kc, nnzc));
+    TRY(dalloc(c, &c->Kc32, nnzc));
+    TRY(dalloc(c, &c->Dc_xy, 2 * nnzc));
+    TRY(dalloc(c, &c->dinvK, nc));
+    TRY(dalloc(c, &c->dinvK32, nc));
+    TRY(dalloc(c, &c->vel_mask, nf));
+    TRY(dalloc(c, &c->p_mask, nc));
+    TRY(dalloc(c, &c->g, 2 * nf));
+    TRY(dalloc(c, &c->grad, 2 * nf));
+    TRY(dalloc(c, &c->w, 2 * nf));
+    TRY(dalloc(c, &c->pf, nf));
+    TRY(dalloc(c, &c->ut, 2 * nf));
+    TRY(dalloc(c, &c->bc, nc));
+    TRY(dalloc(c, &c->u_stage, 2 * nf));
+    TRY(dalloc(c, &c->pc_stage, nc));
+    // Krylov workspace: the largest of BiCGStab (9 pair vectors) and CG (6 vectors), 256-byte carved
+    const size_t need = std::max({9 * 2 * nf * sizeof(double), 6 * 2 * nf * sizeof(double),
+                                  6 * nc * sizeof(double)}) + 16 * 256;
+    c->ws_bytes = need;
+    char* ws = nullptr;
+    TRY(dalloc(c, &ws, need));
+    c->ws = ws;
+    c->max_blocks = std::max(c->num_sms, 1);
+    TRY(dalloc(c, &c->part, 32 * (size_t)c->max_blocks));
+    TRY(dalloc(c, &c->sync, (size_t)SYNC_COUNT));
+    TRY(dalloc(c, &c->stats, 1));
+    CK(cudaMemset(c->stats, 0, sizeof(DevStats)));
+    CK(cudaMemset(c->w, 0, 2 * nf * sizeof(double)));
+    CK(cudaMemset(c->vel_mask, 0, nf));
+    CK(cudaMemset(c->p_mask, 0, nc));
+    CK(cudaMemset(c->g, 0, 2 * nf * sizeof(double)));
+
+    // device assembly of the constant P1 matrices (Eqs. 16-18)
+    double* Kf = nullptr;
+    CK(cudaMalloc(&Kf, nnzf * sizeof(double)));
+    cudaStream_t s = 0;
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((e = cudaMemsetAsync(c->M, 0, nnzf * sizeof(double), s)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(Kf, 0, nnzf * sizeof(double), s)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(c->Gxy, 0, 2 * nnzf * sizeof(double), s)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(c->Kc_raw, 0, nnzc * sizeof(double), s)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(c->Dc_xy, 0, 2 * nnzc * sizeof(double), s)) != cudaSuccess) break;
+        if ((e = launch_geometry(c->xy_f, c->EF.tri, c->EF.t, c->EF.geo, s)) != cudaSuccess) break;
+        if ((e = launch_geometry(c->xy_c, c->EC.tri, c->EC.t, c->EC.geo, s)) != cudaSuccess) break;
+        if ((e = launch_const_assembly(c->EF, c->M, Kf, c->Gxy, s)) != cudaSuccess) break;
+        if ((e = launch_const_assembly(c->EC, nullptr, c->Kc_raw, c->Dc_xy, s)) != cudaSuccess) break;
+        if ((e = launch_make_A0(c, Kf, s)) != cudaSuccess) break;
+        e = cudaStreamSynchronize(s);
+    } while (0);
+    cudaFree(Kf);
+    CK(e);
+
+    const int threads = P.block_threads;
+    const int bps = persistent_blocks_per_sm(threads);
+    if (bps <= 0) return CGP_ERR_CUDA;
+    const int lanes = P.spmv_lanes ? P.spmv_lanes : 4;
+    c->sh_f = make_shape(c->nf, threads, lanes, c->num_sms, bps);
+    c->sh_c = make_shape(c->nc, threads, lanes, c->num_sms, bps);
+    return CGP_OK;
+}
+
+void destroy_impl(cgp_ctx_s* c) {
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+void cgp_default_params(cgp_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->rho = 1.0;
+    p->mu = 0.01;
+    p->dt = 0.01;
+    p->levels = 1;
+    p->precision = CGP_FP64;
+    p->rtol = 1e-8;
+    p->inner_rtol = 1e-4;
+    p->max_iter = 20000;
+    p->max_outer = 30;
+    p->spmv_lanes = 0;
+    p->block_threads = 0;
+}
+
+int cgp_mesh_create(const cgp_mesh_desc* coarse, const cgp_params* prm, cgp_ctx* out) {
+    if (!coarse || !prm || !out) return CGP_ERR_ARG;
+    *out = nullptr;
+    cgp_ctx_s* c = new (std::nothrow) cgp_ctx_s();
+    if (!c) return CGP_ERR_NOMEM;
+    int s = create_impl(coarse, prm, c);
+    if (s != CGP_OK) {
+        destroy_impl(c);
+        delete c;
+        return s;
+    }
+    *out = c;
+    return CGP_OK;
+}
+
+int cgp_refine(const cgp_mesh_desc* coarse, int levels, int* n_fine, int* n_tris_fine, double* xy_host,
+               int* tri_host, int* sp_host, int* colour_host) {
+    if (!coarse) return CGP_ERR_ARG;
+    HostMesh H;
+    int s = build_host_mesh(coarse, levels, H);
+    if (s != CGP_OK) return s;
+    const HostLevel& L = H.lv[levels];
+    if (n_fine) *n_fine = L.n;
+    if (n_tris_fine) *n_tris_fine = L.t;
+    if (xy_host) std::copy(L.xy.begin(), L.xy.end(), xy_host);
+    if (tri_host) std::copy(L.tri.begin(), L.tri.end(), tri_host);
+    if (sp_host) {
+        if (levels == 0) {
+            for (int i = 0; i < L.n; ++i) sp_host[2 * i] = sp_host[2 * i + 1] = i;
+        } else {
+            std::copy(H.sp[levels - 1].begin(), H.sp[levels - 1].end(), sp_host);
+        }
+    }
+    if (colour_host) {
+        const int ncol = (int)H.ef.colptr.size() - 1;
+        for (int k = 0; k < ncol; ++k)
+            for (int q = H.ef.colptr[k]; q < H.ef.colptr[k + 1]; ++q) colour_host[H.ef.perm[q]] = k;
+    }
+    return CGP_OK;
+}
+
+int cgp_mesh_info(cgp_ctx c, cgp_info* info) {
+    if (!c || !info) return CGP_ERR_ARG;
+    info->n_fine = c->nf;
+    info->n_coarse = c->nc;
+    info->tris_fine = c->EF.t;
+    info->tris_coarse = c->EC.t;
+    info->nnz_fine = c->F.nnz;
+    info->nnz_coarse = c->C.nnz;
+    info->levels = c->levels;
+    info->n_colours = c->EF.ncol;
+    info->grid_blocks = c->sh_f.blocks;
+    info->block_threads = c->sh_f.threads;
+    info->spmv_lanes = c->sh_f.lanes;
+    return CGP_OK;
+}
+
+int cgp_fine_mesh(cgp_ctx c, double* xy_host, int* tri_host, unsigned char* onb_host) {
+    if (!c) return CGP_ERR_ARG;
+    const HostLevel& L = c->hm.lv[c->levels];
+    if (xy_host) std::copy(L.xy.begin(), L.xy.end(), xy_host);
+    if (tri_host) std::copy(L.tri.begin(), L.tri.end(), tri_host);
+    if (onb_host) std::copy(c->hm.onb_f.begin(), c->hm.onb_f.end(), onb_host);
+    return CGP_OK;
+}
+
+int cgp_set_bc(cgp_ctx c, const unsigned char* vel_mask, const unsigned char* p_mask, const double* g) {
+    if (!c || !vel_mask || !p_mask || !g) return CGP_ERR_ARG;
+    CK(cudaMemcpy(c->vel_mask, vel_mask, (size_t)c->nf, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->p_mask, p_mask, (size_t)c->nc, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->g, g, 2 * sizeof(double) * (size_t)c->nf, cudaMemcpyHostToDevice));
+    CK(launch_apply_pressure_bc(c, 0));
+    CK(cudaStreamSynchronize(0));
+    c->bc_set = true;
+    return CGP_OK;
+}
+
+int cgp_set_dirichlet_values(cgp_ctx c, const double* g_dev, void* stream) {
+    if (!c || !g_dev) return CGP_ERR_ARG;
+    CK(cudaMemcpyAsync(c->g, g_dev, 2 * sizeof(double) * (size_t)c->nf, cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream));
+    return CGP_OK;
+}
+
+int cgp_assemble(cgp_ctx c, const double* u_dev, void* stream) {
+    if (!c || !u_dev) return CGP_ERR_ARG;
+    if (!c->bc_set) return CGP_ERR_STATE;
+    CK(launch_assemble_step(c, u_dev, (cudaStream_t)stream));
+    return CGP_OK;
+}
+
+int cgp_momentum_solve(cgp_ctx c, const double* u_dev, double* ut_dev, void* stream) {
+    if (!c || !u_dev || !ut_dev) return CGP_ERR_ARG;
+    if (!c->bc_set) return CGP_ERR_STATE;
+    CK(launch_momentum_bicgstab(c, u_dev, ut_dev, (cudaStream_t)stream));
+    return CGP_OK;
+}
+
+int cgp_restrict(cgp_ctx c, const double* ut_dev, double* bc_dev, void* stream) {
+    if (!c || !ut_dev || !bc_dev) return CGP_ERR_ARG;
+    if (!c->bc_set) return CGP_ERR_STATE;
+    CK(launch_restrict_rhs(c, ut_dev, bc_dev, (cudaStream_t)stream));
+    return CGP_OK;
+}
+
+int cgp_poisson_solve(cgp_ctx c, const double* bc_dev, double* pc_dev, void* stream) {
+    if (!c || !bc_dev || !pc_dev) return CGP_ERR_ARG;
+    if (!c->bc_set) return CGP_ERR_STATE;
+    CK(launch_poisson_cg(c, bc_dev, pc_dev, (cudaStream_t)stream));
+    return CGP_OK;
+}
+
+int cgp_prolong_correct(cgp_ctx c, const double* pc_dev, const double* ut_dev, double* u_dev, double* pf_dev,
+                        double* gp_dev, void* stream) {
+    if (!c || !pc_dev || !ut_dev || !u_dev) return CGP_ERR_ARG;
+    if (!c->bc_set) return CGP_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* pf = pf_dev ? pf_dev : c->pf;
+    CK(launch_prolong(c, pc_dev, pf, s));
+    CK(launch_gradient(c, pf, c->grad, s));
+    CK(launch_mass_cg(c, c->grad, c->w, s));
+    CK(launch_correct(c, ut_dev, c->w, u_dev, gp_dev, s));
+    return CGP_OK;
+}
+
+int cgp_step(cgp_ctx c, double* u_dev, double* pc_dev, void* stream) {
+    if (!c || !u_dev || !pc_dev) return CGP_ERR_ARG;
+    if (!c->bc_set) return CGP_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(launch_assemble_step(c, u_dev, s));
+    CK(launch_momentum_bicgstab(c, u_dev, c->ut, s));
+    CK(launch_restrict_rhs(c, c->ut, c->bc, s));
+    CK(launch_poisson_cg(c, c->bc, pc_dev, s));
+    CK(launch_prolong(c, pc_dev, c->pf, s));
+    CK(launch_gradient(c, c->pf, c->grad, s));
+    CK(launch_mass_cg(c, c->grad, c->w, s));
+    CK(launch_correct(c, c->ut, c->w, u_dev, nullptr, s));
+    return CGP_OK;
+}
+
+int cgp_step_host(cgp_ctx c, double* u_host, double* pc_host, void* stream) {
+    if (!c || !u_host || !pc_host) return CGP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bu = 2 * sizeof(double) * (size_t)c->nf, bp = sizeof(double) * (size_t)c->nc;
+    CK(cudaMemcpyAsync(c->u_stage, u_host, bu, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c->pc_stage, pc_host, bp, cudaMemcpyHostToDevice, s));
+    int st = cgp_step(c, c->u_stage, c->pc_stage, stream);
+    if (st != CGP_OK) return st;
+    CK(cudaMemcpyAsync(u_host, c->u_stage, bu, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(pc_host, c->pc_stage, bp, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return CGP_OK;
+}
+
+int cgp_get_stats(cgp_ctx c, void* stream, cgp_stats* st) {
+    if (!c || !st) return CGP_ERR_ARG;
+    DevStats d;
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    CK(cudaMemcpy(&d, c->stats, sizeof(d), cudaMemcpyDeviceToHost));
+    st->momentum_iters = d.mom_iters;
+    st->momentum_outer = d.mom_outer;
+    st->momentum_status = d.mom_status;
+    st->poisson_iters = d.poi_iters;
+    st->poisson_outer = d.poi_outer;
+    st->poisson_status = d.poi_status;
+    st->mass_iters = d.mass_iters;
+    st->mass_status = d.mass_status;
+    st->barrier_status = d.barrier_status;
+    st->momentum_rel_res = d.mom_rel;
+    st->poisson_rel_res = d.poi_rel;
+    st->mass_rel_res = d.mass_rel;
+    if (d.barrier_status) return d.barrier_status;
+    if (d.mom_status) return d.mom_status;
+    if (d.poi_status) return d.poi_status;
+    if (d.mass_status) return d.mass_status;
+    return CGP_OK;
+}
+
+int cgp_autotune(cgp_ctx c, void* stream) {
+    if (!c) return CGP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int cand[] = {1, 2, 4, 8};
+    for (int fine = 0; fine < 2; ++fine) {
+        float best = 1e30f;
+        int best_l = 4;
+        for (int l : cand) {
+            float ms = 0.f;
+            CK(time_spmv_lanes(c, fine != 0, l, s, &ms));
+            if (ms < best) {
+                best = ms;
+                best_l = l;
+            }
+        }
+        if (fine) c->sh_f.lanes = best_l;
+        else c->sh_c.lanes = best_l;
+    }
+    return CGP_OK;
+}
+
+int cgp_mesh_destroy(cgp_ctx c) {
+    if (!c) return CGP_OK;
+    cudaDeviceSynchronize();
+    destroy_impl(c);
+    delete c;
+    return CGP_OK;
+}
+
+const char* cgp_status_str(int s) {
+    switch (s) {
+        case CGP_OK: return "CGP_OK";
+        case CGP_ERR_ARG: return "CGP_ERR_ARG";
+        case CGP_ERR_MESH: return "CGP_ERR_MESH";
+        case CGP_ERR_CUDA: return "CGP_ERR_CUDA";
+        case CGP_ERR_NOT_CONVERGED: return "CGP_ERR_NOT_CONVERGED";
+        case CGP_ERR_NAN: return "CGP_ERR_NAN";
+        case CGP_ERR_TIMEOUT: return "CGP_ERR_TIMEOUT";
+        case CGP_ERR_NOMEM: return "CGP_ERR_NOMEM";
+        case CGP_ERR_STATE: return "CGP_ERR_STATE";
+        default: return "CGP_ERR_UNKNOWN";
+    }
+}
+
+}  // extern "C"

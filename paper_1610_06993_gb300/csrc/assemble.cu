@@ -1,0 +1,236 @@
+// P1 finite-element assembly on the device (the paper's Eqs. 16-19).
+//
+// Element integrals of a triangle T with area |T| and constant shape-function gradients
+// grad phi_i = (y_j - y_k, x_k - x_j) / (2|T|), (i, j, k) cyclic:
+//   mass        M_ab = |T| (1 + delta_ab) / 12
+//   stiffness   K_ab = |T| grad phi_a . grad phi_b
+//   div / grad  D_ab = |T| / 3 * grad phi_b            (int phi_a d phi_b, not integrated by parts)
+//   convection  N_ab = |T| / 12 * (sum_k u_k + u_a) . grad phi_b     (u in P1)
+// Element loops run one colour at a time; elements of one colour share no node, so every CSR
+// slot is updated by one thread per colour: no atomics and a fixed summation order.
+#include "ctx.h"
+
+namespace cgp {
+
+namespace {
+
+__global__ void k_geometry(const double* __restrict__ xy, const int* __restrict__ tri, int t,
+                           double* __restrict__ geo) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= t) return;
+    int v0 = tri[3 * e], v1 = tri[3 * e + 1], v2 = tri[3 * e + 2];
+    double x0 = xy[2 * v0], y0 = xy[2 * v0 + 1];
+    double x1 = xy[2 * v1], y1 = xy[2 * v1 + 1];
+    double x2 = xy[2 * v2], y2 = xy[2 * v2 + 1];
+    double area = 0.5 * ((x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0));
+    double inv2a = 1.0 / (2.0 * area);
+    double* g = geo + 8 * (size_t)e;
+    g[0] = area;
+    g[1] = (y1 - y2) * inv2a;   // d/dx phi_0 = (y_1 - y_2) / 2|T|
+    g[2] = (y2 - y0) * inv2a;
+    g[3] = (y0 - y1) * inv2a;
+    g[4] = (x2 - x1) * inv2a;   // d/dy phi_0 = (x_2 - x_1) / 2|T|
+    g[5] = (x0 - x2) * inv2a;
+    g[6] = (x1 - x0) * inv2a;
+    g[7] = 0.0;
+}
+
+// One colour of the constant matrices: M, K and the interleaved (Dx, Dy) pair.
+__global__ void k_const_colour(int k0, int k1, const int* __restrict__ perm, const int* __restrict__ slot,
+                               const double* __restrict__ geo, double* M, double* K, double* Dxy) {
+    int k = k0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= k1) return;
+    int e = perm[k];
+    const double* g = geo + 8 * (size_t)e;
+    double area = g[0];
+    const int* sl = slot + 9 * (size_t)e;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            int s = sl[a * 3 + b];
+            if (M) M[s] += area * (a == b ? 2.0 : 1.0) / 12.0;
+            if (K) K[s] += area * (g[1 + a] * g[1 + b] + g[4 + a] * g[4 + b]);
+            if (Dxy) {
+                Dxy[2 * (size_t)s] += area / 3.0 * g[1 + b];
+                Dxy[2 * (size_t)s + 1] += area / 3.0 * g[4 + b];
+            }
+        }
+    }
+}
+
+// Symmetric elimination of pressure-Dirichlet rows/columns (Eq. 14 and the pin): zero the row and
+// column, unit diagonal. Also the Jacobi inverse diagonal and the FP32 copies.
+__global__ void k_pressure_bc(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                              const unsigned char* __restrict__ pm, const double* __restrict__ Kraw,
+                              double* K, float* K32, double* dinv, float* dinv32) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool mi = pm[i] != 0;
+    double diag = 1.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        int j = ci[k];
+        double v;
+        if (mi || pm[j]) v = (i == j) ? 1.0 : 0.0;
+        else v = Kraw[k];
+        if (i == j) diag = v;
+        K[k] = v;
+        K32[k] = (float)v;
+    }
+    dinv[i] = 1.0 / diag;
+    dinv32[i] = (float)(1.0 / diag);
+}
+
+__global__ void k_make_A0(int nnz, double rho, double dtmu, const double* __restrict__ M,
+                          const double* __restrict__ K, double* A0) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nnz) A0[k] = rho * M[k] + dtmu * K[k];
+}
+
+__global__ void k_inv_diag(int n, const int* __restrict__ diag, const double* __restrict__ val, double* dinv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dinv[i] = 1.0 / val[diag[i]];
+}
+
+struct StepAsmArgs {
+    int nf, nnz, ncol;
+    const int* colptr;           // device copy of the colour offsets
+    const int* perm;
+    const int* slot;
+    const double* geo;
+    const int* tri;
+    const int* rp;
+    const int* ci;
+    const int* diag;
+    const double* A0;
+    const double* M;
+    const double* u;             // [nf][2] u^n
+    const unsigned char* mask;
+    const double* g;
+    double* A;
+    float* A32;                  // nullptr unless CGP_MIXED
+    double* dinv;                // [nf][2]
+    float* dinv32;
+    double* b;                   // [nf][2]
+    double rho, dtrho;
+    SyncWords* sw;
+    int* barrier_status;
+};
+
+// Per-step momentum matrix A = A0 + dt rho N(u^n), Jacobi diagonals and right-hand side
+// b = rho M u^n (Dirichlet rows: prescribed values). One cooperative launch; grid barriers
+// separate the copy, each colour and the row pass.
+__global__ void __launch_bounds__(1024) k_assemble_step(StepAsmArgs a) {
+    unsigned int epoch = 0;
+    const unsigned int nb = gridDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nthreads = gridDim.x * blockDim.x;
+    for (int k = tid; k < a.nnz; k += nthreads) a.A[k] = a.A0[k];
+    if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.barrier_status);
+    for (int c = 0; c < a.ncol; ++c) {
+        const int k0 = a.colptr[c], k1 = a.colptr[c + 1];
+        for (int k = k0 + tid; k < k1; k += nthreads) {
+            const int e = a.perm[k];
+            const double* g = a.geo + 8 * (size_t)e;
+            const double area12 = g[0] / 12.0;
+            double ux[3], uy[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) load2(a.u, a.tri[3 * e + q], ux[q], uy[q]);
+            const double sx = ux[0] + ux[1] + ux[2], sy = uy[0] + uy[1] + uy[2];
+            const int* sl = a.slot + 9 * (size_t)e;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const double cx = area12 * (sx + ux[r]), cy = area12 * (sy + uy[r]);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) a.A[sl[r * 3 + q]] += a.dtrho * (cx * g[1 + q] + cy * g[4 + q]);
+            }
+        }
+        if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.barrier_status);
+    }
+    for (int i = tid; i < a.nf; i += nthreads) {
+        const unsigned char m = a.mask[i];
+        const double dg = a.A[a.diag[i]];
+        const double di = 1.0 / dg;
+        double dx = (m & CGP_BC_U) ? 1.0 : di, dy = (m & CGP_BC_V) ? 1.0 : di;
+        store2(a.dinv, i, dx, dy);
+        double mx = 0.0, my = 0.0;
+        for (int k = a.rp[i]; k < a.rp[i + 1]; ++k) {
+            double ujx, ujy;
+            load2(a.u, a.ci[k], ujx, ujy);
+            const double mv = a.M[k];
+            mx += mv * ujx;
+            my += mv * ujy;
+            if (a.A32) a.A32[k] = (float)a.A[k];
+        }
+        double gx, gy;
+        load2(a.g, i, gx, gy);
+        store2(a.b, i, (m & CGP_BC_U) ? gx : a.rho * mx, (m & CGP_BC_V) ? gy : a.rho * my);
+        if (a.dinv32) store2(a.dinv32, i, (float)dx, (float)dy);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_geometry(const double* xy, const int* tri, int t, double* geo, cudaStream_t s) {
+    k_geometry<<<(t + 255) / 256, 256, 0, s>>>(xy, tri, t, geo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_const_assembly(const DevElems& E, double* M, double* K, double* Dxy, cudaStream_t s) {
+    for (int c = 0; c < E.ncol; ++c) {
+        int k0 = E.colptr[c], k1 = E.colptr[c + 1];
+        if (k1 <= k0) continue;
+        k_const_colour<<<(k1 - k0 + 255) / 256, 256, 0, s>>>(k0, k1, E.perm, E.slot, E.geo, M, K, Dxy);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_apply_pressure_bc(cgp_ctx_s* c, cudaStream_t s) {
+    k_pressure_bc<<<(c->nc + 255) / 256, 256, 0, s>>>(c->nc, c->C.rp, c->C.ci, c->p_mask, c->Kc_raw, c->Kc,
+                                                       c->Kc32, c->dinvK, c->dinvK32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_make_A0(cgp_ctx_s* c, const double* K, cudaStream_t s) {
+    const int nnz = c->F.nnz;
+    k_make_A0<<<(nnz + 255) / 256, 256, 0, s>>>(nnz, c->prm.rho, c->prm.dt * c->prm.mu, c->M, K, c->A0);
+    k_inv_diag<<<(c->nf + 255) / 256, 256, 0, s>>>(c->nf, c->F.diag, c->M, c->dinvM);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_step(cgp_ctx_s* c, const double* u, cudaStream_t s) {
+    StepAsmArgs a;
+    a.nf = c->nf;
+    a.nnz = c->F.nnz;
+    a.ncol = c->EF.ncol;
+    a.colptr = c->EF.colptr_dev;
+    a.perm = c->EF.perm;
+    a.slot = c->EF.slot;
+    a.geo = c->EF.geo;
+    a.tri = c->EF.tri;
+    a.rp = c->F.rp;
+    a.ci = c->F.ci;
+    a.diag = c->F.diag;
+    a.A0 = c->A0;
+    a.M = c->M;
+    a.u = u;
+    a.mask = c->vel_mask;
+    a.g = c->g;
+    a.A = c->A;
+    const bool mixed = c->prm.precision == CGP_MIXED;
+    a.A32 = mixed ? c->A32 : nullptr;
+    a.dinv = c->dinvA;
+    a.dinv32 = mixed ? c->dinvA32 : nullptr;
+    a.b = c->b_mom;
+    a.rho = c->prm.rho;
+    a.dtrho = c->prm.dt * c->prm.rho;
+    a.sw = c->sync + SYNC_ASM;
+    a.barrier_status = &c->stats->barrier_status;
+    cudaError_t e = cudaMemsetAsync(a.sw, 0, sizeof(SyncWords), s);
+    if (e != cudaSuccess) return e;
+    return coop_launch((const void*)k_assemble_step, c->sh_f.blocks, c->sh_f.threads, a, s);
+}
+
+}  // namespace cgp

@@ -1,0 +1,180 @@
+// Device helpers shared by the CGP kernels: bounded grid barrier, deterministic reductions,
+// CSR row products with a configurable number of lanes per row.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "cgp.h"
+
+#ifndef CGP_BARRIER_SPIN_LIMIT
+// Upper bound on polls of one grid barrier before it gives up with CGP_ERR_TIMEOUT. Each poll
+// sleeps ~64 ns after the first few hundred, so the bound is a few seconds of wall time.
+#define CGP_BARRIER_SPIN_LIMIT (1u << 25)
+#endif
+
+namespace cgp {
+
+// Per-launch synchronisation words of a persistent kernel; zeroed by the host before launch.
+struct SyncWords {
+    unsigned int count;   // grid-barrier arrival counter
+    int err;              // first error code raised by any block (0 = none)
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed_i32(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(unsigned int* p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperative launch. Every block calls it the same number of times.
+// Thread 0 of each block arrives with a release-add and polls with acquire loads; the poll is
+// bounded: after CGP_BARRIER_SPIN_LIMIT polls, or as soon as another block has raised an error,
+// it returns false (and records CGP_ERR_TIMEOUT if it was the one to give up). Callers must stop
+// their work and return when it is false. `epoch` is thread 0's count of barriers passed.
+__device__ __forceinline__ bool grid_sync(SyncWords* sw, unsigned int nblocks, unsigned int& epoch) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        epoch += 1;
+        if (nblocks > 1) {
+            const unsigned int target = epoch * nblocks;
+            __threadfence();
+            red_release_add_u32(&sw->count, 1u);
+            unsigned int spins = 0;
+            while (ld_acquire_u32(&sw->count) < target) {
+                if (ld_relaxed_i32(&sw->err) != 0) { ok = 0; break; }
+                if (++spins > CGP_BARRIER_SPIN_LIMIT) {
+                    atomicCAS(&sw->err, 0, CGP_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                if (spins > 256) __nanosleep(64);
+            }
+            __threadfence();
+        } else {
+            ok = ld_relaxed_i32(&sw->err) == 0;
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Called by a block that leaves a persistent kernel because a barrier failed: thread 0 copies
+// the launch's error code into the context's sticky barrier status.
+__device__ __forceinline__ void record_failure(SyncWords* sw, int* status) {
+    if (threadIdx.x == 0) {
+        int e = ld_relaxed_i32(&sw->err);
+        atomicCAS(status, 0, e != 0 ? e : CGP_ERR_TIMEOUT);
+    }
+}
+
+// Sum K doubles over the block; the result is valid in thread 0 only. Fixed order, so the
+// same inputs give the same bits.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* s_scratch /* [32*K] */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) s_scratch[k * 32 + warp] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = lane < nwarps ? s_scratch[k * 32 + lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            v[k] = t;
+        }
+    }
+}
+
+// Write the block's K partial sums to part[k * nblocks + blockIdx.x].
+template <int K>
+__device__ __forceinline__ void block_partials(double (&v)[K], double* part, unsigned int nblocks,
+                                               double* s_scratch) {
+    block_sum<K>(v, s_scratch);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) part[k * nblocks + blockIdx.x] = v[k];
+    }
+}
+
+// After a grid barrier: every block sums the nblocks partials of each of the K slots in the same
+// fixed order, so all blocks hold bit-identical totals. Result broadcast to all threads.
+template <int K>
+__device__ __forceinline__ void grid_totals(const double* part, unsigned int nblocks, double (&out)[K],
+                                            double* s_bcast /* [K] */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            double t = 0.0;
+            for (unsigned int b = lane; b < nblocks; b += 32) t += __ldcg(part + k * nblocks + b);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) s_bcast[k] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = s_bcast[k];
+    __syncthreads();
+}
+
+// Rows owned by a block: a contiguous slice of [0, n).
+struct RowRange {
+    int r0, r1;
+};
+__device__ __forceinline__ RowRange block_rows(int n) {
+    const long long per = ((long long)n + gridDim.x - 1) / gridDim.x;
+    long long r0 = per * blockIdx.x, r1 = r0 + per;
+    if (r0 > n) r0 = n;
+    if (r1 > n) r1 = n;
+    return {(int)r0, (int)r1};
+}
+
+// Two-wide loads/stores of interleaved pairs.
+template <typename T> struct Pair;
+template <> struct Pair<double> { typedef double2 type; };
+template <> struct Pair<float> { typedef float2 type; };
+
+template <typename T>
+__device__ __forceinline__ void load2(const T* p, int i, T& a, T& b) {
+    typename Pair<T>::type v = reinterpret_cast<const typename Pair<T>::type*>(p)[i];
+    a = v.x;
+    b = v.y;
+}
+template <typename T>
+__device__ __forceinline__ void store2(T* p, int i, T a, T b) {
+    typename Pair<T>::type v;
+    v.x = a;
+    v.y = b;
+    reinterpret_cast<typename Pair<T>::type*>(p)[i] = v;
+}
+
+// Sum over the `lanes` (power of two <= 32) lanes of a row group.
+template <typename T>
+__device__ __forceinline__ T group_sum(T v, int lanes) {
+    for (int o = lanes >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace cgp

@@ -1,0 +1,141 @@
+// Internal state of a CGP context and the kernel launchers shared by the .cu files.
+#pragma once
+#include <cuda_runtime.h>
+#include <vector>
+#include "cgp.h"
+#include "common.cuh"
+#include "host_mesh.h"
+
+namespace cgp {
+
+// Device-side statistics of the latest solves (mirrors cgp_stats).
+struct DevStats {
+    int mom_iters, mom_outer, mom_status;
+    int poi_iters, poi_outer, poi_status;
+    int mass_iters, mass_outer, mass_status;
+    int barrier_status;
+    double mom_rel, poi_rel, mass_rel;
+};
+
+struct DevCsr {
+    int n = 0, nnz = 0;
+    int* rp = nullptr;
+    int* ci = nullptr;
+    int* diag = nullptr;
+};
+
+struct DevElems {
+    int t = 0, ncol = 0;
+    std::vector<int> colptr;   // host copy of colour offsets
+    int* colptr_dev = nullptr; // device copy of colour offsets
+    int* tri = nullptr;        // [t][3]
+    int* slot = nullptr;       // [t][9]
+    int* perm = nullptr;       // [t]
+    double* geo = nullptr;     // [t][8]: area, gx[3], gy[3], pad
+};
+
+// Launch shape of one persistent (cooperative) kernel family.
+struct Shape {
+    int blocks = 1, threads = 512, lanes = 4;
+};
+
+// Sync words: one slot per persistent launch site, zeroed before every launch.
+enum SyncSlot { SYNC_ASM = 0, SYNC_MOM, SYNC_POI, SYNC_MASS, SYNC_COUNT };
+
+}  // namespace cgp
+
+struct cgp_ctx_s {
+    cgp_params prm;
+    int device = 0, num_sms = 0;
+    cgp::HostMesh hm;
+    int nf = 0, nc = 0, levels = 0;
+    bool bc_set = false;
+
+    cgp::DevCsr F, C;            // fine and coarse P1 patterns
+    cgp::DevElems EF, EC;
+    int* cif_su = nullptr;       // coarse CSR columns mapped to fine node indices (ci[k] -> xi)
+    double* xy_f = nullptr;
+    double* xy_c = nullptr;
+
+    // fine operators (values in the fine pattern)
+    double* M = nullptr;         // consistent mass
+    double* A0 = nullptr;        // rho M + dt mu K
+    double* A = nullptr;         // per-step momentum matrix
+    float* A32 = nullptr;        // FP32 copy (CGP_MIXED)
+    double* Gxy = nullptr;       // [nnz][2] gradient (G = D on the fine mesh)
+    double* dinvM = nullptr;     // [nf]
+    double* dinvA = nullptr;     // [nf][2]
+    float* dinvA32 = nullptr;    // [nf][2]
+    double* b_mom = nullptr;     // [nf][2]
+
+    // coarse operators
+    double* Kc_raw = nullptr;    // stiffness before boundary elimination
+    double* Kc = nullptr;        // after symmetric elimination
+    float* Kc32 = nullptr;
+    double* Dc_xy = nullptr;     // [nnz_c][2]
+    double* dinvK = nullptr;
+    float* dinvK32 = nullptr;
+
+    // mapping tables and boundary data
+    std::vector<int2*> sp;       // per level [N_{k+1}] (beta, gamma)
+    std::vector<int> lv_n;       // node count per level
+    std::vector<double*> pl;     // prolongation buffers per level 1..L (level L may be caller's)
+    unsigned char* vel_mask = nullptr;   // [nf]
+    unsigned char* p_mask = nullptr;     // [nc]
+    double* g = nullptr;                 // [nf][2]
+
+    // correction
+    double* grad = nullptr;      // [nf][2] G p_f
+    double* w = nullptr;         // [nf][2] M^{-1} G p_f (kept as the next warm start)
+    double* pf = nullptr;        // [nf]
+    double* ut = nullptr;        // [nf][2] intermediate velocity for cgp_step
+    double* bc = nullptr;        // [nc] coarse right-hand side for cgp_step
+
+    // Krylov workspace and reductions
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    double* part = nullptr;      // partial sums [16][max_blocks]
+    int max_blocks = 0;
+    cgp::SyncWords* sync = nullptr;
+    cgp::DevStats* stats = nullptr;
+
+    // staging for cgp_step_host
+    double* u_stage = nullptr;
+    double* pc_stage = nullptr;
+
+    cgp::Shape sh_f, sh_c;       // persistent shapes for fine and coarse problems
+    std::vector<void*> allocs;   // everything to free
+};
+
+namespace cgp {
+
+// assemble.cu
+cudaError_t launch_geometry(const double* xy, const int* tri, int t, double* geo, cudaStream_t s);
+cudaError_t launch_const_assembly(const DevElems& E, double* M, double* K, double* Dxy, cudaStream_t s);
+cudaError_t launch_apply_pressure_bc(cgp_ctx_s* c, cudaStream_t s);
+cudaError_t launch_make_A0(cgp_ctx_s* c, const double* K, cudaStream_t s);
+cudaError_t launch_assemble_step(cgp_ctx_s* c, const double* u, cudaStream_t s);
+
+// krylov.cu
+cudaError_t launch_poisson_cg(cgp_ctx_s* c, const double* b, double* x, cudaStream_t s);
+cudaError_t launch_mass_cg(cgp_ctx_s* c, const double* b, double* x, cudaStream_t s);
+cudaError_t launch_momentum_bicgstab(cgp_ctx_s* c, const double* u_in, double* x, cudaStream_t s);
+cudaError_t time_spmv_lanes(cgp_ctx_s* c, bool fine, int lanes, cudaStream_t s, float* ms);
+
+// mapping.cu
+cudaError_t launch_restrict_rhs(cgp_ctx_s* c, const double* ut, double* bc, cudaStream_t s);
+cudaError_t launch_prolong(cgp_ctx_s* c, const double* pc, double* pf, cudaStream_t s);
+cudaError_t launch_gradient(cgp_ctx_s* c, const double* pf, double* grad, cudaStream_t s);
+cudaError_t launch_correct(cgp_ctx_s* c, const double* ut, const double* w, double* u, double* gp_out,
+                           cudaStream_t s);
+cudaError_t launch_copy_pairs(const double* src, double* dst, int n, cudaStream_t s);
+
+// Cooperative launch helper: launches `func` with the shape and a single by-value argument.
+template <typename Args>
+cudaError_t coop_launch(const void* func, int blocks, int threads, Args& args, cudaStream_t s) {
+    void* kargs[] = {(void*)&args};
+    if (blocks == 1) return cudaLaunchKernel(func, dim3(1), dim3(threads), kargs, 0, s);
+    return cudaLaunchCooperativeKernel(func, dim3(blocks), dim3(threads), kargs, 0, s);
+}
+
+}  // namespace cgp

@@ -1,0 +1,39 @@
+// Host-side mesh preprocessing of the CGP library (the paper's preprocessing stage, Sect. 2.4):
+// validation, nested 1:4 refinement (Sect. 2.2), the s^p / s^u tables (Remark 2.2, Eqs. 29-30),
+// P1 CSR patterns, element-to-CSR slot maps and the element colouring used by the assembly.
+#pragma once
+#include <vector>
+#include "cgp.h"
+
+namespace cgp {
+
+struct HostLevel {
+    int n = 0, t = 0;
+    std::vector<double> xy;   // [n][2]
+    std::vector<int> tri;     // [t][3]
+};
+
+struct HostCsr {
+    int n = 0, nnz = 0;
+    std::vector<int> rp, ci, diag;   // row pointers [n+1], sorted columns [nnz], diagonal slot [n]
+};
+
+struct HostElems {
+    std::vector<int> slot;     // [t][9]: CSR slot of (row tri[a], col tri[b]) at a*3+b
+    std::vector<int> perm;     // elements sorted by colour
+    std::vector<int> colptr;   // [n_colours+1] offsets into perm
+};
+
+struct HostMesh {
+    std::vector<HostLevel> lv;               // lv[0] coarse (pressure) ... lv[L] fine (velocity)
+    std::vector<std::vector<int>> sp;        // sp[k]: [N_{k+1}][2] parent pair (beta, gamma)
+    std::vector<int> su;                     // [N_c] fine index xi of each coarse node
+    HostCsr fine, coarse;
+    HostElems ef, ec;
+    std::vector<unsigned char> onb_f, onb_c; // on-boundary flags
+};
+
+// Build everything from a coarse mesh. Returns CGP_OK, CGP_ERR_ARG or CGP_ERR_MESH.
+int build_host_mesh(const cgp_mesh_desc* d, int levels, HostMesh& out);
+
+}  // namespace cgp

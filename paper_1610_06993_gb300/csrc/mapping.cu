@@ -1,0 +1,125 @@
+// Grid-transfer and correction kernels of the CGP step (the paper's Eqs. 20-23, 29-30).
+#include "ctx.h"
+
+namespace cgp {
+
+namespace {
+
+// Eqs. 20-21 with Eq. 30: b_c[eta] = -(rho/dt) sum_j (Dx_c[eta,j] u~_f[xi_j].x + Dy_c[eta,j] u~_f[xi_j].y),
+// the injection u~_c[j] = u~_f[xi_j] fused into the gather (cif[k] = xi of column ci[k]).
+// Rows held at p = 0 get 0. One warp-group of `lanes` threads per coarse row.
+__global__ void k_restrict_rhs(int nc, const int* __restrict__ rp, const int* __restrict__ cif,
+                               const double* __restrict__ Dxy, const double* __restrict__ ut,
+                               const unsigned char* __restrict__ pm, double scale, double* __restrict__ bc,
+                               int lanes) {
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x);
+    const int row = gid / lanes, l = gid & (lanes - 1);
+    double acc = 0.0;
+    if (row < nc) {
+        const int k1 = rp[row + 1];
+        for (int k = rp[row] + l; k < k1; k += lanes) {
+            double dx, dy, ux, uy;
+            load2(Dxy, k, dx, dy);
+            load2(ut, cif[k], ux, uy);
+            acc += dx * ux + dy * uy;
+        }
+    }
+    acc = group_sum(acc, lanes);
+    if (row < nc && l == 0) bc[row] = pm[row] ? 0.0 : scale * acc;
+}
+
+// Eq. 22 through the table of Eq. 29: p_{k+1}[alpha] = (p_k[beta] + p_k[gamma]) / 2.
+__global__ void k_prolong(int n, const int2* __restrict__ sp, const double* __restrict__ src, double* __restrict__ dst) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int2 bg = sp[i];
+    dst[i] = 0.5 * (src[bg.x] + src[bg.y]);
+}
+
+// g = G p_f, G_ij = int phi_i grad psi_j (both components), `lanes` threads per row.
+__global__ void k_gradient(int nf, const int* __restrict__ rp, const int* __restrict__ ci,
+                           const double* __restrict__ Gxy, const double* __restrict__ pf, double* __restrict__ g,
+                           int lanes) {
+    const int gid = (blockIdx.x * blockDim.x + threadIdx.x);
+    const int row = gid / lanes, l = gid & (lanes - 1);
+    double ax = 0.0, ay = 0.0;
+    if (row < nf) {
+        const int k1 = rp[row + 1];
+        for (int k = rp[row] + l; k < k1; k += lanes) {
+            double gx, gy;
+            load2(Gxy, k, gx, gy);
+            const double p = pf[ci[k]];
+            ax += gx * p;
+            ay += gy * p;
+        }
+    }
+    ax = group_sum(ax, lanes);
+    ay = group_sum(ay, lanes);
+    if (row < nf && l == 0) store2(g, row, ax, ay);
+}
+
+// Eq. 23 with Eq. 15's dt/rho: u = u~ - (dt/rho) w, then prescribed velocity values at Dirichlet
+// nodes (Eq. 3). Optionally copies w out.
+__global__ void k_correct(int nf, const double* ut, const double* __restrict__ w, double c,
+                          const unsigned char* __restrict__ mask, const double* __restrict__ gd, double* u,
+                          double* gp_out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    double tx, ty, wx, wy, gx, gy;
+    load2(ut, i, tx, ty);
+    load2(w, i, wx, wy);
+    load2(gd, i, gx, gy);
+    const unsigned char m = mask[i];
+    store2(u, i, (m & CGP_BC_U) ? gx : tx - c * wx, (m & CGP_BC_V) ? gy : ty - c * wy);
+    if (gp_out) store2(gp_out, i, wx, wy);
+}
+
+__global__ void k_copy_pairs(const double2* __restrict__ src, double2* __restrict__ dst, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[i];
+}
+
+}  // namespace
+
+cudaError_t launch_restrict_rhs(cgp_ctx_s* c, const double* ut, double* bc, cudaStream_t s) {
+    const int lanes = c->sh_c.lanes, threads = 256;
+    const long long tot = (long long)c->nc * lanes;
+    k_restrict_rhs<<<(int)((tot + threads - 1) / threads), threads, 0, s>>>(
+        c->nc, c->C.rp, c->cif_su, c->Dc_xy, ut, c->p_mask, -(c->prm.rho / c->prm.dt), bc, lanes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(cgp_ctx_s* c, const double* pc, double* pf, cudaStream_t s) {
+    const double* src = pc;
+    for (int k = 0; k < c->levels; ++k) {
+        const int n = c->lv_n[k + 1];
+        double* dst = (k + 1 == c->levels) ? pf : c->pl[k];
+        k_prolong<<<(n + 255) / 256, 256, 0, s>>>(n, c->sp[k], src, dst);
+        src = dst;
+    }
+    if (c->levels == 0) {
+        cudaError_t e = cudaMemcpyAsync(pf, pc, sizeof(double) * (size_t)c->nf, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gradient(cgp_ctx_s* c, const double* pf, double* grad, cudaStream_t s) {
+    const int lanes = c->sh_f.lanes, threads = 256;
+    const long long tot = (long long)c->nf * lanes;
+    k_gradient<<<(int)((tot + threads - 1) / threads), threads, 0, s>>>(c->nf, c->F.rp, c->F.ci, c->Gxy, pf, grad, lanes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_correct(cgp_ctx_s* c, const double* ut, const double* w, double* u, double* gp_out,
+                           cudaStream_t s) {
+    k_correct<<<(c->nf + 255) / 256, 256, 0, s>>>(c->nf, ut, w, c->prm.dt / c->prm.rho, c->vel_mask, c->g, u, gp_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_pairs(const double* src, double* dst, int n, cudaStream_t s) {
+    k_copy_pairs<<<(n + 255) / 256, 256, 0, s>>>((const double2*)src, (double2*)dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace cgp

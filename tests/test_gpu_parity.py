@@ -1,0 +1,255 @@
+"""GPU parity of the CUDA CGP step against the FP64 CPU oracle, through the C ABI.
+
+Tolerances. Each Krylov solve stops at ||b - A x|| <= rtol ||b||. In parity mode rtol = 1e-13.
+For a symmetric positive definite K with condition number kappa, the energy-norm error obeys
+||e||_K / ||x||_K <= sqrt(kappa) * rtol, and the pressure gradient (what the correction uses) is
+measured by that norm, so on the 33x33-node cavity (kappa ~ 1e3) single-step stage errors are
+~1e-12 and the bar for 100 steps is 1e-10 relative L2 in u and in M^-1 G p_f (the requirement).
+Pure-gather stages (restriction, prolongation) are compared at 1e-14.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import cgp_inputs as ci
+from oracle import cgp as ocgp
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1610_06993_gb300 import cgp
+    if not os.path.exists(cgp.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    cgp.load()
+    return cgp
+
+
+def flow(coarse, prob, **kw):
+    from paper_1610_06993_gb300.flow import Flow
+    return Flow(coarse, prob, **kw)
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def cavity_state():
+    coarse, prob, _ = ci.workload("cavity33")
+    res, orc = ocgp.run(coarse, prob, 5, return_oracle=True)
+    return coarse, prob, orc, res
+
+
+def test_fine_mesh_matches_oracle(L, cavity_state):
+    coarse, prob, orc, _ = cavity_state
+    f = flow(coarse, prob)
+    assert np.array_equal(f.fine_xy, orc.fine.xy)
+    assert np.array_equal(f.onb_f, orc.onb_f)
+    assert f.info.n_fine == 4225 and f.info.nnz_fine == 29057 and f.info.nnz_coarse == 7361
+    f.close()
+
+
+def test_stagewise_parity(L, cavity_state):
+    """Each C-ABI stage on the same inputs as the oracle's stage (Eqs. 19, 20-21, 21, 22-23)."""
+    coarse, prob, orc, res = cavity_state
+    f = flow(coarse, prob, rtol=1e-13)
+    u_n, t = res.u, 6 * prob.dt
+    ref = orc.step(u_n, t)
+    ud = dev(u_n)
+    ut = torch.empty_like(ud)
+    L.cgp_assemble(f.ctx, ud)
+    L.cgp_momentum_solve(f.ctx, ud, ut)
+    st = f.stats()
+    assert st.momentum_status == 0 and st.momentum_rel_res <= 1e-13
+    assert rel(ut.cpu().numpy(), ref.ut) < 1e-12
+    # restriction + coarse right-hand side on the oracle's u~
+    bc = torch.empty(f.info.n_coarse, dtype=torch.float64, device="cuda")
+    L.cgp_restrict(f.ctx, dev(ref.ut), bc)
+    assert rel(bc.cpu().numpy(), ref.b_c) < 1e-14
+    # coarse Poisson on the oracle's b_c from a zero guess
+    pc = torch.zeros_like(bc)
+    L.cgp_poisson_solve(f.ctx, dev(ref.b_c), pc)
+    st = f.stats()
+    assert st.poisson_status == 0 and st.poisson_rel_res <= 1e-13
+    assert rel(pc.cpu().numpy(), ref.p_c) < 1e-11
+    # prolongation + correction on the oracle's p_c and u~
+    u1 = torch.empty_like(ud)
+    pf = torch.empty(f.info.n_fine, dtype=torch.float64, device="cuda")
+    gp = torch.empty_like(ud)
+    L.cgp_prolong_correct(f.ctx, dev(ref.p_c), dev(ref.ut), u1, pf, gp)
+    assert rel(pf.cpu().numpy(), ref.p_f) < 1e-15
+    assert rel(gp.cpu().numpy(), ref.gp) < 1e-12
+    assert rel(u1.cpu().numpy(), ref.u) < 1e-12
+    f.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_cavity33_100_steps(L, precision):
+    """The requirement: 1e-10 relative L2 in u and in the pressure gradient after 100 steps."""
+    coarse, prob, n = ci.workload("cavity33")
+    f = flow(coarse, prob, rtol=1e-13, precision=precision)
+    gp = torch.empty_like(f.u)
+    for _ in range(n - 1):
+        f.step()
+    # last step through the stage entry points, to read the gradient out
+    ut = torch.empty_like(f.u)
+    L.cgp_assemble(f.ctx, f.u)
+    L.cgp_momentum_solve(f.ctx, f.u, ut)
+    bc = torch.empty_like(f.pc)
+    L.cgp_restrict(f.ctx, ut, bc)
+    L.cgp_poisson_solve(f.ctx, bc, f.pc)
+    L.cgp_prolong_correct(f.ctx, f.pc, ut, f.u, None, gp)
+    st = f.stats(check=True)
+    ref = ocgp.run(coarse, prob, n)
+    eu, eg = rel(f.u.cpu().numpy(), ref.u), rel(gp.cpu().numpy(), ref.gp)
+    f.close()
+    assert eu < 1e-10 and eg < 1e-10, (eu, eg, st.as_dict())
+
+
+def test_cavity33_default_tolerance_error_is_stated(L):
+    """At the paper's 1e-8 tolerance (Sect. 2.3) the FP32+IR path stays within 1e-6 of the oracle."""
+    coarse, prob, n = ci.workload("cavity33")
+    errs = {}
+    for prec in (0, 1):
+        f = flow(coarse, prob, rtol=1e-8, precision=prec)
+        f.step(n)
+        f.stats(check=True)
+        errs[prec] = rel(f.u.cpu().numpy(), ocgp.run(coarse, prob, n).u) if prec == 0 else \
+            rel(f.u.cpu().numpy(), ocgp.run(coarse, prob, n).u)
+        f.close()
+    assert errs[0] < 1e-6 and errs[1] < 1e-6, errs
+
+
+@pytest.mark.parametrize("levels", [0, 2])
+def test_taylor_green_time_dependent_bc(L, levels):
+    """Taylor-Green (Eqs. 34-36) with exact Dirichlet data at t^{n+1}, levels 0 and 2."""
+    coarse = ci.cavity_mesh(9 if levels == 2 else 25, 8)
+    prob = ci.taylor_green_problem(0.01, 0.01, levels)
+    f = flow(coarse, prob, rtol=1e-13)
+    f.step(10)
+    f.stats(check=True)
+    ref = ocgp.run(coarse, prob, 10)
+    e = rel(f.u.cpu().numpy(), ref.u)
+    f.close()
+    assert e < 1e-10, e
+
+
+def test_backward_facing_step_small(L):
+    """Open outflow (natural velocity, p = 0, Eq. 14), parabolic inflow, several grid blocks."""
+    coarse, prob = ci.bfs_mesh(4, 1001), ci.bfs_problem(400.0, 0.005, 1)
+    f = flow(coarse, prob, rtol=1e-13)
+    assert f.info.grid_blocks > 1
+    f.step(20)
+    f.stats(check=True)
+    ref = ocgp.run(coarse, prob, 20)
+    e = rel(f.u.cpu().numpy(), ref.u)
+    f.close()
+    assert e < 1e-10, e
+
+
+def test_deterministic_and_host_entry(L):
+    """Same inputs give the same bits; cgp_step_host equals cgp_step."""
+    coarse, prob, _ = ci.workload("cavity33")
+    outs = []
+    for _ in range(2):
+        f = flow(coarse, prob, rtol=1e-10)
+        f.step(3)
+        outs.append(f.u.cpu().numpy())
+        f.close()
+    assert np.array_equal(outs[0], outs[1])
+    f = flow(coarse, prob, rtol=1e-10)
+    uh = f.u.cpu().numpy().copy()
+    ph = f.pc.cpu().numpy().copy()
+    for _ in range(3):
+        L.cgp_step_host(f.ctx, uh, ph)
+    f.close()
+    assert np.array_equal(uh, outs[0])
+
+
+def test_zero_flow_stays_zero(L):
+    """All-zero data: every right-hand side is zero and every solve returns exactly zero."""
+    coarse = ci.cavity_mesh(9, 2)
+    prob = ci.cavity_problem(100.0, 0.01, 1)
+    prob.vel_bc = lambda xy, onb, t: (np.where(onb, 3, 0).astype(np.uint8), np.zeros((xy.shape[0], 2)))
+    f = flow(coarse, prob)
+    f.step(2)
+    st = f.stats(check=True)
+    assert torch.count_nonzero(f.u).item() == 0 and torch.count_nonzero(f.pc).item() == 0
+    assert st.poisson_iters == 0
+    f.close()
+
+
+def test_not_converged_status(L):
+    """max_iter = 1: the solve stops, writes its result and reports CGP_ERR_NOT_CONVERGED."""
+    coarse, prob, _ = ci.workload("cavity33")
+    f = flow(coarse, prob, rtol=1e-13, max_iter=1)
+    f.step(1)
+    st = f.stats(check=False)
+    assert st.code == L.CGP_ERR_NOT_CONVERGED
+    assert st.momentum_status == L.CGP_ERR_NOT_CONVERGED or st.poisson_status == L.CGP_ERR_NOT_CONVERGED
+    assert torch.isfinite(f.u).all()
+    f.close()
+
+
+def test_nan_input_status(L):
+    """A non-finite velocity is reported as CGP_ERR_NAN, not propagated silently."""
+    coarse, prob, _ = ci.workload("cavity33")
+    f = flow(coarse, prob)
+    f.u[100, 0] = float("nan")
+    f.step(1)
+    st = f.stats(check=False)
+    assert st.code == L.CGP_ERR_NAN
+    f.close()
+
+
+def test_autotuned_lanes_same_answer(L):
+    coarse, prob, _ = ci.workload("cavity33")
+    f = flow(coarse, prob, rtol=1e-13, autotune=True)
+    assert f.info.spmv_lanes in (1, 2, 4, 8)
+    f.step(5)
+    f.stats(check=True)
+    e = rel(f.u.cpu().numpy(), ocgp.run(coarse, prob, 5).u)
+    f.close()
+    assert e < 1e-10, e
+
+
+@pytest.fixture(scope="module")
+def bfs_full():
+    coarse, prob, _ = ci.workload("bfs33")
+    orc = ocgp.CGPOracle(coarse.xy, coarse.tri, prob.rho, prob.mu, prob.dt, 1, prob.vel_bc, prob.p_bc)
+    return coarse, prob, orc
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_bfs33_full_size_one_step(L, bfs_full, precision):
+    """Full workload size (65,308 / 259,117 nodes), bench launch shape: one step from rest.
+
+    At rtol = 1e-12 the coarse Poisson energy-norm error is <= sqrt(kappa) * 1e-12 with
+    kappa ~ 1e7 on this elongated mesh, so the bar on u and M^-1 G p_f is 1e-8."""
+    coarse, prob, orc = bfs_full
+    f = flow(coarse, prob, rtol=1e-12, precision=precision)
+    u0 = f.u.cpu().numpy().copy()
+    ut = torch.empty_like(f.u)
+    gp = torch.empty_like(f.u)
+    bc = torch.empty_like(f.pc)
+    L.cgp_assemble(f.ctx, f.u)
+    L.cgp_momentum_solve(f.ctx, f.u, ut)
+    L.cgp_restrict(f.ctx, ut, bc)
+    L.cgp_poisson_solve(f.ctx, bc, f.pc)
+    L.cgp_prolong_correct(f.ctx, f.pc, ut, f.u, None, gp)
+    st = f.stats(check=True)
+    ref = orc.step(u0, prob.dt)
+    eu, eg = rel(f.u.cpu().numpy(), ref.u), rel(gp.cpu().numpy(), ref.gp)
+    f.close()
+    assert eu < 1e-8 and eg < 1e-8, (eu, eg, st.as_dict())

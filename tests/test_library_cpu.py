@@ -1,0 +1,82 @@
+"""CPU checks of the C ABI library: it loads, exports every declared symbol, and its host-side
+preprocessing (refinement numbering, s^p table, colouring, mesh validation) agrees with the oracle."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import cgp_inputs as ci
+from oracle import refine
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1610_06993_gb300 import cgp
+    if not os.path.exists(cgp.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    cgp.load()
+    return cgp
+
+
+def test_exports_every_declared_symbol(L):
+    decl = open(os.path.join(ROOT, "include", "cgp.h")).read()
+    names = re.findall(r"^\s*(?:int|void|const char\*)\s+(cgp_\w+)\(", decl, re.M)
+    assert len(names) >= 15
+    lib = L.load()
+    for n in names:
+        assert hasattr(lib, n), n
+    for n in ("cgp_mesh_create", "cgp_assemble", "cgp_momentum_solve", "cgp_restrict", "cgp_poisson_solve",
+              "cgp_prolong_correct", "cgp_step"):
+        assert n in names
+
+
+@pytest.mark.parametrize("mesh", [ci.cavity_mesh(9, 3), ci.bfs_mesh(2, 4)], ids=["cavity", "bfs"])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_native_refinement_matches_oracle(L, mesh, levels):
+    xf, tf, sp, col = L.cgp_refine(mesh.xy, mesh.tri, levels)
+    h = refine.build_hierarchy(mesh.xy, mesh.tri, levels)
+    assert np.array_equal(xf, h.fine.xy)            # same numbering, same midpoint bits
+    assert np.array_equal(tf, h.fine.tri)
+    if levels > 0:
+        assert np.array_equal(sp, h.sp[-1])
+    # colouring: no two elements of one colour share a node
+    for c in np.unique(col):
+        nodes = tf[col == c].ravel()
+        assert len(np.unique(nodes)) == len(nodes)
+    assert col.max() < 32
+
+
+def test_refinement_at_workload_size(L):
+    m = ci.bfs_mesh(33, 1001)
+    xf, tf, sp, col = L.cgp_refine(m.xy, m.tri, 1)
+    assert xf.shape == (259117, 2) and tf.shape == (514008, 3)
+    h = refine.build_hierarchy(m.xy, m.tri, 1)
+    assert np.array_equal(xf, h.fine.xy) and np.array_equal(tf, h.fine.tri)
+
+
+def test_mesh_validation_errors(L):
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])
+    good = np.array([[0, 1, 2], [1, 3, 2]])
+    L.cgp_refine(xy, good, 1)
+    with pytest.raises(L.CGPError) as e:
+        L.cgp_refine(xy, np.array([[0, 2, 1], [1, 3, 2]]), 1)      # clockwise
+    assert e.value.code == L.CGP_ERR_MESH
+    with pytest.raises(L.CGPError) as e:
+        L.cgp_refine(xy, np.array([[0, 1, 7]]), 1)                  # index out of range
+    assert e.value.code == L.CGP_ERR_MESH
+    with pytest.raises(L.CGPError) as e:                             # three triangles on one edge
+        xy5 = np.array([[0.0, 0.0], [1.0, 0.0], [0.5, 1.0], [0.5, 2.0], [0.5, 3.0]])
+        L.cgp_refine(xy5, np.array([[0, 1, 2], [0, 1, 3], [0, 1, 4]]), 0)
+    assert e.value.code == L.CGP_ERR_MESH
+    with pytest.raises(L.CGPError) as e:
+        L.cgp_refine(xy, good, 7)
+    assert e.value.code == L.CGP_ERR_ARG
+
+
+def test_status_strings(L):
+    assert L.cgp_status_str(0) == "CGP_OK"
+    assert L.cgp_status_str(L.CGP_ERR_TIMEOUT) == "CGP_ERR_TIMEOUT"
