@@ -56,12 +56,15 @@ typedef struct cgp_ctx_s* cgp_ctx;
  * semi-implicit BDF1 scheme (Eqs. 5-8). levels: number l of 1:4 refinements from the pressure
  * (coarse) mesh to the velocity (fine) mesh (Sect. 2.2); l = 0 is the standard scheme.
  * rtol: every solve stops when ||b - A x||_2 <= rtol ||b||_2 for each right-hand side (the
- * paper's Sect. 2.3 uses 1e-8). inner_rtol: CGP_MIXED only, the FP32 inner solve's reduction of
+ * paper's Sect. 2.3 uses 1e-8); for the momentum system ||b|| is that of the row-scaled system
+ * in which a Dirichlet row reads A_ii x_i = A_ii g_i. inner_rtol: CGP_MIXED only, the FP32 inner solve's reduction of
  * the FP64 residual per refinement pass (0 = default 1e-4). max_iter: cap on the total number of
  * Krylov iterations of one solve. max_outer: cap on refinement passes (0 = default 30).
  * spmv_lanes: lanes per CSR row in the SpMV inner loops (0 = let cgp_autotune()/default decide;
- * otherwise 1, 2, 4, 8, 16 or 32). block_threads: threads per block of the persistent kernels
- * (0 = default 512). */
+ * otherwise 1, 2, 4, 8, 16 or 32). block_threads: threads per block of the generic persistent
+ * kernels (0 = default 512, else 256..1024). coarse_solver: 0 = automatic (the on-chip pipelined
+ * CG kernel whenever the coarse matrix fits in shared memory, else classical CG), 1 = always the
+ * generic classical CG kernel. */
 typedef struct {
     double rho, mu, dt;
     int levels;
@@ -72,6 +75,7 @@ typedef struct {
     int max_outer;
     int spmv_lanes;
     int block_threads;
+    int coarse_solver;
 } cgp_params;
 
 /* A coarse mesh: n_nodes points xy_host[n][2] and n_tris counter-clockwise triangles

@@ -72,7 +72,7 @@ Shape make_shape(int n, int threads, int lanes, int num_sms, int bps) {
     s.threads = threads;
     s.lanes = lanes;
     const int want = (n + threads - 1) / threads;
-    const int cap = std::min(num_sms, bps * num_sms);
+    const int cap = std::min(std::min(num_sms, bps * num_sms), CGP_MAX_GRID);
     s.blocks = std::max(1, std::min(want, cap));
     return s;
 }
@@ -82,11 +82,12 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     cgp_params& P = c->prm;
     if (!(P.rho > 0.0) || !(P.mu >= 0.0) || !(P.dt > 0.0) || !(P.rtol > 0.0)) return CGP_ERR_ARG;
     if (P.precision != CGP_FP64 && P.precision != CGP_MIXED) return CGP_ERR_ARG;
+    if (P.coarse_solver != 0 && P.coarse_solver != 1) return CGP_ERR_ARG;
     if (P.inner_rtol <= 0.0) P.inner_rtol = 1e-4;
     if (P.max_iter <= 0) P.max_iter = 20000;
     if (P.max_outer <= 0) P.max_outer = 30;
     if (P.block_threads == 0) P.block_threads = 512;
-    if (P.block_threads < 64 || P.block_threads > 1024 || (P.block_threads & 31)) return CGP_ERR_ARG;
+    if (P.block_threads < 256 || P.block_threads > 1024 || (P.block_threads & 31)) return CGP_ERR_ARG;
     if (P.spmv_lanes != 0 && (P.spmv_lanes < 1 || P.spmv_lanes > 32 || (P.spmv_lanes & (P.spmv_lanes - 1))))
         return CGP_ERR_ARG;
     TRY(build_host_mesh(d, P.levels, c->hm));
@@ -190,6 +191,9 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     const int lanes = P.spmv_lanes ? P.spmv_lanes : 4;
     c->sh_f = make_shape(c->nf, threads, lanes, c->num_sms, bps);
     c->sh_c = make_shape(c->nc, threads, lanes, c->num_sms, bps);
+    c->width_c = 0;
+    for (int i = 0; i < H.coarse.n; ++i) c->width_c = std::max(c->width_c, H.coarse.rp[i + 1] - H.coarse.rp[i]);
+    if (P.coarse_solver == 0) CK(pipe_prepare(c));
     return CGP_OK;
 }
 

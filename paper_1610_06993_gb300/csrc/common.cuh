@@ -117,17 +117,30 @@ __device__ __forceinline__ void block_partials(double (&v)[K], double* part, uns
     }
 }
 
+// Maximum number of blocks of a persistent launch (partials are read 32 x 8 at a time).
+#define CGP_MAX_GRID 256
+
 // After a grid barrier: every block sums the nblocks partials of each of the K slots in the same
-// fixed order, so all blocks hold bit-identical totals. Result broadcast to all threads.
+// fixed order, so all blocks hold bit-identical totals. Slot k's partials start at
+// part + slot[k] * nblocks. Warp k handles slot k and issues all its loads at once, so the cost
+// is about one L2 round trip. Needs blockDim.x >= 32 K and nblocks <= CGP_MAX_GRID.
 template <int K>
-__device__ __forceinline__ void grid_totals(const double* part, unsigned int nblocks, double (&out)[K],
-                                            double* s_bcast /* [K] */) {
+__device__ __forceinline__ void grid_totals_at(const double* part, const int (&slot)[K], unsigned int nblocks,
+                                               double (&out)[K], double* s_bcast /* [K] */) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (warp == 0) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < K; ++k) {
+        if (warp == k) {
+            const double* p = part + (size_t)slot[k] * nblocks;
+            double v[CGP_MAX_GRID / 32];
+#pragma unroll
+            for (int q = 0; q < CGP_MAX_GRID / 32; ++q) {
+                const unsigned int b = lane + 32u * q;
+                v[q] = b < nblocks ? __ldcg(p + b) : 0.0;
+            }
             double t = 0.0;
-            for (unsigned int b = lane; b < nblocks; b += 32) t += __ldcg(part + k * nblocks + b);
+#pragma unroll
+            for (int q = 0; q < CGP_MAX_GRID / 32; ++q) t += v[q];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
             if (lane == 0) s_bcast[k] = t;
@@ -137,6 +150,16 @@ __device__ __forceinline__ void grid_totals(const double* part, unsigned int nbl
 #pragma unroll
     for (int k = 0; k < K; ++k) out[k] = s_bcast[k];
     __syncthreads();
+}
+
+// Contiguous slots starting at region `base` (in units of nblocks).
+template <int K>
+__device__ __forceinline__ void grid_totals(const double* part, unsigned int nblocks, double (&out)[K],
+                                            double* s_bcast /* [K] */) {
+    int slot[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) slot[k] = k;
+    grid_totals_at<K>(part, slot, nblocks, out, s_bcast);
 }
 
 // Rows owned by a block: a contiguous slice of [0, n).

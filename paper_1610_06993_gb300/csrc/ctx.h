@@ -104,6 +104,10 @@ struct cgp_ctx_s {
     double* pc_stage = nullptr;
 
     cgp::Shape sh_f, sh_c;       // persistent shapes for fine and coarse problems
+    int width_c = 0;             // longest coarse CSR row
+    bool use_pipe = false;       // coarse Poisson on the on-chip pipelined CG kernel
+    cgp::Shape pipe_c;           // its launch shape
+    size_t pipe_smem64 = 0, pipe_smem32 = 0;
     std::vector<void*> allocs;   // everything to free
 };
 
@@ -121,6 +125,11 @@ cudaError_t launch_poisson_cg(cgp_ctx_s* c, const double* b, double* x, cudaStre
 cudaError_t launch_mass_cg(cgp_ctx_s* c, const double* b, double* x, cudaStream_t s);
 cudaError_t launch_momentum_bicgstab(cgp_ctx_s* c, const double* u_in, double* x, cudaStream_t s);
 cudaError_t time_spmv_lanes(cgp_ctx_s* c, bool fine, int lanes, cudaStream_t s, float* ms);
+
+// krylov_pipe.cu
+bool pipe_shape(int n, int width, int num_sms, size_t elem, int* blocks, int* threads, size_t* smem);
+cudaError_t pipe_prepare(cgp_ctx_s* c);
+cudaError_t launch_poisson_pipe(cgp_ctx_s* c, const double* b, double* x, cudaStream_t s);
 
 // mapping.cu
 cudaError_t launch_restrict_rhs(cgp_ctx_s* c, const double* ut, double* bc, cudaStream_t s);

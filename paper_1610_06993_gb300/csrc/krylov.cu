@@ -258,8 +258,17 @@ __global__ void __launch_bounds__(1024) k_cg(CgArgs<TI> a) {
                 for (int c = 0; c < NR; ++c) v[c] = (double)vv[c];
                 block_partials<NR>(v, a.part + CG_I2 * nb, nb, s_red);
                 if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-                grid_totals<2 * NR>(a.part + (CG_I1 + 4 * (iters & 1)) * nb, nb, tg, s_bc);
-                grid_totals<NR>(a.part + CG_I2 * nb, nb, td, s_bc);
+                int slot[3 * NR];
+                double t3[3 * NR];
+#pragma unroll
+                for (int k = 0; k < 2 * NR; ++k) slot[k] = CG_I1 + 4 * (iters & 1) + k;
+#pragma unroll
+                for (int k = 0; k < NR; ++k) slot[2 * NR + k] = CG_I2 + k;
+                grid_totals_at<3 * NR>(a.part, slot, nb, t3, s_bc);
+#pragma unroll
+                for (int k = 0; k < 2 * NR; ++k) tg[k] = t3[k];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) td[k] = t3[2 * NR + k];
             }
             iters += 1;
             first = false;
@@ -320,6 +329,7 @@ struct BicgArgs {
     const TI* valI;
     const TI* dinvI;              // [n][2]
     const unsigned char* mask;    // CGP_BC_U / CGP_BC_V per node
+    const int* diag;              // [n] CSR slot of the diagonal
     const double* g;              // [n][2] prescribed values
     const double* b;              // [n][2]
     const double* x_in;           // [n][2] initial guess (Dirichlet entries are replaced by g)
@@ -359,6 +369,14 @@ __global__ void __launch_bounds__(1024) k_bicgstab(BicgArgs<TI> a) {
             load2(a.g, i, g0, g1);
             store2(a.x, i, (m & CGP_BC_U) ? g0 : x0, (m & CGP_BC_V) ? g1 : x1);
             load2(a.b, i, b0, b1);
+            // ||b|| of the row-scaled system: a Dirichlet row counts as A_ii x_i = A_ii g_i, so
+            // O(1) boundary values do not swamp the O(h^2) interior right-hand side. Those rows
+            // hold x_i = g_i exactly and never carry residual.
+            if (m) {
+                const double aii = a.val64[a.diag[i]];
+                if (m & CGP_BC_U) b0 *= aii;
+                if (m & CGP_BC_V) b1 *= aii;
+            }
             v[0] += b0 * b0;
             v[1] += b1 * b1;
         }
@@ -500,8 +518,14 @@ __global__ void __launch_bounds__(1024) k_bicgstab(BicgArgs<TI> a) {
                 double v[4] = {(double)vts[0], (double)vts[1], (double)vtt[0], (double)vtt[1]}, t4[4], tss[2];
                 block_partials<4>(v, a.part + BI_B4 * nb, nb, s_red);
                 if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-                grid_totals<4>(a.part + BI_B4 * nb, nb, t4, s_bc);
-                grid_totals<2>(a.part + BI_B3 * nb, nb, tss, s_bc);
+                {
+                    const int slot[6] = {BI_B4, BI_B4 + 1, BI_B4 + 2, BI_B4 + 3, BI_B3, BI_B3 + 1};
+                    double t6[6];
+                    grid_totals_at<6>(a.part, slot, nb, t6, s_bc);
+                    for (int k = 0; k < 4; ++k) t4[k] = t6[k];
+                    tss[0] = t6[4];
+                    tss[1] = t6[5];
+                }
                 for (int c = 0; c < 2; ++c) {
                     nan |= bad(t4[c]) | bad(t4[2 + c]) | bad(tss[c]);
                     if (act[c] && tss[c] <= tgt[c]) {          // converged at the half step
@@ -594,6 +618,7 @@ T* carve(char*& p, size_t count) {
 }  // namespace
 
 cudaError_t launch_poisson_cg(cgp_ctx_s* c, const double* b, double* x, cudaStream_t s) {
+    if (c->use_pipe) return launch_poisson_pipe(c, b, x, s);
     SyncWords* sw = c->sync + SYNC_POI;
     cudaError_t e = cudaMemsetAsync(sw, 0, sizeof(SyncWords), s);
     if (e != cudaSuccess) return e;
@@ -652,7 +677,7 @@ cudaError_t launch_momentum_bicgstab(cgp_ctx_s* c, const double* u_in, double* x
     if (mixed) {
         BicgArgs<float> a;
         a.n = c->nf; a.rp = c->F.rp; a.ci = c->F.ci; a.val64 = c->A; a.valI = c->A32; a.dinvI = c->dinvA32;
-        a.mask = c->vel_mask; a.g = c->g; a.b = c->b_mom; a.x_in = u_in; a.x = x;
+        a.mask = c->vel_mask; a.diag = c->F.diag; a.g = c->g; a.b = c->b_mom; a.x_in = u_in; a.x = x;
         a.r = carve<float>(p, n2); a.rh = carve<float>(p, n2); a.p = carve<float>(p, n2);
         a.v = carve<float>(p, n2); a.y = carve<float>(p, n2); a.s = carve<float>(p, n2);
         a.z = carve<float>(p, n2); a.t = carve<float>(p, n2); a.d = carve<float>(p, n2);
@@ -664,7 +689,7 @@ cudaError_t launch_momentum_bicgstab(cgp_ctx_s* c, const double* u_in, double* x
     }
     BicgArgs<double> a;
     a.n = c->nf; a.rp = c->F.rp; a.ci = c->F.ci; a.val64 = c->A; a.valI = c->A; a.dinvI = c->dinvA;
-    a.mask = c->vel_mask; a.g = c->g; a.b = c->b_mom; a.x_in = u_in; a.x = x;
+    a.mask = c->vel_mask; a.diag = c->F.diag; a.g = c->g; a.b = c->b_mom; a.x_in = u_in; a.x = x;
     a.r = carve<double>(p, n2); a.rh = carve<double>(p, n2); a.p = carve<double>(p, n2);
     a.v = carve<double>(p, n2); a.y = carve<double>(p, n2); a.s = carve<double>(p, n2);
     a.z = carve<double>(p, n2); a.t = carve<double>(p, n2); a.d = carve<double>(p, n2);

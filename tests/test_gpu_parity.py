@@ -146,7 +146,11 @@ def test_taylor_green_time_dependent_bc(L, levels):
 
 
 def test_backward_facing_step_small(L):
-    """Open outflow (natural velocity, p = 0, Eq. 14), parabolic inflow, several grid blocks."""
+    """Open outflow (natural velocity, p = 0, Eq. 14), parabolic inflow, several grid blocks.
+
+    The 30:2 channel makes the coarse Poisson matrix ill-conditioned (kappa ~ 1e5 at h = 1/4), so
+    at rtol = 1e-13 the per-step energy-norm error bound is sqrt(kappa) * 1e-13 ~ 3e-11 and 20
+    steps stay below 1e-9."""
     coarse, prob = ci.bfs_mesh(4, 1001), ci.bfs_problem(400.0, 0.005, 1)
     f = flow(coarse, prob, rtol=1e-13)
     assert f.info.grid_blocks > 1
@@ -155,7 +159,7 @@ def test_backward_facing_step_small(L):
     ref = ocgp.run(coarse, prob, 20)
     e = rel(f.u.cpu().numpy(), ref.u)
     f.close()
-    assert e < 1e-10, e
+    assert e < 1e-9, e
 
 
 def test_deterministic_and_host_entry(L):
@@ -235,10 +239,13 @@ def bfs_full():
 def test_bfs33_full_size_one_step(L, bfs_full, precision):
     """Full workload size (65,308 / 259,117 nodes), bench launch shape: one step from rest.
 
-    At rtol = 1e-12 the coarse Poisson energy-norm error is <= sqrt(kappa) * 1e-12 with
-    kappa ~ 1e7 on this elongated mesh, so the bar on u and M^-1 G p_f is 1e-8."""
+    The coarse matrix of this 30:2 channel has kappa ~ 1e7, and the FP64 evaluation of the true
+    residual itself carries rounding of order eps ||A|| ||x|| / ||b|| ~ 1e-11 (CG stalls near
+    9e-12), so the solves run at rtol = 3e-11. The energy-norm (gradient) error is then
+    <= sqrt(kappa) * 3e-11 ~ 1e-7 in the worst case; the bar on u and M^-1 G p_f is 1e-9
+    (observed: ~1e-11)."""
     coarse, prob, orc = bfs_full
-    f = flow(coarse, prob, rtol=1e-12, precision=precision)
+    f = flow(coarse, prob, rtol=3e-11, precision=precision)
     u0 = f.u.cpu().numpy().copy()
     ut = torch.empty_like(f.u)
     gp = torch.empty_like(f.u)
@@ -252,4 +259,20 @@ def test_bfs33_full_size_one_step(L, bfs_full, precision):
     ref = orc.step(u0, prob.dt)
     eu, eg = rel(f.u.cpu().numpy(), ref.u), rel(gp.cpu().numpy(), ref.gp)
     f.close()
-    assert eu < 1e-8 and eg < 1e-8, (eu, eg, st.as_dict())
+    assert eu < 1e-9 and eg < 1e-9, (eu, eg, st.as_dict())
+
+
+@pytest.mark.parametrize("solver", [0, 1], ids=["onchip_pipelined", "generic_classical"])
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_coarse_solvers_agree(L, cavity_state, solver, precision):
+    """Both coarse Poisson kernels (on-chip pipelined CG, generic classical CG) in both precisions
+    reach the oracle's exact solve of Eq. 21 at parity tolerance."""
+    coarse, prob, orc, res = cavity_state
+    ref = orc.step(res.u, 6 * prob.dt)
+    f = flow(coarse, prob, rtol=1e-13, precision=precision, coarse_solver=solver)
+    pc = torch.zeros(f.info.n_coarse, dtype=torch.float64, device="cuda")
+    L.cgp_poisson_solve(f.ctx, dev(ref.b_c), pc)
+    st = f.stats(check=True)
+    e = rel(pc.cpu().numpy(), ref.p_c)
+    f.close()
+    assert st.poisson_rel_res <= 1e-13 and e < 1e-11, (e, st.as_dict())
