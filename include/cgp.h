@@ -201,6 +201,26 @@ int cgp_get_stats(cgp_ctx ctx, void* stream, cgp_stats* st);
  * for the solver kernels (a project-written autotuner, not in the paper). Synchronous. */
 int cgp_autotune(cgp_ctx ctx, void* stream);
 
+/* Allocation-free conjugate-gradient solve of one symmetric positive definite CSR system
+ * A x = b (no counterpart in the paper: it exists for callers that must not allocate device
+ * memory, such as code embedded in a host program whose allocator owns every device byte, or code
+ * running where a cudaMalloc would synchronise or fail). It runs the same persistent
+ * Jacobi-preconditioned CG kernel inside FP64 refinement that the library uses for Eq. 21, but
+ * takes its scratch from a fixed static device array of about 3.6 MB instead of a context.
+ * Arguments: n rows (1 <= n <= 65536; larger n returns CGP_ERR_ARG), rp_dev [n+1], ci_dev [nnz]
+ * (0-based columns), val_dev [nnz] float64, all device memory; b_dev [n]; x_dev [n] initial
+ * guess in, solution out; stop at ||b - A x|| <= rtol ||b||; max_iter caps CG iterations.
+ * status_dev, iters_dev, rel_res_dev: optional device outputs (NULL to skip) receiving the
+ * CGP_* status, the iteration count and the final true relative residual.
+ * The call is stream-ordered and asynchronous and allocates nothing (no cudaMalloc, no
+ * cudaFree). The first call on each device looks up the scratch array's device address with that
+ * device current; make that first call before any stream capture. All calls share the one
+ * scratch array, so calls whose kernels overlap on the GPU race with each other: serialise them
+ * (one stream, or events). Errors: CGP_ERR_ARG, CGP_ERR_CUDA. */
+int cgp_cg_solve_noalloc(int n, const int* rp_dev, const int* ci_dev, const double* val_dev, const double* b_dev,
+                         double* x_dev, double rtol, int max_iter, int* status_dev, int* iters_dev,
+                         double* rel_res_dev, void* stream);
+
 /* Free everything the context owns. NULL is accepted. */
 int cgp_mesh_destroy(cgp_ctx ctx);
 

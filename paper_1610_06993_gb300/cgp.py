@@ -76,6 +76,8 @@ _SIGNATURES = {
     "cgp_step_host": (C.c_int, [_VP, _VP, _VP, _VP]),
     "cgp_get_stats": (C.c_int, [_VP, _VP, C.POINTER(cgp_stats)]),
     "cgp_autotune": (C.c_int, [_VP, _VP]),
+    "cgp_cg_solve_noalloc": (C.c_int, [C.c_int, _VP, _VP, _VP, _VP, _VP, C.c_double, C.c_int, _VP, _VP, _VP,
+                                       _VP]),
     "cgp_mesh_destroy": (C.c_int, [_VP]),
     "cgp_status_str": (C.c_char_p, [C.c_int]),
 }
@@ -235,6 +237,15 @@ def cgp_get_stats(ctx: int, stream=None, check: bool = False) -> cgp_stats:
 
 def cgp_autotune(ctx: int, stream=None) -> None:
     _check(load().cgp_autotune(ctx, _stream(stream)), "cgp_autotune")
+
+
+def cgp_cg_solve_noalloc(rp_dev, ci_dev, val_dev, b_dev, x_dev, rtol: float, max_iter: int, status_dev=None,
+                         iters_dev=None, rel_res_dev=None, stream=None) -> None:
+    """Allocation-free CG solve of a CSR system held in caller device tensors (see cgp.h)."""
+    n = int(b_dev.numel())
+    _check(load().cgp_cg_solve_noalloc(n, _ptr(rp_dev), _ptr(ci_dev), _ptr(val_dev), _ptr(b_dev), _ptr(x_dev),
+                                       float(rtol), int(max_iter), _ptr(status_dev), _ptr(iters_dev),
+                                       _ptr(rel_res_dev), _stream(stream)), "cgp_cg_solve_noalloc")
 
 
 def cgp_mesh_destroy(ctx: int) -> None:

@@ -18,6 +18,9 @@
 // Rows are split into one contiguous slice per block. Grid-wide reductions are deterministic:
 // each block writes its partial sums, and after a bounded grid barrier every block adds all
 // partials in the same order, so all blocks take identical branch decisions.
+#include <algorithm>
+#include <mutex>
+
 #include "ctx.h"
 
 namespace cgp {
@@ -745,4 +748,116 @@ cudaError_t time_spmv_lanes(cgp_ctx_s* c, bool fine, int lanes, cudaStream_t s, 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------------
+// Allocation-free variant of the classical CG kernel (cgp_cg_solve_noalloc)
+// ------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int NOALLOC_MAX_ROWS = 65536;
+constexpr size_t NOALLOC_VEC_BYTES = (size_t)NOALLOC_MAX_ROWS * sizeof(double);
+constexpr size_t NOALLOC_PART_BYTES = 32 * (size_t)CGP_MAX_GRID * sizeof(double);
+constexpr size_t NOALLOC_BYTES = 7 * NOALLOC_VEC_BYTES + NOALLOC_PART_BYTES + 512;
+
+// All scratch of cgp_cg_solve_noalloc: seven vectors of NOALLOC_MAX_ROWS doubles (r, u, w, p,
+// s, d and the inverse diagonal), the per-block partial sums, the grid-barrier words and a
+// statistics record. About 3.6 MB, held by every device that loads the library until exit.
+__device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+struct NoallocStats {
+    int iters, outer, status, barrier;
+    double rel;
+};
+
+struct NoallocDevice {
+    bool ready = false;
+    unsigned char* base = nullptr;   // device address of g_noalloc_scratch on this device
+    int num_sms = 0;
+};
+std::mutex g_noalloc_mu;
+NoallocDevice g_noalloc_dev[64];
+
+__global__ void k_noalloc_dinv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                               const double* __restrict__ val, double* dinv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k)
+        if (ci[k] == i) d = val[k];
+    dinv[i] = 1.0 / d;
+}
+
+}  // namespace
+
 }  // namespace cgp
+
+extern "C" int cgp_cg_solve_noalloc(int n, const int* rp_dev, const int* ci_dev, const double* val_dev,
+                                    const double* b_dev, double* x_dev, double rtol, int max_iter,
+                                    int* status_dev, int* iters_dev, double* rel_res_dev, void* stream) {
+    using namespace cgp;
+    if (n <= 0 || n > NOALLOC_MAX_ROWS) return CGP_ERR_ARG;
+    if (!rp_dev || !ci_dev || !val_dev || !b_dev || !x_dev || !(rtol > 0.0) || max_iter <= 0) return CGP_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CGP_ERR_CUDA;
+    if (dev < 0 || dev >= 64) return CGP_ERR_ARG;
+    NoallocDevice* nd = &g_noalloc_dev[dev];
+    {
+        // once per device, with that device current: the device address of the scratch array
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!nd->ready) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return CGP_ERR_CUDA;
+            int sms = 0, occ = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CGP_ERR_CUDA;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_cg<double, 1>, 512, 0) !=
+                    cudaSuccess || occ < 1)
+                return CGP_ERR_CUDA;
+            nd->base = (unsigned char*)p;
+            nd->num_sms = sms;
+            nd->ready = true;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* base = nd->base;
+    double* vec[7];
+    for (int k = 0; k < 7; ++k) vec[k] = (double*)(base + k * NOALLOC_VEC_BYTES);
+    double* part = (double*)(base + 7 * NOALLOC_VEC_BYTES);
+    SyncWords* sw = (SyncWords*)(base + 7 * NOALLOC_VEC_BYTES + NOALLOC_PART_BYTES);
+    NoallocStats* st = (NoallocStats*)(base + 7 * NOALLOC_VEC_BYTES + NOALLOC_PART_BYTES + 256);
+    // the scratch keeps the previous call's contents: clear the barrier words and statistics
+    if (cudaMemsetAsync(sw, 0, 512, s) != cudaSuccess) return CGP_ERR_CUDA;
+    if (status_dev && cudaMemsetAsync(status_dev, 0, sizeof(int), s) != cudaSuccess) return CGP_ERR_CUDA;
+    k_noalloc_dinv<<<(n + 255) / 256, 256, 0, s>>>(n, rp_dev, ci_dev, val_dev, vec[6]);
+    if (cudaGetLastError() != cudaSuccess) return CGP_ERR_CUDA;
+    CgArgs<double> a;
+    a.n = n;
+    a.rp = rp_dev;
+    a.ci = ci_dev;
+    a.val64 = val_dev;
+    a.valI = val_dev;
+    a.dinvI = vec[6];
+    a.b = b_dev;
+    a.x = x_dev;
+    a.r = vec[0];
+    a.u = vec[1];
+    a.w = vec[2];
+    a.p = vec[3];
+    a.s = vec[4];
+    a.d = vec[5];
+    a.part = part;
+    a.sw = sw;
+    a.rtol = rtol;
+    a.inner_rtol = 0.0;
+    a.max_iter = max_iter;
+    a.max_outer = 30;
+    a.lanes = 4;
+    a.st_iters = iters_dev ? iters_dev : &st->iters;
+    a.st_outer = &st->outer;
+    a.st_status = status_dev ? status_dev : &st->status;
+    a.st_rel = rel_res_dev ? rel_res_dev : &st->rel;
+    a.st_barrier = status_dev ? status_dev : &st->barrier;
+    const int threads = 512;
+    int blocks = (n + threads - 1) / threads;
+    blocks = std::max(1, std::min(std::min(blocks, nd->num_sms), CGP_MAX_GRID));
+    cudaError_t e = coop_launch((const void*)k_cg<double, 1>, blocks, threads, a, s);
+    return e == cudaSuccess ? CGP_OK : CGP_ERR_CUDA;
+}
