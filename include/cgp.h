@@ -62,9 +62,10 @@ typedef struct cgp_ctx_s* cgp_ctx;
  * Krylov iterations of one solve. max_outer: cap on refinement passes (0 = default 30).
  * spmv_lanes: lanes per CSR row in the SpMV inner loops (0 = let cgp_autotune()/default decide;
  * otherwise 1, 2, 4, 8, 16 or 32). block_threads: threads per block of the generic persistent
- * kernels (0 = default 512, else 256..1024). coarse_solver: 0 = automatic (the on-chip pipelined
- * CG kernel whenever the coarse matrix fits in shared memory, else classical CG), 1 = always the
- * generic classical CG kernel. */
+ * kernels (0 = default 512, else 256..1024). coarse_solver: 0 = automatic (the on-chip classical
+ * CG kernel whenever the coarse matrix slice of a block fits in shared memory, else the generic
+ * classical CG kernel), 1 = always the generic kernel, 2 = the on-chip pipelined CG kernel in
+ * CGP_FP64 (CGP_MIXED falls back to the on-chip classical kernel). */
 typedef struct {
     double rho, mu, dt;
     int levels;

@@ -82,7 +82,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     cgp_params& P = c->prm;
     if (!(P.rho > 0.0) || !(P.mu >= 0.0) || !(P.dt > 0.0) || !(P.rtol > 0.0)) return CGP_ERR_ARG;
     if (P.precision != CGP_FP64 && P.precision != CGP_MIXED) return CGP_ERR_ARG;
-    if (P.coarse_solver != 0 && P.coarse_solver != 1) return CGP_ERR_ARG;
+    if (P.coarse_solver < 0 || P.coarse_solver > 2) return CGP_ERR_ARG;
     if (P.inner_rtol <= 0.0) P.inner_rtol = 1e-4;
     if (P.max_iter <= 0) P.max_iter = 20000;
     if (P.max_outer <= 0) P.max_outer = 30;
@@ -193,7 +193,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     c->sh_c = make_shape(c->nc, threads, lanes, c->num_sms, bps);
     c->width_c = 0;
     for (int i = 0; i < H.coarse.n; ++i) c->width_c = std::max(c->width_c, H.coarse.rp[i + 1] - H.coarse.rp[i]);
-    if (P.coarse_solver == 0) CK(pipe_prepare(c));
+    CK(pipe_prepare(c));
     return CGP_OK;
 }
 

@@ -152,6 +152,34 @@ __device__ __forceinline__ void grid_totals_at(const double* part, const int (&s
     __syncthreads();
 }
 
+// As grid_totals_at, but leaves the K totals in s_bcast (visible to the whole block after the
+// trailing barrier) instead of copying them to every thread: for kernels where one thread does
+// the scalar recurrences and broadcasts the results.
+template <int K>
+__device__ __forceinline__ void grid_totals_shared(const double* part, const int (&slot)[K], unsigned int nblocks,
+                                                   double* s_bcast /* [K] */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (warp == k) {
+            const double* p = part + (size_t)slot[k] * nblocks;
+            double v[CGP_MAX_GRID / 32];
+#pragma unroll
+            for (int q = 0; q < CGP_MAX_GRID / 32; ++q) {
+                const unsigned int b = lane + 32u * q;
+                v[q] = b < nblocks ? __ldcg(p + b) : 0.0;
+            }
+            double t = 0.0;
+#pragma unroll
+            for (int q = 0; q < CGP_MAX_GRID / 32; ++q) t += v[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) s_bcast[k] = t;
+        }
+    }
+    __syncthreads();
+}
+
 // Contiguous slots starting at region `base` (in units of nblocks).
 template <int K>
 __device__ __forceinline__ void grid_totals(const double* part, unsigned int nblocks, double (&out)[K],

@@ -105,7 +105,8 @@ struct cgp_ctx_s {
 
     cgp::Shape sh_f, sh_c;       // persistent shapes for fine and coarse problems
     int width_c = 0;             // longest coarse CSR row
-    bool use_pipe = false;       // coarse Poisson on the on-chip pipelined CG kernel
+    bool use_pipe = false;       // coarse Poisson on an on-chip CG kernel
+    bool onchip_pipelined = false;   // ... in its pipelined form (else classical)
     cgp::Shape pipe_c;           // its launch shape
     size_t pipe_smem64 = 0, pipe_smem32 = 0;
     std::vector<void*> allocs;   // everything to free

@@ -262,7 +262,7 @@ def test_bfs33_full_size_one_step(L, bfs_full, precision):
     assert eu < 1e-9 and eg < 1e-9, (eu, eg, st.as_dict())
 
 
-@pytest.mark.parametrize("solver", [0, 1], ids=["onchip_pipelined", "generic_classical"])
+@pytest.mark.parametrize("solver", [0, 1, 2], ids=["onchip_classical", "generic_classical", "onchip_pipelined"])
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
 def test_coarse_solvers_agree(L, cavity_state, solver, precision):
     """Both coarse Poisson kernels (on-chip pipelined CG, generic classical CG) in both precisions
