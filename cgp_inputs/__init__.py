@@ -267,6 +267,27 @@ def taylor_green_problem(mu: float = 0.01, dt: float = 0.01, levels: int = 1) ->
     return Problem("taylor_green", 1.0, mu, dt, levels, vel_bc, p_bc, u0, time_dependent_bc=True)
 
 
+def batch_cavities(n_inst: int = 64, seed: int = 1003, n_min: int = 2000, n_max: int = 50000,
+                   re_min: float = 100.0, re_max: float = 1000.0, dt: float = 0.005):
+    """Independent lid-driven cavities of uneven size: a list of ``(CoarseMesh, Problem)``.
+
+    Instance i uses the SplitMix64 stream ``seed * 1000 + i``: draw 0 gives the coarse node
+    count N_i = exp(U[ln n_min, ln n_max]) (log-uniform, grid side round(sqrt(N_i))), draw 1 the
+    Reynolds number U[re_min, re_max]; the mesh itself is drawn by ``jittered_grid`` from the
+    stream ``seed * 1000 + i + 7919``."""
+    out = []
+    for i in range(n_inst):
+        s = seed * 1000 + i
+        u = uniform01(s, np.arange(2))
+        n_c = math.exp(math.log(n_min) + u[0] * (math.log(n_max) - math.log(n_min)))
+        side = max(3, int(round(math.sqrt(n_c))))
+        re = re_min + u[1] * (re_max - re_min)
+        mesh = jittered_grid(0.0, 1.0, 0.0, 1.0, side - 1, side - 1, s + 7919)
+        mesh.name = f"cavity{side}"
+        out.append((mesh, cavity_problem(re, dt, 1)))
+    return out
+
+
 # --------------------------------------------------------------------------------------
 # Named workloads
 # --------------------------------------------------------------------------------------

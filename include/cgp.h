@@ -198,6 +198,30 @@ int cgp_step_host(cgp_ctx ctx, double* u_host, double* pc_host, void* stream);
  * non-OK status among them (CGP_ERR_NOT_CONVERGED, CGP_ERR_NAN, CGP_ERR_TIMEOUT) or CGP_OK. */
 int cgp_get_stats(cgp_ctx ctx, void* stream, cgp_stats* st);
 
+/* ---- batched instances (many independent meshes advanced together) ------------------------
+ * A batch advances n contexts (same precision and device, each after cgp_set_bc) by the step of
+ * cgp_step, with one cooperative launch per persistent stage for all instances: the grid (up to
+ * two blocks per SM) is cut into per-instance block groups, sized by the instance's fine nnz for
+ * the fine-mesh solves and by nnz_c * sqrt(n_c) for the coarse CG; barriers and reductions stay
+ * inside a group. The coarse solve uses the generic classical CG kernel. The gathers between
+ * stages are launched per instance. Not in the paper: a systems pattern for many small problems.
+ * u_devs[i] [n_fine_i][2] and pc_devs[i] [n_coarse_i] are the instances' state, caller-owned
+ * device buffers that must stay valid until cgp_batch_destroy. */
+typedef struct cgp_batch_s* cgp_batch;
+int cgp_batch_create(cgp_ctx* ctxs, int n, double* const* u_devs, double* const* pc_devs, cgp_batch* out);
+/* Launch shape: total blocks and each instance's group sizes (arrays of n, may be NULL). */
+int cgp_batch_info(cgp_batch b, int* blocks, int* group_fine, int* group_coarse);
+/* One step of every instance, stream-ordered. */
+int cgp_batch_step(cgp_batch b, void* stream);
+/* `steps` steps of every instance by replaying a CUDA graph of one step (captured on an internal
+ * stream at the first call; make the first call outside any other stream capture). */
+int cgp_batch_run(cgp_batch b, int steps, void* stream);
+/* Synchronise and read every instance's statistics into per_instance[n]; returns the first
+ * non-OK status. */
+int cgp_batch_get_stats(cgp_batch b, void* stream, cgp_stats* per_instance);
+/* Free the batch (not the contexts). NULL is accepted. */
+int cgp_batch_destroy(cgp_batch b);
+
 /* Time the SpMV lane counts {1, 2, 4, 8} on the fine and coarse matrices and keep the fastest
  * for the solver kernels (a project-written autotuner, not in the paper). Synchronous. */
 int cgp_autotune(cgp_ctx ctx, void* stream);

@@ -78,6 +78,12 @@ _SIGNATURES = {
     "cgp_autotune": (C.c_int, [_VP, _VP]),
     "cgp_cg_solve_noalloc": (C.c_int, [C.c_int, _VP, _VP, _VP, _VP, _VP, C.c_double, C.c_int, _VP, _VP, _VP,
                                        _VP]),
+    "cgp_batch_create": (C.c_int, [_VP, C.c_int, _VP, _VP, C.POINTER(_VP)]),
+    "cgp_batch_info": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "cgp_batch_step": (C.c_int, [_VP, _VP]),
+    "cgp_batch_run": (C.c_int, [_VP, C.c_int, _VP]),
+    "cgp_batch_get_stats": (C.c_int, [_VP, _VP, _VP]),
+    "cgp_batch_destroy": (C.c_int, [_VP]),
     "cgp_mesh_destroy": (C.c_int, [_VP]),
     "cgp_status_str": (C.c_char_p, [C.c_int]),
 }
@@ -246,6 +252,44 @@ def cgp_cg_solve_noalloc(rp_dev, ci_dev, val_dev, b_dev, x_dev, rtol: float, max
     _check(load().cgp_cg_solve_noalloc(n, _ptr(rp_dev), _ptr(ci_dev), _ptr(val_dev), _ptr(b_dev), _ptr(x_dev),
                                        float(rtol), int(max_iter), _ptr(status_dev), _ptr(iters_dev),
                                        _ptr(rel_res_dev), _stream(stream)), "cgp_cg_solve_noalloc")
+
+
+def cgp_batch_create(ctxs, u_devs, pc_devs) -> int:
+    n = len(ctxs)
+    arr_c = (C.c_void_p * n)(*ctxs)
+    arr_u = (C.c_void_p * n)(*[_ptr(t) for t in u_devs])
+    arr_p = (C.c_void_p * n)(*[_ptr(t) for t in pc_devs])
+    h = _VP()
+    _check(load().cgp_batch_create(arr_c, n, arr_u, arr_p, C.byref(h)), "cgp_batch_create")
+    return h.value
+
+
+def cgp_batch_info(b: int, n: int):
+    blocks = C.c_int()
+    gf = np.zeros(n, dtype=np.int32)
+    gc = np.zeros(n, dtype=np.int32)
+    _check(load().cgp_batch_info(b, C.byref(blocks), gf.ctypes.data, gc.ctypes.data), "cgp_batch_info")
+    return blocks.value, gf, gc
+
+
+def cgp_batch_step(b: int, stream=None) -> None:
+    _check(load().cgp_batch_step(b, _stream(stream)), "cgp_batch_step")
+
+
+def cgp_batch_run(b: int, steps: int, stream=None) -> None:
+    _check(load().cgp_batch_run(b, int(steps), _stream(stream)), "cgp_batch_run")
+
+
+def cgp_batch_get_stats(b: int, n: int, stream=None, check: bool = False):
+    arr = (cgp_stats * n)()
+    code = load().cgp_batch_get_stats(b, _stream(stream), arr)
+    if code in (CGP_ERR_ARG, CGP_ERR_CUDA) or (check and code != CGP_OK):
+        raise CGPError(code, "cgp_batch_get_stats")
+    return list(arr), code
+
+
+def cgp_batch_destroy(b: int) -> None:
+    _check(load().cgp_batch_destroy(b), "cgp_batch_destroy")
 
 
 def cgp_mesh_destroy(ctx: int) -> None:

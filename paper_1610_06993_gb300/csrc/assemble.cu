@@ -9,6 +9,7 @@
 // Element loops run one colour at a time; elements of one colour share no node, so every CSR
 // slot is updated by one thread per colour: no atomics and a fixed summation order.
 #include "ctx.h"
+#include "assemble_kernels.cuh"
 
 namespace cgp {
 
@@ -92,83 +93,6 @@ __global__ void k_inv_diag(int n, const int* __restrict__ diag, const double* __
     if (i < n) dinv[i] = 1.0 / val[diag[i]];
 }
 
-struct StepAsmArgs {
-    int nf, nnz, ncol;
-    const int* colptr;           // device copy of the colour offsets
-    const int* perm;
-    const int* slot;
-    const double* geo;
-    const int* tri;
-    const int* rp;
-    const int* ci;
-    const int* diag;
-    const double* A0;
-    const double* M;
-    const double* u;             // [nf][2] u^n
-    const unsigned char* mask;
-    const double* g;
-    double* A;
-    float* A32;                  // nullptr unless CGP_MIXED
-    double* dinv;                // [nf][2]
-    float* dinv32;
-    double* b;                   // [nf][2]
-    double rho, dtrho;
-    SyncWords* sw;
-    int* barrier_status;
-};
-
-// Per-step momentum matrix A = A0 + dt rho N(u^n), Jacobi diagonals and right-hand side
-// b = rho M u^n (Dirichlet rows: prescribed values). One cooperative launch; grid barriers
-// separate the copy, each colour and the row pass.
-__global__ void __launch_bounds__(1024) k_assemble_step(StepAsmArgs a) {
-    unsigned int epoch = 0;
-    const unsigned int nb = gridDim.x;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nthreads = gridDim.x * blockDim.x;
-    for (int k = tid; k < a.nnz; k += nthreads) a.A[k] = a.A0[k];
-    if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.barrier_status);
-    for (int c = 0; c < a.ncol; ++c) {
-        const int k0 = a.colptr[c], k1 = a.colptr[c + 1];
-        for (int k = k0 + tid; k < k1; k += nthreads) {
-            const int e = a.perm[k];
-            const double* g = a.geo + 8 * (size_t)e;
-            const double area12 = g[0] / 12.0;
-            double ux[3], uy[3];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) load2(a.u, a.tri[3 * e + q], ux[q], uy[q]);
-            const double sx = ux[0] + ux[1] + ux[2], sy = uy[0] + uy[1] + uy[2];
-            const int* sl = a.slot + 9 * (size_t)e;
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                const double cx = area12 * (sx + ux[r]), cy = area12 * (sy + uy[r]);
-#pragma unroll
-                for (int q = 0; q < 3; ++q) a.A[sl[r * 3 + q]] += a.dtrho * (cx * g[1 + q] + cy * g[4 + q]);
-            }
-        }
-        if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.barrier_status);
-    }
-    for (int i = tid; i < a.nf; i += nthreads) {
-        const unsigned char m = a.mask[i];
-        const double dg = a.A[a.diag[i]];
-        const double di = 1.0 / dg;
-        double dx = (m & CGP_BC_U) ? 1.0 : di, dy = (m & CGP_BC_V) ? 1.0 : di;
-        store2(a.dinv, i, dx, dy);
-        double mx = 0.0, my = 0.0;
-        for (int k = a.rp[i]; k < a.rp[i + 1]; ++k) {
-            double ujx, ujy;
-            load2(a.u, a.ci[k], ujx, ujy);
-            const double mv = a.M[k];
-            mx += mv * ujx;
-            my += mv * ujy;
-            if (a.A32) a.A32[k] = (float)a.A[k];
-        }
-        double gx, gy;
-        load2(a.g, i, gx, gy);
-        store2(a.b, i, (m & CGP_BC_U) ? gx : a.rho * mx, (m & CGP_BC_V) ? gy : a.rho * my);
-        if (a.dinv32) store2(a.dinv32, i, (float)dx, (float)dy);
-    }
-}
-
 }  // namespace
 
 cudaError_t launch_geometry(const double* xy, const int* tri, int t, double* geo, cudaStream_t s) {
@@ -200,7 +124,9 @@ cudaError_t launch_make_A0(cgp_ctx_s* c, const double* K, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_assemble_step(cgp_ctx_s* c, const double* u, cudaStream_t s) {
+namespace {
+
+StepAsmArgs asm_args(cgp_ctx_s* c, const double* u, SyncWords* sw) {
     StepAsmArgs a;
     a.nf = c->nf;
     a.nnz = c->F.nnz;
@@ -226,11 +152,40 @@ cudaError_t launch_assemble_step(cgp_ctx_s* c, const double* u, cudaStream_t s) 
     a.b = c->b_mom;
     a.rho = c->prm.rho;
     a.dtrho = c->prm.dt * c->prm.rho;
-    a.sw = c->sync + SYNC_ASM;
+    a.sw = sw;
     a.barrier_status = &c->stats->barrier_status;
-    cudaError_t e = cudaMemsetAsync(a.sw, 0, sizeof(SyncWords), s);
+    return a;
+}
+
+}  // namespace
+
+cudaError_t launch_assemble_step(cgp_ctx_s* c, const double* u, cudaStream_t s) {
+    Launch<StepAsmArgs> L;
+    L.single = asm_args(c, u, c->sync + SYNC_ASM);
+    L.table = nullptr;
+    L.map = {nullptr, nullptr, nullptr};
+    cudaError_t e = cudaMemsetAsync(L.single.sw, 0, sizeof(SyncWords), s);
     if (e != cudaSuccess) return e;
-    return coop_launch((const void*)k_assemble_step, c->sh_f.blocks, c->sh_f.threads, a, s);
+    return coop_launch(k_assemble_step, c->sh_f.blocks, c->sh_f.threads, L, s);
+}
+
+cudaError_t batch_asm_build(cgp_batch_s* b) {
+    std::vector<StepAsmArgs> tab(b->n);
+    for (int i = 0; i < b->n; ++i) tab[i] = asm_args(b->ctx[i], b->u[i], b->sync + (size_t)i * SYNC_COUNT + SYNC_ASM);
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(StepAsmArgs) * tab.size());
+    if (e != cudaSuccess) return e;
+    b->allocs.push_back(d);
+    b->tab_asm = d;
+    return cudaMemcpy(d, tab.data(), sizeof(StepAsmArgs) * tab.size(), cudaMemcpyHostToDevice);
+}
+
+cudaError_t batch_asm_launch(cgp_batch_s* b, cudaStream_t s) {
+    Launch<StepAsmArgs> L;
+    L.single = StepAsmArgs();
+    L.table = (const StepAsmArgs*)b->tab_asm;
+    L.map = b->map_f;
+    return coop_launch(k_assemble_step, b->blocks_f, b->threads, L, s);
 }
 
 }  // namespace cgp

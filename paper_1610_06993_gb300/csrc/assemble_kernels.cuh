@@ -1,0 +1,89 @@
+// Per-step momentum assembly kernel, shared by the single-instance launcher (assemble.cu)
+// and the batched multi-instance step (batch.cu).
+#pragma once
+#include "ctx.h"
+
+namespace cgp {
+namespace {
+
+struct StepAsmArgs {
+    int nf, nnz, ncol;
+    const int* colptr;           // device copy of the colour offsets
+    const int* perm;
+    const int* slot;
+    const double* geo;
+    const int* tri;
+    const int* rp;
+    const int* ci;
+    const int* diag;
+    const double* A0;
+    const double* M;
+    const double* u;             // [nf][2] u^n
+    const unsigned char* mask;
+    const double* g;
+    double* A;
+    float* A32;                  // nullptr unless CGP_MIXED
+    double* dinv;                // [nf][2]
+    float* dinv32;
+    double* b;                   // [nf][2]
+    double rho, dtrho;
+    SyncWords* sw;
+    int* barrier_status;
+};
+
+// Per-step momentum matrix A = A0 + dt rho N(u^n), Jacobi diagonals and right-hand side
+// b = rho M u^n (Dirichlet rows: prescribed values). One cooperative launch; grid barriers
+// separate the copy, each colour and the row pass.
+__global__ void __launch_bounds__(1024) k_assemble_step(Launch<StepAsmArgs> L) {
+    const Grp grp = group_of(L.map);
+    const StepAsmArgs& a = L.table ? L.table[grp.inst] : L.single;
+    unsigned int epoch = 0;
+    const unsigned int nb = grp.nb;
+    const int tid = grp.bid * blockDim.x + threadIdx.x;
+    const int nthreads = grp.nb * blockDim.x;
+    for (int k = tid; k < a.nnz; k += nthreads) a.A[k] = a.A0[k];
+    if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.barrier_status);
+    for (int c = 0; c < a.ncol; ++c) {
+        const int k0 = a.colptr[c], k1 = a.colptr[c + 1];
+        for (int k = k0 + tid; k < k1; k += nthreads) {
+            const int e = a.perm[k];
+            const double* g = a.geo + 8 * (size_t)e;
+            const double area12 = g[0] / 12.0;
+            double ux[3], uy[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) load2(a.u, a.tri[3 * e + q], ux[q], uy[q]);
+            const double sx = ux[0] + ux[1] + ux[2], sy = uy[0] + uy[1] + uy[2];
+            const int* sl = a.slot + 9 * (size_t)e;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const double cx = area12 * (sx + ux[r]), cy = area12 * (sy + uy[r]);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) a.A[sl[r * 3 + q]] += a.dtrho * (cx * g[1 + q] + cy * g[4 + q]);
+            }
+        }
+        if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.barrier_status);
+    }
+    for (int i = tid; i < a.nf; i += nthreads) {
+        const unsigned char m = a.mask[i];
+        const double dg = a.A[a.diag[i]];
+        const double di = 1.0 / dg;
+        double dx = (m & CGP_BC_U) ? 1.0 : di, dy = (m & CGP_BC_V) ? 1.0 : di;
+        store2(a.dinv, i, dx, dy);
+        double mx = 0.0, my = 0.0;
+        for (int k = a.rp[i]; k < a.rp[i + 1]; ++k) {
+            double ujx, ujy;
+            load2(a.u, a.ci[k], ujx, ujy);
+            const double mv = a.M[k];
+            mx += mv * ujx;
+            my += mv * ujy;
+            if (a.A32) a.A32[k] = (float)a.A[k];
+        }
+        double gx, gy;
+        load2(a.g, i, gx, gy);
+        store2(a.b, i, (m & CGP_BC_U) ? gx : a.rho * mx, (m & CGP_BC_V) ? gy : a.rho * my);
+        if (a.dinv32) store2(a.dinv32, i, (float)dx, (float)dy);
+    }
+}
+
+}  // namespace
+}  // namespace cgp

@@ -117,6 +117,46 @@ __device__ __forceinline__ void block_partials(double (&v)[K], double* part, uns
     }
 }
 
+// Same, for block `bid` of a block group of `nblocks` blocks.
+template <int K>
+__device__ __forceinline__ void block_partials(double (&v)[K], double* part, unsigned int nblocks, unsigned int bid,
+                                               double* s_scratch) {
+    block_sum<K>(v, s_scratch);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) part[k * nblocks + bid] = v[k];
+    }
+}
+
+// Block groups. A batched launch advances several independent problem instances at once: the
+// grid is cut into contiguous block groups, one per instance, and every barrier and reduction
+// runs within a group. map.inst_of_block == nullptr means one group spanning the whole grid.
+struct BatchMap {
+    const int* inst_of_block;   // [gridDim.x] instance of each block
+    const int* inst_b0;         // [instances] first block of each group
+    const int* inst_nb;         // [instances] blocks in each group
+};
+
+struct Grp {
+    unsigned int nb, bid;       // blocks in this block's group, index of this block in it
+    int inst;                   // instance handled by the group
+};
+
+// Kernel parameter of a persistent launch: the arguments of a single instance, or a device table
+// of per-instance arguments plus the block-group map of a batched launch.
+template <typename Args>
+struct Launch {
+    Args single;
+    const Args* table;
+    BatchMap map;
+};
+
+__device__ __forceinline__ Grp group_of(const BatchMap& m) {
+    if (m.inst_of_block == nullptr) return {gridDim.x, blockIdx.x, 0};
+    const int i = m.inst_of_block[blockIdx.x];
+    return {(unsigned int)m.inst_nb[i], blockIdx.x - (unsigned int)m.inst_b0[i], i};
+}
+
 // Maximum number of blocks of a persistent launch (partials are read 32 x 8 at a time).
 #define CGP_MAX_GRID 256
 
@@ -197,6 +237,15 @@ struct RowRange {
 __device__ __forceinline__ RowRange block_rows(int n) {
     const long long per = ((long long)n + gridDim.x - 1) / gridDim.x;
     long long r0 = per * blockIdx.x, r1 = r0 + per;
+    if (r0 > n) r0 = n;
+    if (r1 > n) r1 = n;
+    return {(int)r0, (int)r1};
+}
+
+// Rows owned by a block of a block group.
+__device__ __forceinline__ RowRange group_rows(int n, const Grp& g) {
+    const long long per = ((long long)n + g.nb - 1) / g.nb;
+    long long r0 = per * g.bid, r1 = r0 + per;
     if (r0 > n) r0 = n;
     if (r1 > n) r1 = n;
     return {(int)r0, (int)r1};

@@ -112,7 +112,37 @@ struct cgp_ctx_s {
     std::vector<void*> allocs;   // everything to free
 };
 
+// A batch of independent contexts advanced together: one cooperative launch per persistent stage
+// covers every instance, each on its own group of blocks.
+struct cgp_batch_s {
+    std::vector<cgp_ctx_s*> ctx;
+    std::vector<double*> u, pc;          // per-instance state (caller device buffers)
+    int n = 0, threads = 512, precision = CGP_FP64;
+    int blocks_f = 0, blocks_c = 0, max_group = 1;
+    std::vector<int> b0_f, nb_f, b0_c, nb_c;
+    cgp::BatchMap map_f{nullptr, nullptr, nullptr}, map_c{nullptr, nullptr, nullptr};
+    cgp::SyncWords* sync = nullptr;      // [n][SYNC_COUNT]
+    double* part = nullptr;              // [n][32 * max_group]
+    void* tab_asm = nullptr;             // device tables of per-instance kernel arguments
+    void* tab_mom = nullptr;
+    void* tab_poi = nullptr;
+    void* tab_mass = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<void*> allocs;
+};
+
 namespace cgp {
+
+// batch stages (assemble.cu, krylov.cu)
+cudaError_t batch_asm_build(cgp_batch_s* b);
+cudaError_t batch_asm_launch(cgp_batch_s* b, cudaStream_t s);
+cudaError_t batch_solvers_build(cgp_batch_s* b);
+cudaError_t batch_momentum_launch(cgp_batch_s* b, cudaStream_t s);
+cudaError_t batch_poisson_launch(cgp_batch_s* b, cudaStream_t s);
+cudaError_t batch_mass_launch(cgp_batch_s* b, cudaStream_t s);
+int persistent_blocks_per_sm(int threads);
 
 // assemble.cu
 cudaError_t launch_geometry(const double* xy, const int* tri, int t, double* geo, cudaStream_t s);
@@ -140,12 +170,13 @@ cudaError_t launch_correct(cgp_ctx_s* c, const double* ut, const double* w, doub
                            cudaStream_t s);
 cudaError_t launch_copy_pairs(const double* src, double* dst, int n, cudaStream_t s);
 
-// Cooperative launch helper: launches `func` with the shape and a single by-value argument.
+// Cooperative launch helper: launches `func` with the shape and its single by-value argument
+// (typed, so a kernel cannot be handed the wrong argument structure).
 template <typename Args>
-cudaError_t coop_launch(const void* func, int blocks, int threads, Args& args, cudaStream_t s) {
+cudaError_t coop_launch(void (*func)(Args), int blocks, int threads, Args& args, cudaStream_t s) {
     void* kargs[] = {(void*)&args};
-    if (blocks == 1) return cudaLaunchKernel(func, dim3(1), dim3(threads), kargs, 0, s);
-    return cudaLaunchCooperativeKernel(func, dim3(blocks), dim3(threads), kargs, 0, s);
+    if (blocks == 1) return cudaLaunchKernel((const void*)func, dim3(1), dim3(threads), kargs, 0, s);
+    return cudaLaunchCooperativeKernel((const void*)func, dim3(blocks), dim3(threads), kargs, 0, s);
 }
 
 }  // namespace cgp

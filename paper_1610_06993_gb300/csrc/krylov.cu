@@ -22,600 +22,84 @@
 #include <mutex>
 
 #include "ctx.h"
+#include "krylov_kernels.cuh"
 
 namespace cgp {
 
+
 namespace {
 
-// y = A x over the block's rows, `lanes` consecutive threads per row. emit(row, acc0, acc1) runs
-// on the first lane of each row group. Every thread of the block runs the same number of passes
-// so the group shuffles always see full warps.
-template <int NR, typename TV, typename TX, typename Emit>
-__device__ __forceinline__ void spmv_block(RowRange rr, const int* __restrict__ rp, const int* __restrict__ ci,
-                                           const TV* __restrict__ val, const TX* x, int lanes, Emit emit) {
-    const int groups = blockDim.x / lanes;
-    const int g = threadIdx.x / lanes;
-    const int l = threadIdx.x & (lanes - 1);
-    for (int base = rr.r0; base < rr.r1; base += groups) {
-        const int row = base + g;
-        TX a0 = 0, a1 = 0;
-        if (row < rr.r1) {
-            const int k1 = __ldg(rp + row + 1);
-            for (int k = __ldg(rp + row) + l; k < k1; k += lanes) {
-                const int j = __ldg(ci + k);
-                const TX v = (TX)__ldg(val + k);
-                if (NR == 1) {
-                    a0 += v * x[j];
-                } else {
-                    TX x0, x1;
-                    load2(x, j, x0, x1);
-                    a0 += v * x0;
-                    a1 += v * x1;
-                }
-            }
-        }
-        a0 = group_sum(a0, lanes);
-        if (NR == 2) a1 = group_sum(a1, lanes);
-        if (l == 0 && row < rr.r1) emit(row, a0, a1);
-    }
+// ---- argument builders, shared by the single-instance launchers and the batched stages -------
+template <typename TI>
+CgArgs<TI> poisson_args(cgp_ctx_s* c, const double* b, double* x, SyncWords* sw, double* part) {
+    const bool mixed = sizeof(TI) == sizeof(float);
+    const int n = c->nc;
+    char* p = (char*)c->ws;
+    CgArgs<TI> a;
+    a.n = n;
+    a.rp = c->C.rp;
+    a.ci = c->C.ci;
+    a.val64 = c->Kc;
+    a.valI = mixed ? (const TI*)(const void*)c->Kc32 : (const TI*)(const void*)c->Kc;
+    a.dinvI = mixed ? (const TI*)(const void*)c->dinvK32 : (const TI*)(const void*)c->dinvK;
+    a.b = b;
+    a.x = x;
+    a.r = carve<TI>(p, n); a.u = carve<TI>(p, n); a.w = carve<TI>(p, n);
+    a.p = carve<TI>(p, n); a.s = carve<TI>(p, n); a.d = carve<TI>(p, n);
+    a.part = part;
+    a.sw = sw;
+    a.rtol = c->prm.rtol;
+    a.inner_rtol = mixed ? c->prm.inner_rtol : 0.0;
+    a.max_iter = c->prm.max_iter;
+    a.max_outer = c->prm.max_outer;
+    a.lanes = c->sh_c.lanes;
+    a.st_iters = &c->stats->poi_iters; a.st_outer = &c->stats->poi_outer; a.st_status = &c->stats->poi_status;
+    a.st_rel = &c->stats->poi_rel; a.st_barrier = &c->stats->barrier_status;
+    return a;
 }
 
-__device__ __forceinline__ bool bad(double v) { return !(fabs(v) <= 1.7976931348623157e308); }
-
-// ------------------------------------------------------------------------------------------
-// CG (Chronopoulos-Gear) inside FP64 iterative refinement
-// ------------------------------------------------------------------------------------------
-template <typename TI>
-struct CgArgs {
-    int n;
-    const int* rp;
-    const int* ci;
-    const double* val64;
-    const TI* valI;
-    const TI* dinvI;      // [n]
-    const double* b;      // [n][NR]
-    double* x;            // [n][NR] initial guess in, solution out
-    TI *r, *u, *w, *p, *s, *d;
-    double* part;         // [32][nblocks]
-    SyncWords* sw;
-    double rtol, inner_rtol;
-    int max_iter, max_outer, lanes;
-    int* st_iters;
-    int* st_outer;
-    int* st_status;
-    double* st_rel;
-    int* st_barrier;
-};
-
-// partial-sum regions (units of nblocks doubles)
-enum { CG_P0 = 0, CG_O1 = 2, CG_I0 = 8, CG_I1 = 10 /* two buffers of 4 */, CG_I2 = 18 };
-
-template <typename TI, int NR>
-__global__ void __launch_bounds__(1024) k_cg(CgArgs<TI> a) {
-    __shared__ double s_red[32 * 8];
-    __shared__ double s_bc[8];
-    const unsigned int nb = gridDim.x;
-    unsigned int epoch = 0;
-    const RowRange rr = block_rows(a.n);
-    const int tpb = blockDim.x;
-    double bb[NR], rr64[NR];
-    int iters = 0, outer = 0, status = CGP_OK;
-#pragma unroll
-    for (int c = 0; c < NR; ++c) rr64[c] = 0.0;
-
-    // ||b||^2 per right-hand side; a zero right-hand side has the zero solution
-    {
-        double v[NR];
-#pragma unroll
-        for (int c = 0; c < NR; ++c) v[c] = 0.0;
-        for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb)
-#pragma unroll
-            for (int c = 0; c < NR; ++c) {
-                const double bi = a.b[(size_t)i * NR + c];
-                v[c] += bi * bi;
-            }
-        block_partials<NR>(v, a.part + CG_P0 * nb, nb, s_red);
-        if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-        grid_totals<NR>(a.part + CG_P0 * nb, nb, bb, s_bc);
-        bool any_zero = false;
-#pragma unroll
-        for (int c = 0; c < NR; ++c) any_zero |= (bb[c] == 0.0);
-        if (any_zero) {
-            for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb)
-#pragma unroll
-                for (int c = 0; c < NR; ++c)
-                    if (bb[c] == 0.0) a.x[(size_t)i * NR + c] = 0.0;
-            if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-        }
-    }
-    const double rtol2 = a.rtol * a.rtol, itol2 = a.inner_rtol * a.inner_rtol;
-    const double floor2 = 0.25 * rtol2;
-
-    for (;;) {
-        // ---- refinement pass: FP64 true residual, inner start r = (TI) r64, u = D^-1 r, d = 0
-        double t1[3 * NR];
-        {
-            double v[3 * NR];
-#pragma unroll
-            for (int k = 0; k < 3 * NR; ++k) v[k] = 0.0;
-            spmv_block<NR, double, double>(rr, a.rp, a.ci, a.val64, a.x, a.lanes, [&](int i, double s0, double s1) {
-                const double acc[2] = {s0, s1};
-                const TI di = a.dinvI[i];
-#pragma unroll
-                for (int c = 0; c < NR; ++c) {
-                    const size_t idx = (size_t)i * NR + c;
-                    const double ri = a.b[idx] - acc[c];
-                    v[c] += ri * ri;
-                    const TI rI = (TI)ri, uI = di * rI;
-                    a.r[idx] = rI;
-                    a.u[idx] = uI;
-                    a.d[idx] = (TI)0;
-                    v[NR + c] += (double)(rI * uI);
-                }
-            });
-            block_partials<3 * NR>(v, a.part + CG_O1 * nb, nb, s_red);
-            if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-            grid_totals<3 * NR>(a.part + CG_O1 * nb, nb, t1, s_bc);
-        }
-        bool act[NR], any = false, nan = false;
-        double tgt[NR], gam[NR], alpha[NR], beta[NR];
-#pragma unroll
-        for (int c = 0; c < NR; ++c) {
-            rr64[c] = t1[c];
-            nan |= bad(t1[c]) | bad(t1[NR + c]);
-            act[c] = !(bb[c] == 0.0 || rr64[c] <= rtol2 * bb[c]);
-            any |= act[c];
-            tgt[c] = fmax(itol2 * rr64[c], floor2 * bb[c]);
-            gam[c] = t1[NR + c];
-        }
-        if (nan) { status = CGP_ERR_NAN; break; }
-        if (!any) break;
-        if (outer >= a.max_outer || iters >= a.max_iter) { status = CGP_ERR_NOT_CONVERGED; break; }
-
-        // ---- w = A u, delta = (w, u); alpha_0 = gamma_0 / delta_0
-        {
-            double v[NR], t0[NR];
-#pragma unroll
-            for (int c = 0; c < NR; ++c) v[c] = 0.0;
-            spmv_block<NR, TI, TI>(rr, a.rp, a.ci, a.valI, a.u, a.lanes, [&](int i, TI s0, TI s1) {
-                const TI acc[2] = {s0, s1};
-#pragma unroll
-                for (int c = 0; c < NR; ++c) {
-                    const size_t idx = (size_t)i * NR + c;
-                    a.w[idx] = acc[c];
-                    v[c] += (double)(acc[c] * a.u[idx]);
-                }
-            });
-            block_partials<NR>(v, a.part + CG_I0 * nb, nb, s_red);
-            if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-            grid_totals<NR>(a.part + CG_I0 * nb, nb, t0, s_bc);
-#pragma unroll
-            for (int c = 0; c < NR; ++c) {
-                if (act[c] && t0[c] != 0.0 && !bad(t0[c])) {
-                    alpha[c] = gam[c] / t0[c];
-                } else {
-                    act[c] = false;
-                    alpha[c] = 0.0;
-                }
-                beta[c] = 0.0;
-            }
-        }
-        bool first = true;
-        for (;;) {
-            // ---- local update: p = u + beta p, s = w + beta s, d += alpha p, r -= alpha s, u = D^-1 r
-            {
-                TI vg[NR], vr[NR];
-#pragma unroll
-                for (int c = 0; c < NR; ++c) vg[c] = vr[c] = (TI)0;
-                TI al[NR], be[NR];
-#pragma unroll
-                for (int c = 0; c < NR; ++c) {
-                    al[c] = (TI)alpha[c];
-                    be[c] = (TI)beta[c];
-                }
-                for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
-                    const TI di = a.dinvI[i];
-#pragma unroll
-                    for (int c = 0; c < NR; ++c) {
-                        const size_t idx = (size_t)i * NR + c;
-                        const TI uo = a.u[idx], wo = a.w[idx];
-                        const TI p = first ? uo : uo + be[c] * a.p[idx];
-                        const TI s = first ? wo : wo + be[c] * a.s[idx];
-                        a.p[idx] = p;
-                        a.s[idx] = s;
-                        a.d[idx] += al[c] * p;
-                        const TI r = a.r[idx] - al[c] * s;
-                        a.r[idx] = r;
-                        const TI u = di * r;
-                        a.u[idx] = u;
-                        vg[c] += r * u;
-                        vr[c] += r * r;
-                    }
-                }
-                double v[2 * NR];
-#pragma unroll
-                for (int c = 0; c < NR; ++c) {
-                    v[c] = (double)vg[c];
-                    v[NR + c] = (double)vr[c];
-                }
-                block_partials<2 * NR>(v, a.part + (CG_I1 + 4 * (iters & 1)) * nb, nb, s_red);
-                if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-            }
-            // ---- w = A u, delta = (w, u)
-            double tg[2 * NR], td[NR];
-            {
-                TI vv[NR];
-#pragma unroll
-                for (int c = 0; c < NR; ++c) vv[c] = (TI)0;
-                spmv_block<NR, TI, TI>(rr, a.rp, a.ci, a.valI, a.u, a.lanes, [&](int i, TI s0, TI s1) {
-                    const TI acc[2] = {s0, s1};
-#pragma unroll
-                    for (int c = 0; c < NR; ++c) {
-                        const size_t idx = (size_t)i * NR + c;
-                        a.w[idx] = acc[c];
-                        vv[c] += acc[c] * a.u[idx];
-                    }
-                });
-                double v[NR];
-#pragma unroll
-                for (int c = 0; c < NR; ++c) v[c] = (double)vv[c];
-                block_partials<NR>(v, a.part + CG_I2 * nb, nb, s_red);
-                if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-                int slot[3 * NR];
-                double t3[3 * NR];
-#pragma unroll
-                for (int k = 0; k < 2 * NR; ++k) slot[k] = CG_I1 + 4 * (iters & 1) + k;
-#pragma unroll
-                for (int k = 0; k < NR; ++k) slot[2 * NR + k] = CG_I2 + k;
-                grid_totals_at<3 * NR>(a.part, slot, nb, t3, s_bc);
-#pragma unroll
-                for (int k = 0; k < 2 * NR; ++k) tg[k] = t3[k];
-#pragma unroll
-                for (int k = 0; k < NR; ++k) td[k] = t3[2 * NR + k];
-            }
-            iters += 1;
-            first = false;
-            bool more = false;
-#pragma unroll
-            for (int c = 0; c < NR; ++c) {
-                nan |= bad(tg[c]) | bad(tg[NR + c]) | bad(td[c]);
-                if (act[c] && tg[NR + c] <= tgt[c]) act[c] = false;
-                if (act[c]) {
-                    const double gnew = tg[c];
-                    const double bnew = gnew / gam[c];
-                    const double den = td[c] - bnew * gnew / alpha[c];
-                    if (den != 0.0 && gam[c] != 0.0) {
-                        beta[c] = bnew;
-                        alpha[c] = gnew / den;
-                        gam[c] = gnew;
-                    } else {
-                        act[c] = false;
-                    }
-                }
-                if (!act[c]) alpha[c] = beta[c] = 0.0;
-                more |= act[c];
-            }
-            if (nan || !more || iters >= a.max_iter) break;
-        }
-        if (nan) { status = CGP_ERR_NAN; break; }
-        // ---- x += d (FP64)
-        for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb)
-#pragma unroll
-            for (int c = 0; c < NR; ++c) {
-                const size_t idx = (size_t)i * NR + c;
-                a.x[idx] += (double)a.d[idx];
-            }
-        if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-        outer += 1;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        double rel = 0.0;
-#pragma unroll
-        for (int c = 0; c < NR; ++c)
-            if (bb[c] > 0.0) rel = fmax(rel, sqrt(rr64[c] / bb[c]));
-        *a.st_iters = iters;
-        *a.st_outer = outer;
-        *a.st_status = status;
-        *a.st_rel = rel;
-    }
+CgArgs<double> mass_args(cgp_ctx_s* c, const double* b, double* x, SyncWords* sw, double* part) {
+    const size_t n2 = 2 * (size_t)c->nf;
+    char* p = (char*)c->ws;
+    CgArgs<double> a;
+    a.n = c->nf; a.rp = c->F.rp; a.ci = c->F.ci; a.val64 = c->M; a.valI = c->M; a.dinvI = c->dinvM;
+    a.b = b; a.x = x;
+    a.r = carve<double>(p, n2); a.u = carve<double>(p, n2); a.w = carve<double>(p, n2);
+    a.p = carve<double>(p, n2); a.s = carve<double>(p, n2); a.d = carve<double>(p, n2);
+    a.part = part; a.sw = sw; a.rtol = c->prm.rtol; a.inner_rtol = 0.0;
+    a.max_iter = c->prm.max_iter; a.max_outer = c->prm.max_outer; a.lanes = c->sh_f.lanes;
+    a.st_iters = &c->stats->mass_iters; a.st_outer = &c->stats->mass_outer; a.st_status = &c->stats->mass_status;
+    a.st_rel = &c->stats->mass_rel; a.st_barrier = &c->stats->barrier_status;
+    return a;
 }
-
-// ------------------------------------------------------------------------------------------
-// BiCGStab, two right-hand sides, identity rows at Dirichlet nodes, inside FP64 refinement
-// ------------------------------------------------------------------------------------------
-template <typename TI>
-struct BicgArgs {
-    int n;
-    const int* rp;
-    const int* ci;
-    const double* val64;
-    const TI* valI;
-    const TI* dinvI;              // [n][2]
-    const unsigned char* mask;    // CGP_BC_U / CGP_BC_V per node
-    const int* diag;              // [n] CSR slot of the diagonal
-    const double* g;              // [n][2] prescribed values
-    const double* b;              // [n][2]
-    const double* x_in;           // [n][2] initial guess (Dirichlet entries are replaced by g)
-    double* x;                    // [n][2] solution
-    TI *r, *rh, *p, *v, *y, *s, *z, *t, *d;
-    double* part;
-    SyncWords* sw;
-    double rtol, inner_rtol;
-    int max_iter, max_outer, lanes;
-    int* st_iters;
-    int* st_outer;
-    int* st_status;
-    double* st_rel;
-    int* st_barrier;
-};
-
-enum { BI_P0 = 0, BI_O1 = 2, BI_B2 = 6, BI_B3 = 8, BI_B4 = 10, BI_B5 = 14 };
 
 template <typename TI>
-__global__ void __launch_bounds__(1024) k_bicgstab(BicgArgs<TI> a) {
-    __shared__ double s_red[32 * 8];
-    __shared__ double s_bc[8];
-    const unsigned int nb = gridDim.x;
-    unsigned int epoch = 0;
-    const RowRange rr = block_rows(a.n);
-    const int tpb = blockDim.x;
-    double bb[2], rr64[2] = {0.0, 0.0};
-    int iters = 0, outer = 0, status = CGP_OK;
-
-    // initial guess with prescribed values, ||b||^2
-    {
-        double v[2] = {0.0, 0.0};
-        for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
-            const unsigned char m = a.mask[i];
-            double x0, x1, g0, g1, b0, b1;
-            load2(a.x_in, i, x0, x1);
-            load2(a.g, i, g0, g1);
-            store2(a.x, i, (m & CGP_BC_U) ? g0 : x0, (m & CGP_BC_V) ? g1 : x1);
-            load2(a.b, i, b0, b1);
-            // ||b|| of the row-scaled system: a Dirichlet row counts as A_ii x_i = A_ii g_i, so
-            // O(1) boundary values do not swamp the O(h^2) interior right-hand side. Those rows
-            // hold x_i = g_i exactly and never carry residual.
-            if (m) {
-                const double aii = a.val64[a.diag[i]];
-                if (m & CGP_BC_U) b0 *= aii;
-                if (m & CGP_BC_V) b1 *= aii;
-            }
-            v[0] += b0 * b0;
-            v[1] += b1 * b1;
-        }
-        block_partials<2>(v, a.part + BI_P0 * nb, nb, s_red);
-        if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-        grid_totals<2>(a.part + BI_P0 * nb, nb, bb, s_bc);
-        if (bb[0] == 0.0 || bb[1] == 0.0) {
-            for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb)
-                for (int c = 0; c < 2; ++c)
-                    if (bb[c] == 0.0) a.x[2 * (size_t)i + c] = 0.0;
-            if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-        }
-    }
-    const double rtol2 = a.rtol * a.rtol, itol2 = a.inner_rtol * a.inner_rtol;
-    const double floor2 = 0.25 * rtol2;
-    auto masked = [&](int i, int c, TI acc, const TI* src) -> TI {
-        return (a.mask[i] & (1 << c)) ? src[2 * (size_t)i + c] : acc;
-    };
-
-    for (;;) {
-        double t1[4];
-        {
-            double v[4] = {0.0, 0.0, 0.0, 0.0};
-            spmv_block<2, double, double>(rr, a.rp, a.ci, a.val64, a.x, a.lanes, [&](int i, double s0, double s1) {
-                const double acc[2] = {s0, s1};
-                const unsigned char m = a.mask[i];
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const size_t idx = 2 * (size_t)i + c;
-                    const double ax = (m & (1 << c)) ? a.x[idx] : acc[c];
-                    const double ri = a.b[idx] - ax;
-                    v[c] += ri * ri;
-                    const TI rI = (TI)ri;
-                    a.r[idx] = rI;
-                    a.rh[idx] = rI;
-                    a.d[idx] = (TI)0;
-                    v[2 + c] += (double)(rI * rI);
-                }
-            });
-            block_partials<4>(v, a.part + BI_O1 * nb, nb, s_red);
-            if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-            grid_totals<4>(a.part + BI_O1 * nb, nb, t1, s_bc);
-        }
-        bool act[2], any = false, nan = false;
-        double tgt[2], rho[2], alpha[2] = {0.0, 0.0}, omega[2] = {0.0, 0.0}, beta[2] = {0.0, 0.0};
-        for (int c = 0; c < 2; ++c) {
-            rr64[c] = t1[c];
-            nan |= bad(t1[c]) | bad(t1[2 + c]);
-            act[c] = !(bb[c] == 0.0 || rr64[c] <= rtol2 * bb[c]);
-            any |= act[c];
-            tgt[c] = fmax(itol2 * rr64[c], floor2 * bb[c]);
-            rho[c] = t1[2 + c];
-        }
-        if (nan) { status = CGP_ERR_NAN; break; }
-        if (!any) break;
-        if (outer >= a.max_outer || iters >= a.max_iter) { status = CGP_ERR_NOT_CONVERGED; break; }
-
-        bool first = true;
-        for (;;) {
-            TI al[2], om[2], be[2];
-            // ---- p = r + beta (p - omega v), y = D^-1 p
-            for (int c = 0; c < 2; ++c) {
-                om[c] = (TI)omega[c];
-                be[c] = (TI)beta[c];
-            }
-            for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
-                TI d0, d1;
-                load2(a.dinvI, i, d0, d1);
-                const TI dd[2] = {d0, d1};
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const size_t idx = 2 * (size_t)i + c;
-                    const TI r = a.r[idx];
-                    const TI p = first ? r : r + be[c] * (a.p[idx] - om[c] * a.v[idx]);
-                    a.p[idx] = p;
-                    a.y[idx] = dd[c] * p;
-                }
-            }
-            if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-            // ---- v = A y, sigma = (rh, v)
-            {
-                TI vs[2] = {(TI)0, (TI)0};
-                spmv_block<2, TI, TI>(rr, a.rp, a.ci, a.valI, a.y, a.lanes, [&](int i, TI s0, TI s1) {
-                    const TI acc[2] = {s0, s1};
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const size_t idx = 2 * (size_t)i + c;
-                        const TI vv = masked(i, c, acc[c], a.y);
-                        a.v[idx] = vv;
-                        vs[c] += a.rh[idx] * vv;
-                    }
-                });
-                double v[2] = {(double)vs[0], (double)vs[1]}, ts[2];
-                block_partials<2>(v, a.part + BI_B2 * nb, nb, s_red);
-                if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-                grid_totals<2>(a.part + BI_B2 * nb, nb, ts, s_bc);
-                for (int c = 0; c < 2; ++c) {
-                    nan |= bad(ts[c]);
-                    if (act[c] && ts[c] != 0.0) alpha[c] = rho[c] / ts[c];
-                    else { act[c] = false; alpha[c] = 0.0; }
-                    al[c] = (TI)alpha[c];
-                }
-            }
-            // ---- s = r - alpha v, z = D^-1 s, d += alpha y, (s, s)
-            {
-                TI vs[2] = {(TI)0, (TI)0};
-                for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
-                    TI d0, d1;
-                    load2(a.dinvI, i, d0, d1);
-                    const TI dd[2] = {d0, d1};
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const size_t idx = 2 * (size_t)i + c;
-                        const TI s = a.r[idx] - al[c] * a.v[idx];
-                        a.s[idx] = s;
-                        a.z[idx] = dd[c] * s;
-                        a.d[idx] += al[c] * a.y[idx];
-                        vs[c] += s * s;
-                    }
-                }
-                double v[2] = {(double)vs[0], (double)vs[1]};
-                block_partials<2>(v, a.part + BI_B3 * nb, nb, s_red);
-                if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-            }
-            // ---- t = A z, omega = (t, s) / (t, t)
-            {
-                TI vts[2] = {(TI)0, (TI)0}, vtt[2] = {(TI)0, (TI)0};
-                spmv_block<2, TI, TI>(rr, a.rp, a.ci, a.valI, a.z, a.lanes, [&](int i, TI s0, TI s1) {
-                    const TI acc[2] = {s0, s1};
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const size_t idx = 2 * (size_t)i + c;
-                        const TI tv = masked(i, c, acc[c], a.z);
-                        a.t[idx] = tv;
-                        vts[c] += tv * a.s[idx];
-                        vtt[c] += tv * tv;
-                    }
-                });
-                double v[4] = {(double)vts[0], (double)vts[1], (double)vtt[0], (double)vtt[1]}, t4[4], tss[2];
-                block_partials<4>(v, a.part + BI_B4 * nb, nb, s_red);
-                if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-                {
-                    const int slot[6] = {BI_B4, BI_B4 + 1, BI_B4 + 2, BI_B4 + 3, BI_B3, BI_B3 + 1};
-                    double t6[6];
-                    grid_totals_at<6>(a.part, slot, nb, t6, s_bc);
-                    for (int k = 0; k < 4; ++k) t4[k] = t6[k];
-                    tss[0] = t6[4];
-                    tss[1] = t6[5];
-                }
-                for (int c = 0; c < 2; ++c) {
-                    nan |= bad(t4[c]) | bad(t4[2 + c]) | bad(tss[c]);
-                    if (act[c] && tss[c] <= tgt[c]) {          // converged at the half step
-                        act[c] = false;
-                        omega[c] = 0.0;
-                    } else if (act[c] && t4[2 + c] != 0.0) {
-                        omega[c] = t4[c] / t4[2 + c];
-                    } else {
-                        act[c] = false;
-                        omega[c] = 0.0;
-                    }
-                    om[c] = (TI)omega[c];
-                }
-            }
-            // ---- d += omega z, r = s - omega t, rho' = (rh, r), (r, r)
-            {
-                TI vr[2] = {(TI)0, (TI)0}, vq[2] = {(TI)0, (TI)0};
-                for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const size_t idx = 2 * (size_t)i + c;
-                        a.d[idx] += om[c] * a.z[idx];
-                        const TI r = a.s[idx] - om[c] * a.t[idx];
-                        a.r[idx] = r;
-                        vr[c] += a.rh[idx] * r;
-                        vq[c] += r * r;
-                    }
-                }
-                double v[4] = {(double)vr[0], (double)vr[1], (double)vq[0], (double)vq[1]}, t5[4];
-                block_partials<4>(v, a.part + BI_B5 * nb, nb, s_red);
-                if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-                grid_totals<4>(a.part + BI_B5 * nb, nb, t5, s_bc);
-                iters += 1;
-                first = false;
-                bool more = false;
-                for (int c = 0; c < 2; ++c) {
-                    nan |= bad(t5[c]) | bad(t5[2 + c]);
-                    if (act[c] && t5[2 + c] <= tgt[c]) act[c] = false;
-                    if (act[c]) {
-                        if (t5[c] != 0.0 && omega[c] != 0.0 && rho[c] != 0.0) {
-                            beta[c] = (t5[c] / rho[c]) * (alpha[c] / omega[c]);
-                            rho[c] = t5[c];
-                        } else {
-                            act[c] = false;            // breakdown: restart in the next pass
-                        }
-                    }
-                    if (!act[c]) beta[c] = 0.0;
-                    more |= act[c];
-                }
-                if (nan || !more || iters >= a.max_iter) break;
-            }
-        }
-        if (nan) { status = CGP_ERR_NAN; break; }
-        for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb)
-            for (int c = 0; c < 2; ++c) a.x[2 * (size_t)i + c] += (double)a.d[2 * (size_t)i + c];
-        if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-        outer += 1;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        double rel = 0.0;
-        for (int c = 0; c < 2; ++c)
-            if (bb[c] > 0.0) rel = fmax(rel, sqrt(rr64[c] / bb[c]));
-        *a.st_iters = iters;
-        *a.st_outer = outer;
-        *a.st_status = status;
-        *a.st_rel = rel;
-    }
+BicgArgs<TI> momentum_args(cgp_ctx_s* c, const double* u_in, double* x, SyncWords* sw, double* part) {
+    const bool mixed = sizeof(TI) == sizeof(float);
+    const size_t n2 = 2 * (size_t)c->nf;
+    char* p = (char*)c->ws;
+    BicgArgs<TI> a;
+    a.n = c->nf; a.rp = c->F.rp; a.ci = c->F.ci; a.val64 = c->A;
+    a.valI = mixed ? (const TI*)(const void*)c->A32 : (const TI*)(const void*)c->A;
+    a.dinvI = mixed ? (const TI*)(const void*)c->dinvA32 : (const TI*)(const void*)c->dinvA;
+    a.mask = c->vel_mask; a.diag = c->F.diag; a.g = c->g; a.b = c->b_mom; a.x_in = u_in; a.x = x;
+    a.r = carve<TI>(p, n2); a.rh = carve<TI>(p, n2); a.p = carve<TI>(p, n2);
+    a.v = carve<TI>(p, n2); a.y = carve<TI>(p, n2); a.s = carve<TI>(p, n2);
+    a.z = carve<TI>(p, n2); a.t = carve<TI>(p, n2); a.d = carve<TI>(p, n2);
+    a.part = part; a.sw = sw; a.rtol = c->prm.rtol; a.inner_rtol = mixed ? c->prm.inner_rtol : 0.0;
+    a.max_iter = c->prm.max_iter; a.max_outer = c->prm.max_outer; a.lanes = c->sh_f.lanes;
+    a.st_iters = &c->stats->mom_iters; a.st_outer = &c->stats->mom_outer; a.st_status = &c->stats->mom_status;
+    a.st_rel = &c->stats->mom_rel; a.st_barrier = &c->stats->barrier_status;
+    return a;
 }
 
-// Stand-alone SpMV used by the autotuner: y = A x over all rows, one row slice per block.
-template <int NR>
-__global__ void __launch_bounds__(1024) k_spmv_probe(int n, const int* rp, const int* ci, const double* val,
-                                                     const double* x, double* y, int lanes, int rows_per_block) {
-    RowRange rr;
-    rr.r0 = min(n, blockIdx.x * rows_per_block);
-    rr.r1 = min(n, rr.r0 + rows_per_block);
-    spmv_block<NR, double, double>(rr, rp, ci, val, x, lanes, [&](int i, double s0, double s1) {
-        if (NR == 1) y[i] = s0;
-        else store2(y, i, s0, s1);
-    });
-}
-
-template <typename T>
-T* carve(char*& p, size_t count) {
-    T* r = reinterpret_cast<T*>(p);
-    p += ((count * sizeof(T) + 255) / 256) * 256;
-    return r;
+template <typename Args>
+Launch<Args> single_launch(const Args& a) {
+    Launch<Args> L;
+    L.single = a;
+    L.table = nullptr;
+    L.map = {nullptr, nullptr, nullptr};
+    return L;
 }
 
 }  // namespace
@@ -625,82 +109,103 @@ cudaError_t launch_poisson_cg(cgp_ctx_s* c, const double* b, double* x, cudaStre
     SyncWords* sw = c->sync + SYNC_POI;
     cudaError_t e = cudaMemsetAsync(sw, 0, sizeof(SyncWords), s);
     if (e != cudaSuccess) return e;
-    const bool mixed = c->prm.precision == CGP_MIXED;
-    const int n = c->nc;
-    char* p = (char*)c->ws;
-    if (mixed) {
-        CgArgs<float> a;
-        a.n = n; a.rp = c->C.rp; a.ci = c->C.ci; a.val64 = c->Kc; a.valI = c->Kc32; a.dinvI = c->dinvK32;
-        a.b = b; a.x = x;
-        a.r = carve<float>(p, n); a.u = carve<float>(p, n); a.w = carve<float>(p, n);
-        a.p = carve<float>(p, n); a.s = carve<float>(p, n); a.d = carve<float>(p, n);
-        a.part = c->part; a.sw = sw; a.rtol = c->prm.rtol; a.inner_rtol = c->prm.inner_rtol;
-        a.max_iter = c->prm.max_iter; a.max_outer = c->prm.max_outer; a.lanes = c->sh_c.lanes;
-        a.st_iters = &c->stats->poi_iters; a.st_outer = &c->stats->poi_outer; a.st_status = &c->stats->poi_status;
-        a.st_rel = &c->stats->poi_rel; a.st_barrier = &c->stats->barrier_status;
-        return coop_launch((const void*)k_cg<float, 1>, c->sh_c.blocks, c->sh_c.threads, a, s);
+    if (c->prm.precision == CGP_MIXED) {
+        auto L = single_launch(poisson_args<float>(c, b, x, sw, c->part));
+        return coop_launch(k_cg<float, 1>, c->sh_c.blocks, c->sh_c.threads, L, s);
     }
-    CgArgs<double> a;
-    a.n = n; a.rp = c->C.rp; a.ci = c->C.ci; a.val64 = c->Kc; a.valI = c->Kc; a.dinvI = c->dinvK;
-    a.b = b; a.x = x;
-    a.r = carve<double>(p, n); a.u = carve<double>(p, n); a.w = carve<double>(p, n);
-    a.p = carve<double>(p, n); a.s = carve<double>(p, n); a.d = carve<double>(p, n);
-    a.part = c->part; a.sw = sw; a.rtol = c->prm.rtol; a.inner_rtol = 0.0;
-    a.max_iter = c->prm.max_iter; a.max_outer = c->prm.max_outer; a.lanes = c->sh_c.lanes;
-    a.st_iters = &c->stats->poi_iters; a.st_outer = &c->stats->poi_outer; a.st_status = &c->stats->poi_status;
-    a.st_rel = &c->stats->poi_rel; a.st_barrier = &c->stats->barrier_status;
-    return coop_launch((const void*)k_cg<double, 1>, c->sh_c.blocks, c->sh_c.threads, a, s);
+    auto L = single_launch(poisson_args<double>(c, b, x, sw, c->part));
+    return coop_launch(k_cg<double, 1>, c->sh_c.blocks, c->sh_c.threads, L, s);
 }
 
 cudaError_t launch_mass_cg(cgp_ctx_s* c, const double* b, double* x, cudaStream_t s) {
     SyncWords* sw = c->sync + SYNC_MASS;
     cudaError_t e = cudaMemsetAsync(sw, 0, sizeof(SyncWords), s);
     if (e != cudaSuccess) return e;
-    const int n = c->nf;
-    char* p = (char*)c->ws;
-    CgArgs<double> a;
-    a.n = n; a.rp = c->F.rp; a.ci = c->F.ci; a.val64 = c->M; a.valI = c->M; a.dinvI = c->dinvM;
-    a.b = b; a.x = x;
-    a.r = carve<double>(p, 2 * (size_t)n); a.u = carve<double>(p, 2 * (size_t)n); a.w = carve<double>(p, 2 * (size_t)n);
-    a.p = carve<double>(p, 2 * (size_t)n); a.s = carve<double>(p, 2 * (size_t)n); a.d = carve<double>(p, 2 * (size_t)n);
-    a.part = c->part; a.sw = sw; a.rtol = c->prm.rtol; a.inner_rtol = 0.0;
-    a.max_iter = c->prm.max_iter; a.max_outer = c->prm.max_outer; a.lanes = c->sh_f.lanes;
-    a.st_iters = &c->stats->mass_iters; a.st_outer = &c->stats->mass_outer; a.st_status = &c->stats->mass_status;
-    a.st_rel = &c->stats->mass_rel; a.st_barrier = &c->stats->barrier_status;
-    return coop_launch((const void*)k_cg<double, 2>, c->sh_f.blocks, c->sh_f.threads, a, s);
+    auto L = single_launch(mass_args(c, b, x, sw, c->part));
+    return coop_launch(k_cg<double, 2>, c->sh_f.blocks, c->sh_f.threads, L, s);
 }
 
 cudaError_t launch_momentum_bicgstab(cgp_ctx_s* c, const double* u_in, double* x, cudaStream_t s) {
     SyncWords* sw = c->sync + SYNC_MOM;
     cudaError_t e = cudaMemsetAsync(sw, 0, sizeof(SyncWords), s);
     if (e != cudaSuccess) return e;
-    const bool mixed = c->prm.precision == CGP_MIXED;
-    const size_t n2 = 2 * (size_t)c->nf;
-    char* p = (char*)c->ws;
-    if (mixed) {
-        BicgArgs<float> a;
-        a.n = c->nf; a.rp = c->F.rp; a.ci = c->F.ci; a.val64 = c->A; a.valI = c->A32; a.dinvI = c->dinvA32;
-        a.mask = c->vel_mask; a.diag = c->F.diag; a.g = c->g; a.b = c->b_mom; a.x_in = u_in; a.x = x;
-        a.r = carve<float>(p, n2); a.rh = carve<float>(p, n2); a.p = carve<float>(p, n2);
-        a.v = carve<float>(p, n2); a.y = carve<float>(p, n2); a.s = carve<float>(p, n2);
-        a.z = carve<float>(p, n2); a.t = carve<float>(p, n2); a.d = carve<float>(p, n2);
-        a.part = c->part; a.sw = sw; a.rtol = c->prm.rtol; a.inner_rtol = c->prm.inner_rtol;
-        a.max_iter = c->prm.max_iter; a.max_outer = c->prm.max_outer; a.lanes = c->sh_f.lanes;
-        a.st_iters = &c->stats->mom_iters; a.st_outer = &c->stats->mom_outer; a.st_status = &c->stats->mom_status;
-        a.st_rel = &c->stats->mom_rel; a.st_barrier = &c->stats->barrier_status;
-        return coop_launch((const void*)k_bicgstab<float>, c->sh_f.blocks, c->sh_f.threads, a, s);
+    if (c->prm.precision == CGP_MIXED) {
+        auto L = single_launch(momentum_args<float>(c, u_in, x, sw, c->part));
+        return coop_launch(k_bicgstab<float>, c->sh_f.blocks, c->sh_f.threads, L, s);
     }
-    BicgArgs<double> a;
-    a.n = c->nf; a.rp = c->F.rp; a.ci = c->F.ci; a.val64 = c->A; a.valI = c->A; a.dinvI = c->dinvA;
-    a.mask = c->vel_mask; a.diag = c->F.diag; a.g = c->g; a.b = c->b_mom; a.x_in = u_in; a.x = x;
-    a.r = carve<double>(p, n2); a.rh = carve<double>(p, n2); a.p = carve<double>(p, n2);
-    a.v = carve<double>(p, n2); a.y = carve<double>(p, n2); a.s = carve<double>(p, n2);
-    a.z = carve<double>(p, n2); a.t = carve<double>(p, n2); a.d = carve<double>(p, n2);
-    a.part = c->part; a.sw = sw; a.rtol = c->prm.rtol; a.inner_rtol = 0.0;
-    a.max_iter = c->prm.max_iter; a.max_outer = c->prm.max_outer; a.lanes = c->sh_f.lanes;
-    a.st_iters = &c->stats->mom_iters; a.st_outer = &c->stats->mom_outer; a.st_status = &c->stats->mom_status;
-    a.st_rel = &c->stats->mom_rel; a.st_barrier = &c->stats->barrier_status;
-    return coop_launch((const void*)k_bicgstab<double>, c->sh_f.blocks, c->sh_f.threads, a, s);
+    auto L = single_launch(momentum_args<double>(c, u_in, x, sw, c->part));
+    return coop_launch(k_bicgstab<double>, c->sh_f.blocks, c->sh_f.threads, L, s);
+}
+
+// ---- batched solver stages: one cooperative launch per stage for all instances ----------------
+namespace {
+
+template <typename Args>
+cudaError_t upload_table(cgp_batch_s* b, const std::vector<Args>& tab, void** out) {
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(Args) * tab.size());
+    if (e != cudaSuccess) return e;
+    b->allocs.push_back(d);
+    *out = d;
+    return cudaMemcpy(d, tab.data(), sizeof(Args) * tab.size(), cudaMemcpyHostToDevice);
+}
+
+SyncWords* bsync(cgp_batch_s* b, int i, int slot) { return b->sync + (size_t)i * SYNC_COUNT + slot; }
+double* bpart(cgp_batch_s* b, int i) { return b->part + (size_t)i * 32 * b->max_group; }
+
+template <typename TI>
+cudaError_t build_typed(cgp_batch_s* b) {
+    std::vector<BicgArgs<TI>> mom(b->n);
+    std::vector<CgArgs<TI>> poi(b->n);
+    std::vector<CgArgs<double>> mass(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        cgp_ctx_s* c = b->ctx[i];
+        mom[i] = momentum_args<TI>(c, b->u[i], c->ut, bsync(b, i, SYNC_MOM), bpart(b, i));
+        poi[i] = poisson_args<TI>(c, c->bc, b->pc[i], bsync(b, i, SYNC_POI), bpart(b, i));
+        mass[i] = mass_args(c, c->grad, c->w, bsync(b, i, SYNC_MASS), bpart(b, i));
+    }
+    cudaError_t e = upload_table(b, mom, &b->tab_mom);
+    if (e == cudaSuccess) e = upload_table(b, poi, &b->tab_poi);
+    if (e == cudaSuccess) e = upload_table(b, mass, &b->tab_mass);
+    return e;
+}
+
+template <typename Args>
+Launch<Args> table_launch(const void* tab, const BatchMap& m) {
+    Launch<Args> L;
+    L.single = Args();
+    L.table = (const Args*)tab;
+    L.map = m;
+    return L;
+}
+
+}  // namespace
+
+cudaError_t batch_solvers_build(cgp_batch_s* b) {
+    return b->precision == CGP_MIXED ? build_typed<float>(b) : build_typed<double>(b);
+}
+
+cudaError_t batch_momentum_launch(cgp_batch_s* b, cudaStream_t s) {
+    if (b->precision == CGP_MIXED) {
+        auto L = table_launch<BicgArgs<float>>(b->tab_mom, b->map_f);
+        return coop_launch(k_bicgstab<float>, b->blocks_f, b->threads, L, s);
+    }
+    auto L = table_launch<BicgArgs<double>>(b->tab_mom, b->map_f);
+    return coop_launch(k_bicgstab<double>, b->blocks_f, b->threads, L, s);
+}
+
+cudaError_t batch_poisson_launch(cgp_batch_s* b, cudaStream_t s) {
+    if (b->precision == CGP_MIXED) {
+        auto L = table_launch<CgArgs<float>>(b->tab_poi, b->map_c);
+        return coop_launch(k_cg<float, 1>, b->blocks_c, b->threads, L, s);
+    }
+    auto L = table_launch<CgArgs<double>>(b->tab_poi, b->map_c);
+    return coop_launch(k_cg<double, 1>, b->blocks_c, b->threads, L, s);
+}
+
+cudaError_t batch_mass_launch(cgp_batch_s* b, cudaStream_t s) {
+    auto L = table_launch<CgArgs<double>>(b->tab_mass, b->map_f);
+    return coop_launch(k_cg<double, 2>, b->blocks_f, b->threads, L, s);
 }
 
 // Occupancy of the persistent kernels (blocks per SM at `threads`), the minimum over the family.
@@ -858,6 +363,7 @@ extern "C" int cgp_cg_solve_noalloc(int n, const int* rp_dev, const int* ci_dev,
     const int threads = 512;
     int blocks = (n + threads - 1) / threads;
     blocks = std::max(1, std::min(std::min(blocks, nd->num_sms), CGP_MAX_GRID));
-    cudaError_t e = coop_launch((const void*)k_cg<double, 1>, blocks, threads, a, s);
+    auto La = single_launch(a);
+    cudaError_t e = coop_launch(k_cg<double, 1>, blocks, threads, La, s);
     return e == cudaSuccess ? CGP_OK : CGP_ERR_CUDA;
 }

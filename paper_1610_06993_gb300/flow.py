@@ -72,3 +72,42 @@ class Flow:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Several ``Flow`` instances advanced together by ``cgp_batch_step`` / ``cgp_batch_run``.
+
+    The flows keep their own state tensors; the batch only records their pointers, so the flows
+    must outlive it."""
+
+    def __init__(self, flows):
+        self.flows = list(flows)
+        self.handle = L.cgp_batch_create([f.ctx for f in self.flows], [f.u for f in self.flows],
+                                         [f.pc for f in self.flows])
+        self.blocks, self.group_fine, self.group_coarse = L.cgp_batch_info(self.handle, len(self.flows))
+
+    def step(self, n: int = 1, stream=None) -> None:
+        for _ in range(n):
+            L.cgp_batch_step(self.handle, stream)
+        for f in self.flows:
+            f.t += n * f.problem.dt
+
+    def run(self, n: int, stream=None) -> None:
+        """``n`` steps by replaying the captured CUDA graph of one step."""
+        L.cgp_batch_run(self.handle, n, stream)
+        for f in self.flows:
+            f.t += n * f.problem.dt
+
+    def stats(self, check: bool = True):
+        return L.cgp_batch_get_stats(self.handle, len(self.flows), None, check=check)[0]
+
+    def close(self) -> None:
+        if self.handle:
+            L.cgp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,102 @@
+"""Batched multi-instance step: each instance of a batch must reach the same result as the same
+instance advanced alone (and the oracle), and a replayed CUDA graph of one step must reproduce
+the directly launched steps bit for bit."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import cgp_inputs as ci
+from oracle import cgp as ocgp
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1610_06993_gb300 import cgp
+    if not os.path.exists(cgp.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    cgp.load()
+    return cgp
+
+
+def small_batch():
+    return ci.batch_cavities(n_inst=5, seed=77, n_min=60, n_max=700, re_min=100.0, re_max=1000.0, dt=0.005)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_batch_matches_single_instances_and_oracle(L, precision):
+    from paper_1610_06993_gb300.flow import Batch, Flow
+    cases = small_batch()
+    flows = [Flow(m, p, rtol=1e-13, precision=precision) for m, p in cases]
+    b = Batch(flows)
+    assert b.blocks >= len(flows) and (b.group_fine >= 1).all() and (b.group_coarse >= 1).all()
+    steps = 6
+    b.step(steps)
+    stats = b.stats(check=True)
+    assert all(s.poisson_status == 0 for s in stats)
+    for (m, p), f in zip(cases, flows):
+        alone = Flow(m, p, rtol=1e-13, precision=precision)
+        alone.step(steps)
+        alone.stats(check=True)
+        e1 = rel(f.u.cpu().numpy(), alone.u.cpu().numpy())
+        e2 = rel(f.u.cpu().numpy(), ocgp.run(m, p, steps).u)
+        alone.close()
+        assert e1 < 1e-10 and e2 < 1e-10, (m.name, e1, e2)
+    b.close()
+    for f in flows:
+        f.close()
+
+
+def test_batch_graph_replay_is_bitwise(L):
+    from paper_1610_06993_gb300.flow import Batch, Flow
+    cases = small_batch()
+    res = []
+    for mode in ("step", "graph"):
+        flows = [Flow(m, p, rtol=1e-10) for m, p in cases]
+        b = Batch(flows)
+        if mode == "step":
+            b.step(4)
+        else:
+            b.run(1)
+            b.run(3)
+        b.stats(check=True)
+        res.append([f.u.cpu().numpy() for f in flows])
+        b.close()
+        for f in flows:
+            f.close()
+    for a, c in zip(*res):
+        assert np.array_equal(a, c)
+
+
+def test_batch_workload_full_size(L):
+    """The 64-cavity batch (coarse sizes log-uniform in [2k, 50k]) at the bench's launch shape:
+    two steps, every instance converged; the two smallest instances equal their lone runs."""
+    from paper_1610_06993_gb300.flow import Batch, Flow
+    cases = ci.batch_cavities()
+    sizes = [m.n_nodes for m, _ in cases]
+    assert min(sizes) >= 1900 and max(sizes) <= 51000
+    flows = [Flow(m, p, rtol=1e-10) for m, p in cases]
+    b = Batch(flows)
+    b.step(2)
+    stats = b.stats(check=True)
+    assert len(stats) == 64
+    for i in np.argsort(sizes)[:2]:
+        m, p = cases[i]
+        alone = Flow(m, p, rtol=1e-10)
+        alone.step(2)
+        e = rel(flows[i].u.cpu().numpy(), alone.u.cpu().numpy())
+        alone.close()
+        assert e < 1e-8, (i, e)
+    b.close()
+    for f in flows:
+        f.close()
