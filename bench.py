@@ -267,12 +267,120 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args):
+    """64 independent cavities (coarse sizes log-uniform in [2k, 50k], Re in [100, 1000], dt =
+    0.005, one refinement), advanced together by the batched step replayed as a CUDA graph.
+
+    value = aggregate instance-steps/s. Coarse-solve throughput is compared in the same run:
+    the plain path (FP64, zero initial guess, one instance after another through
+    cgp_poisson_solve) against the batched path (this run's precision, previous-step pressure as
+    the initial guess, one launch for all instances), on the same right-hand sides at rtol."""
+    import torch
+    from paper_1610_06993_gb300 import cgp as L
+    from paper_1610_06993_gb300.flow import Batch, Flow
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
+    cases = ci.batch_cavities()
+    prec = L.CGP_MIXED if args.precision == "mixed" else L.CGP_FP64
+    flows = [Flow(m, p, precision=prec, rtol=args.rtol, device=dev) for m, p in cases]
+    for f in flows:
+        L.cgp_autotune(f.ctx)                        # per-instance SpMV lanes (project autotuner)
+    b = Batch(flows)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    b.run(args.warmup, stream)
+    b.stats(check=True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run(1, stream)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    st = b.stats(check=True)
+    ms = statistics.mean(step_ms)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    n_inst = len(flows)
+
+    # coarse solves: batched, warm-started from the previous step's pressure
+    prev = [f.pc.clone() for f in flows]
+    prev_u = [f.u.clone() for f in flows]
+    b.run(1, stream)
+    for f, p in zip(flows, prev):
+        f.pc.copy_(p)
+    flush.fill_(1.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    L.cgp_batch_poisson_solve(b.handle, stream)
+    e1.record(stream)
+    e1.synchronize()
+    t_batch = e0.elapsed_time(e1)
+    it_batch = [s.poisson_iters for s in b.stats(check=True)]
+    # plain: FP64 contexts on the same right-hand sides, zero initial guess, one after another
+    t_plain, it_plain = 0.0, []
+    for f, u0, (m, p) in zip(flows, prev_u, cases):
+        g = Flow(m, p, precision=L.CGP_FP64, rtol=args.rtol, device=dev)
+        bc = torch.empty_like(f.pc)
+        ut = torch.empty_like(f.u)
+        # the right-hand side of the batched instance's latest step, rebuilt on the FP64 context
+        L.cgp_assemble(g.ctx, u0, stream)
+        L.cgp_momentum_solve(g.ctx, u0, ut, stream)
+        L.cgp_restrict(g.ctx, ut, bc, stream)
+        x = torch.zeros_like(f.pc)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        L.cgp_poisson_solve(g.ctx, bc, x, stream)
+        e1.record(stream)
+        e1.synchronize()
+        t_plain += e0.elapsed_time(e1)
+        it_plain.append(g.stats(check=True).poisson_iters)
+        g.close()
+
+    line = {
+        "metric": METRIC, "value": ws * n_inst * 1000.0 / ms, "unit": "instance-steps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == L.CGP_FP64 else "f32+f64-ir", "data": "synthetic",
+        "config": {"workload": "batch64: 64 lid-driven cavities, coarse nodes log-uniform in [2k, 50k] "
+                               f"(total {sum(f.info.n_coarse for f in flows)} coarse / "
+                               f"{sum(f.info.n_fine for f in flows)} fine), Re U[100,1000], dt=0.005, l=1",
+                   "rtol": args.rtol, "precision": args.precision, "graph": "one CUDA graph per step",
+                   "l2": "flushed between timed steps (512 MB write)", "blocks": b.blocks},
+        "coarse_solves_per_s": {"batched_warm": n_inst * 1000.0 / t_batch, "plain_fp64_zero_sequential":
+                                n_inst * 1000.0 / t_plain, "ratio": t_plain / t_batch,
+                                "iters_batched_mean": statistics.mean(it_batch),
+                                "iters_plain_mean": statistics.mean(it_plain)},
+        "gpu_launches": None, "clocks": clk.summary(),
+    }
+    b.close()
+    for f in flows:
+        f.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="bfs33", choices=["bfs33", "batch64"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--threads", type=int, default=0)
@@ -284,6 +392,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
     else:
         run_gpu(args)
 

@@ -173,7 +173,8 @@ int cgp_restrict(cgp_ctx ctx, const double* ut_dev, double* bc_dev, void* stream
 /* Step 3, Eq. 21: solve K_c p_c = b_c (K_c = coarse stiffness, +(-Laplacian), after symmetric
  * elimination of masked nodes) by Jacobi-preconditioned conjugate gradients in a single
  * persistent kernel (CGP_MIXED: FP32 CG inside FP64 iterative refinement). pc_dev [n_coarse] is
- * the initial guess on entry (warm start) and the solution on exit. */
+ * the initial guess on entry (warm start) and the solution on exit. bc_dev [n_coarse], or NULL
+ * for the context's own right-hand side of its latest cgp_step. */
 int cgp_poisson_solve(cgp_ctx ctx, const double* bc_dev, double* pc_dev, void* stream);
 
 /* Steps 4-5, Eqs. 22-23 with Eq. 29: p_f = P p_c level by level, g = G p_f (G_ij = int phi_i
@@ -216,6 +217,10 @@ int cgp_batch_step(cgp_batch b, void* stream);
 /* `steps` steps of every instance by replaying a CUDA graph of one step (captured on an internal
  * stream at the first call; make the first call outside any other stream capture). */
 int cgp_batch_run(cgp_batch b, int steps, void* stream);
+/* Only the coarse Poisson stage (Eq. 21) of every instance, one batched launch: instance i solves
+ * its context's last coarse right-hand side (from the latest step or cgp_restrict into the
+ * context) into pc_devs[i], which is also the initial guess. */
+int cgp_batch_poisson_solve(cgp_batch b, void* stream);
 /* Synchronise and read every instance's statistics into per_instance[n]; returns the first
  * non-OK status. */
 int cgp_batch_get_stats(cgp_batch b, void* stream, cgp_stats* per_instance);

@@ -83,6 +83,7 @@ _SIGNATURES = {
     "cgp_batch_step": (C.c_int, [_VP, _VP]),
     "cgp_batch_run": (C.c_int, [_VP, C.c_int, _VP]),
     "cgp_batch_get_stats": (C.c_int, [_VP, _VP, _VP]),
+    "cgp_batch_poisson_solve": (C.c_int, [_VP, _VP]),
     "cgp_batch_destroy": (C.c_int, [_VP]),
     "cgp_mesh_destroy": (C.c_int, [_VP]),
     "cgp_status_str": (C.c_char_p, [C.c_int]),
@@ -278,6 +279,10 @@ def cgp_batch_step(b: int, stream=None) -> None:
 
 def cgp_batch_run(b: int, steps: int, stream=None) -> None:
     _check(load().cgp_batch_run(b, int(steps), _stream(stream)), "cgp_batch_run")
+
+
+def cgp_batch_poisson_solve(b: int, stream=None) -> None:
+    _check(load().cgp_batch_poisson_solve(b, _stream(stream)), "cgp_batch_poisson_solve")
 
 
 def cgp_batch_get_stats(b: int, n: int, stream=None, check: bool = False):

@@ -328,9 +328,9 @@ int cgp_restrict(cgp_ctx c, const double* ut_dev, double* bc_dev, void* stream) 
 }
 
 int cgp_poisson_solve(cgp_ctx c, const double* bc_dev, double* pc_dev, void* stream) {
-    if (!c || !bc_dev || !pc_dev) return CGP_ERR_ARG;
+    if (!c || !pc_dev) return CGP_ERR_ARG;
     if (!c->bc_set) return CGP_ERR_STATE;
-    CK(launch_poisson_cg(c, bc_dev, pc_dev, (cudaStream_t)stream));
+    CK(launch_poisson_cg(c, bc_dev ? bc_dev : c->bc, pc_dev, (cudaStream_t)stream));
     return CGP_OK;
 }
 

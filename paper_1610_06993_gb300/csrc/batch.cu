@@ -195,6 +195,14 @@ int cgp_batch_run(cgp_batch b, int steps, void* stream) {
     return CGP_OK;
 }
 
+int cgp_batch_poisson_solve(cgp_batch b, void* stream) {
+    if (!b) return CGP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(b->sync, 0, sizeof(SyncWords) * (size_t)b->n * SYNC_COUNT, s);
+    if (e == cudaSuccess) e = batch_poisson_launch(b, s);
+    return e == cudaSuccess ? CGP_OK : CGP_ERR_CUDA;
+}
+
 int cgp_batch_get_stats(cgp_batch b, void* stream, cgp_stats* per_instance) {
     if (!b || !per_instance) return CGP_ERR_ARG;
     int first = CGP_OK;
