@@ -288,6 +288,23 @@ def batch_cavities(n_inst: int = 64, seed: int = 1003, n_min: int = 2000, n_max:
     return out
 
 
+def mlp_init_params(n: int, hidden: int, seed: int):
+    """Initial weights of the warm-start network n -> hidden -> hidden -> n (float32 arrays).
+
+    Uniform in +-0.5 sqrt(6 / fan_in) from SplitMix64 stream ``seed`` (W1, W2, W3 drawn in that
+    order, row-major [out, in]); biases zero. Returned as [W1, b1, W2, b2, W3, b3]."""
+    shapes = [(hidden, n), (hidden, hidden), (n, hidden)]
+    out, off = [], 0
+    for o, i in shapes:
+        cnt = o * i
+        u = uniform01(seed, np.arange(off, off + cnt, dtype=np.uint64))
+        off += cnt
+        bound = 0.5 * math.sqrt(6.0 / i)
+        out.append(((2.0 * u - 1.0) * bound).astype(np.float32).reshape(o, i))
+        out.append(np.zeros(o, dtype=np.float32))
+    return out
+
+
 # --------------------------------------------------------------------------------------
 # Named workloads
 # --------------------------------------------------------------------------------------

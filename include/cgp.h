@@ -227,6 +227,41 @@ int cgp_batch_get_stats(cgp_batch b, void* stream, cgp_stats* per_instance);
 /* Free the batch (not the contexts). NULL is accepted. */
 int cgp_batch_destroy(cgp_batch b);
 
+/* ---- learned warm start for the coarse solve (not in the paper) -----------------------------
+ * A BF16 network n -> H -> H -> n with GELU (tanh form) maps a coarse right-hand side b to an
+ * initial guess p = ||b|| NN(b / ||b||) for the Poisson solve of Eq. 21 (the solve is linear in b);
+ * PCG still runs to the same tolerance, so the network only changes the iteration count. Products
+ * run on tcgen05 tensor cores (BF16 operands, FP32 accumulation); training uses Adam on FP32
+ * master weights. Weights are row-major [out][in]. */
+typedef struct cgp_ws_s* cgp_ws;
+
+/* C[M][N] (float32, row-major) = A[M][K] * B[N][K]^T with A, B bfloat16 row-major device arrays
+ * (K contiguous, 16-byte aligned). Requires M % 128 == 0, N % 128 == 0, K % 64 == 0 (else
+ * CGP_ERR_ARG). Stream-ordered. The tensor-core product the network is built from. */
+int cgp_gemm_bf16(int M, int N, int K, const void* A_dev, const void* B_dev, float* C_dev, void* stream);
+/* Network for n unknowns, hidden width H (H % 128 == 0), up to batch_max right-hand sides per call. */
+int cgp_ws_create(int n, int hidden, int batch_max, cgp_ws* out);
+/* Host float32 weights: W1 [H][n], b1 [H], W2 [H][H], b2 [H], W3 [n][H], b3 [n]; resets Adam. */
+int cgp_ws_set_params(cgp_ws w, const float* W1, const float* b1, const float* W2, const float* b2, const float* W3,
+                      const float* b3);
+/* Copy the FP32 master weights out (host arrays of the same shapes; NULL skips one). Synchronous. */
+int cgp_ws_get_params(cgp_ws w, float* W1, float* b1, float* W2, float* b2, float* W3, float* b3);
+/* Gradients of the latest cgp_ws_train_step (same shapes as the weights). Synchronous. */
+int cgp_ws_get_grads(cgp_ws w, float* dW1, float* db1, float* dW2, float* db2, float* dW3, float* db3);
+/* held_host[n]: 1 for pressure-held entries (output forced to 0, excluded from the loss). */
+int cgp_ws_set_mask(cgp_ws w, const unsigned char* held_host);
+/* Inference: p_dev [B][n] float64 = ||b|| NN(b / ||b||) for b_dev [B][n] float64, B <= batch_max. */
+int cgp_ws_forward(cgp_ws w, const double* b_dev, int B, double* p_dev, void* stream);
+/* One training step on B pairs (b_dev, p_dev) [B][n] float64: loss L = 1/(B n_free) sum over
+ * unmasked entries of (NN(b/s) - p/s)^2, gradients by back-propagation, then Adam with step size
+ * lr (lr = 0: gradients only). loss_dev (device float, may be NULL) receives L. */
+int cgp_ws_train_step(cgp_ws w, const double* b_dev, const double* p_dev, int B, float lr, float* loss_dev,
+                      void* stream);
+/* Synchronise and return the network's device error word (CGP_ERR_TIMEOUT if a bounded
+ * tensor-core pipeline wait gave up), else CGP_OK. */
+int cgp_ws_status(cgp_ws w, void* stream);
+int cgp_ws_destroy(cgp_ws w);
+
 /* Time the SpMV lane counts {1, 2, 4, 8} on the fine and coarse matrices and keep the fastest
  * for the solver kernels (a project-written autotuner, not in the paper). Synchronous. */
 int cgp_autotune(cgp_ctx ctx, void* stream);

@@ -85,6 +85,16 @@ _SIGNATURES = {
     "cgp_batch_get_stats": (C.c_int, [_VP, _VP, _VP]),
     "cgp_batch_poisson_solve": (C.c_int, [_VP, _VP]),
     "cgp_batch_destroy": (C.c_int, [_VP]),
+    "cgp_gemm_bf16": (C.c_int, [C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP]),
+    "cgp_ws_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_VP)]),
+    "cgp_ws_set_params": (C.c_int, [_VP] + [_VP] * 6),
+    "cgp_ws_get_params": (C.c_int, [_VP] + [_VP] * 6),
+    "cgp_ws_get_grads": (C.c_int, [_VP] + [_VP] * 6),
+    "cgp_ws_set_mask": (C.c_int, [_VP, _VP]),
+    "cgp_ws_forward": (C.c_int, [_VP, _VP, C.c_int, _VP, _VP]),
+    "cgp_ws_train_step": (C.c_int, [_VP, _VP, _VP, C.c_int, C.c_float, _VP, _VP]),
+    "cgp_ws_status": (C.c_int, [_VP, _VP]),
+    "cgp_ws_destroy": (C.c_int, [_VP]),
     "cgp_mesh_destroy": (C.c_int, [_VP]),
     "cgp_status_str": (C.c_char_p, [C.c_int]),
 }
@@ -295,6 +305,65 @@ def cgp_batch_get_stats(b: int, n: int, stream=None, check: bool = False):
 
 def cgp_batch_destroy(b: int) -> None:
     _check(load().cgp_batch_destroy(b), "cgp_batch_destroy")
+
+
+def cgp_gemm_bf16(A_dev, B_dev, C_dev, stream=None) -> None:
+    """C[M,N] (float32) = A[M,K] B[N,K]^T for bfloat16 device tensors A, B."""
+    M, K = A_dev.shape
+    N = B_dev.shape[0]
+    _check(load().cgp_gemm_bf16(M, N, K, _ptr(A_dev), _ptr(B_dev), _ptr(C_dev), _stream(stream)), "cgp_gemm_bf16")
+
+
+def cgp_ws_create(n: int, hidden: int, batch_max: int) -> int:
+    h = _VP()
+    _check(load().cgp_ws_create(n, hidden, batch_max, C.byref(h)), "cgp_ws_create")
+    return h.value
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def cgp_ws_set_params(w: int, params) -> None:
+    arrs = [_f32(p) for p in params]
+    _check(load().cgp_ws_set_params(w, *[a.ctypes.data for a in arrs]), "cgp_ws_set_params")
+
+
+def _ws_read(fn, w: int, n: int, hidden: int):
+    out = [np.empty((hidden, n), np.float32), np.empty(hidden, np.float32), np.empty((hidden, hidden), np.float32),
+           np.empty(hidden, np.float32), np.empty((n, hidden), np.float32), np.empty(n, np.float32)]
+    _check(fn(w, *[a.ctypes.data for a in out]), "cgp_ws_read")
+    return out
+
+
+def cgp_ws_get_params(w: int, n: int, hidden: int):
+    return _ws_read(load().cgp_ws_get_params, w, n, hidden)
+
+
+def cgp_ws_get_grads(w: int, n: int, hidden: int):
+    return _ws_read(load().cgp_ws_get_grads, w, n, hidden)
+
+
+def cgp_ws_set_mask(w: int, held: np.ndarray) -> None:
+    m = np.ascontiguousarray(held, dtype=np.uint8)
+    _check(load().cgp_ws_set_mask(w, m.ctypes.data), "cgp_ws_set_mask")
+
+
+def cgp_ws_forward(w: int, b_dev, p_dev, stream=None) -> None:
+    _check(load().cgp_ws_forward(w, _ptr(b_dev), int(b_dev.shape[0]), _ptr(p_dev), _stream(stream)), "cgp_ws_forward")
+
+
+def cgp_ws_train_step(w: int, b_dev, p_dev, lr: float, loss_dev=None, stream=None) -> None:
+    _check(load().cgp_ws_train_step(w, _ptr(b_dev), _ptr(p_dev), int(b_dev.shape[0]), float(lr), _ptr(loss_dev),
+                                    _stream(stream)), "cgp_ws_train_step")
+
+
+def cgp_ws_status(w: int, stream=None) -> int:
+    return load().cgp_ws_status(w, _stream(stream))
+
+
+def cgp_ws_destroy(w: int) -> None:
+    _check(load().cgp_ws_destroy(w), "cgp_ws_destroy")
 
 
 def cgp_mesh_destroy(ctx: int) -> None:
