@@ -374,13 +374,62 @@ def run_batch(args):
         torch.distributed.destroy_process_group()
 
 
+def run_warmstart(args):
+    """Learned warm start on the 129x129-node cavity: (b_c, p_c) pairs logged from seeded runs
+    (Re uniform in [100, 1000], dt = 0.005) by the batched solver, an 80/20 split by run, training
+    by the tensor-core kernels, then a batch of 256 held-out right-hand sides solved to rtol from
+    zero, previous-step and network initial guesses (network inference time included)."""
+    import torch
+    from paper_1610_06993_gb300 import cgp as L, warmstart
+    from paper_1610_06993_gb300.flow import Flow
+
+    ws_, rank, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    mesh, _, _ = ci.workload("cavity129")
+    res = 100.0 + 900.0 * ci.uniform01(1004, np.arange(args.runs))
+    problems = [ci.cavity_problem(float(r), 0.005, 1) for r in res]
+    t0 = time.perf_counter()
+    B, P, Pp, run, held = warmstart.generate(mesh, problems, args.run_steps)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    test = run >= int(round(0.8 * args.runs))
+    n = B.shape[1]
+    w = L.cgp_ws_create(n, 512, 256)
+    L.cgp_ws_set_params(w, ci.mlp_init_params(n, 512, 4))
+    L.cgp_ws_set_mask(w, held)
+    t0 = time.perf_counter()
+    hist = warmstart.train(w, B[~test].contiguous(), P[~test].contiguous(), epochs=args.epochs, batch=256, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    idx = torch.nonzero(test).flatten()
+    idx = idx[torch.randperm(idx.numel(), generator=torch.Generator().manual_seed(5)).to(idx.device)[:256]]
+    f = Flow(mesh, problems[0], rtol=args.rtol)
+    out = warmstart.evaluate(f, w, B[idx].contiguous(), P[idx].contiguous(), Pp[idx].contiguous())
+    f.close()
+    L.cgp_ws_destroy(w)
+    line = {"metric": "coarse Poisson solves/s at rtol with zero / previous-step / learned warm starts",
+            "value": out["network"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": "bf16 network, f64 CG", "data": "synthetic",
+            "config": {"workload": f"cavity129 (16,641 coarse nodes), {args.runs} runs x {args.run_steps} steps, "
+                                   f"Re U[100,1000], network 16641-512-512-16641 GELU, batch 256, {args.epochs} epochs",
+                       "rtol": args.rtol},
+            "pairs": int(B.shape[0]), "gen_s": t_gen, "train_s": t_train, "loss_first_last": [hist[0], hist[-1]],
+            "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="bfs33", choices=["bfs33", "batch64"])
+    ap.add_argument("--workload", default="bfs33", choices=["bfs33", "batch64", "warmstart"])
+    ap.add_argument("--runs", type=int, default=100)
+    ap.add_argument("--run-steps", type=int, default=200)
+    ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--threads", type=int, default=0)
@@ -394,6 +443,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch64":
         run_batch(args)
+    elif args.workload == "warmstart":
+        run_warmstart(args)
     else:
         run_gpu(args)
 

@@ -190,6 +190,10 @@ int cgp_prolong_correct(cgp_ctx ctx, const double* pc_dev, const double* ut_dev,
  * [n_coarse] holds p_c^n on entry and p_c^{n+1} on exit. Stream-ordered, no host sync. */
 int cgp_step(cgp_ctx ctx, double* u_dev, double* pc_dev, void* stream);
 
+/* Copy the coarse right-hand side b_c of the context's latest cgp_step (or batched step) to
+ * bc_dev [n_coarse] (e.g. to log (b_c, p_c) pairs). Stream-ordered. */
+int cgp_copy_coarse_rhs(cgp_ctx ctx, double* bc_dev, void* stream);
+
 /* The same step on host buffers: copies u_host [n_fine][2] and pc_host [n_coarse] to the
  * context's device staging buffers, runs cgp_step, copies both back and synchronises the
  * stream. For best copy speed the host buffers should be page-locked. */

@@ -85,6 +85,7 @@ _SIGNATURES = {
     "cgp_batch_get_stats": (C.c_int, [_VP, _VP, _VP]),
     "cgp_batch_poisson_solve": (C.c_int, [_VP, _VP]),
     "cgp_batch_destroy": (C.c_int, [_VP]),
+    "cgp_copy_coarse_rhs": (C.c_int, [_VP, _VP, _VP]),
     "cgp_gemm_bf16": (C.c_int, [C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP]),
     "cgp_ws_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_VP)]),
     "cgp_ws_set_params": (C.c_int, [_VP] + [_VP] * 6),
@@ -305,6 +306,10 @@ def cgp_batch_get_stats(b: int, n: int, stream=None, check: bool = False):
 
 def cgp_batch_destroy(b: int) -> None:
     _check(load().cgp_batch_destroy(b), "cgp_batch_destroy")
+
+
+def cgp_copy_coarse_rhs(ctx: int, bc_dev, stream=None) -> None:
+    _check(load().cgp_copy_coarse_rhs(ctx, _ptr(bc_dev), _stream(stream)), "cgp_copy_coarse_rhs")
 
 
 def cgp_gemm_bf16(A_dev, B_dev, C_dev, stream=None) -> None:

@@ -362,6 +362,12 @@ int cgp_step(cgp_ctx c, double* u_dev, double* pc_dev, void* stream) {
     return CGP_OK;
 }
 
+int cgp_copy_coarse_rhs(cgp_ctx c, double* bc_dev, void* stream) {
+    if (!c || !bc_dev) return CGP_ERR_ARG;
+    CK(cudaMemcpyAsync(bc_dev, c->bc, sizeof(double) * (size_t)c->nc, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return CGP_OK;
+}
+
 int cgp_step_host(cgp_ctx c, double* u_host, double* pc_host, void* stream) {
     if (!c || !u_host || !pc_host) return CGP_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
