@@ -93,6 +93,7 @@ typedef struct {
 typedef struct {
     int n_fine, n_coarse, tris_fine, tris_coarse, nnz_fine, nnz_coarse, levels;
     int n_colours, grid_blocks, block_threads, spmv_lanes;
+    int coarse_kernel;   /* 0 generic classical CG, 1 on-chip classical CG, 2 on-chip pipelined CG */
 } cgp_info;
 
 /* Per-solve statistics of the most recent step (read back by cgp_get_stats, which synchronises

@@ -44,7 +44,7 @@ class cgp_mesh_desc(C.Structure):
 class cgp_info(C.Structure):
     _fields_ = [(k, C.c_int) for k in ("n_fine", "n_coarse", "tris_fine", "tris_coarse", "nnz_fine",
                                        "nnz_coarse", "levels", "n_colours", "grid_blocks",
-                                       "block_threads", "spmv_lanes")]
+                                       "block_threads", "spmv_lanes", "coarse_kernel")]
 
 
 class cgp_stats(C.Structure):

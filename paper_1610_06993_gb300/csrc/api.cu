@@ -276,6 +276,7 @@ int cgp_mesh_info(cgp_ctx c, cgp_info* info) {
     info->grid_blocks = c->sh_f.blocks;
     info->block_threads = c->sh_f.threads;
     info->spmv_lanes = c->sh_f.lanes;
+    info->coarse_kernel = c->use_pipe ? (c->onchip_pipelined ? 2 : 1) : 0;
     return CGP_OK;
 }
 
