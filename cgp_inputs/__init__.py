@@ -288,6 +288,134 @@ def batch_cavities(n_inst: int = 64, seed: int = 1003, n_min: int = 2000, n_max:
     return out
 
 
+def cylinder_mesh(h_min: float = 0.0297, seed: int = 1002, length: float = 30.0, height: float = 10.0,
+                  centre=(5.0, 5.0), radius: float = 0.5, grading: float = 5.0) -> CoarseMesh:
+    """Flow past a cylinder: [0,length]x[0,height] minus a disc, Poisson-disk points, Delaunay.
+
+    The target spacing is h(d) = h_min (1 + min(1, d / grading)) with d the distance to the
+    cylinder surface (twice as fine, four times as dense, near the cylinder). Boundary points are
+    placed on the rectangle and the circle at that spacing; interior points come from dart
+    throwing (Cook 1986): candidates drawn from SplitMix64 stream ``seed`` are accepted when no
+    accepted point lies closer than the local spacing. The points are Delaunay-triangulated
+    (scipy.spatial, Qhull), triangles inside the disc removed and all triangles made
+    counter-clockwise."""
+    from scipy.spatial import Delaunay
+
+    cx, cy = centre
+
+    def spacing(x, y):
+        d = np.sqrt((x - cx) ** 2 + (y - cy) ** 2) - radius
+        return h_min * (1.0 + np.minimum(1.0, np.maximum(d, 0.0) / grading))
+
+    pts = []
+    # rectangle edges, walked with the local spacing (corners included once)
+    for (x0, y0, x1, y1) in ((0, 0, length, 0), (length, 0, length, height), (length, height, 0, height),
+                             (0, height, 0, 0)):
+        t = 0.0
+        L = math.hypot(x1 - x0, y1 - y0)
+        while t < L - 1e-12:
+            x = x0 + (x1 - x0) * t / L
+            y = y0 + (y1 - y0) * t / L
+            pts.append((float(x), float(y)))
+            t += float(spacing(np.array(x), np.array(y)))
+    for (x, y) in list(pts):
+        pass
+    # snap the walked coordinates onto the exact edge lines
+    fixed = []
+    for (x, y) in pts:
+        if abs(y) < 1e-9:
+            y = 0.0
+        if abs(y - height) < 1e-9:
+            y = height
+        if abs(x) < 1e-9:
+            x = 0.0
+        if abs(x - length) < 1e-9:
+            x = length
+        fixed.append((x, y))
+    pts = fixed
+    nc = max(12, int(round(2.0 * math.pi * radius / h_min)))
+    for k in range(nc):
+        a = 2.0 * math.pi * k / nc
+        pts.append((cx + radius * math.cos(a), cy + radius * math.sin(a)))
+    # dart throwing on a background grid of cell h_min / sqrt(2) (at most one point per cell)
+    cell = h_min / math.sqrt(2.0)
+    gx, gy = int(math.ceil(length / cell)) + 1, int(math.ceil(height / cell)) + 1
+    grid = -np.ones((gy, gx), dtype=np.int64)
+    P = [np.array(p) for p in pts]
+    for i, (x, y) in enumerate(pts):
+        grid[min(gy - 1, int(y / cell)), min(gx - 1, int(x / cell))] = i
+    reach = int(math.ceil(2.0 * h_min / cell))
+    n_cand = int(6.0 * length * height / (h_min * h_min))
+    u = uniform01(seed, np.arange(2 * n_cand, dtype=np.uint64)).reshape(-1, 2)
+    cand = np.stack([u[:, 0] * length, u[:, 1] * height], axis=1)
+    r_c = spacing(cand[:, 0], cand[:, 1])
+    dc = np.sqrt((cand[:, 0] - cx) ** 2 + (cand[:, 1] - cy) ** 2)
+    margin_ok = (cand[:, 0] > 0.5 * r_c) & (cand[:, 0] < length - 0.5 * r_c) & (cand[:, 1] > 0.5 * r_c) & \
+        (cand[:, 1] < height - 0.5 * r_c) & (dc > radius + 0.5 * r_c)
+    for k in np.flatnonzero(margin_ok):
+        x, y = cand[k]
+        r = r_c[k]
+        i0, j0 = int(y / cell), int(x / cell)
+        ok = True
+        for i in range(max(0, i0 - reach), min(gy, i0 + reach + 1)):
+            row = grid[i]
+            for j in range(max(0, j0 - reach), min(gx, j0 + reach + 1)):
+                q = row[j]
+                if q >= 0:
+                    dx, dy = P[q][0] - x, P[q][1] - y
+                    if dx * dx + dy * dy < r * r:
+                        ok = False
+                        break
+            if not ok:
+                break
+        if ok and grid[i0, j0] < 0:
+            grid[i0, j0] = len(P)
+            P.append(np.array((x, y)))
+    xy = np.array(P, dtype=np.float64)
+    tri = Delaunay(xy).simplices.astype(np.int64)
+    c = xy[tri].mean(axis=1)
+    tri = tri[(c[:, 0] - cx) ** 2 + (c[:, 1] - cy) ** 2 > radius ** 2]
+    p = xy[tri]
+    area2 = (p[:, 1, 0] - p[:, 0, 0]) * (p[:, 2, 1] - p[:, 0, 1]) - (p[:, 2, 0] - p[:, 0, 0]) * (p[:, 1, 1] - p[:, 0, 1])
+    tri[area2 < 0] = tri[area2 < 0][:, [0, 2, 1]]
+    tri = tri[np.abs(area2) > 1e-14]
+    used = np.zeros(len(xy), dtype=bool)
+    used[tri.ravel()] = True
+    remap = -np.ones(len(xy), dtype=np.int64)
+    remap[used] = np.arange(int(used.sum()))
+    m = CoarseMesh(xy=np.ascontiguousarray(xy[used]), tri=np.ascontiguousarray(remap[tri].astype(np.int32)))
+    m.name = f"cylinder{m.n_nodes}"
+    return m
+
+
+def cylinder_problem(re: float = 100.0, dt: float = 0.002, levels: int = 2, length: float = 30.0,
+                     height: float = 10.0) -> Problem:
+    """Cylinder of diameter 1 in a channel (the paper's Sect. 3.3 set-up, shortened domain).
+
+    Inflow x = 0: (u, v) = (1, 0). Top and bottom: slip walls, v = 0 prescribed and u natural
+    (per-component masks). Cylinder: no-slip. Outflow x = length: natural, p = 0. Re = rho d u /
+    mu with d = u = rho = 1, so mu = 1/Re."""
+
+    def vel_bc(xy, onb, t):
+        x, y = xy[:, 0], xy[:, 1]
+        mask = np.zeros(xy.shape[0], dtype=np.uint8)
+        g = np.zeros((xy.shape[0], 2))
+        inflow = onb & (x == 0.0)
+        wall = onb & ~inflow & ((y == 0.0) | (y == height))
+        outflow = onb & (x == length) & ~wall
+        cyl = onb & ~inflow & ~wall & ~outflow
+        mask[inflow] = BC_U | BC_V
+        g[inflow, 0] = 1.0
+        mask[wall] = BC_V
+        mask[cyl] = BC_U | BC_V
+        return mask, g
+
+    def p_bc(xy, onb):
+        return (onb & (xy[:, 0] == length)).astype(np.uint8)
+
+    return Problem("cylinder", 1.0, 1.0 / re, dt, levels, vel_bc, p_bc, _zero_u0)
+
+
 def mlp_init_params(n: int, hidden: int, seed: int):
     """Initial weights of the warm-start network n -> hidden -> hidden -> n (float32 arrays).
 
@@ -316,12 +444,19 @@ def workload(name: str):
     ``bfs33``: backward-facing step, h=1/33 (65,308 coarse nodes), Re=400, dt=0.005, one
     refinement, 500 steps (seed 1001).
     ``cavity129``: 129x129-node cavity, Re=100, dt=0.005, one refinement (seed 1004).
+    ``cylinder``: cylinder in [0,30]x[0,10], ~64k graded Poisson-disk coarse nodes, two
+    refinements (~1M fine nodes), Re=100, dt=0.002, 2,000 steps (seed 1002).
+    ``cylinder_small``: the same geometry at h_min = 0.25 (988 coarse nodes).
     ``cavityN`` for other N: an N x N-node cavity (seed 1000), Re=100, dt=0.01.
     """
     if name == "cavity33":
         return cavity_mesh(33, 1000), cavity_problem(100.0, 0.01, 1), 100
     if name == "bfs33":
         return bfs_mesh(33, 1001), bfs_problem(400.0, 0.005, 1), 500
+    if name == "cylinder":
+        return cylinder_mesh(), cylinder_problem(100.0, 0.002, 2), 2000
+    if name == "cylinder_small":
+        return cylinder_mesh(h_min=0.25), cylinder_problem(100.0, 0.002, 2), 2000
     if name == "cavity129":
         return cavity_mesh(129, 1004), cavity_problem(100.0, 0.005, 1), 200
     if name.startswith("bfs"):
