@@ -77,6 +77,8 @@ typedef struct {
     int spmv_lanes;
     int block_threads;
     int coarse_solver;
+    int spmv_format;   /* stand-alone fine SpMV (cgp_spmv): 0 = CSR until cgp_autotune picks the faster of
+                          CSR and sliced ELL, 1 = sliced ELL, 2 = CSR */
 } cgp_params;
 
 /* A coarse mesh: n_nodes points xy_host[n][2] and n_tris counter-clockwise triangles
@@ -190,6 +192,11 @@ int cgp_prolong_correct(cgp_ctx ctx, const double* pc_dev, const double* ut_dev,
  * pc_dev), prolong-correct. u_dev [n_fine][2] holds u^n on entry and u^{n+1} on exit; pc_dev
  * [n_coarse] holds p_c^n on entry and p_c^{n+1} on exit. Stream-ordered, no host sync. */
 int cgp_step(cgp_ctx ctx, double* u_dev, double* pc_dev, void* stream);
+
+/* y = A0 x with A0 = rho M + dt mu K (the constant part of the momentum matrix of Eq. 19) on the
+ * fine mesh, for two interleaved right-hand sides: x_dev, y_dev [n_fine][2]. The SpMV kernel of
+ * the Krylov solvers as a stand-alone launch (lanes per row from cgp_autotune). Stream-ordered. */
+int cgp_spmv(cgp_ctx ctx, const double* x_dev, double* y_dev, void* stream);
 
 /* Copy the coarse right-hand side b_c of the context's latest cgp_step (or batched step) to
  * bc_dev [n_coarse] (e.g. to log (b_c, p_c) pairs). Stream-ordered. */

@@ -83,6 +83,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     if (!(P.rho > 0.0) || !(P.mu >= 0.0) || !(P.dt > 0.0) || !(P.rtol > 0.0)) return CGP_ERR_ARG;
     if (P.precision != CGP_FP64 && P.precision != CGP_MIXED) return CGP_ERR_ARG;
     if (P.coarse_solver < 0 || P.coarse_solver > 2) return CGP_ERR_ARG;
+    if (P.spmv_format < 0 || P.spmv_format > 2) return CGP_ERR_ARG;
     if (P.inner_rtol <= 0.0) P.inner_rtol = 1e-4;
     if (P.max_iter <= 0) P.max_iter = 20000;
     if (P.max_outer <= 0) P.max_outer = 30;
@@ -110,6 +111,17 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     std::vector<int> cif(H.coarse.nnz);
     for (int k = 0; k < H.coarse.nnz; ++k) cif[k] = H.su[H.coarse.ci[k]];
     TRY(upload(c, &c->cif_su, cif));
+    {
+        HostSell hs;
+        build_sell(H.fine, 32, 32, hs);
+        c->sell_nslices = hs.nslices;
+        c->sell_total = hs.ptr[hs.nslices];
+        TRY(upload(c, &c->sell_ptr, hs.ptr));
+        TRY(upload(c, &c->sell_col, hs.col));
+        TRY(upload(c, &c->sell_src, hs.src));
+        TRY(upload(c, &c->sell_perm, hs.perm));
+        TRY(dalloc(c, &c->sell_val, (size_t)c->sell_total));
+    }
     c->lv_n.clear();
     for (auto& L : H.lv) c->lv_n.push_back(L.n);
     for (int k = 0; k < P.levels; ++k) {
@@ -180,6 +192,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
         if ((e = launch_const_assembly(c->EF, c->M, Kf, c->Gxy, s)) != cudaSuccess) break;
         if ((e = launch_const_assembly(c->EC, nullptr, c->Kc_raw, c->Dc_xy, s)) != cudaSuccess) break;
         if ((e = launch_make_A0(c, Kf, s)) != cudaSuccess) break;
+        if ((e = sell_fill(c, c->A0, s)) != cudaSuccess) break;
         e = cudaStreamSynchronize(s);
     } while (0);
     cudaFree(Kf);
@@ -194,6 +207,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     c->width_c = 0;
     for (int i = 0; i < H.coarse.n; ++i) c->width_c = std::max(c->width_c, H.coarse.rp[i + 1] - H.coarse.rp[i]);
     CK(pipe_prepare(c));
+    c->spmv_sell = P.spmv_format == 1;
     return CGP_OK;
 }
 
@@ -363,6 +377,12 @@ int cgp_step(cgp_ctx c, double* u_dev, double* pc_dev, void* stream) {
     return CGP_OK;
 }
 
+int cgp_spmv(cgp_ctx c, const double* x_dev, double* y_dev, void* stream) {
+    if (!c || !x_dev || !y_dev) return CGP_ERR_ARG;
+    CK(launch_spmv_fine(c, x_dev, y_dev, (cudaStream_t)stream));
+    return CGP_OK;
+}
+
 int cgp_copy_coarse_rhs(cgp_ctx c, double* bc_dev, void* stream) {
     if (!c || !bc_dev) return CGP_ERR_ARG;
     CK(cudaMemcpyAsync(bc_dev, c->bc, sizeof(double) * (size_t)c->nc, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
@@ -424,6 +444,24 @@ int cgp_autotune(cgp_ctx c, void* stream) {
         }
         if (fine) c->sh_f.lanes = best_l;
         else c->sh_c.lanes = best_l;
+        if (fine) {
+            // the stand-alone fine SpMV: sliced ELL against the best CSR lane count
+            double* x = (double*)c->ws;
+            double* y = x + 2 * (size_t)c->nf + 64;
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            for (int w = 0; w < 3; ++w) CK(launch_spmv_sell(c, x, y, s));
+            CK(cudaEventRecord(e0, s));
+            for (int w = 0; w < 20; ++w) CK(launch_spmv_sell(c, x, y, s));
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (c->prm.spmv_format == 0) c->spmv_sell = t / 20 < best;
+        }
     }
     return CGP_OK;
 }

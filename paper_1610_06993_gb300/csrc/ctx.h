@@ -103,6 +103,12 @@ struct cgp_ctx_s {
     double* u_stage = nullptr;
     double* pc_stage = nullptr;
 
+    // sliced-ELL (SELL-32-256) copy of the fine pattern for the stand-alone SpMV
+    int sell_nslices = 0, sell_total = 0;
+    int *sell_ptr = nullptr, *sell_col = nullptr, *sell_src = nullptr, *sell_perm = nullptr;
+    double* sell_val = nullptr;  // A0 values in SELL slot order
+    bool spmv_sell = false;      // cgp_spmv uses the SELL kernel (cgp_autotune decides)
+
     cgp::Shape sh_f, sh_c;       // persistent shapes for fine and coarse problems
     int width_c = 0;             // longest coarse CSR row
     bool use_pipe = false;       // coarse Poisson on an on-chip CG kernel
@@ -156,6 +162,9 @@ cudaError_t launch_poisson_cg(cgp_ctx_s* c, const double* b, double* x, cudaStre
 cudaError_t launch_mass_cg(cgp_ctx_s* c, const double* b, double* x, cudaStream_t s);
 cudaError_t launch_momentum_bicgstab(cgp_ctx_s* c, const double* u_in, double* x, cudaStream_t s);
 cudaError_t time_spmv_lanes(cgp_ctx_s* c, bool fine, int lanes, cudaStream_t s, float* ms);
+cudaError_t launch_spmv_fine(cgp_ctx_s* c, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_spmv_sell(cgp_ctx_s* c, const double* x, double* y, cudaStream_t s);
+cudaError_t sell_fill(cgp_ctx_s* c, const double* csr_val, cudaStream_t s);
 
 // krylov_pipe.cu
 bool pipe_shape(int n, int width, int num_sms, size_t elem, int* blocks, int* threads, size_t* smem);

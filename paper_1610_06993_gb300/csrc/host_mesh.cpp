@@ -118,6 +118,53 @@ void boundary_flags(int n, const std::vector<int>& edges, const std::vector<int>
 
 }  // namespace
 
+void build_sell(const HostCsr& c, int C, int sigma, HostSell& out) {
+    out = HostSell();
+    out.C = C;
+    const int n = c.n;
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    for (int w0 = 0; w0 < n; w0 += sigma) {
+        const int w1 = std::min(n, w0 + sigma);
+        std::stable_sort(order.begin() + w0, order.begin() + w1, [&](int a, int b) {
+            return (c.rp[a + 1] - c.rp[a]) > (c.rp[b + 1] - c.rp[b]);
+        });
+    }
+    out.nslices = (n + C - 1) / C;
+    out.ptr.assign(out.nslices + 1, 0);
+    out.width.assign(out.nslices, 0);
+    out.perm.assign((size_t)out.nslices * C, -1);
+    for (int s = 0; s < out.nslices; ++s) {
+        int w = 0;
+        for (int l = 0; l < C; ++l) {
+            const int q = s * C + l;
+            if (q < n) {
+                out.perm[q] = order[q];
+                w = std::max(w, c.rp[order[q] + 1] - c.rp[order[q]]);
+            }
+        }
+        out.width[s] = w;
+        out.ptr[s + 1] = out.ptr[s] + w * C;
+    }
+    out.col.assign(out.ptr[out.nslices], 0);
+    out.src.assign(out.ptr[out.nslices], -1);
+    for (int s = 0; s < out.nslices; ++s) {
+        for (int l = 0; l < C; ++l) {
+            const int r = out.perm[s * C + l];
+            for (int k = 0; k < out.width[s]; ++k) {
+                const size_t p = (size_t)out.ptr[s] + (size_t)k * C + l;
+                if (r >= 0 && k < c.rp[r + 1] - c.rp[r]) {
+                    out.col[p] = c.ci[c.rp[r] + k];
+                    out.src[p] = c.rp[r] + k;
+                } else {
+                    out.col[p] = r >= 0 ? r : 0;
+                    out.src[p] = -1;
+                }
+            }
+        }
+    }
+}
+
 int build_host_mesh(const cgp_mesh_desc* d, int levels, HostMesh& out) {
     if (!d || !d->xy_host || !d->tri_host || d->n_nodes <= 2 || d->n_tris <= 0) return CGP_ERR_ARG;
     if (levels < 0 || levels > 4) return CGP_ERR_ARG;

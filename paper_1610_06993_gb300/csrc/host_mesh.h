@@ -33,6 +33,16 @@ struct HostMesh {
     std::vector<unsigned char> onb_f, onb_c; // on-boundary flags
 };
 
+// Sliced ELL (SELL-C-sigma) layout of a CSR pattern: rows sorted by decreasing length within
+// windows of `sigma` rows, cut into slices of C rows; slice s holds width[s] slots, slot k of
+// lane l at ptr[s] + k * C + l. src[p] is the CSR index of slot p (-1 for padding, whose column
+// is the row itself); perm[s * C + l] is the CSR row of lane l of slice s (-1 past the end).
+struct HostSell {
+    int C = 32, nslices = 0;
+    std::vector<int> ptr, width, col, src, perm;
+};
+void build_sell(const HostCsr& c, int C, int sigma, HostSell& out);
+
 // Build everything from a coarse mesh. Returns CGP_OK, CGP_ERR_ARG or CGP_ERR_MESH.
 int build_host_mesh(const cgp_mesh_desc* d, int levels, HostMesh& out);
 

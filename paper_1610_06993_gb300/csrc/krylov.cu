@@ -220,6 +220,60 @@ int persistent_blocks_per_sm(int threads) {
     return m;
 }
 
+namespace {
+
+__global__ void k_sell_fill(int total, const int* __restrict__ src, const double* __restrict__ csr_val, double* sell_val) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < total) sell_val[p] = src[p] >= 0 ? csr_val[src[p]] : 0.0;
+}
+
+// Sliced-ELL SpMV, two interleaved right-hand sides: one warp per 32-row slice, slot k of all 32
+// rows contiguous, so every value and column load of a warp is one coalesced 128/256-byte access.
+__global__ void __launch_bounds__(256) k_spmv_sell2(int nslices, const int* __restrict__ ptr, const int* __restrict__ col,
+                                                    const double* __restrict__ val, const int* __restrict__ perm,
+                                                    const double* __restrict__ x, double* __restrict__ y) {
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (s >= nslices) return;
+    const int base = ptr[s], w = (ptr[s + 1] - base) >> 5;
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+        const int p = base + (k << 5) + lane;
+        const int j = __ldg(col + p);
+        const double v = __ldg(val + p);
+        const double2 xv = __ldg(reinterpret_cast<const double2*>(x) + j);
+        a0 += v * xv.x;
+        a1 += v * xv.y;
+    }
+    const int r = perm[(s << 5) + lane];
+    if (r >= 0) reinterpret_cast<double2*>(y)[r] = make_double2(a0, a1);
+}
+
+}  // namespace
+
+cudaError_t sell_fill(cgp_ctx_s* c, const double* csr_val, cudaStream_t s) {
+    k_sell_fill<<<(c->sell_total + 255) / 256, 256, 0, s>>>(c->sell_total, c->sell_src, csr_val, c->sell_val);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_sell(cgp_ctx_s* c, const double* x, double* y, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = (int)(((long long)c->sell_nslices * 32 + threads - 1) / threads);
+    k_spmv_sell2<<<blocks, threads, 0, s>>>(c->sell_nslices, c->sell_ptr, c->sell_col, c->sell_val, c->sell_perm, x, y);
+    return cudaGetLastError();
+}
+
+// y = A0 x on the fine mesh for two interleaved right-hand sides (A0 = rho M + dt mu K): the
+// sliced-ELL kernel when the autotuner chose it, else one row group of sh_f.lanes lanes per row.
+cudaError_t launch_spmv_fine(cgp_ctx_s* c, const double* x, double* y, cudaStream_t s) {
+    if (c->spmv_sell) return launch_spmv_sell(c, x, y, s);
+    const int n = c->nf, threads = 256, lanes = c->sh_f.lanes;
+    const int rows_per_block = threads / lanes;
+    const int blocks = (n + rows_per_block - 1) / rows_per_block;
+    k_spmv_probe<2><<<blocks, threads, 0, s>>>(n, c->F.rp, c->F.ci, c->A0, x, y, lanes, rows_per_block);
+    return cudaGetLastError();
+}
+
 cudaError_t time_spmv_lanes(cgp_ctx_s* c, bool fine, int lanes, cudaStream_t s, float* ms) {
     const int n = fine ? c->nf : c->nc;
     const int threads = 256;

@@ -228,6 +228,19 @@ def test_autotuned_lanes_same_answer(L):
     assert e < 1e-10, e
 
 
+@pytest.mark.parametrize("fmt", [0, 1], ids=["csr", "sliced_ell"])
+def test_spmv_matches_oracle_operator(L, cavity_state, fmt):
+    """cgp_spmv applies A0 = rho M + dt mu K (Eqs. 16-19) to two right-hand sides."""
+    coarse, prob, orc, _ = cavity_state
+    f = flow(coarse, prob, spmv_format=fmt)
+    x = np.random.default_rng(3).standard_normal((f.info.n_fine, 2))
+    y = torch.empty(f.info.n_fine, 2, dtype=torch.float64, device="cuda")
+    L.cgp_spmv(f.ctx, dev(x), y)
+    A0 = prob.rho * orc.fine.M + prob.dt * prob.mu * orc.fine.K
+    assert rel(y.cpu().numpy(), A0 @ x) < 1e-14
+    f.close()
+
+
 @pytest.fixture(scope="module")
 def bfs_full():
     coarse, prob, _ = ci.workload("bfs33")
