@@ -233,7 +233,8 @@ def run_gpu(args):
     coarse, prob, _ = ci.workload(WORKLOAD)
     prec = L.CGP_MIXED if args.precision == "mixed" else L.CGP_FP64
     f = Flow(coarse, prob, precision=prec, rtol=args.rtol, device=f"cuda:{local}",
-             block_threads=args.threads, spmv_lanes=args.lanes)
+             block_threads=args.threads, spmv_lanes=args.lanes, coarse_solver=args.coarse_solver,
+             precond_degree=args.precond_degree, precond_ratio=args.precond_ratio)
     stream = torch.cuda.current_stream()
     flush = L2Flush(f"cuda:{local}")
     bc = torch.empty_like(f.pc)
@@ -313,7 +314,8 @@ def run_gpu(args):
 
     launches_per_step = 7 + f.info.levels
     tname = "double" if prec == L.CGP_FP64 else "float"
-    kname = {0: f"k_cg<{tname}, 1>", 1: f"k_pcg_onchip<{tname}>", 2: f"k_pcg_pipe<{tname}>"}[f.info.coarse_kernel]
+    kname = {0: f"k_cg<{tname}, 1>", 1: f"k_pcg_onchip<{tname}>", 2: f"k_pcg_pipe<{tname}>",
+             3: "k_pcg_schwarz<double, float>", 4: f"k_pcg_schwarz<{tname}, {tname}>"}[f.info.coarse_kernel]
     line = {
         "metric": METRIC, "value": ws * 1000.0 / ms, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -322,7 +324,8 @@ def run_gpu(args):
                                f"l=1, Re=400, dt=0.005", "rtol": args.rtol, "precision": args.precision,
                    "l2": "flushed between timed steps (512 MB write, then 256 MB read)", "parallelism": "replicas" if ws > 1 else "1gpu",
                    "block_threads": f.info.block_threads, "grid_blocks": f.info.grid_blocks,
-                   "spmv_lanes": f.info.spmv_lanes},
+                   "spmv_lanes": f.info.spmv_lanes, "coarse_kernel": kname,
+                   "precond_degree": args.precond_degree},
         "coarse_solves_per_s": 1000.0 / pms,
         "poisson_ms": pms, "poisson_iters": it, "poisson_outer": outer,
         "momentum_iters": statistics.mean(mom_iters), "mass_iters": statistics.mean(mass_iters),
@@ -514,6 +517,9 @@ def main():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--lanes", type=int, default=0)
+    ap.add_argument("--coarse-solver", type=int, default=0)
+    ap.add_argument("--precond-degree", type=int, default=0)
+    ap.add_argument("--precond-ratio", type=float, default=0.0)
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spmv", action="store_true")

@@ -62,10 +62,18 @@ typedef struct cgp_ctx_s* cgp_ctx;
  * Krylov iterations of one solve. max_outer: cap on refinement passes (0 = default 30).
  * spmv_lanes: lanes per CSR row in the SpMV inner loops (0 = let cgp_autotune()/default decide;
  * otherwise 1, 2, 4, 8, 16 or 32). block_threads: threads per block of the generic persistent
- * kernels (0 = default 512, else 256..1024). coarse_solver: 0 = automatic (the on-chip classical
- * CG kernel whenever the coarse matrix slice of a block fits in shared memory, else the generic
- * classical CG kernel), 1 = always the generic kernel, 2 = the on-chip pipelined CG kernel in
- * CGP_FP64 (CGP_MIXED falls back to the on-chip classical kernel). */
+ * kernels (0 = default 512, else 256..1024). coarse_solver: 0 = automatic (kernel 3 whenever the
+ * coarse matrix slice of a block fits in shared memory, else the generic kernel), 1 = the generic
+ * Jacobi-preconditioned classical CG kernel, 2 = the on-chip Jacobi-preconditioned pipelined CG
+ * kernel in CGP_FP64 (CGP_MIXED falls back to kernel 5), 3 = on-chip classical CG with a
+ * two-level additive Schwarz preconditioner applied in FP32 (one subdomain per block of a
+ * Hilbert-curve renumbering of the nodes; local solver: a Chebyshev polynomial of degree
+ * precond_degree in D^-1 A on the subdomain; coarse space: the constant and the two linear
+ * functions on every subdomain, Galerkin matrix inverted on the host), 4 = kernel 3 with the
+ * preconditioner in the iteration precision, 5 = the on-chip Jacobi-preconditioned classical CG
+ * kernel. Explicit choices 2..5 fall back to the generic kernel when the slice does not fit.
+ * precond_degree: 0 = default 6. precond_ratio: lambda_max / lambda_min of the Chebyshev
+ * interval (0 = default 30). */
 typedef struct {
     double rho, mu, dt;
     int levels;
@@ -79,6 +87,8 @@ typedef struct {
     int coarse_solver;
     int spmv_format;   /* stand-alone fine SpMV (cgp_spmv): 0 = CSR until cgp_autotune picks the faster of
                           CSR and sliced ELL, 1 = sliced ELL, 2 = CSR */
+    int precond_degree;
+    double precond_ratio;
 } cgp_params;
 
 /* A coarse mesh: n_nodes points xy_host[n][2] and n_tris counter-clockwise triangles
@@ -95,7 +105,9 @@ typedef struct {
 typedef struct {
     int n_fine, n_coarse, tris_fine, tris_coarse, nnz_fine, nnz_coarse, levels;
     int n_colours, grid_blocks, block_threads, spmv_lanes;
-    int coarse_kernel;   /* 0 generic classical CG, 1 on-chip classical CG, 2 on-chip pipelined CG */
+    int coarse_kernel;   /* 0 generic classical CG, 1 on-chip classical CG, 2 on-chip pipelined CG,
+                            3 on-chip two-level Schwarz CG, preconditioner in FP32,
+                            4 the same, preconditioner in the iteration precision */
 } cgp_info;
 
 /* Per-solve statistics of the most recent step (read back by cgp_get_stats, which synchronises

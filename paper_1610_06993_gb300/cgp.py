@@ -33,7 +33,8 @@ class cgp_params(C.Structure):
     _fields_ = [("rho", C.c_double), ("mu", C.c_double), ("dt", C.c_double), ("levels", C.c_int),
                 ("precision", C.c_int), ("rtol", C.c_double), ("inner_rtol", C.c_double),
                 ("max_iter", C.c_int), ("max_outer", C.c_int), ("spmv_lanes", C.c_int),
-                ("block_threads", C.c_int), ("coarse_solver", C.c_int), ("spmv_format", C.c_int)]
+                ("block_threads", C.c_int), ("coarse_solver", C.c_int), ("spmv_format", C.c_int),
+                ("precond_degree", C.c_int), ("precond_ratio", C.c_double)]
 
 
 class cgp_mesh_desc(C.Structure):

@@ -82,7 +82,8 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     cgp_params& P = c->prm;
     if (!(P.rho > 0.0) || !(P.mu >= 0.0) || !(P.dt > 0.0) || !(P.rtol > 0.0)) return CGP_ERR_ARG;
     if (P.precision != CGP_FP64 && P.precision != CGP_MIXED) return CGP_ERR_ARG;
-    if (P.coarse_solver < 0 || P.coarse_solver > 2) return CGP_ERR_ARG;
+    if (P.coarse_solver < 0 || P.coarse_solver > 5) return CGP_ERR_ARG;
+    if (P.precond_degree < 0 || P.precond_degree > 64 || P.precond_ratio < 0.0) return CGP_ERR_ARG;
     if (P.spmv_format < 0 || P.spmv_format > 2) return CGP_ERR_ARG;
     if (P.inner_rtol <= 0.0) P.inner_rtol = 1e-4;
     if (P.max_iter <= 0) P.max_iter = 20000;
@@ -201,7 +202,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     const int threads = P.block_threads;
     const int bps = persistent_blocks_per_sm(threads);
     if (bps <= 0) return CGP_ERR_CUDA;
-    const int lanes = P.spmv_lanes ? P.spmv_lanes : 4;
+    const int lanes = P.spmv_lanes ? P.spmv_lanes : 1;
     c->sh_f = make_shape(c->nf, threads, lanes, c->num_sms, bps);
     c->sh_c = make_shape(c->nc, threads, lanes, c->num_sms, bps);
     c->width_c = 0;
@@ -290,7 +291,8 @@ int cgp_mesh_info(cgp_ctx c, cgp_info* info) {
     info->grid_blocks = c->sh_f.blocks;
     info->block_threads = c->sh_f.threads;
     info->spmv_lanes = c->sh_f.lanes;
-    info->coarse_kernel = c->use_pipe ? (c->onchip_pipelined ? 2 : 1) : 0;
+    info->coarse_kernel = c->use_schwarz ? (c->schwarz_fp32 && c->prm.precision == CGP_FP64 ? 3 : 4)
+                                         : c->use_pipe ? (c->onchip_pipelined ? 2 : 1) : 0;
     return CGP_OK;
 }
 
@@ -310,6 +312,7 @@ int cgp_set_bc(cgp_ctx c, const unsigned char* vel_mask, const unsigned char* p_
     CK(cudaMemcpy(c->g, g, 2 * sizeof(double) * (size_t)c->nf, cudaMemcpyHostToDevice));
     CK(launch_apply_pressure_bc(c, 0));
     CK(cudaStreamSynchronize(0));
+    TRY(schwarz_values(c));
     c->bc_set = true;
     return CGP_OK;
 }

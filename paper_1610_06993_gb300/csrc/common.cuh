@@ -70,6 +70,46 @@ __device__ __forceinline__ bool grid_sync(SyncWords* sw, unsigned int nblocks, u
     return s_ok != 0;
 }
 
+// Split-phase form of grid_sync: grid_arrive publishes this block's arrival (after its earlier
+// writes), grid_wait completes the barrier. Work placed between the two overlaps the wait.
+__device__ __forceinline__ void grid_arrive(SyncWords* sw, unsigned int nblocks, unsigned int& epoch) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        epoch += 1;
+        if (nblocks > 1) {
+            __threadfence();
+            red_release_add_u32(&sw->count, 1u);
+        }
+    }
+}
+
+__device__ __forceinline__ bool grid_wait(SyncWords* sw, unsigned int nblocks, unsigned int epoch) {
+    __shared__ int s_okw;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (nblocks > 1) {
+            const unsigned int target = epoch * nblocks;
+            unsigned int spins = 0;
+            while (ld_acquire_u32(&sw->count) < target) {
+                if (ld_relaxed_i32(&sw->err) != 0) { ok = 0; break; }
+                if (++spins > CGP_BARRIER_SPIN_LIMIT) {
+                    atomicCAS(&sw->err, 0, CGP_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                if (spins > 256) __nanosleep(64);
+            }
+            __threadfence();
+        } else {
+            ok = ld_relaxed_i32(&sw->err) == 0;
+        }
+        s_okw = ok;
+    }
+    __syncthreads();
+    return s_okw != 0;
+}
+
 // Called by a block that leaves a persistent kernel because a barrier failed: thread 0 copies
 // the launch's error code into the context's sticky barrier status.
 __device__ __forceinline__ void record_failure(SyncWords* sw, int* status) {

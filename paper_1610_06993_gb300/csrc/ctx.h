@@ -115,6 +115,21 @@ struct cgp_ctx_s {
     bool onchip_pipelined = false;   // ... in its pipelined form (else classical)
     cgp::Shape pipe_c;           // its launch shape
     size_t pipe_smem64 = 0, pipe_smem32 = 0;
+
+    // two-level Schwarz preconditioned coarse CG (coarse_solver 3 and 4)
+    bool use_schwarz = false;
+    bool schwarz_fp32 = false;   // preconditioner applied in FP32
+    int sz_degree = 0;
+    double sz_ratio = 0.0, sz_lmin = 0.0, sz_lmax = 0.0;
+    int *sz_perm = nullptr, *sz_rp = nullptr, *sz_ci = nullptr;
+    double *sz_val64 = nullptr, *sz_dinv64 = nullptr, *sz_ainv64 = nullptr;
+    float *sz_val32 = nullptr, *sz_dinv32 = nullptr, *sz_ainv32 = nullptr;
+    double* sz_fxy64 = nullptr;  // [n][2] linear coarse functions, renumbered
+    float* sz_fxy32 = nullptr;
+    std::vector<int> sz_src;     // renumbered CSR entry -> caller CSR entry
+    std::vector<int> sz_rp_h, sz_ci_h;
+    std::vector<double> sz_fxy_h;
+    size_t sz_smem = 0;
     std::vector<void*> allocs;   // everything to free
 };
 
@@ -170,6 +185,7 @@ cudaError_t sell_fill(cgp_ctx_s* c, const double* csr_val, cudaStream_t s);
 bool pipe_shape(int n, int width, int num_sms, size_t elem, int* blocks, int* threads, size_t* smem);
 cudaError_t pipe_prepare(cgp_ctx_s* c);
 cudaError_t launch_poisson_pipe(cgp_ctx_s* c, const double* b, double* x, cudaStream_t s);
+int schwarz_values(cgp_ctx_s* c);
 
 // mapping.cu
 cudaError_t launch_restrict_rhs(cgp_ctx_s* c, const double* ut, double* bc, cudaStream_t s);

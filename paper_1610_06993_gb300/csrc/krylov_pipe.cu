@@ -14,6 +14,9 @@
 // larger gap between recursive and true residual than classical CG; the FP64 refinement loop
 // around it (true residual r = b - A x, inner solve of A d = r, x += d) removes that gap.
 #include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <vector>
 
 #include "ctx.h"
 
@@ -399,6 +402,296 @@ __global__ void __launch_bounds__(512) k_pcg_onchip(PipeArgs<TI> a) {
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Two-level additive Schwarz preconditioned CG, on chip
+// ---------------------------------------------------------------------------------------------
+// The system is renumbered along a Hilbert curve of the node coordinates so that the contiguous
+// row slice of each block is a compact patch (a subdomain). The preconditioner is
+//     M^-1 r = sum_a R_a^T q(D_a^-1 A_aa) D_a^-1 R_a r  +  R_0^T A_0^-1 R_0 r
+// with q the fixed-degree Chebyshev polynomial for the spectrum bounds [lmin, lmax] of D^-1 A
+// (Saad, "Iterative Methods for Sparse Linear Systems", Sect. 12.3, Chebyshev acceleration),
+// applied to the block's own rows in shared memory, and a coarse space of three functions per
+// subdomain a, its restrictions of 1, (x - xbar_a) / H_a and (y - ybar_a) / H_a (centroid xbar_a,
+// ybar_a and RMS radius H_a of the subdomain's nodes): R_0 r holds the three moments of r over
+// every subdomain and A_0 = R_0 A R_0^T is the Galerkin matrix, inverted once on the host. The
+// linear functions capture the smooth error that a constant per subdomain leaves to the local
+// solves, which roughly halves the iteration count again. lmax bounds the spectrum of every D_a^-1 A_aa from
+// above (Cauchy interlacing), which keeps q positive on it, so both parts are symmetric positive
+// definite and M^-1 is a valid CG preconditioner. The local solve overlaps the grid barrier that
+// gathers R_0 r. TI is the precision of the CG iteration, TP that of the preconditioner; with
+// TP = float inside FP64 iterations the preconditioner is a slightly inexact fixed operator,
+// which slows CG a little but leaves its recursive residual exact (it is built from A p alone).
+template <typename TI, typename TP>
+struct SchwarzArgs {
+    int n, rows_per_block, width, degree;
+    const int* perm;        // [n] renumbered row -> caller row
+    const int* rp;          // renumbered CSR
+    const int* ci;
+    const double* val64;
+    const TI* valI;
+    const TP* valP;
+    const TP* dinvP;        // [n] renumbered inverse diagonal
+    const TP* fxy;          // [n][2] renumbered values of the two linear coarse functions
+    const TP* ainv;         // [3 nb][3 nb] inverse of the coarse Galerkin matrix
+    double lmin, lmax;
+    const double* b;        // [n] caller numbering
+    double* x;              // [n] caller numbering
+    double* xp;             // [n] published x, renumbered
+    TI* ubuf;               // [n] published u, renumbered
+    double* part;
+    SyncWords* sw;
+    double rtol, inner_rtol;
+    int max_iter, max_outer;
+    int* st_iters;
+    int* st_outer;
+    int* st_status;
+    double* st_rel;
+    int* st_barrier;
+};
+
+#define SZ_NC 3   // coarse functions per subdomain
+
+enum { PS_P0 = 0, PS_O1 = 1 /* 2 slots */, PS_I0 = 3, PS_R = 4 /* SZ_NC slots */, PS_I = 4 + SZ_NC /* 2 x 3 */ };
+
+// Dynamic shared memory of k_pcg_schwarz: ELL slice (values in TI, columns, values in TP when TP
+// differs), two Chebyshev buffers, the block's SZ_NC rows of A_0^-1 and the gathered R_0 r.
+size_t schwarz_smem(int width, int T, int nb, size_t sti, size_t stp) {
+    const size_t wt = (size_t)width * T;
+    const size_t ncs = (size_t)SZ_NC * nb;
+    return wt * (sti + sizeof(int)) + (sti != stp ? wt * stp : 0) + 2 * (size_t)T * stp + (SZ_NC + 1) * ncs * stp;
+}
+
+template <typename TI, typename TP>
+__global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_red[32 * 4];
+    __shared__ TI s_redT[32 * 4];
+    __shared__ double s_bc[4];
+    __shared__ TI s_ctl[2];
+    __shared__ int s_flag;
+    __shared__ TP s_y[SZ_NC];
+    const int T = blockDim.x, t = threadIdx.x;
+    const unsigned int nb = gridDim.x;
+    unsigned int epoch = 0;
+    const int r0 = min(a.n, (int)blockIdx.x * a.rows_per_block);
+    const int r1 = min(a.n, r0 + a.rows_per_block);
+    const int row = r0 + t;
+    const bool own = row < r1;
+    const size_t wt = (size_t)a.width * T;
+    TI* s_val = reinterpret_cast<TI*>(smem);
+    int* s_ci = reinterpret_cast<int*>(smem + sizeof(TI) * wt);
+    unsigned char* q = smem + (sizeof(TI) + sizeof(int)) * wt;
+    TP* s_pv = reinterpret_cast<TP*>(s_val);
+    if (sizeof(TP) != sizeof(TI)) {
+        s_pv = reinterpret_cast<TP*>(q);
+        q += sizeof(TP) * wt;
+    }
+    TP* s_z = reinterpret_cast<TP*>(q);
+    const unsigned int ncs = SZ_NC * nb;
+    TP* s_ainv = s_z + 2 * T;             // [SZ_NC][ncs]
+    TP* s_rc = s_ainv + SZ_NC * ncs;      // [ncs]
+    {
+        int k0 = 0, len = 0;
+        if (own) {
+            k0 = a.rp[row];
+            len = a.rp[row + 1] - k0;
+        }
+        for (int k = 0; k < a.width; ++k) {
+            const bool in = own && k < len;
+            s_ci[k * T + t] = in ? a.ci[k0 + k] : -1;
+            s_val[k * T + t] = in ? a.valI[k0 + k] : (TI)0;
+            if (sizeof(TP) != sizeof(TI)) s_pv[k * T + t] = in ? a.valP[k0 + k] : (TP)0;
+        }
+        for (unsigned int j = t; j < SZ_NC * ncs; j += T) {
+            const unsigned int k = j / ncs, col = j - k * ncs;
+            s_ainv[j] = a.ainv[(size_t)(k * nb + blockIdx.x) * ncs + col];
+        }
+    }
+    const int crow = own ? a.perm[row] : 0;
+    const double bi = own ? a.b[crow] : 0.0;
+    double xi = own ? a.x[crow] : 0.0;
+    const TP di = own ? a.dinvP[row] : (TP)0;
+    const TP fx = own ? a.fxy[2 * row] : (TP)0, fy = own ? a.fxy[2 * row + 1] : (TP)0;
+    const TP theta = (TP)(0.5 * (a.lmax + a.lmin)), delta = (TP)(0.5 * (a.lmax - a.lmin));
+    const TP sigma = theta / delta;
+    __syncthreads();
+
+    // u = M^-1 r on the block's rows; every thread of every block calls it the same number of
+    // times. False if the grid barrier inside failed.
+    auto precondition = [&](TI rI, TI& u) -> bool {
+        {
+            double v[SZ_NC] = {(double)rI, (double)(fx * (TP)rI), (double)(fy * (TP)rI)};
+            block_partials<SZ_NC>(v, a.part + PS_R * nb, nb, s_red);
+        }
+        grid_arrive(a.sw, nb, epoch);
+        // local part: Chebyshev iteration on A_aa z = r from z = 0, s_z double buffered
+        const TP r = (TP)rI;
+        TP rho = (TP)1 / sigma;
+        TP d = di * r / theta;
+        TP z = d;
+        for (int j = 1; j < a.degree; ++j) {
+            TP* zb = s_z + (j & 1) * T;
+            zb[t] = z;
+            __syncthreads();
+            TP az = (TP)0;
+#pragma unroll
+            for (int k = 0; k < PIPE_WMAX; ++k) {
+                if (k < a.width) {
+                    const int c = s_ci[k * T + t];
+                    if (c >= r0 && c < r1) az += s_pv[k * T + t] * zb[c - r0];
+                }
+            }
+            const TP rn = (TP)1 / ((TP)2 * sigma - rho);
+            d = rn * rho * d + ((TP)2 * rn / delta) * di * (r - az);
+            z += d;
+            rho = rn;
+        }
+        if (!grid_wait(a.sw, nb, epoch)) return false;
+        // coarse part: y = the block's SZ_NC entries of A_0^-1 R_0 r, one warp per entry
+        for (unsigned int j = t; j < ncs; j += T) s_rc[j] = (TP)__ldcg(a.part + PS_R * nb + j);
+        __syncthreads();
+        {
+            const int warp = t >> 5, lane = t & 31;
+            if (warp < SZ_NC) {
+                const TP* arow = s_ainv + warp * ncs;
+                TP acc = (TP)0;
+                for (unsigned int j = lane; j < ncs; j += 32) acc += arow[j] * s_rc[j];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) s_y[warp] = acc;
+            }
+        }
+        __syncthreads();
+        u = own ? (TI)(z + s_y[0] + fx * s_y[1] + fy * s_y[2]) : (TI)0;
+        return true;
+    };
+
+    double bb;
+    {
+        double v[1] = {bi * bi}, tt[1];
+        block_partials<1>(v, a.part + PS_P0 * nb, nb, s_red);
+        if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
+        grid_totals<1>(a.part + PS_P0 * nb, nb, tt, s_bc);
+        bb = tt[0];
+    }
+    if (bb == 0.0) xi = 0.0;
+    const double rtol2 = a.rtol * a.rtol, itol2 = a.inner_rtol * a.inner_rtol, floor2 = 0.25 * rtol2;
+    int iters = 0, outer = 0, status = CGP_OK;
+    double rr64 = 0.0;
+    for (;;) {
+        // ---- refinement pass: publish x, FP64 true residual, u = M^-1 r
+        if (own) a.xp[row] = xi;
+        if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
+        TI r, u;
+        double r64;
+        {
+            double ax = 0.0;
+            if (own)
+                for (int k = a.rp[row]; k < a.rp[row + 1]; ++k) ax += a.val64[k] * a.xp[a.ci[k]];
+            r64 = own ? bi - ax : 0.0;
+            r = (TI)r64;
+        }
+        if (!precondition(r, u)) return record_failure(a.sw, a.st_barrier);
+        double gam;
+        {
+            if (own) a.ubuf[row] = u;
+            double v[2] = {r64 * r64, (double)(r * u)}, tt[2];
+            block_partials<2>(v, a.part + PS_O1 * nb, nb, s_red);
+            if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
+            grid_totals<2>(a.part + PS_O1 * nb, nb, tt, s_bc);
+            rr64 = tt[0];
+            gam = tt[1];
+        }
+        if (bad(rr64) || bad(gam)) { status = CGP_ERR_NAN; break; }
+        if (bb == 0.0 || rr64 <= rtol2 * bb) break;
+        if (outer >= a.max_outer || iters >= a.max_iter) { status = CGP_ERR_NOT_CONVERGED; break; }
+        const double tgt = fmax(itol2 * rr64, floor2 * bb);
+        // ---- w = A u, delta = (w, u)
+        TI w = own ? ell_row<TI, TI>(s_ci, s_val, T, t, a.width, a.ubuf) : (TI)0;
+        double alpha;
+        {
+            double v[1] = {(double)(w * u)}, tt[1];
+            block_partials<1>(v, a.part + PS_I0 * nb, nb, s_red);
+            if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
+            grid_totals<1>(a.part + PS_I0 * nb, nb, tt, s_bc);
+            if (bad(tt[0])) { status = CGP_ERR_NAN; break; }
+            alpha = tt[0] != 0.0 ? gam / tt[0] : 0.0;
+        }
+        TI d = (TI)0, p = (TI)0, s = (TI)0;
+        TI A = (TI)alpha, B = (TI)0;
+        double beta = 0.0;
+        int par = 0;
+        bool first = true, nan = false, fail = false;
+        // every thread leaves this loop on the same broadcast flag (or the same initial alpha)
+        while (alpha != 0.0 || !first) {
+            p = first ? u : u + B * p;
+            s = first ? w : w + B * s;
+            d += A * p;
+            r -= A * s;
+            if (!precondition(r, u)) { fail = true; break; }
+            if (own) a.ubuf[row] = u;
+            const int base = PS_I + 3 * par;
+            {
+                const TI v[2] = {r * u, r * r};
+                block_partials_t<2, TI>(v, a.part + base * nb, nb, s_redT);
+            }
+            if (!grid_sync(a.sw, nb, epoch)) { fail = true; break; }
+            w = own ? ell_row<TI, TI>(s_ci, s_val, T, t, a.width, a.ubuf) : (TI)0;
+            {
+                const TI v[1] = {w * u};
+                block_partials_t<1, TI>(v, a.part + (base + 2) * nb, nb, s_redT);
+            }
+            if (!grid_sync(a.sw, nb, epoch)) { fail = true; break; }
+            {
+                const int slot[3] = {base, base + 1, base + 2};
+                grid_totals_shared<3>(a.part, slot, nb, s_bc);
+            }
+            iters += 1;
+            first = false;
+            par ^= 1;
+            if (t == 0) {
+                const double gnew = s_bc[0], rho = s_bc[1], del = s_bc[2];
+                int flag = 0;
+                if (bad(gnew) || bad(rho) || bad(del)) {
+                    flag = 2;
+                } else if (rho <= tgt || iters >= a.max_iter || gam == 0.0) {
+                    flag = 1;
+                } else {
+                    const double bnew = gnew / gam;
+                    const double den = del - bnew * gnew / alpha;
+                    if (den == 0.0 || gnew == 0.0) {
+                        flag = 1;
+                    } else {
+                        beta = bnew;
+                        alpha = gnew / den;
+                        gam = gnew;
+                    }
+                }
+                s_ctl[0] = (TI)alpha;
+                s_ctl[1] = (TI)beta;
+                s_flag = flag;
+            }
+            __syncthreads();
+            const int flag = s_flag;
+            A = s_ctl[0];
+            B = s_ctl[1];
+            if (flag == 2) { nan = true; break; }
+            if (flag == 1) break;
+        }
+        if (fail) return record_failure(a.sw, a.st_barrier);
+        if (nan) { status = CGP_ERR_NAN; break; }
+        xi += (double)d;
+        outer += 1;
+    }
+    if (own) a.x[crow] = xi;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *a.st_iters = iters;
+        *a.st_outer = outer;
+        *a.st_status = status;
+        *a.st_rel = bb > 0.0 ? sqrt(rr64 / bb) : 0.0;
+    }
+}
+
 }  // namespace
 
 // Shape of the on-chip Poisson kernel for n rows of maximal length `width`; false if it does
@@ -455,14 +748,180 @@ static cudaError_t launch_pipe_t(cgp_ctx_s* c, const double* b, double* x, cudaS
     return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(threads), kargs, smem, s);
 }
 
-// Decide whether the coarse Poisson solve runs on the on-chip kernel and raise its dynamic
+namespace {
+
+template <typename T>
+cudaError_t sz_alloc(cgp_ctx_s* c, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    c->allocs.push_back(q);
+    *p = (T*)q;
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t sz_upload(T* dst, const std::vector<T>& v) {
+    return cudaMemcpy(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Position of the cell (x, y), 0 <= x, y < 2^bits, along the Hilbert curve. At each scale the
+// quadrant of the point gives two digits of the position; the remaining low bits are then
+// reflected and transposed into the orientation of that quadrant's sub-curve (complementing all
+// bits reflects the low bits, which are the only ones read afterwards).
+uint64_t hilbert_index(uint32_t x, uint32_t y, int bits) {
+    uint64_t d = 0;
+    for (int k = bits - 1; k >= 0; --k) {
+        const uint32_t s = 1u << k;
+        const uint32_t rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
+        d += (uint64_t)s * s * ((3u * rx) ^ ry);
+        if (ry == 0) {
+            if (rx == 1) {
+                x = ~x;
+                y = ~y;
+            }
+            std::swap(x, y);
+        }
+    }
+    return d;
+}
+
+// Renumbering of the coarse nodes along a Hilbert curve of their coordinates (one scale for
+// both axes, so a subdomain is compact in physical space), the renumbered CSR pattern and the
+// device buffers of the Schwarz solver.
+cudaError_t schwarz_structure(cgp_ctx_s* c) {
+    const HostCsr& H = c->hm.coarse;
+    const std::vector<double>& xy = c->hm.lv[0].xy;
+    const int n = c->nc, nb = c->pipe_c.blocks;
+    double x0 = xy[0], x1 = xy[0], y0 = xy[1], y1 = xy[1];
+    for (int i = 0; i < n; ++i) {
+        x0 = std::min(x0, xy[2 * i]);
+        x1 = std::max(x1, xy[2 * i]);
+        y0 = std::min(y0, xy[2 * i + 1]);
+        y1 = std::max(y1, xy[2 * i + 1]);
+    }
+    const double ext = std::max(x1 - x0, y1 - y0);
+    const double sc = ext > 0.0 ? 65535.0 / ext : 0.0;
+    std::vector<uint64_t> key(n);
+    for (int i = 0; i < n; ++i) {
+        const uint32_t hx = (uint32_t)std::min(65535.0, std::max(0.0, (xy[2 * i] - x0) * sc));
+        const uint32_t hy = (uint32_t)std::min(65535.0, std::max(0.0, (xy[2 * i + 1] - y0) * sc));
+        key[i] = hilbert_index(hx, hy, 16);
+    }
+    std::vector<int> perm(n), iperm(n);
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    std::stable_sort(perm.begin(), perm.end(), [&](int p, int q) { return key[p] < key[q]; });
+    for (int i = 0; i < n; ++i) iperm[perm[i]] = i;
+    c->sz_rp_h.assign(1, 0);
+    c->sz_ci_h.clear();
+    c->sz_src.clear();
+    for (int i = 0; i < n; ++i) {
+        const int o = perm[i];
+        for (int k = H.rp[o]; k < H.rp[o + 1]; ++k) {
+            c->sz_ci_h.push_back(iperm[H.ci[k]]);
+            c->sz_src.push_back(k);
+        }
+        c->sz_rp_h.push_back((int)c->sz_ci_h.size());
+    }
+    const size_t nnz = c->sz_ci_h.size();
+    // linear coarse functions (x - xbar_a) / H_a, (y - ybar_a) / H_a of each subdomain a
+    const int rpb = (n + nb - 1) / nb;
+    c->sz_fxy_h.assign(2 * (size_t)n, 0.0);
+    for (int a = 0; a < nb; ++a) {
+        const int i0 = std::min(n, a * rpb), i1 = std::min(n, i0 + rpb);
+        if (i1 <= i0) continue;
+        double mx = 0.0, my = 0.0, h2 = 0.0;
+        for (int i = i0; i < i1; ++i) {
+            mx += xy[2 * perm[i]];
+            my += xy[2 * perm[i] + 1];
+        }
+        mx /= (i1 - i0);
+        my /= (i1 - i0);
+        for (int i = i0; i < i1; ++i) {
+            const double dx = xy[2 * perm[i]] - mx, dy = xy[2 * perm[i] + 1] - my;
+            h2 += dx * dx + dy * dy;
+        }
+        const double ih = h2 > 0.0 ? 1.0 / std::sqrt(h2 / (i1 - i0)) : 0.0;
+        for (int i = i0; i < i1; ++i) {
+            c->sz_fxy_h[2 * (size_t)i] = (xy[2 * perm[i]] - mx) * ih;
+            c->sz_fxy_h[2 * (size_t)i + 1] = (xy[2 * perm[i] + 1] - my) * ih;
+        }
+    }
+    const std::vector<float> fxy32(c->sz_fxy_h.begin(), c->sz_fxy_h.end());
+    const size_t ncs = (size_t)SZ_NC * nb;
+    cudaError_t e;
+    if ((e = sz_alloc(c, &c->sz_perm, n)) != cudaSuccess) return e;
+    if ((e = sz_alloc(c, &c->sz_rp, n + 1)) != cudaSuccess) return e;
+    if ((e = sz_alloc(c, &c->sz_ci, nnz)) != cudaSuccess) return e;
+    if ((e = sz_alloc(c, &c->sz_val64, nnz)) != cudaSuccess) return e;
+    if ((e = sz_alloc(c, &c->sz_val32, nnz)) != cudaSuccess) return e;
+    if ((e = sz_alloc(c, &c->sz_dinv64, n)) != cudaSuccess) return e;
+    if ((e = sz_alloc(c, &c->sz_dinv32, n)) != cudaSuccess) return e;
+    if ((e = sz_alloc(c, &c->sz_ainv64, ncs * ncs)) != cudaSuccess) return e;
+    if ((e = sz_alloc(c, &c->sz_ainv32, ncs * ncs)) != cudaSuccess) return e;
+    if ((e = sz_alloc(c, &c->sz_fxy64, 2 * (size_t)n)) != cudaSuccess) return e;
+    if ((e = sz_alloc(c, &c->sz_fxy32, 2 * (size_t)n)) != cudaSuccess) return e;
+    if ((e = sz_upload(c->sz_fxy64, c->sz_fxy_h)) != cudaSuccess) return e;
+    if ((e = sz_upload(c->sz_fxy32, fxy32)) != cudaSuccess) return e;
+    if ((e = sz_upload(c->sz_perm, perm)) != cudaSuccess) return e;
+    if ((e = sz_upload(c->sz_rp, c->sz_rp_h)) != cudaSuccess) return e;
+    return sz_upload(c->sz_ci, c->sz_ci_h);
+}
+
+template <typename TI, typename TP>
+const void* schwarz_kernel() {
+    return (const void*)k_pcg_schwarz<TI, TP>;
+}
+
+const void* schwarz_kernel_for(const cgp_ctx_s* c) {
+    if (c->prm.precision == CGP_MIXED) return schwarz_kernel<float, float>();
+    return c->schwarz_fp32 ? schwarz_kernel<double, float>() : schwarz_kernel<double, double>();
+}
+
+}  // namespace
+
+// Decide whether the coarse Poisson solve runs on an on-chip kernel and raise its dynamic
 // shared-memory limit (once per context, outside any stream capture).
 cudaError_t pipe_prepare(cgp_ctx_s* c) {
     int b64, t64, b32, t32;
     size_t s64, s32;
     c->use_pipe = false;
     c->onchip_pipelined = false;
+    c->use_schwarz = false;
     if (c->prm.coarse_solver == 1) return cudaSuccess;
+    const bool schwarz = c->prm.coarse_solver == 0 || c->prm.coarse_solver == 3 || c->prm.coarse_solver == 4;
+    if (schwarz) {
+        const bool mixed = c->prm.precision == CGP_MIXED;
+        c->schwarz_fp32 = mixed || c->prm.coarse_solver != 4;
+        const size_t sti = mixed ? sizeof(float) : sizeof(double);
+        const size_t stp = c->schwarz_fp32 ? sizeof(float) : sizeof(double);
+        int nb = 0, T = 0;
+        size_t sm0 = 0, sm = 0;
+        const bool fits = pipe_shape(c->nc, c->width_c, c->num_sms, sti, &nb, &T, &sm0) &&
+                          (sm = schwarz_smem(c->width_c, T, nb, sti, stp)) <= 200 * 1024;
+        const void* fn = schwarz_kernel_for(c);
+        int occ = 0;
+        if (fits) {
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, T, sm);
+            if (e != cudaSuccess) return e;
+        }
+        if (fits && occ >= 1) {
+            c->pipe_c.blocks = nb;
+            c->pipe_c.threads = T;
+            c->sz_smem = sm;
+            c->sz_degree = c->prm.precond_degree > 0 ? c->prm.precond_degree : 6;
+            c->sz_ratio = c->prm.precond_ratio > 1.0 ? c->prm.precond_ratio : 30.0;
+            cudaError_t e = schwarz_structure(c);
+            if (e != cudaSuccess) return e;
+            c->use_schwarz = true;
+            c->use_pipe = true;
+            return cudaSuccess;
+        }
+        // automatic choice: the Jacobi on-chip kernel next, then the generic kernel
+        if (c->prm.coarse_solver != 0) return cudaSuccess;
+    }
     // The pipelined form only in FP64: in FP32 its recurrences drift too far from the true
     // residual for the inner solve to reach its target.
     const bool pipelined = c->prm.coarse_solver == 2 && c->prm.precision == CGP_FP64;
@@ -486,8 +945,167 @@ cudaError_t pipe_prepare(cgp_ctx_s* c) {
     return cudaSuccess;
 }
 
+// Values of the Schwarz solver for the current boundary conditions (after the symmetric
+// elimination of the pressure-Dirichlet rows): renumbered FP64/FP32 matrix values and inverse
+// diagonal, the spectrum bound of D^-1 A for the Chebyshev polynomial, and the inverse of the
+// Galerkin coarse matrix A_0 = R_0 A R_0^T by Cholesky factorisation. A coarse function that
+// vanishes on its subdomain (all nodes at one point) gets a unit diagonal and no coupling.
+int schwarz_values(cgp_ctx_s* c) {
+    if (!c->use_schwarz) return CGP_OK;
+    const int n = c->nc, nb = c->pipe_c.blocks;
+    const int rpb = (n + nb - 1) / nb;
+    const std::vector<int>& rp = c->sz_rp_h;
+    const std::vector<int>& ci = c->sz_ci_h;
+    const size_t nnz = ci.size();
+    std::vector<double> K(c->hm.coarse.nnz), v(nnz), dg(n, 0.0);
+    if (cudaMemcpy(K.data(), c->Kc, K.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return CGP_ERR_CUDA;
+    for (size_t k = 0; k < nnz; ++k) v[k] = K[c->sz_src[k]];
+    for (int i = 0; i < n; ++i)
+        for (int k = rp[i]; k < rp[i + 1]; ++k)
+            if (ci[k] == i) dg[i] = v[k];
+    for (int i = 0; i < n; ++i)
+        if (!(dg[i] > 0.0)) return CGP_ERR_ARG;   // not symmetric positive definite
+    // upper bound of the spectrum of D^-1 A: the smaller of the Gershgorin bound and 1.2 times a
+    // power-iteration estimate on D^-1/2 A D^-1/2 (same spectrum)
+    double gersh = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double sum = 0.0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) sum += std::fabs(v[k]);
+        gersh = std::max(gersh, sum / dg[i]);
+    }
+    std::vector<double> z(n), w(n), sq(n);
+    for (int i = 0; i < n; ++i) {
+        sq[i] = 1.0 / std::sqrt(dg[i]);
+        z[i] = 1.0 + 0.5 * std::sin(1.0 + 12.9898 * i);   // fixed, non-smooth start
+    }
+    double lam = 0.0;
+    for (int it = 0; it < 100; ++it) {
+        double zz = 0.0, zw = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int k = rp[i]; k < rp[i + 1]; ++k) acc += v[k] * sq[ci[k]] * z[ci[k]];
+            w[i] = sq[i] * acc;
+            zz += z[i] * z[i];
+            zw += z[i] * w[i];
+        }
+        lam = zw / zz;
+        double ww = 0.0;
+        for (int i = 0; i < n; ++i) ww += w[i] * w[i];
+        const double inv = ww > 0.0 ? 1.0 / std::sqrt(ww) : 0.0;
+        for (int i = 0; i < n; ++i) z[i] = w[i] * inv;
+    }
+    c->sz_lmax = std::min(gersh, 1.2 * lam);
+    c->sz_lmin = c->sz_lmax / c->sz_ratio;
+    // Galerkin coarse matrix; coarse index of function f on subdomain a is f * nb + a
+    const int nc0 = SZ_NC * nb;
+    const std::vector<double>& fxy = c->sz_fxy_h;
+    std::vector<double> A0((size_t)nc0 * nc0, 0.0), Lc((size_t)nc0 * nc0, 0.0), Ai((size_t)nc0 * nc0, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const double pi[SZ_NC] = {1.0, fxy[2 * (size_t)i], fxy[2 * (size_t)i + 1]};
+        const int ai = i / rpb;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            const int j = ci[k], aj = j / rpb;
+            const double pj[SZ_NC] = {1.0, fxy[2 * (size_t)j], fxy[2 * (size_t)j + 1]};
+            for (int f = 0; f < SZ_NC; ++f)
+                for (int g = 0; g < SZ_NC; ++g)
+                    A0[(size_t)(f * nb + ai) * nc0 + g * nb + aj] += pi[f] * v[k] * pj[g];
+        }
+    }
+    for (int q = 0; q < nc0; ++q)
+        if (A0[(size_t)q * nc0 + q] == 0.0) A0[(size_t)q * nc0 + q] = 1.0;
+    for (int j = 0; j < nc0; ++j) {
+        double d = A0[(size_t)j * nc0 + j];
+        for (int k = 0; k < j; ++k) d -= Lc[(size_t)j * nc0 + k] * Lc[(size_t)j * nc0 + k];
+        if (!(d > 0.0)) return CGP_ERR_ARG;
+        const double ljj = std::sqrt(d);
+        Lc[(size_t)j * nc0 + j] = ljj;
+        for (int i = j + 1; i < nc0; ++i) {
+            double s = A0[(size_t)i * nc0 + j];
+            for (int k = 0; k < j; ++k) s -= Lc[(size_t)i * nc0 + k] * Lc[(size_t)j * nc0 + k];
+            Lc[(size_t)i * nc0 + j] = s / ljj;
+        }
+    }
+    std::vector<double> y(nc0);
+    for (int col = 0; col < nc0; ++col) {
+        for (int i = 0; i < nc0; ++i) {   // L y = e_col
+            double s = i == col ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) s -= Lc[(size_t)i * nc0 + k] * y[k];
+            y[i] = s / Lc[(size_t)i * nc0 + i];
+        }
+        for (int i = nc0 - 1; i >= 0; --i) {   // L^T x = y
+            double s = y[i];
+            for (int k = i + 1; k < nc0; ++k) s -= Lc[(size_t)k * nc0 + i] * Ai[(size_t)k * nc0 + col];
+            Ai[(size_t)i * nc0 + col] = s / Lc[(size_t)i * nc0 + i];
+        }
+    }
+    std::vector<double> dinv(n);
+    for (int i = 0; i < n; ++i) dinv[i] = 1.0 / dg[i];
+    std::vector<float> v32(v.begin(), v.end()), dinv32(dinv.begin(), dinv.end()), ai32(Ai.begin(), Ai.end());
+    if (sz_upload(c->sz_val64, v) != cudaSuccess || sz_upload(c->sz_val32, v32) != cudaSuccess ||
+        sz_upload(c->sz_dinv64, dinv) != cudaSuccess || sz_upload(c->sz_dinv32, dinv32) != cudaSuccess ||
+        sz_upload(c->sz_ainv64, Ai) != cudaSuccess || sz_upload(c->sz_ainv32, ai32) != cudaSuccess)
+        return CGP_ERR_CUDA;
+    return CGP_OK;
+}
+
+template <typename TI, typename TP>
+static cudaError_t launch_schwarz_t(cgp_ctx_s* c, const double* b, double* x, cudaStream_t s, const TI* valI,
+                                    const TP* valP, const TP* dinvP, const TP* fxy, const TP* ainv) {
+    SchwarzArgs<TI, TP> a;
+    const int nb = c->pipe_c.blocks;
+    a.n = c->nc;
+    a.rows_per_block = (c->nc + nb - 1) / nb;
+    a.width = c->width_c;
+    a.degree = c->sz_degree;
+    a.perm = c->sz_perm;
+    a.rp = c->sz_rp;
+    a.ci = c->sz_ci;
+    a.val64 = c->sz_val64;
+    a.valI = valI;
+    a.valP = valP;
+    a.dinvP = dinvP;
+    a.fxy = fxy;
+    a.ainv = ainv;
+    a.lmin = c->sz_lmin;
+    a.lmax = c->sz_lmax;
+    a.b = b;
+    a.x = x;
+    char* p = (char*)c->ws;
+    a.xp = reinterpret_cast<double*>(p);
+    p += ((sizeof(double) * (size_t)c->nc + 255) / 256) * 256;
+    a.ubuf = reinterpret_cast<TI*>(p);
+    a.part = c->part;
+    a.sw = c->sync + SYNC_POI;
+    a.rtol = c->prm.rtol;
+    a.inner_rtol = sizeof(TI) == 4 ? c->prm.inner_rtol : 0.0;
+    a.max_iter = c->prm.max_iter;
+    a.max_outer = c->prm.max_outer;
+    a.st_iters = &c->stats->poi_iters;
+    a.st_outer = &c->stats->poi_outer;
+    a.st_status = &c->stats->poi_status;
+    a.st_rel = &c->stats->poi_rel;
+    a.st_barrier = &c->stats->barrier_status;
+    cudaError_t e = cudaMemsetAsync(a.sw, 0, sizeof(SyncWords), s);
+    if (e != cudaSuccess) return e;
+    void* kargs[] = {(void*)&a};
+    const void* fn = (const void*)k_pcg_schwarz<TI, TP>;
+    if (nb == 1) return cudaLaunchKernel(fn, dim3(1), dim3(c->pipe_c.threads), kargs, c->sz_smem, s);
+    return cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(c->pipe_c.threads), kargs, c->sz_smem, s);
+}
+
 cudaError_t launch_poisson_pipe(cgp_ctx_s* c, const double* b, double* x, cudaStream_t s) {
     const bool mixed = c->prm.precision == CGP_MIXED;
+    if (c->use_schwarz) {
+        if (mixed)
+            return launch_schwarz_t<float, float>(c, b, x, s, c->sz_val32, c->sz_val32, c->sz_dinv32, c->sz_fxy32,
+                                                  c->sz_ainv32);
+        if (c->schwarz_fp32)
+            return launch_schwarz_t<double, float>(c, b, x, s, c->sz_val64, c->sz_val32, c->sz_dinv32,
+                                                   c->sz_fxy32, c->sz_ainv32);
+        return launch_schwarz_t<double, double>(c, b, x, s, c->sz_val64, c->sz_val64, c->sz_dinv64, c->sz_fxy64,
+                                                c->sz_ainv64);
+    }
     if (mixed)
         return launch_pipe_t<float>(c, b, x, s, c->Kc32, c->dinvK32, c->pipe_c.blocks, c->pipe_c.threads,
                                     c->pipe_smem32);

@@ -248,8 +248,9 @@ def bfs_full():
     return coarse, prob, orc
 
 
+@pytest.mark.parametrize("solver", [5, 0], ids=["jacobi", "schwarz"])
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
-def test_bfs33_full_size_one_step(L, bfs_full, precision):
+def test_bfs33_full_size_one_step(L, bfs_full, precision, solver):
     """Full workload size (65,308 / 259,117 nodes), bench launch shape: one step from rest.
 
     The coarse matrix of this 30:2 channel has kappa ~ 1e7, and the FP64 evaluation of the true
@@ -258,7 +259,7 @@ def test_bfs33_full_size_one_step(L, bfs_full, precision):
     <= sqrt(kappa) * 3e-11 ~ 1e-7 in the worst case; the bar on u and M^-1 G p_f is 1e-9
     (observed: ~1e-11)."""
     coarse, prob, orc = bfs_full
-    f = flow(coarse, prob, rtol=3e-11, precision=precision)
+    f = flow(coarse, prob, rtol=3e-11, precision=precision, coarse_solver=solver)
     u0 = f.u.cpu().numpy().copy()
     ut = torch.empty_like(f.u)
     gp = torch.empty_like(f.u)
@@ -275,11 +276,13 @@ def test_bfs33_full_size_one_step(L, bfs_full, precision):
     assert eu < 1e-9 and eg < 1e-9, (eu, eg, st.as_dict())
 
 
-@pytest.mark.parametrize("solver", [0, 1, 2], ids=["onchip_classical", "generic_classical", "onchip_pipelined"])
+@pytest.mark.parametrize("solver", [0, 1, 2, 3, 4, 5], ids=["auto", "generic_classical", "onchip_pipelined",
+                                                          "schwarz_fp32", "schwarz", "onchip_classical"])
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
 def test_coarse_solvers_agree(L, cavity_state, solver, precision):
-    """Both coarse Poisson kernels (on-chip pipelined CG, generic classical CG) in both precisions
-    reach the oracle's exact solve of Eq. 21 at parity tolerance."""
+    """Every coarse Poisson kernel (on-chip classical / pipelined / two-level Schwarz CG, generic
+    classical CG) in both precisions reaches the oracle's exact solve of Eq. 21 at parity
+    tolerance."""
     coarse, prob, orc, res = cavity_state
     ref = orc.step(res.u, 6 * prob.dt)
     f = flow(coarse, prob, rtol=1e-13, precision=precision, coarse_solver=solver)
@@ -289,3 +292,31 @@ def test_coarse_solvers_agree(L, cavity_state, solver, precision):
     e = rel(pc.cpu().numpy(), ref.p_c)
     f.close()
     assert st.poisson_rel_res <= 1e-13 and e < 1e-11, (e, st.as_dict())
+    if solver in (0, 3, 4):
+        assert f.info.coarse_kernel == (4 if solver == 4 or precision == 1 else 3)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_schwarz_cuts_iterations(L, bfs_full, precision):
+    """On the full-size 30:2 channel (65,308 coarse nodes, 152 subdomains) the two-level Schwarz
+    preconditioner needs at most a fifth of the Jacobi-preconditioned CG iterations for the same
+    Eq. 21 solve at rtol 1e-8; each solution meets ||b - K p|| <= rtol ||b|| when the residual is
+    recomputed on the host with the oracle's matrix (the margin 1.01 covers the rounding of the
+    two FP64 residual evaluations)."""
+    coarse, prob, orc = bfs_full
+    rng = np.random.default_rng(11)
+    b = orc.coarse.M @ rng.standard_normal(orc.n_coarse)
+    b[orc.p_mask] = 0.0
+    K = ocgp._bc_sym(orc.coarse.K, orc.p_mask)
+    its = {}
+    for solver in (5, 3):
+        f = flow(coarse, prob, rtol=1e-8, precision=precision, coarse_solver=solver)
+        pc = torch.zeros(f.info.n_coarse, dtype=torch.float64, device="cuda")
+        L.cgp_poisson_solve(f.ctx, dev(b), pc)
+        st = f.stats(check=True)
+        its[solver] = st.poisson_iters
+        p = pc.cpu().numpy()
+        f.close()
+        host_rel = np.linalg.norm(b - K @ p) / np.linalg.norm(b)
+        assert st.poisson_rel_res <= 1e-8 and host_rel <= 1.01e-8, (solver, host_rel, st.as_dict())
+    assert its[3] * 5 <= its[5], its
