@@ -43,8 +43,8 @@ extern "C" {
 /* ---- precision modes --------------------------------------------------------------------- */
 #define CGP_FP64   0  /* every Krylov iteration in FP64                                            */
 #define CGP_MIXED  1  /* FP32 inner Krylov iterations inside FP64 iterative refinement for the     */
-                      /* momentum and Poisson solves; true residuals, refinement updates and the   */
-                      /* mass-matrix velocity correction stay FP64                                  */
+                      /* momentum, Poisson and mass-matrix solves; true residuals, refinement      */
+                      /* updates and the velocity correction itself stay FP64                      */
 
 /* ---- boundary masks ------------------------------------------------------------------------ */
 #define CGP_BC_U   1  /* bit 0 of a fine-node velocity mask: x-velocity prescribed (Eqs. 3, 10)   */

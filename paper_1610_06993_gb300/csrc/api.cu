@@ -141,6 +141,8 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     TRY(dalloc(c, &c->A32, nnzf));
     TRY(dalloc(c, &c->Gxy, 2 * nnzf));
     TRY(dalloc(c, &c->dinvM, nf));
+    TRY(dalloc(c, &c->M32, nnzf));
+    TRY(dalloc(c, &c->dinvM32, nf));
     TRY(dalloc(c, &c->dinvA, 2 * nf));
     TRY(dalloc(c, &c->dinvA32, 2 * nf));
     TRY(dalloc(c, &c->b_mom, 2 * nf));
@@ -168,7 +170,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     TRY(dalloc(c, &ws, need));
     c->ws = ws;
     c->max_blocks = std::max(c->num_sms, 1);
-    TRY(dalloc(c, &c->part, 32 * (size_t)c->max_blocks));
+    TRY(dalloc(c, &c->part, CGP_PART_SLOTS * (size_t)c->max_blocks));
     TRY(dalloc(c, &c->sync, (size_t)SYNC_COUNT));
     TRY(dalloc(c, &c->stats, 1));
     CK(cudaMemset(c->stats, 0, sizeof(DevStats)));

@@ -93,6 +93,11 @@ __global__ void k_inv_diag(int n, const int* __restrict__ diag, const double* __
     if (i < n) dinv[i] = 1.0 / val[diag[i]];
 }
 
+__global__ void k_to_f32(int n, const double* __restrict__ src, float* dst) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (float)src[i];
+}
+
 }  // namespace
 
 cudaError_t launch_geometry(const double* xy, const int* tri, int t, double* geo, cudaStream_t s) {
@@ -121,6 +126,8 @@ cudaError_t launch_make_A0(cgp_ctx_s* c, const double* K, cudaStream_t s) {
     const int nnz = c->F.nnz;
     k_make_A0<<<(nnz + 255) / 256, 256, 0, s>>>(nnz, c->prm.rho, c->prm.dt * c->prm.mu, c->M, K, c->A0);
     k_inv_diag<<<(c->nf + 255) / 256, 256, 0, s>>>(c->nf, c->F.diag, c->M, c->dinvM);
+    k_to_f32<<<(nnz + 255) / 256, 256, 0, s>>>(nnz, c->M, c->M32);
+    k_to_f32<<<(c->nf + 255) / 256, 256, 0, s>>>(c->nf, c->dinvM, c->dinvM32);
     return cudaGetLastError();
 }
 

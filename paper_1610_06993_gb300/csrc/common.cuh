@@ -168,6 +168,30 @@ __device__ __forceinline__ void block_partials(double (&v)[K], double* part, uns
     }
 }
 
+// Same result layout as block_partials, written for a GPU with a low FP64 rate: a shuffle tree in
+// every warp costs about 5 x 32 FP64 additions per warp and value, so instead every thread stores
+// its K values in shared memory and warp k adds up value k (blockDim.x additions in a fixed
+// order, then one shuffle tree), about a quarter of the FP64 work. Lane 0 of warp k writes
+// part[k * nblocks + bid]; a following grid barrier (which starts with __syncthreads) publishes
+// it. Needs blockDim.x >= 32 K and s_buf of K * blockDim.x doubles.
+template <int K>
+__device__ __forceinline__ void block_partials_lean(const double (&v)[K], double* part, unsigned int nblocks,
+                                                    unsigned int bid, double* s_buf) {
+    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) s_buf[k * T + t] = v[k];
+    __syncthreads();
+    if (warp < K) {
+        const double* b = s_buf + warp * T;
+        double acc = 0.0;
+        for (int j = lane; j < T; j += 32) acc += b[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) part[(size_t)warp * nblocks + bid] = acc;
+    }
+}
+
 // Block groups. A batched launch advances several independent problem instances at once: the
 // grid is cut into contiguous block groups, one per instance, and every barrier and reduction
 // runs within a group. map.inst_of_block == nullptr means one group spanning the whole grid.
@@ -199,6 +223,8 @@ __device__ __forceinline__ Grp group_of(const BatchMap& m) {
 
 // Maximum number of blocks of a persistent launch (partials are read 32 x 8 at a time).
 #define CGP_MAX_GRID 256
+// Partial-sum slots (of nblocks doubles each) of a single-instance context.
+#define CGP_PART_SLOTS 40
 
 // After a grid barrier: every block sums the nblocks partials of each of the K slots in the same
 // fixed order, so all blocks hold bit-identical totals. Slot k's partials start at

@@ -64,6 +64,8 @@ struct cgp_ctx_s {
     float* A32 = nullptr;        // FP32 copy (CGP_MIXED)
     double* Gxy = nullptr;       // [nnz][2] gradient (G = D on the fine mesh)
     double* dinvM = nullptr;     // [nf]
+    float* M32 = nullptr;        // FP32 copies of M and its inverse diagonal (CGP_MIXED)
+    float* dinvM32 = nullptr;
     double* dinvA = nullptr;     // [nf][2]
     float* dinvA32 = nullptr;    // [nf][2]
     double* b_mom = nullptr;     // [nf][2]
@@ -94,7 +96,7 @@ struct cgp_ctx_s {
     // Krylov workspace and reductions
     void* ws = nullptr;
     size_t ws_bytes = 0;
-    double* part = nullptr;      // partial sums [16][max_blocks]
+    double* part = nullptr;      // partial sums [CGP_PART_SLOTS][max_blocks]
     int max_blocks = 0;
     cgp::SyncWords* sync = nullptr;
     cgp::DevStats* stats = nullptr;

@@ -58,15 +58,19 @@ CgArgs<TI> poisson_args(cgp_ctx_s* c, const double* b, double* x, SyncWords* sw,
     return a;
 }
 
-CgArgs<double> mass_args(cgp_ctx_s* c, const double* b, double* x, SyncWords* sw, double* part) {
+template <typename TI>
+CgArgs<TI> mass_args(cgp_ctx_s* c, const double* b, double* x, SyncWords* sw, double* part) {
+    const bool mixed = sizeof(TI) == sizeof(float);
     const size_t n2 = 2 * (size_t)c->nf;
     char* p = (char*)c->ws;
-    CgArgs<double> a;
-    a.n = c->nf; a.rp = c->F.rp; a.ci = c->F.ci; a.val64 = c->M; a.valI = c->M; a.dinvI = c->dinvM;
+    CgArgs<TI> a;
+    a.n = c->nf; a.rp = c->F.rp; a.ci = c->F.ci; a.val64 = c->M;
+    a.valI = mixed ? (const TI*)(const void*)c->M32 : (const TI*)(const void*)c->M;
+    a.dinvI = mixed ? (const TI*)(const void*)c->dinvM32 : (const TI*)(const void*)c->dinvM;
     a.b = b; a.x = x;
-    a.r = carve<double>(p, n2); a.u = carve<double>(p, n2); a.w = carve<double>(p, n2);
-    a.p = carve<double>(p, n2); a.s = carve<double>(p, n2); a.d = carve<double>(p, n2);
-    a.part = part; a.sw = sw; a.rtol = c->prm.rtol; a.inner_rtol = 0.0;
+    a.r = carve<TI>(p, n2); a.u = carve<TI>(p, n2); a.w = carve<TI>(p, n2);
+    a.p = carve<TI>(p, n2); a.s = carve<TI>(p, n2); a.d = carve<TI>(p, n2);
+    a.part = part; a.sw = sw; a.rtol = c->prm.rtol; a.inner_rtol = mixed ? c->prm.inner_rtol : 0.0;
     a.max_iter = c->prm.max_iter; a.max_outer = c->prm.max_outer; a.lanes = c->sh_f.lanes;
     a.st_iters = &c->stats->mass_iters; a.st_outer = &c->stats->mass_outer; a.st_status = &c->stats->mass_status;
     a.st_rel = &c->stats->mass_rel; a.st_barrier = &c->stats->barrier_status;
@@ -121,7 +125,11 @@ cudaError_t launch_mass_cg(cgp_ctx_s* c, const double* b, double* x, cudaStream_
     SyncWords* sw = c->sync + SYNC_MASS;
     cudaError_t e = cudaMemsetAsync(sw, 0, sizeof(SyncWords), s);
     if (e != cudaSuccess) return e;
-    auto L = single_launch(mass_args(c, b, x, sw, c->part));
+    if (c->prm.precision == CGP_MIXED) {
+        auto L = single_launch(mass_args<float>(c, b, x, sw, c->part));
+        return coop_launch(k_cg<float, 2>, c->sh_f.blocks, c->sh_f.threads, L, s);
+    }
+    auto L = single_launch(mass_args<double>(c, b, x, sw, c->part));
     return coop_launch(k_cg<double, 2>, c->sh_f.blocks, c->sh_f.threads, L, s);
 }
 
@@ -157,12 +165,12 @@ template <typename TI>
 cudaError_t build_typed(cgp_batch_s* b) {
     std::vector<BicgArgs<TI>> mom(b->n);
     std::vector<CgArgs<TI>> poi(b->n);
-    std::vector<CgArgs<double>> mass(b->n);
+    std::vector<CgArgs<TI>> mass(b->n);
     for (int i = 0; i < b->n; ++i) {
         cgp_ctx_s* c = b->ctx[i];
         mom[i] = momentum_args<TI>(c, b->u[i], c->ut, bsync(b, i, SYNC_MOM), bpart(b, i));
         poi[i] = poisson_args<TI>(c, c->bc, b->pc[i], bsync(b, i, SYNC_POI), bpart(b, i));
-        mass[i] = mass_args(c, c->grad, c->w, bsync(b, i, SYNC_MASS), bpart(b, i));
+        mass[i] = mass_args<TI>(c, c->grad, c->w, bsync(b, i, SYNC_MASS), bpart(b, i));
     }
     cudaError_t e = upload_table(b, mom, &b->tab_mom);
     if (e == cudaSuccess) e = upload_table(b, poi, &b->tab_poi);
@@ -204,6 +212,10 @@ cudaError_t batch_poisson_launch(cgp_batch_s* b, cudaStream_t s) {
 }
 
 cudaError_t batch_mass_launch(cgp_batch_s* b, cudaStream_t s) {
+    if (b->precision == CGP_MIXED) {
+        auto L = table_launch<CgArgs<float>>(b->tab_mass, b->map_f);
+        return coop_launch(k_cg<float, 2>, b->blocks_f, b->threads, L, s);
+    }
     auto L = table_launch<CgArgs<double>>(b->tab_mass, b->map_f);
     return coop_launch(k_cg<double, 2>, b->blocks_f, b->threads, L, s);
 }
@@ -212,7 +224,7 @@ cudaError_t batch_mass_launch(cgp_batch_s* b, cudaStream_t s) {
 int persistent_blocks_per_sm(int threads) {
     int m = 1 << 30, v = 0;
     const void* fns[] = {(const void*)k_cg<double, 1>, (const void*)k_cg<float, 1>, (const void*)k_cg<double, 2>,
-                         (const void*)k_bicgstab<double>, (const void*)k_bicgstab<float>};
+                         (const void*)k_cg<float, 2>, (const void*)k_bicgstab<double>, (const void*)k_bicgstab<float>};
     for (const void* f : fns) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, f, threads, 0) != cudaSuccess) return 0;
         m = v < m ? v : m;

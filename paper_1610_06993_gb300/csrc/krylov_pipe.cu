@@ -453,19 +453,29 @@ struct SchwarzArgs {
 
 enum { PS_P0 = 0, PS_O1 = 1 /* 2 slots */, PS_I0 = 3, PS_R = 4 /* SZ_NC slots */, PS_I = 4 + SZ_NC /* 2 x 3 */ };
 
-// Dynamic shared memory of k_pcg_schwarz: ELL slice (values in TI, columns, values in TP when TP
-// differs), two Chebyshev buffers, the block's SZ_NC rows of A_0^-1 and the gathered R_0 r.
+// One entry of the subdomain matrix A_aa in shared memory: column local to the block, value.
+template <typename TP> struct LocEnt;
+template <> struct __align__(8) LocEnt<float> { int c; float v; };
+template <> struct __align__(16) LocEnt<double> { int c; int pad; double v; };
+
+// Dynamic shared memory of k_pcg_schwarz: the block's ELL slice of A (values in TI, global
+// columns), the compact ELL slice of A_aa (local columns, values in TP), two Chebyshev buffers,
+// the FP64 reduction buffer (three values per thread), the block's SZ_NC rows of A_0^-1 and the
+// gathered R_0 r. T is a multiple of 32, so every region before the TP arrays ends on a 128-byte
+// boundary.
 size_t schwarz_smem(int width, int T, int nb, size_t sti, size_t stp) {
     const size_t wt = (size_t)width * T;
     const size_t ncs = (size_t)SZ_NC * nb;
-    return wt * (sti + sizeof(int)) + (sti != stp ? wt * stp : 0) + 2 * (size_t)T * stp + (SZ_NC + 1) * ncs * stp;
+    const size_t loc = stp == sizeof(float) ? sizeof(LocEnt<float>) : sizeof(LocEnt<double>);
+    return wt * (sti + sizeof(int)) + wt * loc + 2 * (size_t)T * stp + 3 * (size_t)T * sizeof(double) +
+           (SZ_NC + 1) * ncs * stp;
 }
 
 template <typename TI, typename TP>
 __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double s_red[32 * 4];
     __shared__ TI s_redT[32 * 4];
+    __shared__ TP s_redP[32 * SZ_NC];
     __shared__ double s_bc[4];
     __shared__ TI s_ctl[2];
     __shared__ int s_flag;
@@ -480,27 +490,39 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
     const size_t wt = (size_t)a.width * T;
     TI* s_val = reinterpret_cast<TI*>(smem);
     int* s_ci = reinterpret_cast<int*>(smem + sizeof(TI) * wt);
-    unsigned char* q = smem + (sizeof(TI) + sizeof(int)) * wt;
-    TP* s_pv = reinterpret_cast<TP*>(s_val);
-    if (sizeof(TP) != sizeof(TI)) {
-        s_pv = reinterpret_cast<TP*>(q);
-        q += sizeof(TP) * wt;
-    }
-    TP* s_z = reinterpret_cast<TP*>(q);
+    LocEnt<TP>* s_loc = reinterpret_cast<LocEnt<TP>*>(smem + (sizeof(TI) + sizeof(int)) * wt);
+    TP* s_z = reinterpret_cast<TP*>(s_loc + wt);                                  // [2][T]
+    double* s_lean = reinterpret_cast<double*>(s_z + 2 * T);                      // [3][T]
     const unsigned int ncs = SZ_NC * nb;
-    TP* s_ainv = s_z + 2 * T;             // [SZ_NC][ncs]
+    TP* s_ainv = reinterpret_cast<TP*>(s_lean + 3 * T);   // [SZ_NC][ncs]
     TP* s_rc = s_ainv + SZ_NC * ncs;      // [ncs]
+    int wl, wloc;   // longest row / longest A_aa row among this warp's rows (warp-uniform loop ends)
     {
-        int k0 = 0, len = 0;
+        int k0 = 0, len = 0, m = 0;
         if (own) {
             k0 = a.rp[row];
             len = a.rp[row + 1] - k0;
         }
+        wl = __reduce_max_sync(0xffffffffu, len);
         for (int k = 0; k < a.width; ++k) {
             const bool in = own && k < len;
-            s_ci[k * T + t] = in ? a.ci[k0 + k] : -1;
+            const int c = in ? a.ci[k0 + k] : -1;
+            s_ci[k * T + t] = c;
             s_val[k * T + t] = in ? a.valI[k0 + k] : (TI)0;
-            if (sizeof(TP) != sizeof(TI)) s_pv[k * T + t] = in ? a.valP[k0 + k] : (TP)0;
+            if (c >= r0 && c < r1) {
+                LocEnt<TP> e;
+                e.c = c - r0;
+                e.v = a.valP[k0 + k];
+                s_loc[m * T + t] = e;
+                m += 1;
+            }
+        }
+        wloc = __reduce_max_sync(0xffffffffu, m);
+        for (int k = m; k < a.width; ++k) {   // padding: own slot, zero weight
+            LocEnt<TP> e;
+            e.c = t;
+            e.v = (TP)0;
+            s_loc[k * T + t] = e;
         }
         for (unsigned int j = t; j < SZ_NC * ncs; j += T) {
             const unsigned int k = j / ncs, col = j - k * ncs;
@@ -520,8 +542,9 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
     // times. False if the grid barrier inside failed.
     auto precondition = [&](TI rI, TI& u) -> bool {
         {
-            double v[SZ_NC] = {(double)rI, (double)(fx * (TP)rI), (double)(fy * (TP)rI)};
-            block_partials<SZ_NC>(v, a.part + PS_R * nb, nb, s_red);
+            // moments in the preconditioner's precision (they only feed the coarse correction)
+            const TP v[SZ_NC] = {(TP)rI, fx * (TP)rI, fy * (TP)rI};
+            block_partials_t<SZ_NC, TP>(v, a.part + PS_R * nb, nb, s_redP);
         }
         grid_arrive(a.sw, nb, epoch);
         // local part: Chebyshev iteration on A_aa z = r from z = 0, s_z double buffered
@@ -536,9 +559,9 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
             TP az = (TP)0;
 #pragma unroll
             for (int k = 0; k < PIPE_WMAX; ++k) {
-                if (k < a.width) {
-                    const int c = s_ci[k * T + t];
-                    if (c >= r0 && c < r1) az += s_pv[k * T + t] * zb[c - r0];
+                if (k < wloc) {
+                    const LocEnt<TP> e = s_loc[k * T + t];
+                    az += e.v * zb[e.c];
                 }
             }
             const TP rn = (TP)1 / ((TP)2 * sigma - rho);
@@ -569,7 +592,7 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
     double bb;
     {
         double v[1] = {bi * bi}, tt[1];
-        block_partials<1>(v, a.part + PS_P0 * nb, nb, s_red);
+        block_partials_lean<1>(v, a.part + PS_P0 * nb, nb, blockIdx.x, s_lean);
         if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
         grid_totals<1>(a.part + PS_P0 * nb, nb, tt, s_bc);
         bb = tt[0];
@@ -596,7 +619,7 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
         {
             if (own) a.ubuf[row] = u;
             double v[2] = {r64 * r64, (double)(r * u)}, tt[2];
-            block_partials<2>(v, a.part + PS_O1 * nb, nb, s_red);
+            block_partials_lean<2>(v, a.part + PS_O1 * nb, nb, blockIdx.x, s_lean);
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
             grid_totals<2>(a.part + PS_O1 * nb, nb, tt, s_bc);
             rr64 = tt[0];
@@ -607,11 +630,11 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
         if (outer >= a.max_outer || iters >= a.max_iter) { status = CGP_ERR_NOT_CONVERGED; break; }
         const double tgt = fmax(itol2 * rr64, floor2 * bb);
         // ---- w = A u, delta = (w, u)
-        TI w = own ? ell_row<TI, TI>(s_ci, s_val, T, t, a.width, a.ubuf) : (TI)0;
+        TI w = own ? ell_row<TI, TI>(s_ci, s_val, T, t, wl, a.ubuf) : (TI)0;
         double alpha;
         {
             double v[1] = {(double)(w * u)}, tt[1];
-            block_partials<1>(v, a.part + PS_I0 * nb, nb, s_red);
+            block_partials_lean<1>(v, a.part + PS_I0 * nb, nb, blockIdx.x, s_lean);
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
             grid_totals<1>(a.part + PS_I0 * nb, nb, tt, s_bc);
             if (bad(tt[0])) { status = CGP_ERR_NAN; break; }
@@ -629,17 +652,18 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
             d += A * p;
             r -= A * s;
             if (!precondition(r, u)) { fail = true; break; }
+            // publish u (a pure barrier), then w = A u and all three inner products in one
+            // reduction
             if (own) a.ubuf[row] = u;
             const int base = PS_I + 3 * par;
-            {
-                const TI v[2] = {r * u, r * r};
-                block_partials_t<2, TI>(v, a.part + base * nb, nb, s_redT);
-            }
             if (!grid_sync(a.sw, nb, epoch)) { fail = true; break; }
-            w = own ? ell_row<TI, TI>(s_ci, s_val, T, t, a.width, a.ubuf) : (TI)0;
-            {
-                const TI v[1] = {w * u};
-                block_partials_t<1, TI>(v, a.part + (base + 2) * nb, nb, s_redT);
+            w = own ? ell_row<TI, TI>(s_ci, s_val, T, t, wl, a.ubuf) : (TI)0;
+            if constexpr (sizeof(TI) == sizeof(double)) {
+                const double v[3] = {(double)(r * u), (double)(r * r), (double)(w * u)};
+                block_partials_lean<3>(v, a.part + base * nb, nb, blockIdx.x, s_lean);
+            } else {
+                const TI v[3] = {r * u, r * r, w * u};
+                block_partials_t<3, TI>(v, a.part + base * nb, nb, s_redT);
             }
             if (!grid_sync(a.sw, nb, epoch)) { fail = true; break; }
             {
@@ -657,8 +681,11 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
                 } else if (rho <= tgt || iters >= a.max_iter || gam == 0.0) {
                     flag = 1;
                 } else {
-                    const double bnew = gnew / gam;
-                    const double den = del - bnew * gnew / alpha;
+                    // beta = gnew / gam and beta gnew / alpha = gnew^2 / (gam alpha) from one
+                    // reciprocal: FP64 division is slow on this GPU
+                    const double rga = 1.0 / (gam * alpha);
+                    const double bnew = gnew * alpha * rga;
+                    const double den = del - gnew * gnew * rga;
                     if (den == 0.0 || gnew == 0.0) {
                         flag = 1;
                     } else {
@@ -811,6 +838,15 @@ cudaError_t schwarz_structure(cgp_ctx_s* c) {
     std::vector<int> perm(n), iperm(n);
     for (int i = 0; i < n; ++i) perm[i] = i;
     std::stable_sort(perm.begin(), perm.end(), [&](int p, int q) { return key[p] < key[q]; });
+    // within each subdomain, longest rows first: the warps of a block then see nearly uniform row
+    // lengths and their ELL loops stop at the warp's own longest row
+    {
+        const int rpb0 = (n + nb - 1) / nb;
+        auto len = [&](int i) { return H.rp[i + 1] - H.rp[i]; };
+        for (int b0 = 0; b0 < n; b0 += rpb0)
+            std::stable_sort(perm.begin() + b0, perm.begin() + std::min(n, b0 + rpb0),
+                             [&](int p, int q) { return len(p) > len(q); });
+    }
     for (int i = 0; i < n; ++i) iperm[perm[i]] = i;
     c->sz_rp_h.assign(1, 0);
     c->sz_ci_h.clear();
