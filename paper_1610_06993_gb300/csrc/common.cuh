@@ -171,24 +171,77 @@ __device__ __forceinline__ void block_partials(double (&v)[K], double* part, uns
 // Same result layout as block_partials, written for a GPU with a low FP64 rate: a shuffle tree in
 // every warp costs about 5 x 32 FP64 additions per warp and value, so instead every thread stores
 // its K values in shared memory and warp k adds up value k (blockDim.x additions in a fixed
-// order, then one shuffle tree), about a quarter of the FP64 work. Lane 0 of warp k writes
-// part[k * nblocks + bid]; a following grid barrier (which starts with __syncthreads) publishes
-// it. Needs blockDim.x >= 32 K and s_buf of K * blockDim.x doubles.
+// order, then one shuffle tree), about a quarter of the FP64 work; with fewer warps than values a
+// warp takes values k, k + warps, ... Lane 0 of the summing warp writes part[k * nblocks + bid];
+// a following grid barrier (which starts with __syncthreads) publishes it. Needs s_buf of
+// K * blockDim.x doubles.
 template <int K>
 __device__ __forceinline__ void block_partials_lean(const double (&v)[K], double* part, unsigned int nblocks,
                                                     unsigned int bid, double* s_buf) {
-    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = T >> 5;
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < K; ++k) s_buf[k * T + t] = v[k];
     __syncthreads();
-    if (warp < K) {
-        const double* b = s_buf + warp * T;
-        double acc = 0.0;
-        for (int j = lane; j < T; j += 32) acc += b[j];
+    for (int k = warp; k < K; k += nwarps) {
+        // four independent chains shorten the dependent FP64 latency; the order is fixed
+        const double* b = s_buf + k * T;
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int j = lane;
+        for (; j + 96 < T; j += 128) {
+            a0 += b[j];
+            a1 += b[j + 32];
+            a2 += b[j + 64];
+            a3 += b[j + 96];
+        }
+        for (; j < T; j += 32) a0 += b[j];
+        double acc = (a0 + a1) + (a2 + a3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) part[(size_t)warp * nblocks + bid] = acc;
+        if (lane == 0) part[(size_t)k * nblocks + bid] = acc;
+    }
+}
+
+// Sum K floats over the block in FP32 (shuffle tree in every warp, then one warp over the warp
+// sums) and store the block's totals as doubles at part[k * nblocks + bid]. Written by thread 0;
+// needs s_scratch of 32 K floats.
+template <int K>
+__device__ __forceinline__ void block_partials_f32(const float (&v0)[K], double* part, unsigned int nblocks,
+                                                   unsigned int bid, float* s_scratch) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = (blockDim.x + 31) >> 5;
+    float v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        v[k] = v0[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) s_scratch[k * 32 + warp] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            float s = lane < nwarps ? s_scratch[k * 32 + lane] : 0.f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) part[(size_t)k * nblocks + bid] = (double)s;
+        }
+    }
+}
+
+// Block partial sums of K values of the iteration type: FP32 shuffle trees for float, the lean
+// shared-memory reduction for double.
+template <int K, typename T>
+__device__ __forceinline__ void block_partials_it(const T (&v)[K], double* part, unsigned int nblocks, unsigned int bid,
+                                                  double* s_lean, float* s_f32) {
+    if constexpr (sizeof(T) == sizeof(double)) {
+        block_partials_lean<K>(v, part, nblocks, bid, s_lean);
+    } else {
+        block_partials_f32<K>(v, part, nblocks, bid, s_f32);
     }
 }
 
@@ -228,15 +281,15 @@ __device__ __forceinline__ Grp group_of(const BatchMap& m) {
 
 // After a grid barrier: every block sums the nblocks partials of each of the K slots in the same
 // fixed order, so all blocks hold bit-identical totals. Slot k's partials start at
-// part + slot[k] * nblocks. Warp k handles slot k and issues all its loads at once, so the cost
-// is about one L2 round trip. Needs blockDim.x >= 32 K and nblocks <= CGP_MAX_GRID.
+// part + slot[k] * nblocks. Warp k (mod the number of warps) handles slot k and issues all its
+// loads at once, so the cost is about one L2 round trip. Needs nblocks <= CGP_MAX_GRID.
 template <int K>
 __device__ __forceinline__ void grid_totals_at(const double* part, const int (&slot)[K], unsigned int nblocks,
                                                double (&out)[K], double* s_bcast /* [K] */) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        if (warp == k) {
+        if (warp == k % nwarps) {
             const double* p = part + (size_t)slot[k] * nblocks;
             double v[CGP_MAX_GRID / 32];
 #pragma unroll
@@ -264,10 +317,10 @@ __device__ __forceinline__ void grid_totals_at(const double* part, const int (&s
 template <int K>
 __device__ __forceinline__ void grid_totals_shared(const double* part, const int (&slot)[K], unsigned int nblocks,
                                                    double* s_bcast /* [K] */) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        if (warp == k) {
+        if (warp == k % nwarps) {
             const double* p = part + (size_t)slot[k] * nblocks;
             double v[CGP_MAX_GRID / 32];
 #pragma unroll

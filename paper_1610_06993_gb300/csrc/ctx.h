@@ -197,13 +197,14 @@ cudaError_t launch_correct(cgp_ctx_s* c, const double* ut, const double* w, doub
                            cudaStream_t s);
 cudaError_t launch_copy_pairs(const double* src, double* dst, int n, cudaStream_t s);
 
-// Cooperative launch helper: launches `func` with the shape and its single by-value argument
-// (typed, so a kernel cannot be handed the wrong argument structure).
+// Cooperative launch helper: launches `func` with the shape, `smem` bytes of dynamic shared
+// memory and its single by-value argument (typed, so a kernel cannot be handed the wrong
+// argument structure).
 template <typename Args>
-cudaError_t coop_launch(void (*func)(Args), int blocks, int threads, Args& args, cudaStream_t s) {
+cudaError_t coop_launch(void (*func)(Args), int blocks, int threads, Args& args, cudaStream_t s, size_t smem = 0) {
     void* kargs[] = {(void*)&args};
-    if (blocks == 1) return cudaLaunchKernel((const void*)func, dim3(1), dim3(threads), kargs, 0, s);
-    return cudaLaunchCooperativeKernel((const void*)func, dim3(blocks), dim3(threads), kargs, 0, s);
+    if (blocks == 1) return cudaLaunchKernel((const void*)func, dim3(1), dim3(threads), kargs, smem, s);
+    return cudaLaunchCooperativeKernel((const void*)func, dim3(blocks), dim3(threads), kargs, smem, s);
 }
 
 }  // namespace cgp

@@ -115,10 +115,10 @@ cudaError_t launch_poisson_cg(cgp_ctx_s* c, const double* b, double* x, cudaStre
     if (e != cudaSuccess) return e;
     if (c->prm.precision == CGP_MIXED) {
         auto L = single_launch(poisson_args<float>(c, b, x, sw, c->part));
-        return coop_launch(k_cg<float, 1>, c->sh_c.blocks, c->sh_c.threads, L, s);
+        return coop_launch(k_cg<float, 1>, c->sh_c.blocks, c->sh_c.threads, L, s, cg_smem<1>(c->sh_c.threads));
     }
     auto L = single_launch(poisson_args<double>(c, b, x, sw, c->part));
-    return coop_launch(k_cg<double, 1>, c->sh_c.blocks, c->sh_c.threads, L, s);
+    return coop_launch(k_cg<double, 1>, c->sh_c.blocks, c->sh_c.threads, L, s, cg_smem<1>(c->sh_c.threads));
 }
 
 cudaError_t launch_mass_cg(cgp_ctx_s* c, const double* b, double* x, cudaStream_t s) {
@@ -127,10 +127,10 @@ cudaError_t launch_mass_cg(cgp_ctx_s* c, const double* b, double* x, cudaStream_
     if (e != cudaSuccess) return e;
     if (c->prm.precision == CGP_MIXED) {
         auto L = single_launch(mass_args<float>(c, b, x, sw, c->part));
-        return coop_launch(k_cg<float, 2>, c->sh_f.blocks, c->sh_f.threads, L, s);
+        return coop_launch(k_cg<float, 2>, c->sh_f.blocks, c->sh_f.threads, L, s, cg_smem<2>(c->sh_f.threads));
     }
     auto L = single_launch(mass_args<double>(c, b, x, sw, c->part));
-    return coop_launch(k_cg<double, 2>, c->sh_f.blocks, c->sh_f.threads, L, s);
+    return coop_launch(k_cg<double, 2>, c->sh_f.blocks, c->sh_f.threads, L, s, cg_smem<2>(c->sh_f.threads));
 }
 
 cudaError_t launch_momentum_bicgstab(cgp_ctx_s* c, const double* u_in, double* x, cudaStream_t s) {
@@ -139,10 +139,10 @@ cudaError_t launch_momentum_bicgstab(cgp_ctx_s* c, const double* u_in, double* x
     if (e != cudaSuccess) return e;
     if (c->prm.precision == CGP_MIXED) {
         auto L = single_launch(momentum_args<float>(c, u_in, x, sw, c->part));
-        return coop_launch(k_bicgstab<float>, c->sh_f.blocks, c->sh_f.threads, L, s);
+        return coop_launch(k_bicgstab<float>, c->sh_f.blocks, c->sh_f.threads, L, s, bicg_smem(c->sh_f.threads));
     }
     auto L = single_launch(momentum_args<double>(c, u_in, x, sw, c->part));
-    return coop_launch(k_bicgstab<double>, c->sh_f.blocks, c->sh_f.threads, L, s);
+    return coop_launch(k_bicgstab<double>, c->sh_f.blocks, c->sh_f.threads, L, s, bicg_smem(c->sh_f.threads));
 }
 
 // ---- batched solver stages: one cooperative launch per stage for all instances ----------------
@@ -196,37 +196,43 @@ cudaError_t batch_solvers_build(cgp_batch_s* b) {
 cudaError_t batch_momentum_launch(cgp_batch_s* b, cudaStream_t s) {
     if (b->precision == CGP_MIXED) {
         auto L = table_launch<BicgArgs<float>>(b->tab_mom, b->map_f);
-        return coop_launch(k_bicgstab<float>, b->blocks_f, b->threads, L, s);
+        return coop_launch(k_bicgstab<float>, b->blocks_f, b->threads, L, s, bicg_smem(b->threads));
     }
     auto L = table_launch<BicgArgs<double>>(b->tab_mom, b->map_f);
-    return coop_launch(k_bicgstab<double>, b->blocks_f, b->threads, L, s);
+    return coop_launch(k_bicgstab<double>, b->blocks_f, b->threads, L, s, bicg_smem(b->threads));
 }
 
 cudaError_t batch_poisson_launch(cgp_batch_s* b, cudaStream_t s) {
     if (b->precision == CGP_MIXED) {
         auto L = table_launch<CgArgs<float>>(b->tab_poi, b->map_c);
-        return coop_launch(k_cg<float, 1>, b->blocks_c, b->threads, L, s);
+        return coop_launch(k_cg<float, 1>, b->blocks_c, b->threads, L, s, cg_smem<1>(b->threads));
     }
     auto L = table_launch<CgArgs<double>>(b->tab_poi, b->map_c);
-    return coop_launch(k_cg<double, 1>, b->blocks_c, b->threads, L, s);
+    return coop_launch(k_cg<double, 1>, b->blocks_c, b->threads, L, s, cg_smem<1>(b->threads));
 }
 
 cudaError_t batch_mass_launch(cgp_batch_s* b, cudaStream_t s) {
     if (b->precision == CGP_MIXED) {
         auto L = table_launch<CgArgs<float>>(b->tab_mass, b->map_f);
-        return coop_launch(k_cg<float, 2>, b->blocks_f, b->threads, L, s);
+        return coop_launch(k_cg<float, 2>, b->blocks_f, b->threads, L, s, cg_smem<2>(b->threads));
     }
     auto L = table_launch<CgArgs<double>>(b->tab_mass, b->map_f);
-    return coop_launch(k_cg<double, 2>, b->blocks_f, b->threads, L, s);
+    return coop_launch(k_cg<double, 2>, b->blocks_f, b->threads, L, s, cg_smem<2>(b->threads));
 }
 
 // Occupancy of the persistent kernels (blocks per SM at `threads`), the minimum over the family.
+// Resident blocks per SM of the generic persistent kernels at `threads` threads (the minimum over
+// all of them, with their dynamic shared memory); also raises their dynamic shared-memory limit.
 int persistent_blocks_per_sm(int threads) {
     int m = 1 << 30, v = 0;
     const void* fns[] = {(const void*)k_cg<double, 1>, (const void*)k_cg<float, 1>, (const void*)k_cg<double, 2>,
                          (const void*)k_cg<float, 2>, (const void*)k_bicgstab<double>, (const void*)k_bicgstab<float>};
-    for (const void* f : fns) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, f, threads, 0) != cudaSuccess) return 0;
+    const size_t smem[] = {cg_smem<1>(threads), cg_smem<1>(threads), cg_smem<2>(threads),
+                           cg_smem<2>(threads), bicg_smem(threads), bicg_smem(threads)};
+    for (int k = 0; k < 6; ++k) {
+        if (cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem[k]) != cudaSuccess)
+            return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fns[k], threads, smem[k]) != cudaSuccess) return 0;
         m = v < m ? v : m;
     }
     return m;
@@ -379,7 +385,7 @@ extern "C" int cgp_cg_solve_noalloc(int n, const int* rp_dev, const int* ci_dev,
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return CGP_ERR_CUDA;
             int sms = 0, occ = 0;
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CGP_ERR_CUDA;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_cg<double, 1>, 512, 0) !=
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)k_cg<double, 1>, 512, cg_smem<1>(512)) !=
                     cudaSuccess || occ < 1)
                 return CGP_ERR_CUDA;
             nd->base = (unsigned char*)p;
@@ -430,6 +436,6 @@ extern "C" int cgp_cg_solve_noalloc(int n, const int* rp_dev, const int* ci_dev,
     int blocks = (n + threads - 1) / threads;
     blocks = std::max(1, std::min(std::min(blocks, nd->num_sms), CGP_MAX_GRID));
     auto La = single_launch(a);
-    cudaError_t e = coop_launch(k_cg<double, 1>, blocks, threads, La, s);
+    cudaError_t e = coop_launch(k_cg<double, 1>, blocks, threads, La, s, cg_smem<1>(threads));
     return e == cudaSuccess ? CGP_OK : CGP_ERR_CUDA;
 }

@@ -68,12 +68,22 @@ struct CgArgs {
 };
 
 // partial-sum regions (units of nblocks doubles)
-enum { CG_P0 = 0, CG_O1 = 2, CG_I0 = 8, CG_I1 = 10 /* two buffers of 4 */, CG_I2 = 18 };
+enum { CG_P0 = 0, CG_O1 = 2, CG_I0 = 8, CG_I1 = 10 /* 3 NR */ };
 
+// Dynamic shared memory of k_cg: the lean FP64 reduction buffer, 3 NR doubles per thread.
+template <int NR>
+constexpr size_t cg_smem(int threads) {
+    return (size_t)3 * NR * threads * sizeof(double);
+}
+
+// Iteration (Chronopoulos-Gear form, two grid barriers per iteration, one of them a reduction):
+//   p = u + beta p,  s = w + beta s,  d += alpha p,  r -= alpha s,  u = D^-1 r     (local)
+//   publish u | barrier | w = A u; partials (r,u), (r,r), (w,u) | barrier
 template <typename TI, int NR>
 __global__ void __launch_bounds__(1024) k_cg(Launch<CgArgs<TI>> L) {
-    __shared__ double s_red[32 * 8];
+    extern __shared__ double s_lean[];   // [3 NR][blockDim.x]
     __shared__ double s_bc[8];
+    __shared__ float s_f32[32 * 3 * NR];
     const Grp g = group_of(L.map);
     const CgArgs<TI>& a = L.table ? L.table[g.inst] : L.single;
     const unsigned int nb = g.nb;
@@ -96,7 +106,7 @@ __global__ void __launch_bounds__(1024) k_cg(Launch<CgArgs<TI>> L) {
                 const double bi = a.b[(size_t)i * NR + c];
                 v[c] += bi * bi;
             }
-        block_partials<NR>(v, a.part + CG_P0 * nb, nb, g.bid, s_red);
+        block_partials_lean<NR>(v, a.part + CG_P0 * nb, nb, g.bid, s_lean);
         if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
         grid_totals<NR>(a.part + CG_P0 * nb, nb, bb, s_bc);
         bool any_zero = false;
@@ -115,11 +125,11 @@ __global__ void __launch_bounds__(1024) k_cg(Launch<CgArgs<TI>> L) {
 
     for (;;) {
         // ---- refinement pass: FP64 true residual, inner start r = (TI) r64, u = D^-1 r, d = 0
-        double t1[3 * NR];
+        double t1[2 * NR];
         {
-            double v[3 * NR];
+            double v[2 * NR];
 #pragma unroll
-            for (int k = 0; k < 3 * NR; ++k) v[k] = 0.0;
+            for (int k = 0; k < 2 * NR; ++k) v[k] = 0.0;
             spmv_block<NR, double, double>(rr, a.rp, a.ci, a.val64, a.x, a.lanes, [&](int i, double s0, double s1) {
                 const double acc[2] = {s0, s1};
                 const TI di = a.dinvI[i];
@@ -135,9 +145,9 @@ __global__ void __launch_bounds__(1024) k_cg(Launch<CgArgs<TI>> L) {
                     v[NR + c] += (double)(rI * uI);
                 }
             });
-            block_partials<3 * NR>(v, a.part + CG_O1 * nb, nb, g.bid, s_red);
+            block_partials_lean<2 * NR>(v, a.part + CG_O1 * nb, nb, g.bid, s_lean);
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-            grid_totals<3 * NR>(a.part + CG_O1 * nb, nb, t1, s_bc);
+            grid_totals<2 * NR>(a.part + CG_O1 * nb, nb, t1, s_bc);
         }
         bool act[NR], any = false, nan = false;
         double tgt[NR], gam[NR], alpha[NR], beta[NR];
@@ -156,19 +166,20 @@ __global__ void __launch_bounds__(1024) k_cg(Launch<CgArgs<TI>> L) {
 
         // ---- w = A u, delta = (w, u); alpha_0 = gamma_0 / delta_0
         {
-            double v[NR], t0[NR];
+            TI vv[NR];
 #pragma unroll
-            for (int c = 0; c < NR; ++c) v[c] = 0.0;
+            for (int c = 0; c < NR; ++c) vv[c] = (TI)0;
             spmv_block<NR, TI, TI>(rr, a.rp, a.ci, a.valI, a.u, a.lanes, [&](int i, TI s0, TI s1) {
                 const TI acc[2] = {s0, s1};
 #pragma unroll
                 for (int c = 0; c < NR; ++c) {
                     const size_t idx = (size_t)i * NR + c;
                     a.w[idx] = acc[c];
-                    v[c] += (double)(acc[c] * a.u[idx]);
+                    vv[c] += acc[c] * a.u[idx];
                 }
             });
-            block_partials<NR>(v, a.part + CG_I0 * nb, nb, g.bid, s_red);
+            double t0[NR];
+            block_partials_it<NR, TI>(vv, a.part + CG_I0 * nb, nb, g.bid, s_lean, s_f32);
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
             grid_totals<NR>(a.part + CG_I0 * nb, nb, t0, s_bc);
 #pragma unroll
@@ -185,10 +196,10 @@ __global__ void __launch_bounds__(1024) k_cg(Launch<CgArgs<TI>> L) {
         bool first = true;
         for (;;) {
             // ---- local update: p = u + beta p, s = w + beta s, d += alpha p, r -= alpha s, u = D^-1 r
-            {
-                TI vg[NR], vr[NR];
+            TI vg[NR], vr[NR], vd[NR];
 #pragma unroll
-                for (int c = 0; c < NR; ++c) vg[c] = vr[c] = (TI)0;
+            for (int c = 0; c < NR; ++c) vg[c] = vr[c] = vd[c] = (TI)0;
+            {
                 TI al[NR], be[NR];
 #pragma unroll
                 for (int c = 0; c < NR; ++c) {
@@ -214,58 +225,44 @@ __global__ void __launch_bounds__(1024) k_cg(Launch<CgArgs<TI>> L) {
                         vr[c] += r * r;
                     }
                 }
-                double v[2 * NR];
+            }
+            if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
+            // ---- w = A u; (r, u), (r, r), (w, u) in one reduction
+            spmv_block<NR, TI, TI>(rr, a.rp, a.ci, a.valI, a.u, a.lanes, [&](int i, TI s0, TI s1) {
+                const TI acc[2] = {s0, s1};
 #pragma unroll
                 for (int c = 0; c < NR; ++c) {
-                    v[c] = (double)vg[c];
-                    v[NR + c] = (double)vr[c];
+                    const size_t idx = (size_t)i * NR + c;
+                    a.w[idx] = acc[c];
+                    vd[c] += acc[c] * a.u[idx];
                 }
-                block_partials<2 * NR>(v, a.part + (CG_I1 + 4 * (iters & 1)) * nb, nb, g.bid, s_red);
-                if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-            }
-            // ---- w = A u, delta = (w, u)
-            double tg[2 * NR], td[NR];
+            });
+            double t3[3 * NR];
             {
-                TI vv[NR];
+                TI v[3 * NR];
 #pragma unroll
-                for (int c = 0; c < NR; ++c) vv[c] = (TI)0;
-                spmv_block<NR, TI, TI>(rr, a.rp, a.ci, a.valI, a.u, a.lanes, [&](int i, TI s0, TI s1) {
-                    const TI acc[2] = {s0, s1};
-#pragma unroll
-                    for (int c = 0; c < NR; ++c) {
-                        const size_t idx = (size_t)i * NR + c;
-                        a.w[idx] = acc[c];
-                        vv[c] += acc[c] * a.u[idx];
-                    }
-                });
-                double v[NR];
-#pragma unroll
-                for (int c = 0; c < NR; ++c) v[c] = (double)vv[c];
-                block_partials<NR>(v, a.part + CG_I2 * nb, nb, g.bid, s_red);
+                for (int c = 0; c < NR; ++c) {
+                    v[c] = vg[c];
+                    v[NR + c] = vr[c];
+                    v[2 * NR + c] = vd[c];
+                }
+                block_partials_it<3 * NR, TI>(v, a.part + CG_I1 * nb, nb, g.bid, s_lean, s_f32);
                 if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-                int slot[3 * NR];
-                double t3[3 * NR];
-#pragma unroll
-                for (int k = 0; k < 2 * NR; ++k) slot[k] = CG_I1 + 4 * (iters & 1) + k;
-#pragma unroll
-                for (int k = 0; k < NR; ++k) slot[2 * NR + k] = CG_I2 + k;
-                grid_totals_at<3 * NR>(a.part, slot, nb, t3, s_bc);
-#pragma unroll
-                for (int k = 0; k < 2 * NR; ++k) tg[k] = t3[k];
-#pragma unroll
-                for (int k = 0; k < NR; ++k) td[k] = t3[2 * NR + k];
+                grid_totals<3 * NR>(a.part + CG_I1 * nb, nb, t3, s_bc);
             }
             iters += 1;
             first = false;
             bool more = false;
 #pragma unroll
             for (int c = 0; c < NR; ++c) {
-                nan |= bad(tg[c]) | bad(tg[NR + c]) | bad(td[c]);
-                if (act[c] && tg[NR + c] <= tgt[c]) act[c] = false;
+                const double gnew = t3[c], rho = t3[NR + c], del = t3[2 * NR + c];
+                nan |= bad(gnew) | bad(rho) | bad(del);
+                if (act[c] && rho <= tgt[c]) act[c] = false;
                 if (act[c]) {
-                    const double gnew = tg[c];
-                    const double bnew = gnew / gam[c];
-                    const double den = td[c] - bnew * gnew / alpha[c];
+                    // beta = gnew / gam and beta gnew / alpha from one reciprocal
+                    const double rga = 1.0 / (gam[c] * alpha[c]);
+                    const double bnew = gnew * alpha[c] * rga;
+                    const double den = del - gnew * gnew * rga;
                     if (den != 0.0 && gam[c] != 0.0) {
                         beta[c] = bnew;
                         alpha[c] = gnew / den;
@@ -331,12 +328,25 @@ struct BicgArgs {
     int* st_barrier;
 };
 
-enum { BI_P0 = 0, BI_O1 = 2, BI_B2 = 6, BI_B3 = 8, BI_B4 = 10, BI_B5 = 14 };
+enum { BI_P0 = 0, BI_O1 = 2, BI_B2 = 6, BI_B4 = 8 /* 10 slots */ };
 
+// Dynamic shared memory of k_bicgstab: the lean FP64 reduction buffer, 10 doubles per thread.
+constexpr size_t bicg_smem(int threads) { return (size_t)10 * threads * sizeof(double); }
+
+// Iteration, per right-hand side c (four grid barriers, two of them reductions):
+//   p = r + beta (p - omega v),  y = D^-1 p                      (fused with the r update below)
+//   publish y | barrier | v = A y; sigma = (rh, v) | barrier;  alpha = rho / sigma
+//   s = r - alpha v,  z = D^-1 s,  d += alpha y
+//   publish z | barrier | t = A z; (t, s), (t, t), (rh, t), (rh, s), (s, s) | barrier
+//   omega = (t, s) / (t, t);  d += omega z,  r = s - omega t
+//   rho' = (rh, s) - omega (rh, t),  (r, r) = (s, s) - 2 omega (t, s) + omega^2 (t, t)
+// The next rho and ||r||^2 follow from inner products of s and t taken in the same reduction
+// (exact identities for r = s - omega t), which saves the fifth barrier of the textbook form.
 template <typename TI>
 __global__ void __launch_bounds__(1024) k_bicgstab(Launch<BicgArgs<TI>> L) {
-    __shared__ double s_red[32 * 8];
-    __shared__ double s_bc[8];
+    extern __shared__ double s_lean[];   // [10][blockDim.x]
+    __shared__ double s_bc[10];
+    __shared__ float s_f32[32 * 10];
     const Grp g = group_of(L.map);
     const BicgArgs<TI>& a = L.table ? L.table[g.inst] : L.single;
     const unsigned int nb = g.nb;
@@ -367,7 +377,7 @@ __global__ void __launch_bounds__(1024) k_bicgstab(Launch<BicgArgs<TI>> L) {
             v[0] += b0 * b0;
             v[1] += b1 * b1;
         }
-        block_partials<2>(v, a.part + BI_P0 * nb, nb, g.bid, s_red);
+        block_partials_lean<2>(v, a.part + BI_P0 * nb, nb, g.bid, s_lean);
         if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
         grid_totals<2>(a.part + BI_P0 * nb, nb, bb, s_bc);
         if (bb[0] == 0.0 || bb[1] == 0.0) {
@@ -403,7 +413,7 @@ __global__ void __launch_bounds__(1024) k_bicgstab(Launch<BicgArgs<TI>> L) {
                     v[2 + c] += (double)(rI * rI);
                 }
             });
-            block_partials<4>(v, a.part + BI_O1 * nb, nb, g.bid, s_red);
+            block_partials_lean<4>(v, a.part + BI_O1 * nb, nb, g.bid, s_lean);
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
             grid_totals<4>(a.part + BI_O1 * nb, nb, t1, s_bc);
         }
@@ -422,13 +432,12 @@ __global__ void __launch_bounds__(1024) k_bicgstab(Launch<BicgArgs<TI>> L) {
         if (outer >= a.max_outer || iters >= a.max_iter) { status = CGP_ERR_NOT_CONVERGED; break; }
 
         bool first = true;
+        TI om[2] = {(TI)0, (TI)0};
         for (;;) {
-            TI al[2], om[2], be[2];
-            // ---- p = r + beta (p - omega v), y = D^-1 p
-            for (int c = 0; c < 2; ++c) {
-                om[c] = (TI)omega[c];
-                be[c] = (TI)beta[c];
-            }
+            TI al[2], be[2];
+            // ---- (previous omega) d += omega z, r = s - omega t; then p = r + beta (p - omega v),
+            //      y = D^-1 p
+            for (int c = 0; c < 2; ++c) be[c] = (TI)beta[c];
             for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
                 TI d0, d1;
                 load2(a.dinvI, i, d0, d1);
@@ -436,7 +445,14 @@ __global__ void __launch_bounds__(1024) k_bicgstab(Launch<BicgArgs<TI>> L) {
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     const size_t idx = 2 * (size_t)i + c;
-                    const TI r = a.r[idx];
+                    TI r;
+                    if (first) {
+                        r = a.r[idx];
+                    } else {
+                        a.d[idx] += om[c] * a.z[idx];
+                        r = a.s[idx] - om[c] * a.t[idx];
+                        a.r[idx] = r;
+                    }
                     const TI p = first ? r : r + be[c] * (a.p[idx] - om[c] * a.v[idx]);
                     a.p[idx] = p;
                     a.y[idx] = dd[c] * p;
@@ -456,8 +472,8 @@ __global__ void __launch_bounds__(1024) k_bicgstab(Launch<BicgArgs<TI>> L) {
                         vs[c] += a.rh[idx] * vv;
                     }
                 });
-                double v[2] = {(double)vs[0], (double)vs[1]}, ts[2];
-                block_partials<2>(v, a.part + BI_B2 * nb, nb, g.bid, s_red);
+                double ts[2];
+                block_partials_it<2, TI>(vs, a.part + BI_B2 * nb, nb, g.bid, s_lean, s_f32);
                 if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
                 grid_totals<2>(a.part + BI_B2 * nb, nb, ts, s_bc);
                 for (int c = 0; c < 2; ++c) {
@@ -467,30 +483,26 @@ __global__ void __launch_bounds__(1024) k_bicgstab(Launch<BicgArgs<TI>> L) {
                     al[c] = (TI)alpha[c];
                 }
             }
-            // ---- s = r - alpha v, z = D^-1 s, d += alpha y, (s, s)
-            {
-                TI vs[2] = {(TI)0, (TI)0};
-                for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
-                    TI d0, d1;
-                    load2(a.dinvI, i, d0, d1);
-                    const TI dd[2] = {d0, d1};
+            // ---- s = r - alpha v, z = D^-1 s, d += alpha y
+            for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
+                TI d0, d1;
+                load2(a.dinvI, i, d0, d1);
+                const TI dd[2] = {d0, d1};
 #pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const size_t idx = 2 * (size_t)i + c;
-                        const TI s = a.r[idx] - al[c] * a.v[idx];
-                        a.s[idx] = s;
-                        a.z[idx] = dd[c] * s;
-                        a.d[idx] += al[c] * a.y[idx];
-                        vs[c] += s * s;
-                    }
+                for (int c = 0; c < 2; ++c) {
+                    const size_t idx = 2 * (size_t)i + c;
+                    const TI s = a.r[idx] - al[c] * a.v[idx];
+                    a.s[idx] = s;
+                    a.z[idx] = dd[c] * s;
+                    a.d[idx] += al[c] * a.y[idx];
                 }
-                double v[2] = {(double)vs[0], (double)vs[1]};
-                block_partials<2>(v, a.part + BI_B3 * nb, nb, g.bid, s_red);
-                if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
             }
-            // ---- t = A z, omega = (t, s) / (t, t)
+            if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
+            // ---- t = A z; (t, s), (t, t), (rh, t), (rh, s), (s, s) in one reduction
             {
-                TI vts[2] = {(TI)0, (TI)0}, vtt[2] = {(TI)0, (TI)0};
+                TI q[10];
+#pragma unroll
+                for (int k = 0; k < 10; ++k) q[k] = (TI)0;
                 spmv_block<2, TI, TI>(rr, a.rp, a.ci, a.valI, a.z, a.lanes, [&](int i, TI s0, TI s1) {
                     const TI acc[2] = {s0, s1};
 #pragma unroll
@@ -498,71 +510,64 @@ __global__ void __launch_bounds__(1024) k_bicgstab(Launch<BicgArgs<TI>> L) {
                         const size_t idx = 2 * (size_t)i + c;
                         const TI tv = masked(i, c, acc[c], a.z);
                         a.t[idx] = tv;
-                        vts[c] += tv * a.s[idx];
-                        vtt[c] += tv * tv;
+                        const TI sv = a.s[idx], hv = a.rh[idx];
+                        q[c] += tv * sv;
+                        q[2 + c] += tv * tv;
+                        q[4 + c] += hv * tv;
+                        q[6 + c] += hv * sv;
+                        q[8 + c] += sv * sv;
                     }
                 });
-                double v[4] = {(double)vts[0], (double)vts[1], (double)vtt[0], (double)vtt[1]}, t4[4], tss[2];
-                block_partials<4>(v, a.part + BI_B4 * nb, nb, g.bid, s_red);
+                double t10[10];
+                block_partials_it<10, TI>(q, a.part + BI_B4 * nb, nb, g.bid, s_lean, s_f32);
                 if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
                 {
-                    const int slot[6] = {BI_B4, BI_B4 + 1, BI_B4 + 2, BI_B4 + 3, BI_B3, BI_B3 + 1};
-                    double t6[6];
-                    grid_totals_at<6>(a.part, slot, nb, t6, s_bc);
-                    for (int k = 0; k < 4; ++k) t4[k] = t6[k];
-                    tss[0] = t6[4];
-                    tss[1] = t6[5];
-                }
-                for (int c = 0; c < 2; ++c) {
-                    nan |= bad(t4[c]) | bad(t4[2 + c]) | bad(tss[c]);
-                    if (act[c] && tss[c] <= tgt[c]) {          // converged at the half step
-                        act[c] = false;
-                        omega[c] = 0.0;
-                    } else if (act[c] && t4[2 + c] != 0.0) {
-                        omega[c] = t4[c] / t4[2 + c];
-                    } else {
-                        act[c] = false;
-                        omega[c] = 0.0;
-                    }
-                    om[c] = (TI)omega[c];
-                }
-            }
-            // ---- d += omega z, r = s - omega t, rho' = (rh, r), (r, r)
-            {
-                TI vr[2] = {(TI)0, (TI)0}, vq[2] = {(TI)0, (TI)0};
-                for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
+                    int slot[10];
 #pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const size_t idx = 2 * (size_t)i + c;
-                        a.d[idx] += om[c] * a.z[idx];
-                        const TI r = a.s[idx] - om[c] * a.t[idx];
-                        a.r[idx] = r;
-                        vr[c] += a.rh[idx] * r;
-                        vq[c] += r * r;
-                    }
+                    for (int k = 0; k < 10; ++k) slot[k] = BI_B4 + k;
+                    grid_totals_at<10>(a.part, slot, nb, t10, s_bc);
                 }
-                double v[4] = {(double)vr[0], (double)vr[1], (double)vq[0], (double)vq[1]}, t5[4];
-                block_partials<4>(v, a.part + BI_B5 * nb, nb, g.bid, s_red);
-                if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-                grid_totals<4>(a.part + BI_B5 * nb, nb, t5, s_bc);
                 iters += 1;
                 first = false;
                 bool more = false;
                 for (int c = 0; c < 2; ++c) {
-                    nan |= bad(t5[c]) | bad(t5[2 + c]);
-                    if (act[c] && t5[2 + c] <= tgt[c]) act[c] = false;
+                    const double ts = t10[c], tt = t10[2 + c], ht = t10[4 + c], hs = t10[6 + c], ss = t10[8 + c];
+                    nan |= bad(ts) | bad(tt) | bad(ht) | bad(hs) | bad(ss);
+                    if (act[c] && ss <= tgt[c]) {          // converged at the half step
+                        act[c] = false;
+                        omega[c] = 0.0;
+                    } else if (act[c] && tt != 0.0) {
+                        omega[c] = ts / tt;
+                    } else {
+                        act[c] = false;
+                        omega[c] = 0.0;
+                    }
                     if (act[c]) {
-                        if (t5[c] != 0.0 && omega[c] != 0.0 && rho[c] != 0.0) {
-                            beta[c] = (t5[c] / rho[c]) * (alpha[c] / omega[c]);
-                            rho[c] = t5[c];
+                        const double rnew = hs - omega[c] * ht;
+                        const double rr2 = ss - 2.0 * omega[c] * ts + omega[c] * omega[c] * tt;
+                        if (rr2 <= tgt[c]) {
+                            act[c] = false;
+                        } else if (rnew != 0.0 && omega[c] != 0.0 && rho[c] != 0.0) {
+                            beta[c] = (rnew / rho[c]) * (alpha[c] / omega[c]);
+                            rho[c] = rnew;
                         } else {
                             act[c] = false;            // breakdown: restart in the next pass
                         }
                     }
                     if (!act[c]) beta[c] = 0.0;
+                    om[c] = (TI)omega[c];
                     more |= act[c];
                 }
-                if (nan || !more || iters >= a.max_iter) break;
+                if (nan || !more || iters >= a.max_iter) {
+                    // last update of this pass: d += omega z
+                    for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb)
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            const size_t idx = 2 * (size_t)i + c;
+                            a.d[idx] += om[c] * a.z[idx];
+                        }
+                    break;
+                }
             }
         }
         if (nan) { status = CGP_ERR_NAN; break; }
