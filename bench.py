@@ -185,7 +185,7 @@ def spmv_hbm(L, Flow, dev, flush, stream, reps: int = 10):
     prob = ci.bfs_problem(400.0, 0.005, 2)
     peak, kind = peaks()
     best = None
-    for fmt, kname in ((2, "k_spmv_probe<2> (CSR, autotuned lanes)"), (1, "k_spmv_sell2 (sliced ELL 32/256)")):
+    for fmt, kname in ((2, "k_spmv_probe<2> (CSR, autotuned lanes)"), (1, "k_spmv_sell2 (sliced ELL, 32-row slices)")):
         f = Flow(coarse, prob, device=dev, spmv_format=fmt)
         L.cgp_autotune(f.ctx, stream)
         info = L.cgp_mesh_info(f.ctx)
@@ -413,25 +413,30 @@ def run_batch(args):
     e1.synchronize()
     t_batch = e0.elapsed_time(e1)
     it_batch = [s.poisson_iters for s in b.stats(check=True)]
-    # plain: FP64 contexts on the same right-hand sides, zero initial guess, one after another
-    t_plain, it_plain = 0.0, []
-    for f, u0, (m, p) in zip(flows, prev_u, cases):
-        g = Flow(m, p, precision=L.CGP_FP64, rtol=args.rtol, device=dev)
-        bc = torch.empty_like(f.pc)
-        ut = torch.empty_like(f.u)
-        # the right-hand side of the batched instance's latest step, rebuilt on the FP64 context
-        L.cgp_assemble(g.ctx, u0, stream)
-        L.cgp_momentum_solve(g.ctx, u0, ut, stream)
-        L.cgp_restrict(g.ctx, ut, bc, stream)
-        x = torch.zeros_like(f.pc)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        L.cgp_poisson_solve(g.ctx, bc, x, stream)
-        e1.record(stream)
-        e1.synchronize()
-        t_plain += e0.elapsed_time(e1)
-        it_plain.append(g.stats(check=True).poisson_iters)
-        g.close()
+    # plain: FP64 contexts on the same right-hand sides, zero initial guess, one after another;
+    # coarse_solver 5 is the paper's Jacobi-preconditioned CG, 0 this library's default (two-level
+    # Schwarz preconditioned CG)
+    plain = {}
+    for solver in (5, 0):
+        t_plain, it_plain = 0.0, []
+        for f, u0, (m, p) in zip(flows, prev_u, cases):
+            g = Flow(m, p, precision=L.CGP_FP64, rtol=args.rtol, device=dev, coarse_solver=solver)
+            bc = torch.empty_like(f.pc)
+            ut = torch.empty_like(f.u)
+            # the right-hand side of the batched instance's latest step, rebuilt on the FP64 context
+            L.cgp_assemble(g.ctx, u0, stream)
+            L.cgp_momentum_solve(g.ctx, u0, ut, stream)
+            L.cgp_restrict(g.ctx, ut, bc, stream)
+            x = torch.zeros_like(f.pc)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            L.cgp_poisson_solve(g.ctx, bc, x, stream)
+            e1.record(stream)
+            e1.synchronize()
+            t_plain += e0.elapsed_time(e1)
+            it_plain.append(g.stats(check=True).poisson_iters)
+            g.close()
+        plain[solver] = (t_plain, it_plain)
 
     line = {
         "metric": METRIC, "value": ws * n_inst * 1000.0 / ms, "unit": "instance-steps/s", "n_gpus": ws,
@@ -442,10 +447,14 @@ def run_batch(args):
                                f"{sum(f.info.n_fine for f in flows)} fine), Re U[100,1000], dt=0.005, l=1",
                    "rtol": args.rtol, "precision": args.precision, "graph": "one CUDA graph per step",
                    "l2": "flushed between timed steps (512 MB write, then 256 MB read)", "blocks": b.blocks},
-        "coarse_solves_per_s": {"batched_warm": n_inst * 1000.0 / t_batch, "plain_fp64_zero_sequential":
-                                n_inst * 1000.0 / t_plain, "ratio": t_plain / t_batch,
+        "coarse_solves_per_s": {"batched_warm": n_inst * 1000.0 / t_batch,
+                                "plain_fp64_jacobi_zero_sequential": n_inst * 1000.0 / plain[5][0],
+                                "ratio": plain[5][0] / t_batch,
+                                "plain_fp64_schwarz_zero_sequential": n_inst * 1000.0 / plain[0][0],
+                                "ratio_vs_schwarz": plain[0][0] / t_batch,
                                 "iters_batched_mean": statistics.mean(it_batch),
-                                "iters_plain_mean": statistics.mean(it_plain)},
+                                "iters_plain_jacobi_mean": statistics.mean(plain[5][1]),
+                                "iters_plain_schwarz_mean": statistics.mean(plain[0][1])},
         "gpu_launches": None, "clocks": clk.summary(),
     }
     b.close()

@@ -247,24 +247,43 @@ __global__ void k_sell_fill(int total, const int* __restrict__ src, const double
 
 // Sliced-ELL SpMV, two interleaved right-hand sides: one warp per 32-row slice, slot k of all 32
 // rows contiguous, so every value and column load of a warp is one coalesced 128/256-byte access.
+// Slots are taken four at a time, all column and value loads of a group issued before its x
+// gathers; the matrix is streamed with the evict-first hint and y written the same way, so the
+// gathered x keeps its place in L2.
 __global__ void __launch_bounds__(256) k_spmv_sell2(int nslices, const int* __restrict__ ptr, const int* __restrict__ col,
                                                     const double* __restrict__ val, const int* __restrict__ perm,
                                                     const double* __restrict__ x, double* __restrict__ y) {
     const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (s >= nslices) return;
     const int base = ptr[s], w = (ptr[s + 1] - base) >> 5;
+    const double2* x2 = reinterpret_cast<const double2*>(x);
     double a0 = 0.0, a1 = 0.0;
-#pragma unroll 4
-    for (int k = 0; k < w; ++k) {
+    int k = 0;
+    for (; k + 4 <= w; k += 4) {
+        int j[4];
+        double v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int p = base + ((k + q) << 5) + lane;
+            j[q] = __ldcs(col + p);
+            v[q] = __ldcs(val + p);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double2 xv = __ldg(x2 + j[q]);
+            a0 += v[q] * xv.x;
+            a1 += v[q] * xv.y;
+        }
+    }
+    for (; k < w; ++k) {
         const int p = base + (k << 5) + lane;
-        const int j = __ldg(col + p);
-        const double v = __ldg(val + p);
-        const double2 xv = __ldg(reinterpret_cast<const double2*>(x) + j);
+        const double2 xv = __ldg(x2 + __ldcs(col + p));
+        const double v = __ldcs(val + p);
         a0 += v * xv.x;
         a1 += v * xv.y;
     }
     const int r = perm[(s << 5) + lane];
-    if (r >= 0) reinterpret_cast<double2*>(y)[r] = make_double2(a0, a1);
+    if (r >= 0) __stcs(reinterpret_cast<double2*>(y) + r, make_double2(a0, a1));
 }
 
 }  // namespace
