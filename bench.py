@@ -300,6 +300,11 @@ def run_gpu(args):
         per_iter = 12 * nnz + 60 * n
     else:
         per_iter = 8 * nnz + 32 * n
+    if f.info.coarse_kernel in (3, 4):
+        # Schwarz preconditioner: degree - 1 Chebyshev products with the subdomain matrices
+        # (FP32 values + columns, read and write of the iterate) per application
+        deg = args.precond_degree if args.precond_degree > 0 else 6
+        per_iter += (deg - 1) * (8 * nnz + 8 * n)
     per_pass = 12 * nnz + 20 * n + 8 * n       # FP64 true residual (+ x update) per refinement pass
     alg_bytes = it * per_iter + (outer + 1) * per_pass
     pms = statistics.mean(poi_ms)
@@ -332,8 +337,10 @@ def run_gpu(args):
         "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": measured_traffic(kname),
                      "alg_bytes_per_launch": alg_bytes,
-                     "note": "coarse matrix + vectors (~9 MB) live on chip and in L2: latency- and FP64-bound, not "
-                             "HBM-bound; achieved counts algorithmic bytes per CG iteration x iterations"},
+                     "note": "coarse matrix + vectors live in shared memory, registers and L2 (ncu: 0.1 % DRAM "
+                             "throughput); the kernel is bound by barrier latency, so achieved is an effective rate: "
+                             "the bytes a memory-streaming CG would move per iteration x iterations / time",
+                     "latency": {"us_per_iter": 1000.0 * pms / max(it, 1.0), "grid_barriers_per_iter": 3}},
         "e2e": {"value": 1000.0 / statistics.mean(e2e_ms), "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d},
         "gpu_launches": launches_per_step * args.steps,
