@@ -62,7 +62,7 @@ typedef struct cgp_ctx_s* cgp_ctx;
  * Krylov iterations of one solve. max_outer: cap on refinement passes (0 = default 30).
  * spmv_lanes: lanes per CSR row in the SpMV inner loops (0 = let cgp_autotune()/default decide;
  * otherwise 1, 2, 4, 8, 16 or 32). block_threads: threads per block of the generic persistent
- * kernels (0 = default 512, else 256..1024). coarse_solver: 0 = automatic (kernel 3 whenever the
+ * kernels (0 = default 512, else 256..512, a multiple of 32). coarse_solver: 0 = automatic (kernel 3 whenever the
  * coarse matrix slice of a block fits in shared memory, else the generic kernel), 1 = the generic
  * Jacobi-preconditioned classical CG kernel, 2 = the on-chip Jacobi-preconditioned pipelined CG
  * kernel in CGP_FP64 (CGP_MIXED falls back to kernel 5), 3 = on-chip classical CG with a

@@ -89,7 +89,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     if (P.max_iter <= 0) P.max_iter = 20000;
     if (P.max_outer <= 0) P.max_outer = 30;
     if (P.block_threads == 0) P.block_threads = 512;
-    if (P.block_threads < 256 || P.block_threads > 1024 || (P.block_threads & 31)) return CGP_ERR_ARG;
+    if (P.block_threads < 256 || P.block_threads > 512 || (P.block_threads & 31)) return CGP_ERR_ARG;
     if (P.spmv_lanes != 0 && (P.spmv_lanes < 1 || P.spmv_lanes > 32 || (P.spmv_lanes & (P.spmv_lanes - 1))))
         return CGP_ERR_ARG;
     TRY(build_host_mesh(d, P.levels, c->hm));

@@ -7,12 +7,72 @@ namespace cgp {
 
 namespace {
 
+// y = A x over the block's rows with one thread per row: two rows per thread in flight, the
+// column and value loads of each row issued four at a time before their x gathers, so a row pair
+// costs about three dependent memory round trips per four entries instead of two per entry. x is
+// written by other blocks during the launch, so it is read with ordinary (coherent) loads; the
+// matrix is read-only and goes through the read-only path.
+template <int NR, typename TV, typename TX, typename Emit>
+__device__ __forceinline__ void spmv_rows(RowRange rr, const int* __restrict__ rp, const int* __restrict__ ci,
+                                          const TV* __restrict__ val, const TX* x, Emit emit) {
+    const int T = blockDim.x;
+    for (int i0 = rr.r0 + threadIdx.x; i0 < rr.r1; i0 += 2 * T) {
+        const int i1 = i0 + T;
+        const bool h1 = i1 < rr.r1;
+        const int ka = __ldg(rp + i0), na = __ldg(rp + i0 + 1) - ka;
+        const int kb = h1 ? __ldg(rp + i1) : 0, nbr = h1 ? __ldg(rp + i1 + 1) - kb : 0;
+        const int m = max(na, nbr);
+        TX a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+        for (int k = 0; k < m; k += 4) {
+            int ja[4], jb[4];
+            TX va[4], vb[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool ia = k + q < na, ib = k + q < nbr;
+                ja[q] = ia ? __ldg(ci + ka + k + q) : -1;
+                va[q] = ia ? (TX)__ldg(val + ka + k + q) : (TX)0;
+                jb[q] = ib ? __ldg(ci + kb + k + q) : -1;
+                vb[q] = ib ? (TX)__ldg(val + kb + k + q) : (TX)0;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (ja[q] >= 0) {
+                    if (NR == 1) {
+                        a0 += va[q] * x[ja[q]];
+                    } else {
+                        TX x0, x1;
+                        load2(x, ja[q], x0, x1);
+                        a0 += va[q] * x0;
+                        a1 += va[q] * x1;
+                    }
+                }
+                if (jb[q] >= 0) {
+                    if (NR == 1) {
+                        b0 += vb[q] * x[jb[q]];
+                    } else {
+                        TX x0, x1;
+                        load2(x, jb[q], x0, x1);
+                        b0 += vb[q] * x0;
+                        b1 += vb[q] * x1;
+                    }
+                }
+            }
+        }
+        emit(i0, a0, a1);
+        if (h1) emit(i1, b0, b1);
+    }
+}
+
 // y = A x over the block's rows, `lanes` consecutive threads per row. emit(row, acc0, acc1) runs
 // on the first lane of each row group. Every thread of the block runs the same number of passes
-// so the group shuffles always see full warps.
+// so the group shuffles always see full warps. One lane per row takes the spmv_rows path.
 template <int NR, typename TV, typename TX, typename Emit>
 __device__ __forceinline__ void spmv_block(RowRange rr, const int* __restrict__ rp, const int* __restrict__ ci,
                                            const TV* __restrict__ val, const TX* x, int lanes, Emit emit) {
+    if (lanes == 1) {
+        spmv_rows<NR, TV, TX>(rr, rp, ci, val, x, emit);
+        return;
+    }
     const int groups = blockDim.x / lanes;
     const int g = threadIdx.x / lanes;
     const int l = threadIdx.x & (lanes - 1);
@@ -80,10 +140,12 @@ constexpr size_t cg_smem(int threads) {
 //   p = u + beta p,  s = w + beta s,  d += alpha p,  r -= alpha s,  u = D^-1 r     (local)
 //   publish u | barrier | w = A u; partials (r,u), (r,r), (w,u) | barrier
 template <typename TI, int NR>
-__global__ void __launch_bounds__(1024) k_cg(Launch<CgArgs<TI>> L) {
+__global__ void __launch_bounds__(512) k_cg(Launch<CgArgs<TI>> L) {
     extern __shared__ double s_lean[];   // [3 NR][blockDim.x]
     __shared__ double s_bc[8];
     __shared__ float s_f32[32 * 3 * NR];
+    __shared__ double s_sc[2 * NR];
+    __shared__ int s_fl[2];
     const Grp g = group_of(L.map);
     const CgArgs<TI>& a = L.table ? L.table[g.inst] : L.single;
     const unsigned int nb = g.nb;
@@ -196,6 +258,7 @@ __global__ void __launch_bounds__(1024) k_cg(Launch<CgArgs<TI>> L) {
         bool first = true;
         for (;;) {
             // ---- local update: p = u + beta p, s = w + beta s, d += alpha p, r -= alpha s, u = D^-1 r
+            // (two rows per thread: all loads of both rows before the first store)
             TI vg[NR], vr[NR], vd[NR];
 #pragma unroll
             for (int c = 0; c < NR; ++c) vg[c] = vr[c] = vd[c] = (TI)0;
@@ -206,23 +269,43 @@ __global__ void __launch_bounds__(1024) k_cg(Launch<CgArgs<TI>> L) {
                     al[c] = (TI)alpha[c];
                     be[c] = (TI)beta[c];
                 }
-                for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
-                    const TI di = a.dinvI[i];
+                for (int i0 = rr.r0 + threadIdx.x; i0 < rr.r1; i0 += 2 * tpb) {
+                    const int i1 = i0 + tpb;
+                    const bool h1 = i1 < rr.r1;
+                    const int row[2] = {i0, h1 ? i1 : i0};
+                    TI di[2], uo[2][NR], wo[2][NR], po[2][NR], so[2][NR], dd[2][NR], ro[2][NR];
 #pragma unroll
-                    for (int c = 0; c < NR; ++c) {
-                        const size_t idx = (size_t)i * NR + c;
-                        const TI uo = a.u[idx], wo = a.w[idx];
-                        const TI p = first ? uo : uo + be[c] * a.p[idx];
-                        const TI s = first ? wo : wo + be[c] * a.s[idx];
-                        a.p[idx] = p;
-                        a.s[idx] = s;
-                        a.d[idx] += al[c] * p;
-                        const TI r = a.r[idx] - al[c] * s;
-                        a.r[idx] = r;
-                        const TI u = di * r;
-                        a.u[idx] = u;
-                        vg[c] += r * u;
-                        vr[c] += r * r;
+                    for (int h = 0; h < 2; ++h) {
+                        di[h] = a.dinvI[row[h]];
+#pragma unroll
+                        for (int c = 0; c < NR; ++c) {
+                            const size_t idx = (size_t)row[h] * NR + c;
+                            uo[h][c] = a.u[idx];
+                            wo[h][c] = a.w[idx];
+                            po[h][c] = first ? (TI)0 : a.p[idx];
+                            so[h][c] = first ? (TI)0 : a.s[idx];
+                            dd[h][c] = a.d[idx];
+                            ro[h][c] = a.r[idx];
+                        }
+                    }
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (h == 1 && !h1) break;
+#pragma unroll
+                        for (int c = 0; c < NR; ++c) {
+                            const size_t idx = (size_t)row[h] * NR + c;
+                            const TI p = uo[h][c] + be[c] * po[h][c];
+                            const TI sv = wo[h][c] + be[c] * so[h][c];
+                            a.p[idx] = p;
+                            a.s[idx] = sv;
+                            a.d[idx] = dd[h][c] + al[c] * p;
+                            const TI r = ro[h][c] - al[c] * sv;
+                            a.r[idx] = r;
+                            const TI u = di[h] * r;
+                            a.u[idx] = u;
+                            vg[c] += r * u;
+                            vr[c] += r * r;
+                        }
                     }
                 }
             }
@@ -237,7 +320,6 @@ __global__ void __launch_bounds__(1024) k_cg(Launch<CgArgs<TI>> L) {
                     vd[c] += acc[c] * a.u[idx];
                 }
             });
-            double t3[3 * NR];
             {
                 TI v[3 * NR];
 #pragma unroll
@@ -248,32 +330,52 @@ __global__ void __launch_bounds__(1024) k_cg(Launch<CgArgs<TI>> L) {
                 }
                 block_partials_it<3 * NR, TI>(v, a.part + CG_I1 * nb, nb, g.bid, s_lean, s_f32);
                 if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-                grid_totals<3 * NR>(a.part + CG_I1 * nb, nb, t3, s_bc);
+                int slot[3 * NR];
+#pragma unroll
+                for (int k = 0; k < 3 * NR; ++k) slot[k] = CG_I1 + k;
+                grid_totals_shared<3 * NR>(a.part, slot, nb, s_bc);
             }
             iters += 1;
             first = false;
-            bool more = false;
+            // scalar recurrences once per block (thread 0; FP64 division is slow on this GPU),
+            // broadcast through shared memory
+            if (threadIdx.x == 0) {
+                bool more = false, bad_any = false;
+#pragma unroll
+                for (int c = 0; c < NR; ++c) {
+                    const double gnew = s_bc[c], rho = s_bc[NR + c], del = s_bc[2 * NR + c];
+                    bad_any |= bad(gnew) | bad(rho) | bad(del);
+                    if (act[c] && rho <= tgt[c]) act[c] = false;
+                    if (act[c]) {
+                        // beta = gnew / gam and beta gnew / alpha from one reciprocal
+                        const double rga = 1.0 / (gam[c] * alpha[c]);
+                        const double bnew = gnew * alpha[c] * rga;
+                        const double den = del - gnew * gnew * rga;
+                        if (den != 0.0 && gam[c] != 0.0) {
+                            beta[c] = bnew;
+                            alpha[c] = gnew / den;
+                            gam[c] = gnew;
+                        } else {
+                            act[c] = false;
+                        }
+                    }
+                    if (!act[c]) alpha[c] = beta[c] = 0.0;
+                    more |= act[c];
+                    s_sc[c] = alpha[c];
+                    s_sc[NR + c] = beta[c];
+                }
+                s_fl[0] = more;
+                s_fl[1] = bad_any;
+            }
+            __syncthreads();
 #pragma unroll
             for (int c = 0; c < NR; ++c) {
-                const double gnew = t3[c], rho = t3[NR + c], del = t3[2 * NR + c];
-                nan |= bad(gnew) | bad(rho) | bad(del);
-                if (act[c] && rho <= tgt[c]) act[c] = false;
-                if (act[c]) {
-                    // beta = gnew / gam and beta gnew / alpha from one reciprocal
-                    const double rga = 1.0 / (gam[c] * alpha[c]);
-                    const double bnew = gnew * alpha[c] * rga;
-                    const double den = del - gnew * gnew * rga;
-                    if (den != 0.0 && gam[c] != 0.0) {
-                        beta[c] = bnew;
-                        alpha[c] = gnew / den;
-                        gam[c] = gnew;
-                    } else {
-                        act[c] = false;
-                    }
-                }
-                if (!act[c]) alpha[c] = beta[c] = 0.0;
-                more |= act[c];
+                alpha[c] = s_sc[c];
+                beta[c] = s_sc[NR + c];
             }
+            const bool more = s_fl[0] != 0;
+            nan |= s_fl[1] != 0;
+            __syncthreads();   // s_sc / s_fl read by all before thread 0 writes them again
             if (nan || !more || iters >= a.max_iter) break;
         }
         if (nan) { status = CGP_ERR_NAN; break; }
@@ -333,7 +435,8 @@ enum { BI_P0 = 0, BI_O1 = 2, BI_B2 = 6, BI_B4 = 8 /* 10 slots */ };
 // Dynamic shared memory of k_bicgstab: the lean FP64 reduction buffer, 10 doubles per thread.
 constexpr size_t bicg_smem(int threads) { return (size_t)10 * threads * sizeof(double); }
 
-// Iteration, per right-hand side c (four grid barriers, two of them reductions):
+// Iteration, per right-hand side c (four grid barriers, two of them reductions; the scalar
+// recurrences run on thread 0 and are broadcast through shared memory):
 //   p = r + beta (p - omega v),  y = D^-1 p                      (fused with the r update below)
 //   publish y | barrier | v = A y; sigma = (rh, v) | barrier;  alpha = rho / sigma
 //   s = r - alpha v,  z = D^-1 s,  d += alpha y
@@ -343,10 +446,12 @@ constexpr size_t bicg_smem(int threads) { return (size_t)10 * threads * sizeof(d
 // The next rho and ||r||^2 follow from inner products of s and t taken in the same reduction
 // (exact identities for r = s - omega t), which saves the fifth barrier of the textbook form.
 template <typename TI>
-__global__ void __launch_bounds__(1024) k_bicgstab(Launch<BicgArgs<TI>> L) {
+__global__ void __launch_bounds__(512) k_bicgstab(Launch<BicgArgs<TI>> L) {
     extern __shared__ double s_lean[];   // [10][blockDim.x]
     __shared__ double s_bc[10];
     __shared__ float s_f32[32 * 10];
+    __shared__ double s_sc[4];
+    __shared__ int s_fl[2];
     const Grp g = group_of(L.map);
     const BicgArgs<TI>& a = L.table ? L.table[g.inst] : L.single;
     const unsigned int nb = g.nb;
@@ -389,9 +494,6 @@ __global__ void __launch_bounds__(1024) k_bicgstab(Launch<BicgArgs<TI>> L) {
     }
     const double rtol2 = a.rtol * a.rtol, itol2 = a.inner_rtol * a.inner_rtol;
     const double floor2 = 0.25 * rtol2;
-    auto masked = [&](int i, int c, TI acc, const TI* src) -> TI {
-        return (a.mask[i] & (1 << c)) ? src[2 * (size_t)i + c] : acc;
-    };
 
     for (;;) {
         double t1[4];
@@ -436,65 +538,112 @@ __global__ void __launch_bounds__(1024) k_bicgstab(Launch<BicgArgs<TI>> L) {
         for (;;) {
             TI al[2], be[2];
             // ---- (previous omega) d += omega z, r = s - omega t; then p = r + beta (p - omega v),
-            //      y = D^-1 p
+            //      y = D^-1 p; two rows per thread, all loads of both rows before the first store
             for (int c = 0; c < 2; ++c) be[c] = (TI)beta[c];
-            for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
-                TI d0, d1;
-                load2(a.dinvI, i, d0, d1);
-                const TI dd[2] = {d0, d1};
+            for (int i0 = rr.r0 + threadIdx.x; i0 < rr.r1; i0 += 2 * tpb) {
+                const int i1 = i0 + tpb;
+                const bool h1 = i1 < rr.r1;
+                const int row[2] = {i0, h1 ? i1 : i0};
+                TI dv[2][2], rv[2][2], zv[2][2], sv[2][2], tv[2][2], pv[2][2], vv[2][2], dg[2][2];
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const size_t idx = 2 * (size_t)i + c;
-                    TI r;
+                for (int h = 0; h < 2; ++h) {
+                    load2(a.dinvI, row[h], dg[h][0], dg[h][1]);
                     if (first) {
-                        r = a.r[idx];
+                        load2(a.r, row[h], rv[h][0], rv[h][1]);
                     } else {
-                        a.d[idx] += om[c] * a.z[idx];
-                        r = a.s[idx] - om[c] * a.t[idx];
-                        a.r[idx] = r;
+                        load2(a.d, row[h], dv[h][0], dv[h][1]);
+                        load2(a.z, row[h], zv[h][0], zv[h][1]);
+                        load2(a.s, row[h], sv[h][0], sv[h][1]);
+                        load2(a.t, row[h], tv[h][0], tv[h][1]);
+                        load2(a.p, row[h], pv[h][0], pv[h][1]);
+                        load2(a.v, row[h], vv[h][0], vv[h][1]);
                     }
-                    const TI p = first ? r : r + be[c] * (a.p[idx] - om[c] * a.v[idx]);
-                    a.p[idx] = p;
-                    a.y[idx] = dd[c] * p;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 1 && !h1) break;
+                    TI pn[2], yn[2];
+                    if (first) {
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) pn[c] = rv[h][c];
+                    } else {
+                        TI dn[2], rn[2];
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            dn[c] = dv[h][c] + om[c] * zv[h][c];
+                            rn[c] = sv[h][c] - om[c] * tv[h][c];
+                            pn[c] = rn[c] + be[c] * (pv[h][c] - om[c] * vv[h][c]);
+                        }
+                        store2(a.d, row[h], dn[0], dn[1]);
+                        store2(a.r, row[h], rn[0], rn[1]);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) yn[c] = dg[h][c] * pn[c];
+                    store2(a.p, row[h], pn[0], pn[1]);
+                    store2(a.y, row[h], yn[0], yn[1]);
                 }
             }
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-            // ---- v = A y, sigma = (rh, v)
+            // ---- v = A y, sigma = (rh, v); alpha = rho / sigma (thread 0, broadcast)
             {
                 TI vs[2] = {(TI)0, (TI)0};
                 spmv_block<2, TI, TI>(rr, a.rp, a.ci, a.valI, a.y, a.lanes, [&](int i, TI s0, TI s1) {
                     const TI acc[2] = {s0, s1};
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        const size_t idx = 2 * (size_t)i + c;
-                        const TI vv = masked(i, c, acc[c], a.y);
-                        a.v[idx] = vv;
-                        vs[c] += a.rh[idx] * vv;
-                    }
+                    TI r0, r1, y0 = (TI)0, y1 = (TI)0;
+                    load2(a.rh, i, r0, r1);
+                    const unsigned char m = a.mask[i];
+                    if (m) load2(a.y, i, y0, y1);
+                    const TI v0 = (m & 1) ? y0 : acc[0], v1 = (m & 2) ? y1 : acc[1];
+                    store2(a.v, i, v0, v1);
+                    vs[0] += r0 * v0;
+                    vs[1] += r1 * v1;
                 });
-                double ts[2];
                 block_partials_it<2, TI>(vs, a.part + BI_B2 * nb, nb, g.bid, s_lean, s_f32);
                 if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-                grid_totals<2>(a.part + BI_B2 * nb, nb, ts, s_bc);
-                for (int c = 0; c < 2; ++c) {
-                    nan |= bad(ts[c]);
-                    if (act[c] && ts[c] != 0.0) alpha[c] = rho[c] / ts[c];
-                    else { act[c] = false; alpha[c] = 0.0; }
-                    al[c] = (TI)alpha[c];
+                const int slot[2] = {BI_B2, BI_B2 + 1};
+                grid_totals_shared<2>(a.part, slot, nb, s_bc);
+                if (threadIdx.x == 0) {
+                    int fl = 0;
+                    for (int c = 0; c < 2; ++c) {
+                        const double ts = s_bc[c];
+                        fl |= bad(ts) ? 1 : 0;
+                        if (act[c] && ts != 0.0) alpha[c] = rho[c] / ts;
+                        else { act[c] = false; alpha[c] = 0.0; }
+                        s_sc[c] = alpha[c];
+                    }
+                    s_fl[1] = fl;
                 }
+                __syncthreads();
+                for (int c = 0; c < 2; ++c) al[c] = (TI)s_sc[c];
+                nan |= s_fl[1] != 0;
             }
-            // ---- s = r - alpha v, z = D^-1 s, d += alpha y
-            for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
-                TI d0, d1;
-                load2(a.dinvI, i, d0, d1);
-                const TI dd[2] = {d0, d1};
+            // ---- s = r - alpha v, z = D^-1 s, d += alpha y (two rows per thread)
+            for (int i0 = rr.r0 + threadIdx.x; i0 < rr.r1; i0 += 2 * tpb) {
+                const int i1 = i0 + tpb;
+                const bool h1 = i1 < rr.r1;
+                const int row[2] = {i0, h1 ? i1 : i0};
+                TI dg[2][2], rv[2][2], vv[2][2], yv[2][2], dv[2][2];
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    const size_t idx = 2 * (size_t)i + c;
-                    const TI s = a.r[idx] - al[c] * a.v[idx];
-                    a.s[idx] = s;
-                    a.z[idx] = dd[c] * s;
-                    a.d[idx] += al[c] * a.y[idx];
+                for (int h = 0; h < 2; ++h) {
+                    load2(a.dinvI, row[h], dg[h][0], dg[h][1]);
+                    load2(a.r, row[h], rv[h][0], rv[h][1]);
+                    load2(a.v, row[h], vv[h][0], vv[h][1]);
+                    load2(a.y, row[h], yv[h][0], yv[h][1]);
+                    load2(a.d, row[h], dv[h][0], dv[h][1]);
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 1 && !h1) break;
+                    TI sn[2], zn[2], dn[2];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        sn[c] = rv[h][c] - al[c] * vv[h][c];
+                        zn[c] = dg[h][c] * sn[c];
+                        dn[c] = dv[h][c] + al[c] * yv[h][c];
+                    }
+                    store2(a.s, row[h], sn[0], sn[1]);
+                    store2(a.z, row[h], zn[0], zn[1]);
+                    store2(a.d, row[h], dn[0], dn[1]);
                 }
             }
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
@@ -505,67 +654,85 @@ __global__ void __launch_bounds__(1024) k_bicgstab(Launch<BicgArgs<TI>> L) {
                 for (int k = 0; k < 10; ++k) q[k] = (TI)0;
                 spmv_block<2, TI, TI>(rr, a.rp, a.ci, a.valI, a.z, a.lanes, [&](int i, TI s0, TI s1) {
                     const TI acc[2] = {s0, s1};
+                    TI z0 = (TI)0, z1 = (TI)0, sv[2], hv[2];
+                    const unsigned char m = a.mask[i];
+                    if (m) load2(a.z, i, z0, z1);
+                    load2(a.s, i, sv[0], sv[1]);
+                    load2(a.rh, i, hv[0], hv[1]);
+                    const TI tv[2] = {(m & 1) ? z0 : acc[0], (m & 2) ? z1 : acc[1]};
+                    store2(a.t, i, tv[0], tv[1]);
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
-                        const size_t idx = 2 * (size_t)i + c;
-                        const TI tv = masked(i, c, acc[c], a.z);
-                        a.t[idx] = tv;
-                        const TI sv = a.s[idx], hv = a.rh[idx];
-                        q[c] += tv * sv;
-                        q[2 + c] += tv * tv;
-                        q[4 + c] += hv * tv;
-                        q[6 + c] += hv * sv;
-                        q[8 + c] += sv * sv;
+                        q[c] += tv[c] * sv[c];
+                        q[2 + c] += tv[c] * tv[c];
+                        q[4 + c] += hv[c] * tv[c];
+                        q[6 + c] += hv[c] * sv[c];
+                        q[8 + c] += sv[c] * sv[c];
                     }
                 });
-                double t10[10];
                 block_partials_it<10, TI>(q, a.part + BI_B4 * nb, nb, g.bid, s_lean, s_f32);
                 if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
                 {
                     int slot[10];
 #pragma unroll
                     for (int k = 0; k < 10; ++k) slot[k] = BI_B4 + k;
-                    grid_totals_at<10>(a.part, slot, nb, t10, s_bc);
+                    grid_totals_shared<10>(a.part, slot, nb, s_bc);
                 }
                 iters += 1;
                 first = false;
-                bool more = false;
-                for (int c = 0; c < 2; ++c) {
-                    const double ts = t10[c], tt = t10[2 + c], ht = t10[4 + c], hs = t10[6 + c], ss = t10[8 + c];
-                    nan |= bad(ts) | bad(tt) | bad(ht) | bad(hs) | bad(ss);
-                    if (act[c] && ss <= tgt[c]) {          // converged at the half step
-                        act[c] = false;
-                        omega[c] = 0.0;
-                    } else if (act[c] && tt != 0.0) {
-                        omega[c] = ts / tt;
-                    } else {
-                        act[c] = false;
-                        omega[c] = 0.0;
-                    }
-                    if (act[c]) {
-                        const double rnew = hs - omega[c] * ht;
-                        const double rr2 = ss - 2.0 * omega[c] * ts + omega[c] * omega[c] * tt;
-                        if (rr2 <= tgt[c]) {
+                // omega, the next rho and beta, convergence: thread 0, broadcast
+                if (threadIdx.x == 0) {
+                    int more = 0, fl = 0;
+                    for (int c = 0; c < 2; ++c) {
+                        const double ts = s_bc[c], tt = s_bc[2 + c], ht = s_bc[4 + c], hs = s_bc[6 + c];
+                        const double ss = s_bc[8 + c];
+                        fl |= (bad(ts) | bad(tt) | bad(ht) | bad(hs) | bad(ss)) ? 1 : 0;
+                        if (act[c] && ss <= tgt[c]) {          // converged at the half step
                             act[c] = false;
-                        } else if (rnew != 0.0 && omega[c] != 0.0 && rho[c] != 0.0) {
-                            beta[c] = (rnew / rho[c]) * (alpha[c] / omega[c]);
-                            rho[c] = rnew;
+                            omega[c] = 0.0;
+                        } else if (act[c] && tt != 0.0) {
+                            omega[c] = ts / tt;
                         } else {
-                            act[c] = false;            // breakdown: restart in the next pass
+                            act[c] = false;
+                            omega[c] = 0.0;
                         }
+                        if (act[c]) {
+                            const double rnew = hs - omega[c] * ht;
+                            const double rr2 = ss - 2.0 * omega[c] * ts + omega[c] * omega[c] * tt;
+                            if (rr2 <= tgt[c]) {
+                                act[c] = false;
+                            } else if (rnew != 0.0 && omega[c] != 0.0 && rho[c] != 0.0) {
+                                beta[c] = (rnew / rho[c]) * (alpha[c] / omega[c]);
+                                rho[c] = rnew;
+                            } else {
+                                act[c] = false;            // breakdown: restart in the next pass
+                            }
+                        }
+                        if (!act[c]) beta[c] = 0.0;
+                        more |= act[c] ? 1 : 0;
+                        s_sc[c] = omega[c];
+                        s_sc[2 + c] = beta[c];
                     }
-                    if (!act[c]) beta[c] = 0.0;
-                    om[c] = (TI)omega[c];
-                    more |= act[c];
+                    s_fl[0] = more;
+                    s_fl[1] = fl;
                 }
+                __syncthreads();
+                for (int c = 0; c < 2; ++c) {
+                    omega[c] = s_sc[c];
+                    beta[c] = s_sc[2 + c];
+                    om[c] = (TI)omega[c];
+                }
+                const bool more = s_fl[0] != 0;
+                nan |= s_fl[1] != 0;
+                __syncthreads();   // s_sc / s_fl read by all before thread 0 writes them again
                 if (nan || !more || iters >= a.max_iter) {
                     // last update of this pass: d += omega z
-                    for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb)
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            const size_t idx = 2 * (size_t)i + c;
-                            a.d[idx] += om[c] * a.z[idx];
-                        }
+                    for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
+                        TI d0, d1, z0, z1;
+                        load2(a.d, i, d0, d1);
+                        load2(a.z, i, z0, z1);
+                        store2(a.d, i, d0 + om[0] * z0, d1 + om[1] * z1);
+                    }
                     break;
                 }
             }
