@@ -30,7 +30,10 @@ sys.path.insert(0, ROOT)
 
 import cgp_inputs as ci  # noqa: E402
 
-WORKLOAD = "bfs33"
+WORKLOAD = "bfs33"       # the headline workload; --workload cylinder / cavity33 time the other meshes
+DESCR = {"bfs33": "backward-facing step",
+         "cylinder": "flow past a cylinder, graded Poisson-disk Delaunay mesh, slip walls",
+         "cavity33": "lid-driven cavity"}
 METRIC = "time steps/sec & coarse Poisson solves/sec at 1e-8 rel. residual; SpMV HBM GB/s vs peak"
 
 
@@ -59,7 +62,7 @@ class L2Flush:
         torch.sum(self.r, dim=0, out=self.acc)
 
 
-def measured_traffic(kernel: str):
+def measured_traffic(kernel: str, workload: str = WORKLOAD):
     """DRAM bytes per launch of ``kernel`` from the committed ncu capture, or None when there is
     none or the kernel's source has changed since it was taken (its SHA-256 is recorded)."""
     import hashlib
@@ -69,7 +72,7 @@ def measured_traffic(kernel: str):
         with open(os.path.join(ROOT, rec["source"]), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest() != rec["sha256"]:
                 return None
-        return rec["bytes_per_launch"] if rec.get("workload") == WORKLOAD else None
+        return rec["bytes_per_launch"] if rec.get("workload") == workload else None
     except Exception:
         return None
 
@@ -230,7 +233,8 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if not os.path.exists(L.LIB_PATH):
         raise RuntimeError("libcgp.so is not built; run python -c 'import __graft_entry__ as g; g.build()'")
-    coarse, prob, _ = ci.workload(WORKLOAD)
+    wname = args.workload
+    coarse, prob, _ = ci.workload(wname)
     prec = L.CGP_MIXED if args.precision == "mixed" else L.CGP_FP64
     f = Flow(coarse, prob, precision=prec, rtol=args.rtol, device=f"cuda:{local}",
              block_threads=args.threads, spmv_lanes=args.lanes, coarse_solver=args.coarse_solver,
@@ -312,7 +316,7 @@ def run_gpu(args):
     peak, peak_kind = peaks()
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and wname == WORKLOAD:
         times, t_setup, cores = oracle_sample(args.cpu_steps)
         cpu = {"value": 1.0 / statistics.mean(times), "unit": "steps/s", "cores": cores, "kind": "oracle",
                "sample": f"{len(times)} oracle steps of the same workload from rest (setup {t_setup:.1f}s excluded)"}
@@ -325,8 +329,9 @@ def run_gpu(args):
         "metric": METRIC, "value": ws * 1000.0 / ms, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == L.CGP_FP64 else "f32+f64-ir", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: backward-facing step, coarse 65,308 / fine 259,117 nodes, "
-                               f"l=1, Re=400, dt=0.005", "rtol": args.rtol, "precision": args.precision,
+        "config": {"workload": f"{wname}: {DESCR[wname]}, coarse {f.info.n_coarse:,} / fine {f.info.n_fine:,} nodes, "
+                               f"l={f.info.levels}, Re={prob.mu and round(1.0 / prob.mu * (2.0 if wname == 'bfs33' else 1.0))}, "
+                               f"dt={prob.dt}", "rtol": args.rtol, "precision": args.precision,
                    "l2": "flushed between timed steps (512 MB write, then 256 MB read)", "parallelism": "replicas" if ws > 1 else "1gpu",
                    "block_threads": f.info.block_threads, "grid_blocks": f.info.grid_blocks,
                    "spmv_lanes": f.info.spmv_lanes, "coarse_kernel": kname,
@@ -335,7 +340,7 @@ def run_gpu(args):
         "poisson_ms": pms, "poisson_iters": it, "poisson_outer": outer,
         "momentum_iters": statistics.mean(mom_iters), "mass_iters": statistics.mean(mass_iters),
         "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": measured_traffic(kname),
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": measured_traffic(kname, wname),
                      "alg_bytes_per_launch": alg_bytes,
                      "note": "coarse matrix + vectors live in shared memory, registers and L2 (ncu: 0.1 % DRAM "
                              "throughput); the kernel is bound by barrier latency, so achieved is an effective rate: "
@@ -525,7 +530,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="bfs33", choices=["bfs33", "batch64", "warmstart", "spmv"])
+    ap.add_argument("--workload", default="bfs33",
+                    choices=["bfs33", "cylinder", "cavity33", "batch64", "warmstart", "spmv"])
     ap.add_argument("--runs", type=int, default=100)
     ap.add_argument("--run-steps", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=30)

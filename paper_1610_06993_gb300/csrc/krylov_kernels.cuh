@@ -65,14 +65,11 @@ __device__ __forceinline__ void spmv_rows(RowRange rr, const int* __restrict__ r
 
 // y = A x over the block's rows, `lanes` consecutive threads per row. emit(row, acc0, acc1) runs
 // on the first lane of each row group. Every thread of the block runs the same number of passes
-// so the group shuffles always see full warps. One lane per row takes the spmv_rows path.
+// so the group shuffles always see full warps. Plain loop: for kernels with many resident warps
+// (the stand-alone product), where occupancy hides the latency.
 template <int NR, typename TV, typename TX, typename Emit>
-__device__ __forceinline__ void spmv_block(RowRange rr, const int* __restrict__ rp, const int* __restrict__ ci,
+__device__ __forceinline__ void spmv_lanes(RowRange rr, const int* __restrict__ rp, const int* __restrict__ ci,
                                            const TV* __restrict__ val, const TX* x, int lanes, Emit emit) {
-    if (lanes == 1) {
-        spmv_rows<NR, TV, TX>(rr, rp, ci, val, x, emit);
-        return;
-    }
     const int groups = blockDim.x / lanes;
     const int g = threadIdx.x / lanes;
     const int l = threadIdx.x & (lanes - 1);
@@ -98,6 +95,15 @@ __device__ __forceinline__ void spmv_block(RowRange rr, const int* __restrict__ 
         if (NR == 2) a1 = group_sum(a1, lanes);
         if (l == 0 && row < rr.r1) emit(row, a0, a1);
     }
+}
+
+// The product of the persistent Krylov kernels (one block per SM): one lane per row takes the
+// spmv_rows path, more lanes the group loop.
+template <int NR, typename TV, typename TX, typename Emit>
+__device__ __forceinline__ void spmv_block(RowRange rr, const int* __restrict__ rp, const int* __restrict__ ci,
+                                           const TV* __restrict__ val, const TX* x, int lanes, Emit emit) {
+    if (lanes == 1) spmv_rows<NR, TV, TX>(rr, rp, ci, val, x, emit);
+    else spmv_lanes<NR, TV, TX>(rr, rp, ci, val, x, lanes, emit);
 }
 
 __device__ __forceinline__ bool bad(double v) { return !(fabs(v) <= 1.7976931348623157e308); }
@@ -761,7 +767,7 @@ __global__ void __launch_bounds__(1024) k_spmv_probe(int n, const int* rp, const
     RowRange rr;
     rr.r0 = min(n, blockIdx.x * rows_per_block);
     rr.r1 = min(n, rr.r0 + rows_per_block);
-    spmv_block<NR, double, double>(rr, rp, ci, val, x, lanes, [&](int i, double s0, double s1) {
+    spmv_lanes<NR, double, double>(rr, rp, ci, val, x, lanes, [&](int i, double s0, double s1) {
         if (NR == 1) y[i] = s0;
         else store2(y, i, s0, s1);
     });
