@@ -5,10 +5,6 @@
 
 #include "ctx.h"
 
-namespace cgp {
-int persistent_blocks_per_sm(int threads);
-}
-
 using namespace cgp;
 
 #define CK(call)                                         \
@@ -202,7 +198,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     CK(e);
 
     const int threads = P.block_threads;
-    const int bps = persistent_blocks_per_sm(threads);
+    const int bps = persistent_blocks_per_sm(threads, false);
     if (bps <= 0) return CGP_ERR_CUDA;
     const int lanes = P.spmv_lanes ? P.spmv_lanes : 1;
     c->sh_f = make_shape(c->nf, threads, lanes, c->num_sms, bps);

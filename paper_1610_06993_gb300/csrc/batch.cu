@@ -101,7 +101,7 @@ int create_impl(cgp_ctx* ctxs, int n, double* const* u, double* const* pc, cgp_b
         if (ctxs[i]->device != ctxs[0]->device) return CGP_ERR_ARG;
     }
     const int sms = ctxs[0]->num_sms;
-    const int bps = std::min(2, persistent_blocks_per_sm(b->threads));
+    const int bps = std::min(2, persistent_blocks_per_sm(b->threads, true));
     if (bps < 1) return CGP_ERR_CUDA;
     const int total = sms * bps;
     std::vector<double> wf(n), wc(n);

@@ -165,7 +165,7 @@ cudaError_t batch_solvers_build(cgp_batch_s* b);
 cudaError_t batch_momentum_launch(cgp_batch_s* b, cudaStream_t s);
 cudaError_t batch_poisson_launch(cgp_batch_s* b, cudaStream_t s);
 cudaError_t batch_mass_launch(cgp_batch_s* b, cudaStream_t s);
-int persistent_blocks_per_sm(int threads);
+int persistent_blocks_per_sm(int threads, bool batch);
 
 // assemble.cu
 cudaError_t launch_geometry(const double* xy, const int* tri, int t, double* geo, cudaStream_t s);

@@ -196,39 +196,45 @@ cudaError_t batch_solvers_build(cgp_batch_s* b) {
 cudaError_t batch_momentum_launch(cgp_batch_s* b, cudaStream_t s) {
     if (b->precision == CGP_MIXED) {
         auto L = table_launch<BicgArgs<float>>(b->tab_mom, b->map_f);
-        return coop_launch(k_bicgstab<float>, b->blocks_f, b->threads, L, s, bicg_smem(b->threads));
+        return coop_launch(k_bicgstab<float, 2>, b->blocks_f, b->threads, L, s, bicg_smem(b->threads));
     }
     auto L = table_launch<BicgArgs<double>>(b->tab_mom, b->map_f);
-    return coop_launch(k_bicgstab<double>, b->blocks_f, b->threads, L, s, bicg_smem(b->threads));
+    return coop_launch(k_bicgstab<double, 2>, b->blocks_f, b->threads, L, s, bicg_smem(b->threads));
 }
 
 cudaError_t batch_poisson_launch(cgp_batch_s* b, cudaStream_t s) {
     if (b->precision == CGP_MIXED) {
         auto L = table_launch<CgArgs<float>>(b->tab_poi, b->map_c);
-        return coop_launch(k_cg<float, 1>, b->blocks_c, b->threads, L, s, cg_smem<1>(b->threads));
+        return coop_launch(k_cg<float, 1, 2>, b->blocks_c, b->threads, L, s, cg_smem<1>(b->threads));
     }
     auto L = table_launch<CgArgs<double>>(b->tab_poi, b->map_c);
-    return coop_launch(k_cg<double, 1>, b->blocks_c, b->threads, L, s, cg_smem<1>(b->threads));
+    return coop_launch(k_cg<double, 1, 2>, b->blocks_c, b->threads, L, s, cg_smem<1>(b->threads));
 }
 
 cudaError_t batch_mass_launch(cgp_batch_s* b, cudaStream_t s) {
     if (b->precision == CGP_MIXED) {
         auto L = table_launch<CgArgs<float>>(b->tab_mass, b->map_f);
-        return coop_launch(k_cg<float, 2>, b->blocks_f, b->threads, L, s, cg_smem<2>(b->threads));
+        return coop_launch(k_cg<float, 2, 2>, b->blocks_f, b->threads, L, s, cg_smem<2>(b->threads));
     }
     auto L = table_launch<CgArgs<double>>(b->tab_mass, b->map_f);
-    return coop_launch(k_cg<double, 2>, b->blocks_f, b->threads, L, s, cg_smem<2>(b->threads));
+    return coop_launch(k_cg<double, 2, 2>, b->blocks_f, b->threads, L, s, cg_smem<2>(b->threads));
 }
 
 // Occupancy of the persistent kernels (blocks per SM at `threads`), the minimum over the family.
 // Resident blocks per SM of the generic persistent kernels at `threads` threads (the minimum over
-// all of them, with their dynamic shared memory); also raises their dynamic shared-memory limit.
-int persistent_blocks_per_sm(int threads) {
+// all of them, with their dynamic shared memory) for single contexts (batch = false) or for the
+// batch instantiations; also raises their dynamic shared-memory limit.
+int persistent_blocks_per_sm(int threads, bool batch) {
     int m = 1 << 30, v = 0;
-    const void* fns[] = {(const void*)k_cg<double, 1>, (const void*)k_cg<float, 1>, (const void*)k_cg<double, 2>,
-                         (const void*)k_cg<float, 2>, (const void*)k_bicgstab<double>, (const void*)k_bicgstab<float>};
+    const void* single[] = {(const void*)k_cg<double, 1>, (const void*)k_cg<float, 1>, (const void*)k_cg<double, 2>,
+                            (const void*)k_cg<float, 2>, (const void*)k_bicgstab<double>,
+                            (const void*)k_bicgstab<float>};
+    const void* batched[] = {(const void*)k_cg<double, 1, 2>, (const void*)k_cg<float, 1, 2>,
+                             (const void*)k_cg<double, 2, 2>, (const void*)k_cg<float, 2, 2>,
+                             (const void*)k_bicgstab<double, 2>, (const void*)k_bicgstab<float, 2>};
     const size_t smem[] = {cg_smem<1>(threads), cg_smem<1>(threads), cg_smem<2>(threads),
                            cg_smem<2>(threads), bicg_smem(threads), bicg_smem(threads)};
+    const void* const* fns = batch ? batched : single;
     for (int k = 0; k < 6; ++k) {
         if (cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem[k]) != cudaSuccess)
             return 0;

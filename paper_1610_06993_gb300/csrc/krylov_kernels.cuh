@@ -145,8 +145,11 @@ constexpr size_t cg_smem(int threads) {
 // Iteration (Chronopoulos-Gear form, two grid barriers per iteration, one of them a reduction):
 //   p = u + beta p,  s = w + beta s,  d += alpha p,  r -= alpha s,  u = D^-1 r     (local)
 //   publish u | barrier | w = A u; partials (r,u), (r,r), (w,u) | barrier
-template <typename TI, int NR>
-__global__ void __launch_bounds__(512) k_cg(Launch<CgArgs<TI>> L) {
+// MINB: resident blocks per SM the launch is compiled for: 1 for a single context (128 registers
+// per thread, no spills), 2 for batches, whose many small block groups gain more from twice the
+// threads per SM than from registers.
+template <typename TI, int NR, int MINB = 1>
+__global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
     extern __shared__ double s_lean[];   // [3 NR][blockDim.x]
     __shared__ double s_bc[8];
     __shared__ float s_f32[32 * 3 * NR];
@@ -451,8 +454,8 @@ constexpr size_t bicg_smem(int threads) { return (size_t)10 * threads * sizeof(d
 //   rho' = (rh, s) - omega (rh, t),  (r, r) = (s, s) - 2 omega (t, s) + omega^2 (t, t)
 // The next rho and ||r||^2 follow from inner products of s and t taken in the same reduction
 // (exact identities for r = s - omega t), which saves the fifth barrier of the textbook form.
-template <typename TI>
-__global__ void __launch_bounds__(512) k_bicgstab(Launch<BicgArgs<TI>> L) {
+template <typename TI, int MINB = 1>
+__global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) {
     extern __shared__ double s_lean[];   // [10][blockDim.x]
     __shared__ double s_bc[10];
     __shared__ float s_f32[32 * 10];
