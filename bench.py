@@ -131,6 +131,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_time_ms(ms: float, ws: int, device) -> float:
+    """The job's time per step: the maximum of the ranks' times (each rank runs its own replica;
+    the slowest one bounds the whole job). Identity for a single rank."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, ms: float, ws: int) -> float:
+    """Whole-job throughput: the units all ranks processed per second at the job's step time."""
+    return ws * units_per_rank * 1000.0 / ms
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -277,11 +294,7 @@ def run_gpu(args):
             mom_iters.append(st.momentum_iters)
             mass_iters.append(st.mass_iters)
     torch.cuda.synchronize()
-    ms = statistics.mean(step_ms)
-    if ws > 1:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_time_ms(statistics.mean(step_ms), ws, f"cuda:{local}")
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     uh = torch.empty(f.u.shape, dtype=torch.float64, pin_memory=True)
@@ -326,7 +339,7 @@ def run_gpu(args):
     kname = {0: f"k_cg<{tname}, 1>", 1: f"k_pcg_onchip<{tname}>", 2: f"k_pcg_pipe<{tname}>",
              3: "k_pcg_schwarz<double, float>", 4: f"k_pcg_schwarz<{tname}, {tname}>"}[f.info.coarse_kernel]
     line = {
-        "metric": METRIC, "value": ws * 1000.0 / ms, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+        "metric": METRIC, "value": job_rate(1.0, ms, ws), "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == L.CGP_FP64 else "f32+f64-ir", "data": "synthetic",
         "config": {"workload": f"{wname}: {DESCR[wname]}, coarse {f.info.n_coarse:,} / fine {f.info.n_fine:,} nodes, "
@@ -404,11 +417,7 @@ def run_batch(args):
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
     st = b.stats(check=True)
-    ms = statistics.mean(step_ms)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_time_ms(statistics.mean(step_ms), ws, dev)
     n_inst = len(flows)
 
     # coarse solves: batched, warm-started from the previous step's pressure
@@ -451,7 +460,7 @@ def run_batch(args):
         plain[solver] = (t_plain, it_plain)
 
     line = {
-        "metric": METRIC, "value": ws * n_inst * 1000.0 / ms, "unit": "instance-steps/s", "n_gpus": ws,
+        "metric": METRIC, "value": job_rate(n_inst, ms, ws), "unit": "instance-steps/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == L.CGP_FP64 else "f32+f64-ir", "data": "synthetic",
         "config": {"workload": "batch64: 64 lid-driven cavities, coarse nodes log-uniform in [2k, 50k] "

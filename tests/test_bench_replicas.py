@@ -1,0 +1,58 @@
+"""The multi-rank path of bench.py (N independent replicas, one per rank), checked on CPU with
+two gloo ranks: the job's step time is the maximum over ranks, the whole-job rate counts every
+rank's units at that time, and only rank 0 reports. No GPU is involved."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank: int, ws: int, port: int, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        local_ms = 10.0 + 5.0 * rank            # rank 1 is the slow replica
+        ms = bench.job_time_ms(local_ms, ws, "cpu")
+        rate = bench.job_rate(64, ms, ws)
+        env = bench.dist_env()
+        out.put((rank, ms, rate, env))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_replicas_report_max_time_and_job_rate():
+    ws, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank, args=(r, ws, port, q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(ws))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, rate, env in res:
+        assert ms == pytest.approx(15.0)                 # max over ranks, seen by every rank
+        assert rate == pytest.approx(2 * 64 * 1000.0 / 15.0)
+        assert env == (ws, rank, rank)
+
+
+def test_single_rank_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.job_time_ms(12.5, 1, "cpu") == 12.5
+    assert bench.job_rate(1.0, 4.0, 1) == pytest.approx(250.0)
