@@ -120,6 +120,10 @@ int create_impl(cgp_ctx* ctxs, int n, double* const* u, double* const* pc, cgp_b
     if ((s = dalloc(b, &b->sync, (size_t)n * SYNC_COUNT))) return s;
     if ((s = dalloc(b, &b->part, (size_t)n * 32 * b->max_group))) return s;
     if (batch_asm_build(b) != cudaSuccess || batch_solvers_build(b) != cudaSuccess) return CGP_ERR_CUDA;
+    // coarse Poisson on the two-level kernel when every instance asks for the automatic coarse
+    // solver and fits it; otherwise the Jacobi kernel
+    batch_poisson2l_build(b);
+    cudaGetLastError();
     return CGP_OK;
 }
 
@@ -128,7 +132,7 @@ cudaError_t enqueue_step(cgp_batch_s* b, cudaStream_t s) {
     if (e == cudaSuccess) e = batch_asm_launch(b, s);
     if (e == cudaSuccess) e = batch_momentum_launch(b, s);
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) e = launch_restrict_rhs(b->ctx[i], b->ctx[i]->ut, b->ctx[i]->bc, s);
-    if (e == cudaSuccess) e = batch_poisson_launch(b, s);
+    if (e == cudaSuccess) e = b->poisson_2l ? batch_poisson2l_launch(b, s) : batch_poisson_launch(b, s);
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
         cgp_ctx_s* c = b->ctx[i];
         e = launch_prolong(c, b->pc[i], c->pf, s);
@@ -199,7 +203,7 @@ int cgp_batch_poisson_solve(cgp_batch b, void* stream) {
     if (!b) return CGP_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(b->sync, 0, sizeof(SyncWords) * (size_t)b->n * SYNC_COUNT, s);
-    if (e == cudaSuccess) e = batch_poisson_launch(b, s);
+    if (e == cudaSuccess) e = b->poisson_2l ? batch_poisson2l_launch(b, s) : batch_poisson_launch(b, s);
     return e == cudaSuccess ? CGP_OK : CGP_ERR_CUDA;
 }
 

@@ -42,6 +42,16 @@ struct Shape {
 // Sync words: one slot per persistent launch site, zeroed before every launch.
 enum SyncSlot { SYNC_ASM = 0, SYNC_MOM, SYNC_POI, SYNC_MASS, SYNC_COUNT };
 
+// Coarse space of the batched two-level coarse CG (krylov_2l.cu): Hilbert renumbering, the
+// renumbered matrix, and 256-row subdomains with three coarse functions each.
+struct TwoLevel {
+    bool ready = false;
+    int nsub = 0;
+    int *perm = nullptr, *rp = nullptr, *ci = nullptr;
+    double *val64 = nullptr, *dinv64 = nullptr, *mom = nullptr;
+    float *val32 = nullptr, *dinv32 = nullptr, *fxy32 = nullptr, *ainv32 = nullptr;
+};
+
 }  // namespace cgp
 
 struct cgp_ctx_s {
@@ -132,6 +142,7 @@ struct cgp_ctx_s {
     std::vector<int> sz_rp_h, sz_ci_h;
     std::vector<double> sz_fxy_h;
     size_t sz_smem = 0;
+    cgp::TwoLevel tl;            // batched two-level coarse CG
     std::vector<void*> allocs;   // everything to free
 };
 
@@ -150,6 +161,9 @@ struct cgp_batch_s {
     void* tab_mom = nullptr;
     void* tab_poi = nullptr;
     void* tab_mass = nullptr;
+    void* tab_poi2 = nullptr;            // two-level coarse CG arguments (poisson_2l)
+    bool poisson_2l = false;
+    size_t smem_poi2 = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -165,6 +179,10 @@ cudaError_t batch_solvers_build(cgp_batch_s* b);
 cudaError_t batch_momentum_launch(cgp_batch_s* b, cudaStream_t s);
 cudaError_t batch_poisson_launch(cgp_batch_s* b, cudaStream_t s);
 cudaError_t batch_mass_launch(cgp_batch_s* b, cudaStream_t s);
+// krylov_2l.cu
+int twolevel_build(cgp_ctx_s* c);
+bool batch_poisson2l_build(cgp_batch_s* b);
+cudaError_t batch_poisson2l_launch(cgp_batch_s* b, cudaStream_t s);
 int persistent_blocks_per_sm(int threads, bool batch);
 
 // assemble.cu

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "subdomain.h"
 
 namespace cgp {
 
@@ -449,8 +450,6 @@ struct SchwarzArgs {
     int* st_barrier;
 };
 
-#define SZ_NC 3   // coarse functions per subdomain
-
 enum { PS_P0 = 0, PS_O1 = 1 /* 2 slots */, PS_I0 = 3, PS_R = 4 /* SZ_NC slots */, PS_I = 4 + SZ_NC /* 2 x 3 */ };
 
 // One entry of the subdomain matrix A_aa in shared memory: column local to the block, value.
@@ -792,27 +791,6 @@ cudaError_t sz_upload(T* dst, const std::vector<T>& v) {
     return cudaMemcpy(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
-// Position of the cell (x, y), 0 <= x, y < 2^bits, along the Hilbert curve. At each scale the
-// quadrant of the point gives two digits of the position; the remaining low bits are then
-// reflected and transposed into the orientation of that quadrant's sub-curve (complementing all
-// bits reflects the low bits, which are the only ones read afterwards).
-uint64_t hilbert_index(uint32_t x, uint32_t y, int bits) {
-    uint64_t d = 0;
-    for (int k = bits - 1; k >= 0; --k) {
-        const uint32_t s = 1u << k;
-        const uint32_t rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
-        d += (uint64_t)s * s * ((3u * rx) ^ ry);
-        if (ry == 0) {
-            if (rx == 1) {
-                x = ~x;
-                y = ~y;
-            }
-            std::swap(x, y);
-        }
-    }
-    return d;
-}
-
 // Renumbering of the coarse nodes along a Hilbert curve of their coordinates (one scale for
 // both axes, so a subdomain is compact in physical space), the renumbered CSR pattern and the
 // device buffers of the Schwarz solver.
@@ -820,24 +798,7 @@ cudaError_t schwarz_structure(cgp_ctx_s* c) {
     const HostCsr& H = c->hm.coarse;
     const std::vector<double>& xy = c->hm.lv[0].xy;
     const int n = c->nc, nb = c->pipe_c.blocks;
-    double x0 = xy[0], x1 = xy[0], y0 = xy[1], y1 = xy[1];
-    for (int i = 0; i < n; ++i) {
-        x0 = std::min(x0, xy[2 * i]);
-        x1 = std::max(x1, xy[2 * i]);
-        y0 = std::min(y0, xy[2 * i + 1]);
-        y1 = std::max(y1, xy[2 * i + 1]);
-    }
-    const double ext = std::max(x1 - x0, y1 - y0);
-    const double sc = ext > 0.0 ? 65535.0 / ext : 0.0;
-    std::vector<uint64_t> key(n);
-    for (int i = 0; i < n; ++i) {
-        const uint32_t hx = (uint32_t)std::min(65535.0, std::max(0.0, (xy[2 * i] - x0) * sc));
-        const uint32_t hy = (uint32_t)std::min(65535.0, std::max(0.0, (xy[2 * i + 1] - y0) * sc));
-        key[i] = hilbert_index(hx, hy, 16);
-    }
-    std::vector<int> perm(n), iperm(n);
-    for (int i = 0; i < n; ++i) perm[i] = i;
-    std::stable_sort(perm.begin(), perm.end(), [&](int p, int q) { return key[p] < key[q]; });
+    std::vector<int> perm = hilbert_order(xy, n), iperm(n);
     // within each subdomain, longest rows first: the warps of a block then see nearly uniform row
     // lengths and their ELL loops stop at the warp's own longest row
     {
@@ -862,27 +823,7 @@ cudaError_t schwarz_structure(cgp_ctx_s* c) {
     const size_t nnz = c->sz_ci_h.size();
     // linear coarse functions (x - xbar_a) / H_a, (y - ybar_a) / H_a of each subdomain a
     const int rpb = (n + nb - 1) / nb;
-    c->sz_fxy_h.assign(2 * (size_t)n, 0.0);
-    for (int a = 0; a < nb; ++a) {
-        const int i0 = std::min(n, a * rpb), i1 = std::min(n, i0 + rpb);
-        if (i1 <= i0) continue;
-        double mx = 0.0, my = 0.0, h2 = 0.0;
-        for (int i = i0; i < i1; ++i) {
-            mx += xy[2 * perm[i]];
-            my += xy[2 * perm[i] + 1];
-        }
-        mx /= (i1 - i0);
-        my /= (i1 - i0);
-        for (int i = i0; i < i1; ++i) {
-            const double dx = xy[2 * perm[i]] - mx, dy = xy[2 * perm[i] + 1] - my;
-            h2 += dx * dx + dy * dy;
-        }
-        const double ih = h2 > 0.0 ? 1.0 / std::sqrt(h2 / (i1 - i0)) : 0.0;
-        for (int i = i0; i < i1; ++i) {
-            c->sz_fxy_h[2 * (size_t)i] = (xy[2 * perm[i]] - mx) * ih;
-            c->sz_fxy_h[2 * (size_t)i + 1] = (xy[2 * perm[i] + 1] - my) * ih;
-        }
-    }
+    c->sz_fxy_h = linear_functions(xy, perm, n, rpb);
     const std::vector<float> fxy32(c->sz_fxy_h.begin(), c->sz_fxy_h.end());
     const size_t ncs = (size_t)SZ_NC * nb;
     cudaError_t e;
@@ -1033,47 +974,10 @@ int schwarz_values(cgp_ctx_s* c) {
     }
     c->sz_lmax = std::min(gersh, 1.2 * lam);
     c->sz_lmin = c->sz_lmax / c->sz_ratio;
-    // Galerkin coarse matrix; coarse index of function f on subdomain a is f * nb + a
-    const int nc0 = SZ_NC * nb;
-    const std::vector<double>& fxy = c->sz_fxy_h;
-    std::vector<double> A0((size_t)nc0 * nc0, 0.0), Lc((size_t)nc0 * nc0, 0.0), Ai((size_t)nc0 * nc0, 0.0);
-    for (int i = 0; i < n; ++i) {
-        const double pi[SZ_NC] = {1.0, fxy[2 * (size_t)i], fxy[2 * (size_t)i + 1]};
-        const int ai = i / rpb;
-        for (int k = rp[i]; k < rp[i + 1]; ++k) {
-            const int j = ci[k], aj = j / rpb;
-            const double pj[SZ_NC] = {1.0, fxy[2 * (size_t)j], fxy[2 * (size_t)j + 1]};
-            for (int f = 0; f < SZ_NC; ++f)
-                for (int g = 0; g < SZ_NC; ++g)
-                    A0[(size_t)(f * nb + ai) * nc0 + g * nb + aj] += pi[f] * v[k] * pj[g];
-        }
-    }
-    for (int q = 0; q < nc0; ++q)
-        if (A0[(size_t)q * nc0 + q] == 0.0) A0[(size_t)q * nc0 + q] = 1.0;
-    for (int j = 0; j < nc0; ++j) {
-        double d = A0[(size_t)j * nc0 + j];
-        for (int k = 0; k < j; ++k) d -= Lc[(size_t)j * nc0 + k] * Lc[(size_t)j * nc0 + k];
-        if (!(d > 0.0)) return CGP_ERR_ARG;
-        const double ljj = std::sqrt(d);
-        Lc[(size_t)j * nc0 + j] = ljj;
-        for (int i = j + 1; i < nc0; ++i) {
-            double s = A0[(size_t)i * nc0 + j];
-            for (int k = 0; k < j; ++k) s -= Lc[(size_t)i * nc0 + k] * Lc[(size_t)j * nc0 + k];
-            Lc[(size_t)i * nc0 + j] = s / ljj;
-        }
-    }
-    std::vector<double> y(nc0);
-    for (int col = 0; col < nc0; ++col) {
-        for (int i = 0; i < nc0; ++i) {   // L y = e_col
-            double s = i == col ? 1.0 : 0.0;
-            for (int k = 0; k < i; ++k) s -= Lc[(size_t)i * nc0 + k] * y[k];
-            y[i] = s / Lc[(size_t)i * nc0 + i];
-        }
-        for (int i = nc0 - 1; i >= 0; --i) {   // L^T x = y
-            double s = y[i];
-            for (int k = i + 1; k < nc0; ++k) s -= Lc[(size_t)k * nc0 + i] * Ai[(size_t)k * nc0 + col];
-            Ai[(size_t)i * nc0 + col] = s / Lc[(size_t)i * nc0 + i];
-        }
+    std::vector<double> Ai;
+    {
+        const int st = galerkin_inverse(rp, ci, v, c->sz_fxy_h, n, rpb, nb, Ai);
+        if (st != CGP_OK) return st;
     }
     std::vector<double> dinv(n);
     for (int i = 0; i < n; ++i) dinv[i] = 1.0 / dg[i];
