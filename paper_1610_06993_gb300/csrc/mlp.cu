@@ -35,7 +35,7 @@ constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int GEMM_SMEM = STAGES * STAGE_BYTES + 1024;   // + slack for 1024-byte alignment
 constexpr uint32_t WAIT_LIMIT = 1u << 20;    // try_wait may suspend per attempt: about a second
 
-enum { EPI_F32 = 0, EPI_GELU = 1, EPI_GELU_BWD = 2 };
+enum { EPI_F32 = 0, EPI_GELU = 1, EPI_GELU_BWD = 2, EPI_RAW = 3 /* split-K partial, no bias */ };
 
 struct GemmArgs {
     int M, N, K;
@@ -46,6 +46,7 @@ struct GemmArgs {
     const float* zin;           // [M][ldo] pre-activation for EPI_GELU_BWD
     int ldo;
     int* err;
+    int splits;                 // K split across blockIdx.z (EPI_RAW: partial z at out_f32 + z M ldo)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -136,7 +137,9 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 }
 
 // C[M, N] = A[M, K] * B[N, K]^T, A and B bf16 row-major with K contiguous (K-major), fp32
-// accumulation in TMEM. One CTA of 4 warps per 128 x 128 output tile.
+// accumulation in TMEM. One CTA of 4 warps per 128 x 128 output tile and K range: with
+// g.splits > 1, CTA z of a tile takes its share of the 64-wide K blocks and stores the raw
+// partial tile (EPI_RAW); k_splitk_reduce adds the partials in order and applies the epilogue.
 __global__ void __launch_bounds__(128, 1) k_gemm_tn(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB, GemmArgs g) {
     extern __shared__ uint8_t smem_raw[];
@@ -148,7 +151,9 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(const __grid_constant__ CUte
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
-    const int nk = g.K / GK;
+    const int nk_all = g.K / GK, per = (nk_all + g.splits - 1) / g.splits;
+    const int kb0 = min(nk_all, (int)blockIdx.z * per);
+    const int nk = min(nk_all, kb0 + per) - kb0;     // >= 1: the host drops empty splits
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
@@ -184,8 +189,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(const __grid_constant__ CUte
             const uint32_t fb = smem_u32(&full_bar[s]);
             mbar_expect_tx(fb, STAGE_BYTES);
             const uint32_t sa = smem_u32(smem + (size_t)s * STAGE_BYTES);
-            tma_load_2d(sa, &tmA, kb * GK, m0, fb);
-            tma_load_2d(sa + A_BYTES, &tmB, kb * GK, n0, fb);
+            tma_load_2d(sa, &tmA, (kb0 + kb) * GK, m0, fb);
+            tma_load_2d(sa + A_BYTES, &tmB, (kb0 + kb) * GK, n0, fb);
             s_issued = kb + 1;
         }
     } else if (threadIdx.x == 32) {
@@ -219,6 +224,14 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(const __grid_constant__ CUte
             const int col0 = n0 + c;
             const size_t o = (size_t)row * g.ldo + col0;
             float v[16];
+            if (g.epi == EPI_RAW) {
+                float* dst = g.out_f32 + (size_t)blockIdx.z * g.M * g.ldo + o;
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    *reinterpret_cast<float4*>(dst + j) = make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                                      __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                continue;
+            }
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) + (g.bias ? g.bias[col0 + j] : 0.0f);
             if (g.epi == EPI_F32) {
@@ -261,6 +274,46 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(const __grid_constant__ CUte
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(GN) : "memory");
 }
 
+// Sum of the split-K partials W[z][M][N] (z in order, so the result does not depend on timing),
+// then bias and the epilogue of g, four outputs per thread.
+__global__ void k_splitk_reduce(const float* __restrict__ W, int splits, GemmArgs g) {
+    const size_t i4 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t total = (size_t)g.M * g.N;
+    if (i4 * 4 >= total) return;
+    const size_t o = i4 * 4;
+    const int col = (int)(o % g.N), row = (int)(o / g.N);
+    float4 acc = *reinterpret_cast<const float4*>(W + o);
+    for (int z = 1; z < splits; ++z) {
+        const float4 q = *reinterpret_cast<const float4*>(W + (size_t)z * total + o);
+        acc.x += q.x;
+        acc.y += q.y;
+        acc.z += q.z;
+        acc.w += q.w;
+    }
+    float v[4] = {acc.x, acc.y, acc.z, acc.w};
+    const size_t oo = (size_t)row * g.ldo + col;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] += g.bias ? g.bias[col + j] : 0.0f;
+    if (g.epi == EPI_F32) {
+        *reinterpret_cast<float4*>(g.out_f32 + oo) = make_float4(v[0], v[1], v[2], v[3]);
+        return;
+    }
+    __nv_bfloat16 hb[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float outv;
+        if (g.epi == EPI_GELU) {
+            outv = gelu_f(v[j]);
+        } else {
+            v[j] = v[j] * gelu_grad_f(g.zin[oo + j]);
+            outv = v[j];
+        }
+        hb[j] = __float2bfloat16_rn(outv);
+    }
+    if (g.out_f32) *reinterpret_cast<float4*>(g.out_f32 + oo) = make_float4(v[0], v[1], v[2], v[3]);
+    if (g.out_bf16) *reinterpret_cast<uint2*>(g.out_bf16 + oo) = *reinterpret_cast<const uint2*>(&hb[0]);
+}
+
 // ---- host side of the GEMM -----------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -291,9 +344,26 @@ cudaError_t make_map(CUtensorMap* m, const void* ptr, int rows, int cols) {
 
 bool g_gemm_attr = false;
 
+// Number of K splits for an M x N x K product: enough CTAs to cover the SMs when the output has
+// few tiles, at least two 64-wide K blocks per split, and no more than the workspace holds.
+int choose_splits(int M, int N, int K, int num_sms, size_t work_floats) {
+    const int tiles = (M / GM) * (N / GN), nk = K / GK;
+    int sp = std::max(1, std::min(num_sms / std::max(1, tiles), nk / 2));
+    while (sp > 1 && (size_t)sp * M * N > work_floats) --sp;
+    if (sp > 1) {
+        const int per = (nk + sp - 1) / sp;
+        sp = (nk + per - 1) / per;   // no empty split
+    }
+    return sp;
+}
+
 // C[M,N] = A[M,K] B[N,K]^T with the requirements M % 128 == 0, N % 128 == 0, K % 64 == 0,
-// 16-byte aligned A, B, C.
-cudaError_t gemm_tn(const __nv_bfloat16* A, const __nv_bfloat16* B, const GemmArgs& ga, cudaStream_t s) {
+// 16-byte aligned A, B, C. With a workspace (work, work_floats), a product with few output tiles
+// is split along K across more CTAs and reduced by k_splitk_reduce.
+cudaError_t gemm_tn(const __nv_bfloat16* A, const __nv_bfloat16* B, const GemmArgs& ga_in, cudaStream_t s,
+                    float* work = nullptr, size_t work_floats = 0, int num_sms = 0) {
+    GemmArgs ga = ga_in;
+    ga.splits = 1;
     if (ga.M % GM || ga.N % GN || ga.K % GK || ga.M <= 0 || ga.N <= 0 || ga.K <= 0) return cudaErrorInvalidValue;
     if (((uintptr_t)A | (uintptr_t)B) & 15) return cudaErrorInvalidValue;
     cudaError_t e = get_encoder();
@@ -306,8 +376,24 @@ cudaError_t gemm_tn(const __nv_bfloat16* A, const __nv_bfloat16* B, const GemmAr
     CUtensorMap ma, mb;
     if ((e = make_map(&ma, A, ga.M, ga.K)) != cudaSuccess) return e;
     if ((e = make_map(&mb, B, ga.N, ga.K)) != cudaSuccess) return e;
-    dim3 grid(ga.N / GN, ga.M / GM);
-    k_gemm_tn<<<grid, 128, GEMM_SMEM, s>>>(ma, mb, ga);
+    const int sp = work ? choose_splits(ga.M, ga.N, ga.K, num_sms, work_floats) : 1;
+    if (sp <= 1) {
+        dim3 grid(ga.N / GN, ga.M / GM);
+        k_gemm_tn<<<grid, 128, GEMM_SMEM, s>>>(ma, mb, ga);
+        return cudaGetLastError();
+    }
+    GemmArgs gp = ga;
+    gp.epi = EPI_RAW;
+    gp.out_f32 = work;
+    gp.out_bf16 = nullptr;
+    gp.bias = nullptr;
+    gp.ldo = ga.N;
+    gp.splits = sp;
+    dim3 grid(ga.N / GN, ga.M / GM, sp);
+    k_gemm_tn<<<grid, 128, GEMM_SMEM, s>>>(ma, mb, gp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t quads = (size_t)ga.M * ga.N / 4;
+    k_splitk_reduce<<<(unsigned)((quads + 255) / 256), 256, 0, s>>>(work, sp, ga);
     return cudaGetLastError();
 }
 
@@ -471,6 +557,10 @@ struct cgp_ws_s {
     double* loss_part;
     float* loss;
     unsigned char *mask, *keep_n, *keep_all;
+    // split-K workspace of the GEMMs with few output tiles
+    float* work = nullptr;
+    size_t work_floats = 0;
+    int num_sms = 0;
 };
 
 namespace {
@@ -511,7 +601,15 @@ int ws_create(cgp_ws_s* w, int n, int H, int bmax) {
     A(w->gW1, h * np); A(w->gb1, h); A(w->gW2, h * h); A(w->gb2, h); A(w->gW3, np * h); A(w->gb3, np);
     A(w->loss_part, bp); A(w->loss, 1);
     A(w->mask, np); A(w->keep_n, np); A(w->keep_all, np > h ? np : h);
+    w->work_floats = 32 * std::max(bp * h, h * h);
+    A(w->work, w->work_floats);
 #undef A
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&w->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return CGP_ERR_CUDA;
+    }
     std::vector<unsigned char> kn(np, 0), ka(std::max(np, h), 1);
     for (int j = 0; j < n; ++j) kn[j] = 1;
     std::vector<unsigned char> mk(np, 1);
@@ -527,7 +625,7 @@ GemmArgs gargs(int M, int N, int K, int epi, const float* bias, float* of, __nv_
                int ldo, int* err) {
     GemmArgs g;
     g.M = M; g.N = N; g.K = K; g.epi = epi; g.bias = bias; g.out_f32 = of; g.out_bf16 = ob; g.zin = zin;
-    g.ldo = ldo; g.err = err;
+    g.ldo = ldo; g.err = err; g.splits = 1;
     return g;
 }
 
@@ -549,9 +647,9 @@ cudaError_t forward(cgp_ws_s* w, const double* b, const double* p, int B, cudaSt
     const int np = w->np, H = w->H, bp = ((B + 127) / 128) * 128;
     k_prep<<<bp, 256, 0, s>>>(B, w->n, np, b, p, w->X, p ? w->T : nullptr, w->S);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = gemm_tn(w->X, w->W1b, gargs(bp, H, np, EPI_GELU, w->b1, w->Z1, w->H1, nullptr, H, w->err), s);
-    if (e == cudaSuccess) e = gemm_tn(w->H1, w->W2b, gargs(bp, H, H, EPI_GELU, w->b2, w->Z2, w->H2, nullptr, H, w->err), s);
-    if (e == cudaSuccess) e = gemm_tn(w->H2, w->W3b, gargs(bp, np, H, EPI_F32, w->b3, w->Y, nullptr, nullptr, np, w->err), s);
+    if (e == cudaSuccess) e = gemm_tn(w->X, w->W1b, gargs(bp, H, np, EPI_GELU, w->b1, w->Z1, w->H1, nullptr, H, w->err), s, w->work, w->work_floats, w->num_sms);
+    if (e == cudaSuccess) e = gemm_tn(w->H1, w->W2b, gargs(bp, H, H, EPI_GELU, w->b2, w->Z2, w->H2, nullptr, H, w->err), s, w->work, w->work_floats, w->num_sms);
+    if (e == cudaSuccess) e = gemm_tn(w->H2, w->W3b, gargs(bp, np, H, EPI_F32, w->b3, w->Y, nullptr, nullptr, np, w->err), s, w->work, w->work_floats, w->num_sms);
     return e;
 }
 
@@ -579,19 +677,19 @@ cudaError_t train_step(cgp_ws_s* w, const double* b, const double* p, int B, flo
     if ((e = transpose(bp, H, w->H1, w->H1t, s)) != cudaSuccess) return e;
     if ((e = transpose(bp, np, w->X, w->Xt, s)) != cudaSuccess) return e;
     // dW3 = dY^T h2 ; dz2 = (dY W3) * gelu'(z2)
-    if ((e = gemm_tn(w->dYt, w->H2t, gargs(np, H, bp, EPI_F32, nullptr, w->gW3, nullptr, nullptr, H, w->err), s))) return e;
-    if ((e = gemm_tn(w->dYb, w->W3t, gargs(bp, H, np, EPI_GELU_BWD, nullptr, w->dZ2, w->dZ2b, w->Z2, H, w->err), s)))
+    if ((e = gemm_tn(w->dYt, w->H2t, gargs(np, H, bp, EPI_F32, nullptr, w->gW3, nullptr, nullptr, H, w->err), s, w->work, w->work_floats, w->num_sms))) return e;
+    if ((e = gemm_tn(w->dYb, w->W3t, gargs(bp, H, np, EPI_GELU_BWD, nullptr, w->dZ2, w->dZ2b, w->Z2, H, w->err), s, w->work, w->work_floats, w->num_sms)))
         return e;
     k_colsum<<<(H + 255) / 256, 256, 0, s>>>(B, H, w->dZ2, w->gb2);
     if ((e = transpose(bp, H, w->dZ2b, w->dZ2t, s)) != cudaSuccess) return e;
     // dW2 = dz2^T h1 ; dz1 = (dz2 W2) * gelu'(z1)
-    if ((e = gemm_tn(w->dZ2t, w->H1t, gargs(H, H, bp, EPI_F32, nullptr, w->gW2, nullptr, nullptr, H, w->err), s))) return e;
-    if ((e = gemm_tn(w->dZ2b, w->W2t, gargs(bp, H, H, EPI_GELU_BWD, nullptr, w->dZ1, w->dZ1b, w->Z1, H, w->err), s)))
+    if ((e = gemm_tn(w->dZ2t, w->H1t, gargs(H, H, bp, EPI_F32, nullptr, w->gW2, nullptr, nullptr, H, w->err), s, w->work, w->work_floats, w->num_sms))) return e;
+    if ((e = gemm_tn(w->dZ2b, w->W2t, gargs(bp, H, H, EPI_GELU_BWD, nullptr, w->dZ1, w->dZ1b, w->Z1, H, w->err), s, w->work, w->work_floats, w->num_sms)))
         return e;
     k_colsum<<<(H + 255) / 256, 256, 0, s>>>(B, H, w->dZ1, w->gb1);
     if ((e = transpose(bp, H, w->dZ1b, w->dZ1t, s)) != cudaSuccess) return e;
     // dW1 = dz1^T x
-    if ((e = gemm_tn(w->dZ1t, w->Xt, gargs(H, np, bp, EPI_F32, nullptr, w->gW1, nullptr, nullptr, np, w->err), s)))
+    if ((e = gemm_tn(w->dZ1t, w->Xt, gargs(H, np, bp, EPI_F32, nullptr, w->gW1, nullptr, nullptr, np, w->err), s, w->work, w->work_floats, w->num_sms)))
         return e;
     if (lr <= 0.0f) return cudaSuccess;     // gradients only
     w->step += 1;
