@@ -177,39 +177,48 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(const __grid_constant__ CUte
     tc_fence_after();
     const uint32_t tbase = tmem_slot;
 
-    if (threadIdx.x == 0) {
-        // TMA producer
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(smem_u32(&empty_bar[s]), ((kb / STAGES) & 1) ^ 1)) {
-                s_fail = 1;
-                break;
+    // Warp 0 lane 0 produces (TMA), warp 1 lane 0 issues the MMAs; the other lanes of those two
+    // warps wait converged at __syncwarp rather than polling the completion barrier, which would
+    // share the warp's issue slots with the producer or issuer lane.
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % STAGES;
+                if (kb >= STAGES && !mbar_wait(smem_u32(&empty_bar[s]), ((kb / STAGES) & 1) ^ 1)) {
+                    s_fail = 1;
+                    break;
+                }
+                if (s_fail) break;
+                const uint32_t fb = smem_u32(&full_bar[s]);
+                mbar_expect_tx(fb, STAGE_BYTES);
+                const uint32_t sa = smem_u32(smem + (size_t)s * STAGE_BYTES);
+                tma_load_2d(sa, &tmA, (kb0 + kb) * GK, m0, fb);
+                tma_load_2d(sa + A_BYTES, &tmB, (kb0 + kb) * GK, n0, fb);
+                s_issued = kb + 1;
             }
-            if (s_fail) break;
-            const uint32_t fb = smem_u32(&full_bar[s]);
-            mbar_expect_tx(fb, STAGE_BYTES);
-            const uint32_t sa = smem_u32(smem + (size_t)s * STAGE_BYTES);
-            tma_load_2d(sa, &tmA, (kb0 + kb) * GK, m0, fb);
-            tma_load_2d(sa + A_BYTES, &tmB, (kb0 + kb) * GK, n0, fb);
-            s_issued = kb + 1;
         }
-    } else if (threadIdx.x == 32) {
-        // MMA issuer
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % STAGES;
-            if (!mbar_wait(smem_u32(&full_bar[s]), (kb / STAGES) & 1)) {
-                s_fail = 1;
-                break;
-            }
-            tc_fence_after();
-            const uint32_t sa = smem_u32(smem + (size_t)s * STAGE_BYTES);
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % STAGES;
+                if (!mbar_wait(smem_u32(&full_bar[s]), (kb / STAGES) & 1)) {
+                    s_fail = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + (size_t)s * STAGE_BYTES);
 #pragma unroll
-            for (int k = 0; k < GK / 16; ++k)
-                mma_bf16(tbase, umma_desc(sa + 32 * k), umma_desc(sa + A_BYTES + 32 * k), (kb > 0 || k > 0) ? 1u : 0u);
-            mma_commit(smem_u32(&empty_bar[s]));
-            s_consumed = kb + 1;
+                for (int k = 0; k < GK / 16; ++k)
+                    mma_bf16(tbase, umma_desc(sa + 32 * k), umma_desc(sa + A_BYTES + 32 * k), (kb > 0 || k > 0) ? 1u : 0u);
+                mma_commit(smem_u32(&empty_bar[s]));
+                s_consumed = kb + 1;
+            }
+            mma_commit(smem_u32(&done_bar));
         }
-        mma_commit(smem_u32(&done_bar));
+        __syncwarp();
     }
     // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31
     if (!mbar_wait(smem_u32(&done_bar), 0)) s_fail = 1;
