@@ -255,7 +255,8 @@ def run_gpu(args):
     prec = L.CGP_MIXED if args.precision == "mixed" else L.CGP_FP64
     f = Flow(coarse, prob, precision=prec, rtol=args.rtol, device=f"cuda:{local}",
              block_threads=args.threads, spmv_lanes=args.lanes, coarse_solver=args.coarse_solver,
-             precond_degree=args.precond_degree, precond_ratio=args.precond_ratio)
+             precond_degree=args.precond_degree, precond_ratio=args.precond_ratio,
+             **({"warm_start": args.warm_start} if args.warm_start >= 0 else {}))
     stream = torch.cuda.current_stream()
     flush = L2Flush(f"cuda:{local}")
     bc = torch.empty_like(f.pc)
@@ -266,6 +267,8 @@ def run_gpu(args):
         L.cgp_assemble(f.ctx, f.u, stream)
         L.cgp_momentum_solve(f.ctx, f.u, ut, stream)
         L.cgp_restrict(f.ctx, ut, bc, stream)
+        if f.params.warm_start == 1:
+            L.cgp_predict_pressure(f.ctx, f.pc, stream)
         ev[0].record(stream)
         L.cgp_poisson_solve(f.ctx, bc, f.pc, stream)
         ev[1].record(stream)
@@ -334,7 +337,7 @@ def run_gpu(args):
         cpu = {"value": 1.0 / statistics.mean(times), "unit": "steps/s", "cores": cores, "kind": "oracle",
                "sample": f"{len(times)} oracle steps of the same workload from rest (setup {t_setup:.1f}s excluded)"}
 
-    launches_per_step = 7 + f.info.levels
+    launches_per_step = 7 + f.info.levels + (2 if f.params.warm_start == 1 else 0)
     tname = "double" if prec == L.CGP_FP64 else "float"
     kname = {0: f"k_cg<{tname}, 1>", 1: f"k_pcg_onchip<{tname}>", 2: f"k_pcg_pipe<{tname}>",
              3: "k_pcg_schwarz<double, float>", 4: f"k_pcg_schwarz<{tname}, {tname}>"}[f.info.coarse_kernel]
@@ -348,7 +351,8 @@ def run_gpu(args):
                    "l2": "flushed between timed steps (512 MB write, then 256 MB read)", "parallelism": "replicas" if ws > 1 else "1gpu",
                    "block_threads": f.info.block_threads, "grid_blocks": f.info.grid_blocks,
                    "spmv_lanes": f.info.spmv_lanes, "coarse_kernel": kname,
-                   "precond_degree": args.precond_degree},
+                   "precond_degree": args.precond_degree,
+                   "coarse_initial_guess": "2 p^n - p^(n-1)" if f.params.warm_start == 1 else "p^n"},
         "coarse_solves_per_s": 1000.0 / pms,
         "poisson_ms": pms, "poisson_iters": it, "poisson_outer": outer,
         "momentum_iters": statistics.mean(mom_iters), "mass_iters": statistics.mean(mass_iters),
@@ -551,6 +555,7 @@ def main():
     ap.add_argument("--coarse-solver", type=int, default=0)
     ap.add_argument("--precond-degree", type=int, default=0)
     ap.add_argument("--precond-ratio", type=float, default=0.0)
+    ap.add_argument("--warm-start", type=int, default=-1)   # -1: the library default (1, extrapolation)
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spmv", action="store_true")

@@ -89,6 +89,9 @@ typedef struct {
                           CSR and sliced ELL, 1 = sliced ELL, 2 = CSR */
     int precond_degree;
     double precond_ratio;
+    int warm_start;    /* initial guess of the coarse Poisson solve inside cgp_step and the batched
+                          step: 0 = the previous step's pressure, 1 (default) = its linear
+                          extrapolation from the two previous steps (cgp_predict_pressure) */
 } cgp_params;
 
 /* A coarse mesh: n_nodes points xy_host[n][2] and n_tris counter-clockwise triangles
@@ -123,7 +126,8 @@ typedef struct {
 } cgp_stats;
 
 /* Fill *p with the defaults: rho = 1, mu = 0.01, dt = 0.01, levels = 1, CGP_FP64, rtol = 1e-8,
- * inner_rtol = 1e-4, max_iter = 20000, max_outer = 30, spmv_lanes = 0, block_threads = 0. */
+ * inner_rtol = 1e-4, max_iter = 20000, max_outer = 30, spmv_lanes = 0, block_threads = 0,
+ * coarse_solver = 0, spmv_format = 0, precond_degree = 0, precond_ratio = 0, warm_start = 1. */
 void cgp_default_params(cgp_params* p);
 
 /* Preprocessing (the paper's C_pre, Sect. 2.4): validates the coarse mesh, refines it
@@ -146,6 +150,13 @@ int cgp_mesh_create(const cgp_mesh_desc* coarse, const cgp_params* prm, cgp_ctx*
  * the fine assembly). Any output may be NULL. Errors: CGP_ERR_ARG, CGP_ERR_MESH. */
 int cgp_refine(const cgp_mesh_desc* coarse, int levels, int* n_fine, int* n_tris_fine, double* xy_host,
                int* tri_host, int* sp_host, int* colour_host);
+
+/* Coarse-pressure predictor for time stepping: pc <- 2 pc - pc_prev, where pc_prev is the pc the
+ * context saw at its previous call (the previous step's pressure when pc holds the latest one);
+ * then pc_prev <- the incoming pc. The first call after cgp_set_bc only records pc. pc_dev:
+ * [n_coarse] float64, device. Stream-ordered; cgp_step calls it when warm_start = 1. Errors:
+ * CGP_ERR_ARG, CGP_ERR_STATE, CGP_ERR_CUDA. */
+int cgp_predict_pressure(cgp_ctx ctx, double* pc_dev, void* stream);
 
 /* Sizes and launch shapes of the context. */
 int cgp_mesh_info(cgp_ctx ctx, cgp_info* info);

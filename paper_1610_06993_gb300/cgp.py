@@ -34,7 +34,7 @@ class cgp_params(C.Structure):
                 ("precision", C.c_int), ("rtol", C.c_double), ("inner_rtol", C.c_double),
                 ("max_iter", C.c_int), ("max_outer", C.c_int), ("spmv_lanes", C.c_int),
                 ("block_threads", C.c_int), ("coarse_solver", C.c_int), ("spmv_format", C.c_int),
-                ("precond_degree", C.c_int), ("precond_ratio", C.c_double)]
+                ("precond_degree", C.c_int), ("precond_ratio", C.c_double), ("warm_start", C.c_int)]
 
 
 class cgp_mesh_desc(C.Structure):
@@ -87,6 +87,7 @@ _SIGNATURES = {
     "cgp_batch_poisson_solve": (C.c_int, [_VP, _VP]),
     "cgp_batch_destroy": (C.c_int, [_VP]),
     "cgp_copy_coarse_rhs": (C.c_int, [_VP, _VP, _VP]),
+    "cgp_predict_pressure": (C.c_int, [_VP, _VP, _VP]),
     "cgp_spmv": (C.c_int, [_VP, _VP, _VP, _VP]),
     "cgp_gemm_bf16": (C.c_int, [C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP]),
     "cgp_ws_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_VP)]),
@@ -312,6 +313,10 @@ def cgp_batch_destroy(b: int) -> None:
 
 def cgp_spmv(ctx: int, x_dev, y_dev, stream=None) -> None:
     _check(load().cgp_spmv(ctx, _ptr(x_dev), _ptr(y_dev), _stream(stream)), "cgp_spmv")
+
+
+def cgp_predict_pressure(ctx: int, pc_dev, stream=None) -> None:
+    _check(load().cgp_predict_pressure(ctx, _ptr(pc_dev), _stream(stream)), "cgp_predict_pressure")
 
 
 def cgp_copy_coarse_rhs(ctx: int, bc_dev, stream=None) -> None:

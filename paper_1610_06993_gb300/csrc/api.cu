@@ -80,6 +80,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     if (P.precision != CGP_FP64 && P.precision != CGP_MIXED) return CGP_ERR_ARG;
     if (P.coarse_solver < 0 || P.coarse_solver > 5) return CGP_ERR_ARG;
     if (P.precond_degree < 0 || P.precond_degree > 64 || P.precond_ratio < 0.0) return CGP_ERR_ARG;
+    if (P.warm_start < 0 || P.warm_start > 1) return CGP_ERR_ARG;
     if (P.spmv_format < 0 || P.spmv_format > 2) return CGP_ERR_ARG;
     if (P.inner_rtol <= 0.0) P.inner_rtol = 1e-4;
     if (P.max_iter <= 0) P.max_iter = 20000;
@@ -156,6 +157,9 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     TRY(dalloc(c, &c->pf, nf));
     TRY(dalloc(c, &c->ut, 2 * nf));
     TRY(dalloc(c, &c->bc, nc));
+    TRY(dalloc(c, &c->pc_prev, nc));
+    TRY(dalloc(c, &c->pc_flag, 1));
+    CK(cudaMemset(c->pc_flag, 0, sizeof(int)));
     TRY(dalloc(c, &c->u_stage, 2 * nf));
     TRY(dalloc(c, &c->pc_stage, nc));
     // Krylov workspace: the largest of BiCGStab (9 pair vectors) and CG (6 vectors), 256-byte carved
@@ -233,6 +237,7 @@ void cgp_default_params(cgp_params* p) {
     p->max_outer = 30;
     p->spmv_lanes = 0;
     p->block_threads = 0;
+    p->warm_start = 1;
 }
 
 int cgp_mesh_create(const cgp_mesh_desc* coarse, const cgp_params* prm, cgp_ctx* out) {
@@ -309,6 +314,7 @@ int cgp_set_bc(cgp_ctx c, const unsigned char* vel_mask, const unsigned char* p_
     CK(cudaMemcpy(c->p_mask, p_mask, (size_t)c->nc, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->g, g, 2 * sizeof(double) * (size_t)c->nf, cudaMemcpyHostToDevice));
     CK(launch_apply_pressure_bc(c, 0));
+    CK(cudaMemset(c->pc_flag, 0, sizeof(int)));   // the predictor starts over
     CK(cudaStreamSynchronize(0));
     TRY(schwarz_values(c));
     c->bc_set = true;
@@ -343,6 +349,13 @@ int cgp_restrict(cgp_ctx c, const double* ut_dev, double* bc_dev, void* stream) 
     return CGP_OK;
 }
 
+int cgp_predict_pressure(cgp_ctx c, double* pc_dev, void* stream) {
+    if (!c || !pc_dev) return CGP_ERR_ARG;
+    if (!c->bc_set) return CGP_ERR_STATE;
+    CK(launch_predict(c, pc_dev, (cudaStream_t)stream));
+    return CGP_OK;
+}
+
 int cgp_poisson_solve(cgp_ctx c, const double* bc_dev, double* pc_dev, void* stream) {
     if (!c || !pc_dev) return CGP_ERR_ARG;
     if (!c->bc_set) return CGP_ERR_STATE;
@@ -370,6 +383,7 @@ int cgp_step(cgp_ctx c, double* u_dev, double* pc_dev, void* stream) {
     CK(launch_assemble_step(c, u_dev, s));
     CK(launch_momentum_bicgstab(c, u_dev, c->ut, s));
     CK(launch_restrict_rhs(c, c->ut, c->bc, s));
+    if (c->prm.warm_start == 1) CK(launch_predict(c, pc_dev, s));
     CK(launch_poisson_cg(c, c->bc, pc_dev, s));
     CK(launch_prolong(c, pc_dev, c->pf, s));
     CK(launch_gradient(c, c->pf, c->grad, s));

@@ -124,6 +124,7 @@ int create_impl(cgp_ctx* ctxs, int n, double* const* u, double* const* pc, cgp_b
     // solver and fits it; otherwise the Jacobi kernel
     batch_poisson2l_build(b);
     cudaGetLastError();
+    if (batch_predict_build(b) != cudaSuccess) return CGP_ERR_CUDA;
     return CGP_OK;
 }
 
@@ -132,6 +133,7 @@ cudaError_t enqueue_step(cgp_batch_s* b, cudaStream_t s) {
     if (e == cudaSuccess) e = batch_asm_launch(b, s);
     if (e == cudaSuccess) e = batch_momentum_launch(b, s);
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) e = launch_restrict_rhs(b->ctx[i], b->ctx[i]->ut, b->ctx[i]->bc, s);
+    if (e == cudaSuccess) e = batch_predict_launch(b, s);
     if (e == cudaSuccess) e = b->poisson_2l ? batch_poisson2l_launch(b, s) : batch_poisson_launch(b, s);
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
         cgp_ctx_s* c = b->ctx[i];

@@ -102,6 +102,8 @@ struct cgp_ctx_s {
     double* pf = nullptr;        // [nf]
     double* ut = nullptr;        // [nf][2] intermediate velocity for cgp_step
     double* bc = nullptr;        // [nc] coarse right-hand side for cgp_step
+    double* pc_prev = nullptr;   // [nc] pressure seen by the previous predictor call
+    int* pc_flag = nullptr;      // 1 once pc_prev holds a pressure
 
     // Krylov workspace and reductions
     void* ws = nullptr;
@@ -162,6 +164,9 @@ struct cgp_batch_s {
     void* tab_poi = nullptr;
     void* tab_mass = nullptr;
     void* tab_poi2 = nullptr;            // two-level coarse CG arguments (poisson_2l)
+    void* tab_predict = nullptr;         // coarse-pressure predictor arguments (warm_start = 1)
+    bool predict = false;
+    int predict_nmax = 0;
     bool poisson_2l = false;
     size_t smem_poi2 = 0;
     cudaStream_t cap_stream = nullptr;
@@ -214,6 +219,9 @@ cudaError_t launch_gradient(cgp_ctx_s* c, const double* pf, double* grad, cudaSt
 cudaError_t launch_correct(cgp_ctx_s* c, const double* ut, const double* w, double* u, double* gp_out,
                            cudaStream_t s);
 cudaError_t launch_copy_pairs(const double* src, double* dst, int n, cudaStream_t s);
+cudaError_t launch_predict(cgp_ctx_s* c, double* pc, cudaStream_t s);
+cudaError_t batch_predict_launch(cgp_batch_s* b, cudaStream_t s);
+cudaError_t batch_predict_build(cgp_batch_s* b);
 
 // Cooperative launch helper: launches `func` with the shape, `smem` bytes of dynamic shared
 // memory and its single by-value argument (typed, so a kernel cannot be handed the wrong

@@ -1,4 +1,7 @@
 // Grid-transfer and correction kernels of the CGP step (the paper's Eqs. 20-23, 29-30).
+#include <algorithm>
+#include <vector>
+
 #include "ctx.h"
 
 namespace cgp {
@@ -114,6 +117,73 @@ cudaError_t launch_gradient(cgp_ctx_s* c, const double* pf, double* grad, cudaSt
 cudaError_t launch_correct(cgp_ctx_s* c, const double* ut, const double* w, double* u, double* gp_out,
                            cudaStream_t s) {
     k_correct<<<(c->nf + 255) / 256, 256, 0, s>>>(c->nf, ut, w, c->prm.dt / c->prm.rho, c->vel_mask, c->g, u, gp_out);
+    return cudaGetLastError();
+}
+
+namespace {
+
+struct PredictArgs {
+    double* pc;
+    double* prev;
+    int* flag;
+    int n;
+};
+
+// Linear extrapolation of the coarse pressure in time: p <- 2 p - p_prev once a previous pressure
+// is recorded (flag), then p_prev <- the incoming p. blockIdx.y selects the instance of a batch.
+// The flag is only read here; k_predict_flag, launched after this kernel, sets it.
+__global__ void k_predict(const PredictArgs* __restrict__ tab, PredictArgs single) {
+    const PredictArgs a = tab ? tab[blockIdx.y] : single;
+    const int have = *a.flag;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const double pn = a.pc[i];
+    if (have) a.pc[i] = 2.0 * pn - a.prev[i];
+    a.prev[i] = pn;
+}
+
+__global__ void k_predict_flag(const PredictArgs* __restrict__ tab, PredictArgs single) {
+    const PredictArgs a = tab ? tab[blockIdx.x] : single;
+    if (threadIdx.x == 0) *a.flag = 1;
+}
+
+}  // namespace
+
+cudaError_t launch_predict(cgp_ctx_s* c, double* pc, cudaStream_t s) {
+    const PredictArgs a{pc, c->pc_prev, c->pc_flag, c->nc};
+    k_predict<<<dim3((c->nc + 255) / 256, 1), 256, 0, s>>>(nullptr, a);
+    k_predict_flag<<<1, 32, 0, s>>>(nullptr, a);
+    return cudaGetLastError();
+}
+
+// Batched predictor (used when every instance has warm_start = 1): one launch over all instances.
+cudaError_t batch_predict_build(cgp_batch_s* b) {
+    b->predict = false;
+    int nmax = 0;
+    std::vector<PredictArgs> tab(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        cgp_ctx_s* c = b->ctx[i];
+        if (c->prm.warm_start != 1) return cudaSuccess;
+        tab[i] = PredictArgs{b->pc[i], c->pc_prev, c->pc_flag, c->nc};
+        nmax = std::max(nmax, c->nc);
+    }
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(PredictArgs) * tab.size());
+    if (e != cudaSuccess) return e;
+    b->allocs.push_back(d);
+    if ((e = cudaMemcpy(d, tab.data(), sizeof(PredictArgs) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    b->tab_predict = d;
+    b->predict_nmax = nmax;
+    b->predict = true;
+    return cudaSuccess;
+}
+
+cudaError_t batch_predict_launch(cgp_batch_s* b, cudaStream_t s) {
+    if (!b->predict) return cudaSuccess;
+    const PredictArgs* tab = (const PredictArgs*)b->tab_predict;
+    k_predict<<<dim3((b->predict_nmax + 255) / 256, b->n), 256, 0, s>>>(tab, PredictArgs{});
+    k_predict_flag<<<b->n, 32, 0, s>>>(tab, PredictArgs{});
     return cudaGetLastError();
 }
 

@@ -320,3 +320,27 @@ def test_schwarz_cuts_iterations(L, bfs_full, precision):
         host_rel = np.linalg.norm(b - K @ p) / np.linalg.norm(b)
         assert st.poisson_rel_res <= 1e-8 and host_rel <= 1.01e-8, (solver, host_rel, st.as_dict())
     assert its[3] * 5 <= its[5], its
+
+
+def test_pressure_predictor(L, cavity_state):
+    """warm_start = 1 starts every coarse solve of cgp_step from 2 p^n - p^(n-1) instead of p^n. The
+    initial guess does not change what the solve converges to, so 30 cavity steps still match the
+    oracle at the parity bar (1e-10 relative L2 in u), while the solves from step 3 on (once two
+    previous pressures exist and the start-up transient has passed) need fewer CG iterations in
+    total. The first call only records the pressure."""
+    coarse, prob, _, _ = cavity_state
+    steps, its = 30, {}
+    ref = ocgp.run(coarse, prob, steps).u
+    for ws in (0, 1):
+        f = flow(coarse, prob, rtol=1e-13, warm_start=ws)
+        tot = 0
+        for k in range(steps):
+            f.step()
+            st = f.stats(check=True)
+            if k >= 2:
+                tot += st.poisson_iters
+        its[ws] = tot
+        u = f.u.cpu().numpy()
+        f.close()
+        assert rel(u, ref) < 1e-10, (ws, rel(u, ref))
+    assert its[1] < its[0], its

@@ -34,6 +34,15 @@ def test_exports_every_declared_symbol(L):
         assert n in names
 
 
+def test_binding_declares_every_entry_point(L):
+    """Every entry point of the header has explicit ctypes argument types in the binding: without
+    them ctypes passes Python integers as 32-bit C ints, which truncates device pointers."""
+    decl = open(os.path.join(ROOT, "include", "cgp.h")).read()
+    names = re.findall(r"^\s*(?:int|void|const char\*)\s+(cgp_\w+)\(", decl, re.M)
+    missing = [n for n in names if n not in L._SIGNATURES]
+    assert not missing, missing
+
+
 @pytest.mark.parametrize("mesh", [ci.cavity_mesh(9, 3), ci.bfs_mesh(2, 4)], ids=["cavity", "bfs"])
 @pytest.mark.parametrize("levels", [0, 1, 2])
 def test_native_refinement_matches_oracle(L, mesh, levels):
