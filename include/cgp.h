@@ -89,9 +89,11 @@ typedef struct {
                           CSR and sliced ELL, 1 = sliced ELL, 2 = CSR */
     int precond_degree;
     double precond_ratio;
-    int warm_start;    /* initial guess of the coarse Poisson solve inside cgp_step and the batched
-                          step: 0 = the previous step's pressure, 1 (default) = its linear
-                          extrapolation from the two previous steps (cgp_predict_pressure) */
+    int warm_start;    /* initial guesses of the coarse Poisson and mass solves of a step: 0 = the
+                          previous step's p^n and w^n, 1 (default) = their linear extrapolations
+                          2 v^n - v^(n-1), history kept by the context (cgp_step, the batched step,
+                          cgp_prolong_correct for w, cgp_predict_pressure for p); the momentum solve
+                          starts from u^n either way */
 } cgp_params;
 
 /* A coarse mesh: n_nodes points xy_host[n][2] and n_tris counter-clockwise triangles

@@ -159,7 +159,10 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     TRY(dalloc(c, &c->bc, nc));
     TRY(dalloc(c, &c->pc_prev, nc));
     TRY(dalloc(c, &c->pc_flag, 1));
+    TRY(dalloc(c, &c->w_prev, 2 * nf));
+    TRY(dalloc(c, &c->w_flag, 1));
     CK(cudaMemset(c->pc_flag, 0, sizeof(int)));
+    CK(cudaMemset(c->w_flag, 0, sizeof(int)));
     TRY(dalloc(c, &c->u_stage, 2 * nf));
     TRY(dalloc(c, &c->pc_stage, nc));
     // Krylov workspace: the largest of BiCGStab (9 pair vectors) and CG (6 vectors), 256-byte carved
@@ -212,6 +215,16 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     CK(pipe_prepare(c));
     c->spmv_sell = P.spmv_format == 1;
     return CGP_OK;
+}
+
+// Mass solve of the correction (Eq. 23), M w = G p_f, from the previous step's w, or with
+// warm_start = 1 from its extrapolation 2 w^n - w^(n-1) (w is linear in the pressure).
+cudaError_t mass_stage(cgp_ctx_s* c, cudaStream_t s) {
+    if (c->prm.warm_start == 1) {
+        cudaError_t e = launch_predict_vec(c->w, c->w, c->w_prev, c->w_flag, 2 * c->nf, s);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_mass_cg(c, c->grad, c->w, s);
 }
 
 void destroy_impl(cgp_ctx_s* c) {
@@ -314,7 +327,8 @@ int cgp_set_bc(cgp_ctx c, const unsigned char* vel_mask, const unsigned char* p_
     CK(cudaMemcpy(c->p_mask, p_mask, (size_t)c->nc, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->g, g, 2 * sizeof(double) * (size_t)c->nf, cudaMemcpyHostToDevice));
     CK(launch_apply_pressure_bc(c, 0));
-    CK(cudaMemset(c->pc_flag, 0, sizeof(int)));   // the predictor starts over
+    CK(cudaMemset(c->pc_flag, 0, sizeof(int)));   // the predictors start over
+    CK(cudaMemset(c->w_flag, 0, sizeof(int)));
     CK(cudaStreamSynchronize(0));
     TRY(schwarz_values(c));
     c->bc_set = true;
@@ -371,7 +385,7 @@ int cgp_prolong_correct(cgp_ctx c, const double* pc_dev, const double* ut_dev, d
     double* pf = pf_dev ? pf_dev : c->pf;
     CK(launch_prolong(c, pc_dev, pf, s));
     CK(launch_gradient(c, pf, c->grad, s));
-    CK(launch_mass_cg(c, c->grad, c->w, s));
+    CK(mass_stage(c, s));
     CK(launch_correct(c, ut_dev, c->w, u_dev, gp_dev, s));
     return CGP_OK;
 }
@@ -387,7 +401,7 @@ int cgp_step(cgp_ctx c, double* u_dev, double* pc_dev, void* stream) {
     CK(launch_poisson_cg(c, c->bc, pc_dev, s));
     CK(launch_prolong(c, pc_dev, c->pf, s));
     CK(launch_gradient(c, c->pf, c->grad, s));
-    CK(launch_mass_cg(c, c->grad, c->w, s));
+    CK(mass_stage(c, s));
     CK(launch_correct(c, c->ut, c->w, u_dev, nullptr, s));
     return CGP_OK;
 }

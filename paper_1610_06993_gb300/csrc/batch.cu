@@ -131,9 +131,9 @@ int create_impl(cgp_ctx* ctxs, int n, double* const* u, double* const* pc, cgp_b
 cudaError_t enqueue_step(cgp_batch_s* b, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(b->sync, 0, sizeof(SyncWords) * (size_t)b->n * SYNC_COUNT, s);
     if (e == cudaSuccess) e = batch_asm_launch(b, s);
+    if (e == cudaSuccess) e = batch_predict_launch(b, s);   // p_c and w still hold step n
     if (e == cudaSuccess) e = batch_momentum_launch(b, s);
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) e = launch_restrict_rhs(b->ctx[i], b->ctx[i]->ut, b->ctx[i]->bc, s);
-    if (e == cudaSuccess) e = batch_predict_launch(b, s);
     if (e == cudaSuccess) e = b->poisson_2l ? batch_poisson2l_launch(b, s) : batch_poisson_launch(b, s);
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
         cgp_ctx_s* c = b->ctx[i];

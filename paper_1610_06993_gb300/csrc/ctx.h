@@ -104,6 +104,8 @@ struct cgp_ctx_s {
     double* bc = nullptr;        // [nc] coarse right-hand side for cgp_step
     double* pc_prev = nullptr;   // [nc] pressure seen by the previous predictor call
     int* pc_flag = nullptr;      // 1 once pc_prev holds a pressure
+    double* w_prev = nullptr;    // [nf][2] previous mass-solve solution (warm_start = 1)
+    int* w_flag = nullptr;
 
     // Krylov workspace and reductions
     void* ws = nullptr;
@@ -166,7 +168,7 @@ struct cgp_batch_s {
     void* tab_poi2 = nullptr;            // two-level coarse CG arguments (poisson_2l)
     void* tab_predict = nullptr;         // coarse-pressure predictor arguments (warm_start = 1)
     bool predict = false;
-    int predict_nmax = 0;
+    int predict_nmax = 0, predict_count = 0;
     bool poisson_2l = false;
     size_t smem_poi2 = 0;
     cudaStream_t cap_stream = nullptr;
@@ -220,6 +222,7 @@ cudaError_t launch_correct(cgp_ctx_s* c, const double* ut, const double* w, doub
                            cudaStream_t s);
 cudaError_t launch_copy_pairs(const double* src, double* dst, int n, cudaStream_t s);
 cudaError_t launch_predict(cgp_ctx_s* c, double* pc, cudaStream_t s);
+cudaError_t launch_predict_vec(const double* in, double* out, double* prev, int* flag, int n, cudaStream_t s);
 cudaError_t batch_predict_launch(cgp_batch_s* b, cudaStream_t s);
 cudaError_t batch_predict_build(cgp_batch_s* b);
 

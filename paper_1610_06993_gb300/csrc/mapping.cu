@@ -123,23 +123,24 @@ cudaError_t launch_correct(cgp_ctx_s* c, const double* ut, const double* w, doub
 namespace {
 
 struct PredictArgs {
-    double* pc;
-    double* prev;
-    int* flag;
+    const double* in;   // the latest value v^n
+    double* out;        // the prediction (may be `in`)
+    double* prev;       // v^(n-1), replaced by v^n
+    int* flag;          // 1 once prev holds a value
     int n;
 };
 
-// Linear extrapolation of the coarse pressure in time: p <- 2 p - p_prev once a previous pressure
-// is recorded (flag), then p_prev <- the incoming p. blockIdx.y selects the instance of a batch.
-// The flag is only read here; k_predict_flag, launched after this kernel, sets it.
+// Linear extrapolation in time of a solver's initial guess: out <- 2 v^n - v^(n-1) once a previous
+// value is recorded (flag; else out <- v^n), then prev <- v^n. blockIdx.y selects the vector of a
+// batch. The flag is only read here; k_predict_flag, launched after this kernel, sets it.
 __global__ void k_predict(const PredictArgs* __restrict__ tab, PredictArgs single) {
     const PredictArgs a = tab ? tab[blockIdx.y] : single;
     const int have = *a.flag;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    const double pn = a.pc[i];
-    if (have) a.pc[i] = 2.0 * pn - a.prev[i];
-    a.prev[i] = pn;
+    const double vn = a.in[i];
+    a.out[i] = have ? 2.0 * vn - a.prev[i] : vn;
+    a.prev[i] = vn;
 }
 
 __global__ void k_predict_flag(const PredictArgs* __restrict__ tab, PredictArgs single) {
@@ -149,24 +150,33 @@ __global__ void k_predict_flag(const PredictArgs* __restrict__ tab, PredictArgs 
 
 }  // namespace
 
-cudaError_t launch_predict(cgp_ctx_s* c, double* pc, cudaStream_t s) {
-    const PredictArgs a{pc, c->pc_prev, c->pc_flag, c->nc};
-    k_predict<<<dim3((c->nc + 255) / 256, 1), 256, 0, s>>>(nullptr, a);
+cudaError_t launch_predict_vec(const double* in, double* out, double* prev, int* flag, int n, cudaStream_t s) {
+    const PredictArgs a{in, out, prev, flag, n};
+    k_predict<<<dim3((n + 255) / 256, 1), 256, 0, s>>>(nullptr, a);
     k_predict_flag<<<1, 32, 0, s>>>(nullptr, a);
     return cudaGetLastError();
 }
 
-// Batched predictor (used when every instance has warm_start = 1): one launch over all instances.
+cudaError_t launch_predict(cgp_ctx_s* c, double* pc, cudaStream_t s) {
+    return launch_predict_vec(pc, pc, c->pc_prev, c->pc_flag, c->nc, s);
+}
+
+// Batched predictors of every instance with warm_start = 1 (coarse pressure and mass-solve initial
+// guess, both in place), one launch at the start of a step, while both vectors still hold their
+// values from the previous step.
 cudaError_t batch_predict_build(cgp_batch_s* b) {
     b->predict = false;
     int nmax = 0;
-    std::vector<PredictArgs> tab(b->n);
+    std::vector<PredictArgs> tab;
     for (int i = 0; i < b->n; ++i) {
         cgp_ctx_s* c = b->ctx[i];
-        if (c->prm.warm_start != 1) return cudaSuccess;
-        tab[i] = PredictArgs{b->pc[i], c->pc_prev, c->pc_flag, c->nc};
-        nmax = std::max(nmax, c->nc);
+        if (c->prm.warm_start != 1) continue;
+        const int n2 = 2 * c->nf;
+        tab.push_back(PredictArgs{b->pc[i], b->pc[i], c->pc_prev, c->pc_flag, c->nc});
+        tab.push_back(PredictArgs{c->w, c->w, c->w_prev, c->w_flag, n2});
+        nmax = std::max({nmax, c->nc, n2});
     }
+    if (tab.empty()) return cudaSuccess;
     void* d = nullptr;
     cudaError_t e = cudaMalloc(&d, sizeof(PredictArgs) * tab.size());
     if (e != cudaSuccess) return e;
@@ -175,6 +185,7 @@ cudaError_t batch_predict_build(cgp_batch_s* b) {
         return e;
     b->tab_predict = d;
     b->predict_nmax = nmax;
+    b->predict_count = (int)tab.size();
     b->predict = true;
     return cudaSuccess;
 }
@@ -182,8 +193,8 @@ cudaError_t batch_predict_build(cgp_batch_s* b) {
 cudaError_t batch_predict_launch(cgp_batch_s* b, cudaStream_t s) {
     if (!b->predict) return cudaSuccess;
     const PredictArgs* tab = (const PredictArgs*)b->tab_predict;
-    k_predict<<<dim3((b->predict_nmax + 255) / 256, b->n), 256, 0, s>>>(tab, PredictArgs{});
-    k_predict_flag<<<b->n, 32, 0, s>>>(tab, PredictArgs{});
+    k_predict<<<dim3((b->predict_nmax + 255) / 256, b->predict_count), 256, 0, s>>>(tab, PredictArgs{});
+    k_predict_flag<<<b->predict_count, 32, 0, s>>>(tab, PredictArgs{});
     return cudaGetLastError();
 }
 

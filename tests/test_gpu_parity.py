@@ -323,11 +323,11 @@ def test_schwarz_cuts_iterations(L, bfs_full, precision):
 
 
 def test_pressure_predictor(L, cavity_state):
-    """warm_start = 1 starts every coarse solve of cgp_step from 2 p^n - p^(n-1) instead of p^n. The
-    initial guess does not change what the solve converges to, so 30 cavity steps still match the
-    oracle at the parity bar (1e-10 relative L2 in u), while the solves from step 3 on (once two
-    previous pressures exist and the start-up transient has passed) need fewer CG iterations in
-    total. The first call only records the pressure."""
+    """warm_start = 1 starts the coarse Poisson and mass solves of cgp_step from the linear
+    extrapolations 2 v^n - v^(n-1) instead of v^n. The initial guess does not change what a solve
+    converges to, so 30 cavity steps still match the oracle at the parity bar (1e-10 relative L2 in
+    u), while from step 3 on (two previous values exist, the start-up transient has passed) the
+    solves need fewer iterations in total. The first call only records the values."""
     coarse, prob, _, _ = cavity_state
     steps, its = 30, {}
     ref = ocgp.run(coarse, prob, steps).u
@@ -338,7 +338,7 @@ def test_pressure_predictor(L, cavity_state):
             f.step()
             st = f.stats(check=True)
             if k >= 2:
-                tot += st.poisson_iters
+                tot += st.poisson_iters + st.momentum_iters + st.mass_iters
         its[ws] = tot
         u = f.u.cpu().numpy()
         f.close()
