@@ -337,7 +337,7 @@ def run_gpu(args):
         cpu = {"value": 1.0 / statistics.mean(times), "unit": "steps/s", "cores": cores, "kind": "oracle",
                "sample": f"{len(times)} oracle steps of the same workload from rest (setup {t_setup:.1f}s excluded)"}
 
-    launches_per_step = 7 + f.info.levels + (4 if f.params.warm_start == 1 else 0)
+    launches_per_step = 9 + f.info.levels + (4 if f.params.warm_start == 1 else 0)
     tname = "double" if prec == L.CGP_FP64 else "float"
     kname = {0: f"k_cg<{tname}, 1>", 1: f"k_pcg_onchip<{tname}>", 2: f"k_pcg_pipe<{tname}>",
              3: "k_pcg_schwarz<double, float>", 4: f"k_pcg_schwarz<{tname}, {tname}>"}[f.info.coarse_kernel]

@@ -213,6 +213,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     c->width_c = 0;
     for (int i = 0; i < H.coarse.n; ++i) c->width_c = std::max(c->width_c, H.coarse.rp[i + 1] - H.coarse.rp[i]);
     CK(pipe_prepare(c));
+    TRY(assemble_gather_build(c));
     c->spmv_sell = P.spmv_format == 1;
     return CGP_OK;
 }

@@ -166,7 +166,110 @@ StepAsmArgs asm_args(cgp_ctx_s* c, const double* u, SyncWords* sw) {
 
 }  // namespace
 
+// ---- per-step assembly without colours (single contexts) ------------------------------------
+// The convection matrix is a sum of element contributions. Instead of scattering them colour by
+// colour behind grid barriers, each element writes its 9 contributions to a buffer and each CSR
+// entry then gathers its own (the list of contributions per entry is fixed by the mesh and built
+// once, in element order, so the sum is deterministic): three plain launches, no barrier.
+namespace {
+
+// ev[9 e + 3 r + q] = dt rho (|T|/12) ((u_sum + u_r) . grad phi_q)  (Eq. 16's N, element e)
+__global__ void k_conv_elements(int t, const int* __restrict__ tri, const double* __restrict__ geo,
+                                const double* __restrict__ u, double dtrho, double* __restrict__ ev) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= t) return;
+    const double* g = geo + 8 * (size_t)e;
+    const double area12 = g[0] / 12.0;
+    double ux[3], uy[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) load2(u, tri[3 * e + q], ux[q], uy[q]);
+    const double sx = ux[0] + ux[1] + ux[2], sy = uy[0] + uy[1] + uy[2];
+    double* o = ev + 9 * (size_t)e;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const double cx = area12 * (sx + ux[r]), cy = area12 * (sy + uy[r]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) o[r * 3 + q] = dtrho * (cx * g[1 + q] + cy * g[4 + q]);
+    }
+}
+
+// A[k] = A0[k] + the element contributions of entry k (and its FP32 copy)
+__global__ void k_gather_entries(int nnz, const int* __restrict__ ip, const int* __restrict__ idx,
+                                 const double* __restrict__ ev, const double* __restrict__ A0, double* __restrict__ A,
+                                 float* __restrict__ A32) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nnz) return;
+    double v = A0[k];
+    for (int m = ip[k]; m < ip[k + 1]; ++m) v += ev[idx[m]];
+    A[k] = v;
+    if (A32) A32[k] = (float)v;
+}
+
+// Jacobi diagonals and the right-hand side b = rho M u^n (Dirichlet rows: prescribed values)
+__global__ void k_rows(int nf, const int* __restrict__ rp, const int* __restrict__ ci, const int* __restrict__ diag,
+                       const double* __restrict__ A, const double* __restrict__ M, const double* __restrict__ u,
+                       const unsigned char* __restrict__ mask, const double* __restrict__ g, double rho,
+                       double* __restrict__ dinv, float* __restrict__ dinv32, double* __restrict__ b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const unsigned char m = mask[i];
+    const double di = 1.0 / A[diag[i]];
+    const double dx = (m & CGP_BC_U) ? 1.0 : di, dy = (m & CGP_BC_V) ? 1.0 : di;
+    store2(dinv, i, dx, dy);
+    if (dinv32) store2(dinv32, i, (float)dx, (float)dy);
+    double mx = 0.0, my = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        double ujx, ujy;
+        load2(u, ci[k], ujx, ujy);
+        mx += M[k] * ujx;
+        my += M[k] * ujy;
+    }
+    double gx, gy;
+    load2(g, i, gx, gy);
+    store2(b, i, (m & CGP_BC_U) ? gx : rho * mx, (m & CGP_BC_V) ? gy : rho * my);
+}
+
+}  // namespace
+
+// Entry -> contribution lists of the fine pattern (host, once per context).
+int assemble_gather_build(cgp_ctx_s* c) {
+    const HostElems& h = c->hm.ef;
+    const int nnz = c->F.nnz;
+    const size_t nc = h.slot.size();   // 9 per element
+    std::vector<int> ip(nnz + 1, 0), idx(nc);
+    for (size_t m = 0; m < nc; ++m) ip[h.slot[m] + 1] += 1;
+    for (int k = 0; k < nnz; ++k) ip[k + 1] += ip[k];
+    std::vector<int> pos(ip.begin(), ip.end() - 1);
+    for (size_t m = 0; m < nc; ++m) idx[pos[h.slot[m]]++] = (int)m;   // element order within an entry
+    void *d_ip = nullptr, *d_idx = nullptr, *d_ev = nullptr;
+    if (cudaMalloc(&d_ip, sizeof(int) * ip.size()) != cudaSuccess) return CGP_ERR_NOMEM;
+    c->allocs.push_back(d_ip);
+    if (cudaMalloc(&d_idx, sizeof(int) * idx.size()) != cudaSuccess) return CGP_ERR_NOMEM;
+    c->allocs.push_back(d_idx);
+    if (cudaMalloc(&d_ev, sizeof(double) * nc) != cudaSuccess) return CGP_ERR_NOMEM;
+    c->allocs.push_back(d_ev);
+    if (cudaMemcpy(d_ip, ip.data(), sizeof(int) * ip.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_idx, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return CGP_ERR_CUDA;
+    c->asm_ip = (int*)d_ip;
+    c->asm_idx = (int*)d_idx;
+    c->asm_ev = (double*)d_ev;
+    return CGP_OK;
+}
+
 cudaError_t launch_assemble_step(cgp_ctx_s* c, const double* u, cudaStream_t s) {
+    const bool mixed = c->prm.precision == CGP_MIXED;
+    const int t = c->EF.t, nnz = c->F.nnz, nf = c->nf;
+    k_conv_elements<<<(t + 255) / 256, 256, 0, s>>>(t, c->EF.tri, c->EF.geo, u, c->prm.dt * c->prm.rho, c->asm_ev);
+    k_gather_entries<<<(nnz + 255) / 256, 256, 0, s>>>(nnz, c->asm_ip, c->asm_idx, c->asm_ev, c->A0, c->A,
+                                                      mixed ? c->A32 : nullptr);
+    k_rows<<<(nf + 255) / 256, 256, 0, s>>>(nf, c->F.rp, c->F.ci, c->F.diag, c->A, c->M, u, c->vel_mask, c->g,
+                                          c->prm.rho, c->dinvA, mixed ? c->dinvA32 : nullptr, c->b_mom);
+    return cudaGetLastError();
+}
+
+// The colour-scheduled persistent assembly, one cooperative launch (the batched step's form).
+cudaError_t launch_assemble_step_coloured(cgp_ctx_s* c, const double* u, cudaStream_t s) {
     Launch<StepAsmArgs> L;
     L.single = asm_args(c, u, c->sync + SYNC_ASM);
     L.table = nullptr;

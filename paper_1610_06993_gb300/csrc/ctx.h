@@ -105,6 +105,9 @@ struct cgp_ctx_s {
     double* pc_prev = nullptr;   // [nc] pressure seen by the previous predictor call
     int* pc_flag = nullptr;      // 1 once pc_prev holds a pressure
     double* w_prev = nullptr;    // [nf][2] previous mass-solve solution (warm_start = 1)
+    int* asm_ip = nullptr;       // [nnz_f + 1] per CSR entry: offsets into asm_idx
+    int* asm_idx = nullptr;      // [9 t_f] element contributions of each entry, element order
+    double* asm_ev = nullptr;    // [9 t_f] the step's element contributions
     int* w_flag = nullptr;
 
     // Krylov workspace and reductions
@@ -198,6 +201,8 @@ cudaError_t launch_const_assembly(const DevElems& E, double* M, double* K, doubl
 cudaError_t launch_apply_pressure_bc(cgp_ctx_s* c, cudaStream_t s);
 cudaError_t launch_make_A0(cgp_ctx_s* c, const double* K, cudaStream_t s);
 cudaError_t launch_assemble_step(cgp_ctx_s* c, const double* u, cudaStream_t s);
+cudaError_t launch_assemble_step_coloured(cgp_ctx_s* c, const double* u, cudaStream_t s);
+int assemble_gather_build(cgp_ctx_s* c);
 
 // krylov.cu
 cudaError_t launch_poisson_cg(cgp_ctx_s* c, const double* b, double* x, cudaStream_t s);
