@@ -411,9 +411,10 @@ int twolevel_build(cgp_ctx_s* c) {
         if (!(dinv[i] > 0.0)) return CGP_ERR_ARG;
         dinv[i] = 1.0 / dinv[i];
     }
-    const std::vector<double> fxy = linear_functions(xy, perm, n, CG2_S);
+    const std::vector<int> sub = chunk_subdomains(n, CG2_S);
+    const std::vector<double> fxy = linear_functions(xy, perm, sub, n, nsub);
     std::vector<double> Ai;
-    int st = galerkin_inverse(rp, ci, v, fxy, n, CG2_S, nsub, Ai);
+    int st = galerkin_inverse(rp, ci, v, fxy, sub, n, nsub, Ai);
     if (st != CGP_OK) return st;
     if (!tl.ready) {
         if ((st = tl_alloc(c, &tl.mom, 9 * (size_t)nsub))) return st;

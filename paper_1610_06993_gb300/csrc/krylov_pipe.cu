@@ -450,7 +450,20 @@ struct SchwarzArgs {
     int* st_barrier;
 };
 
-enum { PS_P0 = 0, PS_O1 = 1 /* 2 slots */, PS_I0 = 3, PS_R = 4 /* SZ_NC slots */, PS_I = 4 + SZ_NC /* 2 x 3 */ };
+// Subdomains per block: the two halves of the block's row slice. Coarse index of function f on
+// subdomain h of block b: f * (SZ_SUB nb) + SZ_SUB b + h.
+#define SZ_SUB 2
+
+enum { PS_P0 = 0, PS_O1 = 1 /* 2 slots */, PS_I0 = 3, PS_R = 4 /* SZ_NC SZ_SUB slots */,
+       PS_I = 4 + SZ_NC * SZ_SUB /* 2 x 3 */ };
+
+// Subdomain of every renumbered row: the half of its block's slice of rpb rows.
+std::vector<int> onchip_subdomains(int n, int rpb) {
+    const int hs = (rpb + 1) / 2;
+    std::vector<int> sub(n);
+    for (int i = 0; i < n; ++i) sub[i] = SZ_SUB * (i / rpb) + ((i % rpb) >= hs ? 1 : 0);
+    return sub;
+}
 
 // One entry of the subdomain matrix A_aa in shared memory: column local to the block, value.
 template <typename TP> struct LocEnt;
@@ -464,21 +477,21 @@ template <> struct __align__(16) LocEnt<double> { int c; int pad; double v; };
 // boundary.
 size_t schwarz_smem(int width, int T, int nb, size_t sti, size_t stp) {
     const size_t wt = (size_t)width * T;
-    const size_t ncs = (size_t)SZ_NC * nb;
+    const size_t ncs = (size_t)SZ_NC * SZ_SUB * nb;
     const size_t loc = stp == sizeof(float) ? sizeof(LocEnt<float>) : sizeof(LocEnt<double>);
     return wt * (sti + sizeof(int)) + wt * loc + 2 * (size_t)T * stp + 3 * (size_t)T * sizeof(double) +
-           (SZ_NC + 1) * ncs * stp;
+           (SZ_NC * SZ_SUB + 1) * ncs * stp;
 }
 
 template <typename TI, typename TP>
 __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ TI s_redT[32 * 4];
-    __shared__ TP s_redP[32 * SZ_NC];
+    __shared__ TP s_redP[32 * SZ_NC * SZ_SUB];
     __shared__ double s_bc[4];
     __shared__ TI s_ctl[2];
     __shared__ int s_flag;
-    __shared__ TP s_y[SZ_NC];
+    __shared__ TP s_y[SZ_NC * SZ_SUB];   // [f][h]
     const int T = blockDim.x, t = threadIdx.x;
     const unsigned int nb = gridDim.x;
     unsigned int epoch = 0;
@@ -492,9 +505,10 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
     LocEnt<TP>* s_loc = reinterpret_cast<LocEnt<TP>*>(smem + (sizeof(TI) + sizeof(int)) * wt);
     TP* s_z = reinterpret_cast<TP*>(s_loc + wt);                                  // [2][T]
     double* s_lean = reinterpret_cast<double*>(s_z + 2 * T);                      // [3][T]
-    const unsigned int ncs = SZ_NC * nb;
-    TP* s_ainv = reinterpret_cast<TP*>(s_lean + 3 * T);   // [SZ_NC][ncs]
-    TP* s_rc = s_ainv + SZ_NC * ncs;      // [ncs]
+    const unsigned int nsub = SZ_SUB * nb, ncs = SZ_NC * nsub;
+    TP* s_ainv = reinterpret_cast<TP*>(s_lean + 3 * T);   // [SZ_NC SZ_SUB][ncs]: rows (f, h)
+    TP* s_rc = s_ainv + SZ_NC * SZ_SUB * ncs;             // [ncs]
+    const int hh = t >= (a.rows_per_block + 1) / 2 ? 1 : 0;   // this row's half of the slice
     int wl, wloc;   // longest row / longest A_aa row among this warp's rows (warp-uniform loop ends)
     {
         int k0 = 0, len = 0, m = 0;
@@ -523,9 +537,9 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
             e.v = (TP)0;
             s_loc[k * T + t] = e;
         }
-        for (unsigned int j = t; j < SZ_NC * ncs; j += T) {
-            const unsigned int k = j / ncs, col = j - k * ncs;
-            s_ainv[j] = a.ainv[(size_t)(k * nb + blockIdx.x) * ncs + col];
+        for (unsigned int j = t; j < SZ_NC * SZ_SUB * ncs; j += T) {
+            const unsigned int k = j / ncs, col = j - k * ncs, f = k / SZ_SUB, h = k - f * SZ_SUB;
+            s_ainv[j] = a.ainv[(size_t)(f * nsub + SZ_SUB * blockIdx.x + h) * ncs + col];
         }
     }
     const int crow = own ? a.perm[row] : 0;
@@ -542,8 +556,11 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
     auto precondition = [&](TI rI, TI& u) -> bool {
         {
             // moments in the preconditioner's precision (they only feed the coarse correction)
-            const TP v[SZ_NC] = {(TP)rI, fx * (TP)rI, fy * (TP)rI};
-            block_partials_t<SZ_NC, TP>(v, a.part + PS_R * nb, nb, s_redP);
+            // slot PS_R + 3 h + f holds function f on half h of every block
+            const TP r = (TP)rI, z0 = (TP)0;
+            const TP v[SZ_NC * SZ_SUB] = {hh ? z0 : r, hh ? z0 : fx * r, hh ? z0 : fy * r,
+                                          hh ? r : z0, hh ? fx * r : z0, hh ? fy * r : z0};
+            block_partials_t<SZ_NC * SZ_SUB, TP>(v, a.part + PS_R * nb, nb, s_redP);
         }
         grid_arrive(a.sw, nb, epoch);
         // local part: Chebyshev iteration on A_aa z = r from z = 0, s_z double buffered
@@ -569,22 +586,27 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
             rho = rn;
         }
         if (!grid_wait(a.sw, nb, epoch)) return false;
-        // coarse part: y = the block's SZ_NC entries of A_0^-1 R_0 r, one warp per entry
-        for (unsigned int j = t; j < ncs; j += T) s_rc[j] = (TP)__ldcg(a.part + PS_R * nb + j);
+        // coarse part: y = the block's SZ_NC SZ_SUB entries of A_0^-1 R_0 r, warp w taking entries
+        // w, w + warps, ... (a 128-thread block has fewer warps than entries); R_0 r gathered into
+        // coarse-index order
+        for (unsigned int j = t; j < ncs; j += T) {
+            const unsigned int f = j / nsub, rem = j - f * nsub, b = rem / SZ_SUB, h = rem - b * SZ_SUB;
+            s_rc[j] = (TP)__ldcg(a.part + (size_t)(PS_R + SZ_NC * h + f) * nb + b);
+        }
         __syncthreads();
         {
             const int warp = t >> 5, lane = t & 31;
-            if (warp < SZ_NC) {
-                const TP* arow = s_ainv + warp * ncs;
+            for (int k = warp; k < SZ_NC * SZ_SUB; k += T >> 5) {
+                const TP* arow = s_ainv + k * ncs;
                 TP acc = (TP)0;
                 for (unsigned int j = lane; j < ncs; j += 32) acc += arow[j] * s_rc[j];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0) s_y[warp] = acc;
+                if (lane == 0) s_y[k] = acc;
             }
         }
         __syncthreads();
-        u = own ? (TI)(z + s_y[0] + fx * s_y[1] + fy * s_y[2]) : (TI)0;
+        u = own ? (TI)(z + s_y[hh] + fx * s_y[SZ_SUB + hh] + fy * s_y[2 * SZ_SUB + hh]) : (TI)0;
         return true;
     };
 
@@ -802,11 +824,12 @@ cudaError_t schwarz_structure(cgp_ctx_s* c) {
     // within each subdomain, longest rows first: the warps of a block then see nearly uniform row
     // lengths and their ELL loops stop at the warp's own longest row
     {
-        const int rpb0 = (n + nb - 1) / nb;
+        const int rpb0 = (n + nb - 1) / nb, hs = (rpb0 + 1) / 2;
         auto len = [&](int i) { return H.rp[i + 1] - H.rp[i]; };
         for (int b0 = 0; b0 < n; b0 += rpb0)
-            std::stable_sort(perm.begin() + b0, perm.begin() + std::min(n, b0 + rpb0),
-                             [&](int p, int q) { return len(p) > len(q); });
+            for (int h0 = b0; h0 < std::min(n, b0 + rpb0); h0 += hs)   // within each half (subdomain)
+                std::stable_sort(perm.begin() + h0, perm.begin() + std::min({n, b0 + rpb0, h0 + hs}),
+                                 [&](int p, int q) { return len(p) > len(q); });
     }
     for (int i = 0; i < n; ++i) iperm[perm[i]] = i;
     c->sz_rp_h.assign(1, 0);
@@ -823,9 +846,9 @@ cudaError_t schwarz_structure(cgp_ctx_s* c) {
     const size_t nnz = c->sz_ci_h.size();
     // linear coarse functions (x - xbar_a) / H_a, (y - ybar_a) / H_a of each subdomain a
     const int rpb = (n + nb - 1) / nb;
-    c->sz_fxy_h = linear_functions(xy, perm, n, rpb);
+    c->sz_fxy_h = linear_functions(xy, perm, onchip_subdomains(n, rpb), n, SZ_SUB * nb);
     const std::vector<float> fxy32(c->sz_fxy_h.begin(), c->sz_fxy_h.end());
-    const size_t ncs = (size_t)SZ_NC * nb;
+    const size_t ncs = (size_t)SZ_NC * SZ_SUB * nb;
     cudaError_t e;
     if ((e = sz_alloc(c, &c->sz_perm, n)) != cudaSuccess) return e;
     if ((e = sz_alloc(c, &c->sz_rp, n + 1)) != cudaSuccess) return e;
@@ -976,7 +999,7 @@ int schwarz_values(cgp_ctx_s* c) {
     c->sz_lmin = c->sz_lmax / c->sz_ratio;
     std::vector<double> Ai;
     {
-        const int st = galerkin_inverse(rp, ci, v, c->sz_fxy_h, n, rpb, nb, Ai);
+        const int st = galerkin_inverse(rp, ci, v, c->sz_fxy_h, onchip_subdomains(n, rpb), n, SZ_SUB * nb, Ai);
         if (st != CGP_OK) return st;
     }
     std::vector<double> dinv(n);

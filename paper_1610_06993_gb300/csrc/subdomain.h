@@ -61,46 +61,56 @@ inline std::vector<int> hilbert_order(const std::vector<double>& xy, int n) {
     return perm;
 }
 
-// The two linear coarse functions at every renumbered node (fxy[2 i], fxy[2 i + 1]) for
-// subdomains of S consecutive renumbered rows (the last one may be shorter).
-inline std::vector<double> linear_functions(const std::vector<double>& xy, const std::vector<int>& perm, int n, int S) {
-    std::vector<double> f(2 * (size_t)n, 0.0);
-    for (int i0 = 0; i0 < n; i0 += S) {
-        const int i1 = std::min(n, i0 + S);
-        double mx = 0.0, my = 0.0, h2 = 0.0;
-        for (int i = i0; i < i1; ++i) {
-            mx += xy[2 * perm[i]];
-            my += xy[2 * perm[i] + 1];
+// Subdomain of every renumbered row for subdomains of S consecutive rows (the last may be shorter).
+inline std::vector<int> chunk_subdomains(int n, int S) {
+    std::vector<int> sub(n);
+    for (int i = 0; i < n; ++i) sub[i] = i / S;
+    return sub;
+}
+
+// The two linear coarse functions at every renumbered node (fxy[2 i], fxy[2 i + 1]), for the
+// subdomain sub[i] of each renumbered row (nsub subdomains; an empty one has no functions).
+inline std::vector<double> linear_functions(const std::vector<double>& xy, const std::vector<int>& perm,
+                                            const std::vector<int>& sub, int n, int nsub) {
+    std::vector<double> mx(nsub, 0.0), my(nsub, 0.0), h2(nsub, 0.0), cnt(nsub, 0.0), f(2 * (size_t)n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        mx[sub[i]] += xy[2 * perm[i]];
+        my[sub[i]] += xy[2 * perm[i] + 1];
+        cnt[sub[i]] += 1.0;
+    }
+    for (int a = 0; a < nsub; ++a)
+        if (cnt[a] > 0.0) {
+            mx[a] /= cnt[a];
+            my[a] /= cnt[a];
         }
-        mx /= (i1 - i0);
-        my /= (i1 - i0);
-        for (int i = i0; i < i1; ++i) {
-            const double dx = xy[2 * perm[i]] - mx, dy = xy[2 * perm[i] + 1] - my;
-            h2 += dx * dx + dy * dy;
-        }
-        const double ih = h2 > 0.0 ? 1.0 / std::sqrt(h2 / (i1 - i0)) : 0.0;
-        for (int i = i0; i < i1; ++i) {
-            f[2 * (size_t)i] = (xy[2 * perm[i]] - mx) * ih;
-            f[2 * (size_t)i + 1] = (xy[2 * perm[i] + 1] - my) * ih;
-        }
+    for (int i = 0; i < n; ++i) {
+        const double dx = xy[2 * perm[i]] - mx[sub[i]], dy = xy[2 * perm[i] + 1] - my[sub[i]];
+        h2[sub[i]] += dx * dx + dy * dy;
+    }
+    for (int i = 0; i < n; ++i) {
+        const int a = sub[i];
+        const double ih = h2[a] > 0.0 ? 1.0 / std::sqrt(h2[a] / cnt[a]) : 0.0;
+        f[2 * (size_t)i] = (xy[2 * perm[i]] - mx[a]) * ih;
+        f[2 * (size_t)i + 1] = (xy[2 * perm[i] + 1] - my[a]) * ih;
     }
     return f;
 }
 
-// Inverse of the Galerkin coarse matrix for subdomains of S consecutive rows of the renumbered
+// Inverse of the Galerkin coarse matrix for the subdomains sub[i] of the rows of the renumbered
 // CSR matrix (rp, ci, v): coarse index of function f on subdomain a is f * nsub + a. A coarse
 // function that vanishes on its subdomain gets a unit diagonal and no coupling. Returns CGP_OK,
 // or CGP_ERR_ARG if the matrix is not positive definite on the coarse space.
 inline int galerkin_inverse(const std::vector<int>& rp, const std::vector<int>& ci, const std::vector<double>& v,
-                            const std::vector<double>& fxy, int n, int S, int nsub, std::vector<double>& Ai) {
+                            const std::vector<double>& fxy, const std::vector<int>& sub, int n, int nsub,
+                            std::vector<double>& Ai) {
     const int nc0 = SZ_NC * nsub;
     std::vector<double> A0((size_t)nc0 * nc0, 0.0), Lc((size_t)nc0 * nc0, 0.0);
     Ai.assign((size_t)nc0 * nc0, 0.0);
     for (int i = 0; i < n; ++i) {
         const double pi[SZ_NC] = {1.0, fxy[2 * (size_t)i], fxy[2 * (size_t)i + 1]};
-        const int ai = i / S;
+        const int ai = sub[i];
         for (int k = rp[i]; k < rp[i + 1]; ++k) {
-            const int j = ci[k], aj = j / S;
+            const int j = ci[k], aj = sub[j];
             const double pj[SZ_NC] = {1.0, fxy[2 * (size_t)j], fxy[2 * (size_t)j + 1]};
             for (int f = 0; f < SZ_NC; ++f)
                 for (int g = 0; g < SZ_NC; ++g)
@@ -121,19 +131,31 @@ inline int galerkin_inverse(const std::vector<int>& rp, const std::vector<int>& 
             Lc[(size_t)i * nc0 + j] = s / ljj;
         }
     }
-    std::vector<double> y(nc0);
-    for (int col = 0; col < nc0; ++col) {
-        for (int i = 0; i < nc0; ++i) {   // L y = e_col
-            double s = i == col ? 1.0 : 0.0;
-            for (int k = 0; k < i; ++k) s -= Lc[(size_t)i * nc0 + k] * y[k];
-            y[i] = s / Lc[(size_t)i * nc0 + i];
+    // A_0^-1 = Y^T Y with Y = L^-1: rows of Y by axpys of earlier rows (row-major, contiguous)
+    std::vector<double> Y((size_t)nc0 * nc0, 0.0);
+    for (int i = 0; i < nc0; ++i) {
+        double* yi = &Y[(size_t)i * nc0];
+        yi[i] = 1.0;
+        for (int k = 0; k < i; ++k) {
+            const double lik = Lc[(size_t)i * nc0 + k];
+            if (lik == 0.0) continue;
+            const double* yk = &Y[(size_t)k * nc0];
+            for (int j = 0; j <= k; ++j) yi[j] -= lik * yk[j];
         }
-        for (int i = nc0 - 1; i >= 0; --i) {   // L^T x = y
-            double s = y[i];
-            for (int k = i + 1; k < nc0; ++k) s -= Lc[(size_t)k * nc0 + i] * Ai[(size_t)k * nc0 + col];
-            Ai[(size_t)i * nc0 + col] = s / Lc[(size_t)i * nc0 + i];
+        const double inv = 1.0 / Lc[(size_t)i * nc0 + i];
+        for (int j = 0; j <= i; ++j) yi[j] *= inv;
+    }
+    for (int i = 0; i < nc0; ++i) {
+        const double* yi = &Y[(size_t)i * nc0];
+        for (int a = 0; a <= i; ++a) {
+            const double ya = yi[a];
+            if (ya == 0.0) continue;
+            double* ra = &Ai[(size_t)a * nc0];
+            for (int c = 0; c <= a; ++c) ra[c] += ya * yi[c];
         }
     }
+    for (int a = 0; a < nc0; ++a)
+        for (int c = 0; c < a; ++c) Ai[(size_t)c * nc0 + a] = Ai[(size_t)a * nc0 + c];
     return CGP_OK;
 }
 
