@@ -450,18 +450,20 @@ struct SchwarzArgs {
     int* st_barrier;
 };
 
-// Subdomains per block: the two halves of the block's row slice. Coarse index of function f on
-// subdomain h of block b: f * (SZ_SUB nb) + SZ_SUB b + h.
-#define SZ_SUB 2
+// Subdomains per block: consecutive parts of ceil(rpb / SZ_SUB) rows of the block's row slice.
+// Coarse index of function f on subdomain h of block b: f * (SZ_SUB nb) + SZ_SUB b + h.
+#ifndef SZ_SUB
+#define SZ_SUB 3
+#endif
 
 enum { PS_P0 = 0, PS_O1 = 1 /* 2 slots */, PS_I0 = 3, PS_R = 4 /* SZ_NC SZ_SUB slots */,
        PS_I = 4 + SZ_NC * SZ_SUB /* 2 x 3 */ };
 
-// Subdomain of every renumbered row: the half of its block's slice of rpb rows.
+// Subdomain of every renumbered row: the part of its block's slice of rpb rows.
 std::vector<int> onchip_subdomains(int n, int rpb) {
-    const int hs = (rpb + 1) / 2;
+    const int hs = (rpb + SZ_SUB - 1) / SZ_SUB;
     std::vector<int> sub(n);
-    for (int i = 0; i < n; ++i) sub[i] = SZ_SUB * (i / rpb) + ((i % rpb) >= hs ? 1 : 0);
+    for (int i = 0; i < n; ++i) sub[i] = SZ_SUB * (i / rpb) + (i % rpb) / hs;
     return sub;
 }
 
@@ -508,7 +510,7 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
     const unsigned int nsub = SZ_SUB * nb, ncs = SZ_NC * nsub;
     TP* s_ainv = reinterpret_cast<TP*>(s_lean + 3 * T);   // [SZ_NC SZ_SUB][ncs]: rows (f, h)
     TP* s_rc = s_ainv + SZ_NC * SZ_SUB * ncs;             // [ncs]
-    const int hh = t >= (a.rows_per_block + 1) / 2 ? 1 : 0;   // this row's half of the slice
+    const int hh = t / ((a.rows_per_block + SZ_SUB - 1) / SZ_SUB);   // this row's part of the slice
     int wl, wloc;   // longest row / longest A_aa row among this warp's rows (warp-uniform loop ends)
     {
         int k0 = 0, len = 0, m = 0;
@@ -556,10 +558,13 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
     auto precondition = [&](TI rI, TI& u) -> bool {
         {
             // moments in the preconditioner's precision (they only feed the coarse correction)
-            // slot PS_R + 3 h + f holds function f on half h of every block
-            const TP r = (TP)rI, z0 = (TP)0;
-            const TP v[SZ_NC * SZ_SUB] = {hh ? z0 : r, hh ? z0 : fx * r, hh ? z0 : fy * r,
-                                          hh ? r : z0, hh ? fx * r : z0, hh ? fy * r : z0};
+            // slot PS_R + 3 h + f holds function f on part h of every block
+            const TP r = (TP)rI, rf[SZ_NC] = {r, fx * r, fy * r};
+            TP v[SZ_NC * SZ_SUB];
+#pragma unroll
+            for (int h = 0; h < SZ_SUB; ++h)
+#pragma unroll
+                for (int f = 0; f < SZ_NC; ++f) v[SZ_NC * h + f] = hh == h ? rf[f] : (TP)0;
             block_partials_t<SZ_NC * SZ_SUB, TP>(v, a.part + PS_R * nb, nb, s_redP);
         }
         grid_arrive(a.sw, nb, epoch);
@@ -824,10 +829,10 @@ cudaError_t schwarz_structure(cgp_ctx_s* c) {
     // within each subdomain, longest rows first: the warps of a block then see nearly uniform row
     // lengths and their ELL loops stop at the warp's own longest row
     {
-        const int rpb0 = (n + nb - 1) / nb, hs = (rpb0 + 1) / 2;
+        const int rpb0 = (n + nb - 1) / nb, hs = (rpb0 + SZ_SUB - 1) / SZ_SUB;
         auto len = [&](int i) { return H.rp[i + 1] - H.rp[i]; };
         for (int b0 = 0; b0 < n; b0 += rpb0)
-            for (int h0 = b0; h0 < std::min(n, b0 + rpb0); h0 += hs)   // within each half (subdomain)
+            for (int h0 = b0; h0 < std::min(n, b0 + rpb0); h0 += hs)   // within each part (subdomain)
                 std::stable_sort(perm.begin() + h0, perm.begin() + std::min({n, b0 + rpb0, h0 + hs}),
                                  [&](int p, int q) { return len(p) > len(q); });
     }
