@@ -89,11 +89,12 @@ typedef struct {
                           CSR and sliced ELL, 1 = sliced ELL, 2 = CSR */
     int precond_degree;
     double precond_ratio;
-    int warm_start;    /* initial guesses of the coarse Poisson and mass solves of a step: 0 = the
-                          previous step's p^n and w^n, 1 (default) = their linear extrapolations
-                          2 v^n - v^(n-1), history kept by the context (cgp_step, the batched step,
-                          cgp_prolong_correct for w, cgp_predict_pressure for p); the momentum solve
-                          starts from u^n either way */
+    int warm_start;    /* initial guesses of the solves of a step: 0 = u^n (momentum), p^n, w^n
+                          (coarse Poisson, mass); 1 (default) = u^n + (u~^n - u^(n-1)) (the last
+                          converged momentum increment, repeated) and the linear extrapolations
+                          2 v^n - v^(n-1) of p and w, history kept by the context (cgp_step, the
+                          batched step, cgp_momentum_solve, cgp_prolong_correct for w,
+                          cgp_predict_pressure for p). cgp_set_bc clears the history */
 } cgp_params;
 
 /* A coarse mesh: n_nodes points xy_host[n][2] and n_tris counter-clockwise triangles
@@ -182,15 +183,16 @@ int cgp_set_bc(cgp_ctx ctx, const unsigned char* vel_mask_host, const unsigned c
 int cgp_set_dirichlet_values(cgp_ctx ctx, const double* g_dev, void* stream);
 
 /* Step 1 set-up, Eq. 19: A = rho M + dt (rho N(u^n) + mu K) written into the fixed fine CSR
- * pattern by a colour-scheduled element loop (no atomics, deterministic), the Jacobi diagonal
+ * pattern from per-element contributions gathered per entry (no atomics, deterministic), the Jacobi diagonal
  * per component, and the right-hand side b = rho M u^n with Dirichlet rows set to the prescribed
  * values. u_dev: [n_fine][2] velocity u^n. */
 int cgp_assemble(cgp_ctx ctx, const double* u_dev, void* stream);
 
 /* Step 1, Eq. 19: solve A u~ = b (per component, Dirichlet rows replaced by identity rows) by
  * Jacobi-preconditioned BiCGStab on both components at once (CGP_MIXED: FP32 BiCGStab inside FP64
- * iterative refinement). Requires cgp_assemble() on the same u^n first. u_dev is the initial guess
- * (u^n); ut_dev: [n_fine][2] output u~^{n+1}. ut_dev may equal u_dev. */
+ * iterative refinement). Requires cgp_assemble() on the same u^n first. u_dev: u^n, the initial
+ * guess, plus the previous converged increment when warm_start = 1; ut_dev: [n_fine][2] output
+ * u~^{n+1}. ut_dev may equal u_dev (the increment kept for the next guess is then zero). */
 int cgp_momentum_solve(cgp_ctx ctx, const double* u_dev, double* ut_dev, void* stream);
 
 /* Steps 2-3 right-hand side, Eqs. 20-21 with Eq. 30: u~_c = u~_f[xi] (injection), then

@@ -161,8 +161,11 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     TRY(dalloc(c, &c->pc_flag, 1));
     TRY(dalloc(c, &c->w_prev, 2 * nf));
     TRY(dalloc(c, &c->w_flag, 1));
+    TRY(dalloc(c, &c->mom_dx, 2 * nf));
+    TRY(dalloc(c, &c->mom_flag, 1));
     CK(cudaMemset(c->pc_flag, 0, sizeof(int)));
     CK(cudaMemset(c->w_flag, 0, sizeof(int)));
+    CK(cudaMemset(c->mom_flag, 0, sizeof(int)));
     TRY(dalloc(c, &c->u_stage, 2 * nf));
     TRY(dalloc(c, &c->pc_stage, nc));
     // Krylov workspace: the largest of BiCGStab (9 pair vectors) and CG (6 vectors), 256-byte carved
@@ -330,6 +333,7 @@ int cgp_set_bc(cgp_ctx c, const unsigned char* vel_mask, const unsigned char* p_
     CK(launch_apply_pressure_bc(c, 0));
     CK(cudaMemset(c->pc_flag, 0, sizeof(int)));   // the predictors start over
     CK(cudaMemset(c->w_flag, 0, sizeof(int)));
+    CK(cudaMemset(c->mom_flag, 0, sizeof(int)));
     CK(cudaStreamSynchronize(0));
     TRY(schwarz_values(c));
     c->bc_set = true;

@@ -109,6 +109,8 @@ struct cgp_ctx_s {
     int* asm_idx = nullptr;      // [9 t_f] element contributions of each entry, element order
     double* asm_ev = nullptr;    // [9 t_f] the step's element contributions
     int* w_flag = nullptr;
+    double* mom_dx = nullptr;    // [nf][2] last momentum increment u~^n - u^(n-1) (warm_start = 1)
+    int* mom_flag = nullptr;     // 1 once mom_dx holds an increment
 
     // Krylov workspace and reductions
     void* ws = nullptr;

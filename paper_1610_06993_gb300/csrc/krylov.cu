@@ -87,6 +87,9 @@ BicgArgs<TI> momentum_args(cgp_ctx_s* c, const double* u_in, double* x, SyncWord
     a.valI = mixed ? (const TI*)(const void*)c->A32 : (const TI*)(const void*)c->A;
     a.dinvI = mixed ? (const TI*)(const void*)c->dinvA32 : (const TI*)(const void*)c->dinvA;
     a.mask = c->vel_mask; a.diag = c->F.diag; a.g = c->g; a.b = c->b_mom; a.x_in = u_in; a.x = x;
+    const bool pred = c->prm.warm_start == 1;
+    a.dx = pred ? c->mom_dx : nullptr;
+    a.dx_flag = pred ? c->mom_flag : nullptr;
     a.r = carve<TI>(p, n2); a.rh = carve<TI>(p, n2); a.p = carve<TI>(p, n2);
     a.v = carve<TI>(p, n2); a.y = carve<TI>(p, n2); a.s = carve<TI>(p, n2);
     a.z = carve<TI>(p, n2); a.t = carve<TI>(p, n2); a.d = carve<TI>(p, n2);

@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(512, MINB) k_cg2l(Launch<Cg2Args<TI>> L) {
                 a.w[i] = s0;
                 vd[0] += s0 * a.u[i];
             });
+            __syncthreads();   // w of the block's rows, written by other threads of the product
             subdomain_sums(0, 3, [&](int row, bool in, float* vv) {
                 const float w = in ? (float)a.w[row] : 0.f;
                 vv[0] = w;
@@ -265,6 +266,7 @@ __global__ void __launch_bounds__(512, MINB) k_cg2l(Launch<Cg2Args<TI>> L) {
                 q3[1] += r * r;
                 q3[2] += s0 * u;
             });
+            __syncthreads();   // w of the block's rows, written by other threads of the product
             subdomain_sums(0, 9, [&](int row, bool in, float* vv) {
                 const float fx = in ? a.fxy[2 * row] : 0.f, fy = in ? a.fxy[2 * row + 1] : 0.f;
                 const float w = in ? (float)a.w[row] : 0.f, r = in ? (float)a.r[row] : 0.f;

@@ -7,56 +7,76 @@ namespace cgp {
 
 namespace {
 
-// y = A x over the block's rows with one thread per row: two rows per thread in flight, the
-// column and value loads of each row issued four at a time before their x gathers, so a row pair
-// costs about three dependent memory round trips per four entries instead of two per entry. x is
-// written by other blocks during the launch, so it is read with ordinary (coherent) loads; the
-// matrix is read-only and goes through the read-only path.
+// CNT consecutive entries (from k) of row pair (a, b): column and value loads first, then the x
+// gathers and products; entries past a row's end are skipped per lane.
+template <int CNT, int NR, typename TV, typename TX>
+__device__ __forceinline__ void spmv_pair_chunk(int k, int ka, int na, int kb, int nbr, const int* __restrict__ ci,
+                                                const TV* __restrict__ val, const TX* x, TX& a0, TX& a1, TX& b0,
+                                                TX& b1) {
+    int ja[CNT], jb[CNT];
+    TX va[CNT], vb[CNT];
+#pragma unroll
+    for (int q = 0; q < CNT; ++q) {
+        const bool ia = k + q < na, ib = k + q < nbr;
+        ja[q] = ia ? __ldg(ci + ka + k + q) : -1;
+        va[q] = ia ? (TX)__ldg(val + ka + k + q) : (TX)0;
+        jb[q] = ib ? __ldg(ci + kb + k + q) : -1;
+        vb[q] = ib ? (TX)__ldg(val + kb + k + q) : (TX)0;
+    }
+#pragma unroll
+    for (int q = 0; q < CNT; ++q) {
+        if (ja[q] >= 0) {
+            if (NR == 1) {
+                a0 += va[q] * x[ja[q]];
+            } else {
+                TX x0, x1;
+                load2(x, ja[q], x0, x1);
+                a0 += va[q] * x0;
+                a1 += va[q] * x1;
+            }
+        }
+        if (jb[q] >= 0) {
+            if (NR == 1) {
+                b0 += vb[q] * x[jb[q]];
+            } else {
+                TX x0, x1;
+                load2(x, jb[q], x0, x1);
+                b0 += vb[q] * x0;
+                b1 += vb[q] * x1;
+            }
+        }
+    }
+}
+
+// y = A x over the block's rows with one thread per row, two rows per thread in flight: row i of
+// the first half of the block's range together with row i + H of the second half, so that every
+// pass but the last has both rows in all lanes. The entries of a row pair go four at a time
+// (loads of a group before its x gathers: about three dependent memory round trips per four
+// entries instead of two per entry), and the warp stops at its longest row exactly: the FP64
+// products of a warp issue once per entry slot that some lane needs, which on a part with few
+// FP64 units per SM is what an FP64 product costs. x is written by other blocks during the
+// launch, so it is read with ordinary (coherent) loads; the matrix goes through the read-only
+// path.
 template <int NR, typename TV, typename TX, typename Emit>
 __device__ __forceinline__ void spmv_rows(RowRange rr, const int* __restrict__ rp, const int* __restrict__ ci,
                                           const TV* __restrict__ val, const TX* x, Emit emit) {
     const int T = blockDim.x;
-    for (int i0 = rr.r0 + threadIdx.x; i0 < rr.r1; i0 += 2 * T) {
-        const int i1 = i0 + T;
+    const int H = (rr.r1 - rr.r0 + 1) >> 1;
+    for (int i0 = rr.r0 + threadIdx.x; i0 < rr.r0 + H; i0 += T) {
+        const int i1 = i0 + H;
         const bool h1 = i1 < rr.r1;
         const int ka = __ldg(rp + i0), na = __ldg(rp + i0 + 1) - ka;
         const int kb = h1 ? __ldg(rp + i1) : 0, nbr = h1 ? __ldg(rp + i1 + 1) - kb : 0;
-        const int m = max(na, nbr);
+        // the longest row among the lanes here; each lane's own rows are no longer than that
+        const int mw = (int)__reduce_max_sync(__activemask(), (unsigned)max(na, nbr));
         TX a0 = 0, a1 = 0, b0 = 0, b1 = 0;
-        for (int k = 0; k < m; k += 4) {
-            int ja[4], jb[4];
-            TX va[4], vb[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const bool ia = k + q < na, ib = k + q < nbr;
-                ja[q] = ia ? __ldg(ci + ka + k + q) : -1;
-                va[q] = ia ? (TX)__ldg(val + ka + k + q) : (TX)0;
-                jb[q] = ib ? __ldg(ci + kb + k + q) : -1;
-                vb[q] = ib ? (TX)__ldg(val + kb + k + q) : (TX)0;
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (ja[q] >= 0) {
-                    if (NR == 1) {
-                        a0 += va[q] * x[ja[q]];
-                    } else {
-                        TX x0, x1;
-                        load2(x, ja[q], x0, x1);
-                        a0 += va[q] * x0;
-                        a1 += va[q] * x1;
-                    }
-                }
-                if (jb[q] >= 0) {
-                    if (NR == 1) {
-                        b0 += vb[q] * x[jb[q]];
-                    } else {
-                        TX x0, x1;
-                        load2(x, jb[q], x0, x1);
-                        b0 += vb[q] * x0;
-                        b1 += vb[q] * x1;
-                    }
-                }
-            }
+        int k = 0;
+        for (; k + 4 <= mw; k += 4) spmv_pair_chunk<4, NR, TV, TX>(k, ka, na, kb, nbr, ci, val, x, a0, a1, b0, b1);
+        switch (mw - k) {
+            case 3: spmv_pair_chunk<3, NR, TV, TX>(k, ka, na, kb, nbr, ci, val, x, a0, a1, b0, b1); break;
+            case 2: spmv_pair_chunk<2, NR, TV, TX>(k, ka, na, kb, nbr, ci, val, x, a0, a1, b0, b1); break;
+            case 1: spmv_pair_chunk<1, NR, TV, TX>(k, ka, na, kb, nbr, ci, val, x, a0, a1, b0, b1); break;
+            default: break;
         }
         emit(i0, a0, a1);
         if (h1) emit(i1, b0, b1);
@@ -425,8 +445,10 @@ struct BicgArgs {
     const int* diag;              // [n] CSR slot of the diagonal
     const double* g;              // [n][2] prescribed values
     const double* b;              // [n][2]
-    const double* x_in;           // [n][2] initial guess (Dirichlet entries are replaced by g)
-    double* x;                    // [n][2] solution
+    const double* x_in;           // [n][2] u^n (Dirichlet entries of the guess are replaced by g)
+    double* x;                    // [n][2] solution (x == x_in gives a zero increment)
+    double* dx;                   // [n][2] increment x - x_in of the last converged solve, or nullptr
+    int* dx_flag;                 // 1 once dx holds an increment
     TI *r, *rh, *p, *v, *y, *s, *z, *t, *d;
     double* part;
     SyncWords* sw;
@@ -469,6 +491,9 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
     const int tpb = blockDim.x;
     double bb[2], rr64[2] = {0.0, 0.0};
     int iters = 0, outer = 0, status = CGP_OK;
+    // Initial guess u^n + (u~^n - u^(n-1)): the last step's increment, repeated. Every block reads
+    // the flag before the first grid barrier; block 0 rewrites it only after the last one.
+    const bool have_dx = a.dx != nullptr && *a.dx_flag != 0;
 
     // initial guess with prescribed values, ||b||^2
     {
@@ -477,6 +502,12 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
             const unsigned char m = a.mask[i];
             double x0, x1, g0, g1, b0, b1;
             load2(a.x_in, i, x0, x1);
+            if (have_dx) {
+                double d0, d1;
+                load2(a.dx, i, d0, d1);
+                x0 += d0;
+                x1 += d1;
+            }
             load2(a.g, i, g0, g1);
             store2(a.x, i, (m & CGP_BC_U) ? g0 : x0, (m & CGP_BC_V) ? g1 : x1);
             load2(a.b, i, b0, b1);
@@ -751,6 +782,18 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
             for (int c = 0; c < 2; ++c) a.x[2 * (size_t)i + c] += (double)a.d[2 * (size_t)i + c];
         if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
         outer += 1;
+    }
+    if (a.dx != nullptr) {
+        // the increment of this solve, kept for the next step's guess (converged solves only;
+        // the block's own rows, written by this block before its last barrier)
+        if (status == CGP_OK)
+            for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
+                double x0, x1, u0, u1;
+                load2(a.x, i, x0, x1);
+                load2(a.x_in, i, u0, u1);
+                store2(a.dx, i, x0 - u0, x1 - u1);
+            }
+        if (g.bid == 0 && threadIdx.x == 0) *a.dx_flag = status == CGP_OK ? 1 : 0;
     }
     if (g.bid == 0 && threadIdx.x == 0) {
         double rel = 0.0;
