@@ -6,8 +6,9 @@
 #include "cgp.h"
 
 #ifndef CGP_BARRIER_SPIN_LIMIT
-// Upper bound on polls of one grid barrier before it gives up with CGP_ERR_TIMEOUT. Each poll
-// sleeps ~64 ns after the first few hundred, so the bound is a few seconds of wall time.
+// Upper bound on polls of one grid barrier before it gives up with CGP_ERR_TIMEOUT. A poll is
+// one L2 round trip (under a microsecond), with a short sleep every 32 polls once the wait has
+// passed a few milliseconds, so the bound is some tens of seconds of wall time.
 #define CGP_BARRIER_SPIN_LIMIT (1u << 25)
 #endif
 
@@ -35,11 +36,33 @@ __device__ __forceinline__ void red_release_add_u32(unsigned int* p, unsigned in
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Bounded wait of thread 0 until the arrival counter reaches `target`: polls with acquire loads
+// and, every 32 polls, looks for an error raised by another block and counts against
+// CGP_BARRIER_SPIN_LIMIT. Returns 0 on an error or when it gives up (then it records
+// CGP_ERR_TIMEOUT), 1 once every block has arrived.
+__device__ __forceinline__ int grid_poll(SyncWords* sw, unsigned int target) {
+    unsigned int spins = 0;
+    while (ld_acquire_u32(&sw->count) < target) {
+        if ((++spins & 31u) == 0) {
+            if (ld_relaxed_i32(&sw->err) != 0) return 0;
+            if (spins > CGP_BARRIER_SPIN_LIMIT) {
+                atomicCAS(&sw->err, 0, CGP_ERR_TIMEOUT);
+                return 0;
+            }
+            if (spins > 8192) __nanosleep(256);
+        }
+    }
+    return 1;
+}
+
 // Grid-wide barrier for a cooperative launch. Every block calls it the same number of times.
-// Thread 0 of each block arrives with a release-add and polls with acquire loads; the poll is
-// bounded: after CGP_BARRIER_SPIN_LIMIT polls, or as soon as another block has raised an error,
-// it returns false (and records CGP_ERR_TIMEOUT if it was the one to give up). Callers must stop
-// their work and return when it is false. `epoch` is thread 0's count of barriers passed.
+// After a block barrier, thread 0 of each block arrives with a release-add (it orders the block's
+// earlier writes, which the block barrier made visible to thread 0, before the arrival) and polls
+// with acquire loads (they order the block's later reads after every arrival, again through the
+// trailing block barrier); no further fence is needed. The poll is bounded: after
+// CGP_BARRIER_SPIN_LIMIT polls, or as soon as another block has raised an error, it returns false
+// (and records CGP_ERR_TIMEOUT if it was the one to give up). Callers must stop their work and
+// return when it is false. `epoch` is thread 0's count of barriers passed.
 __device__ __forceinline__ bool grid_sync(SyncWords* sw, unsigned int nblocks, unsigned int& epoch) {
     __shared__ int s_ok;
     __syncthreads();
@@ -47,20 +70,8 @@ __device__ __forceinline__ bool grid_sync(SyncWords* sw, unsigned int nblocks, u
         int ok = 1;
         epoch += 1;
         if (nblocks > 1) {
-            const unsigned int target = epoch * nblocks;
-            __threadfence();
             red_release_add_u32(&sw->count, 1u);
-            unsigned int spins = 0;
-            while (ld_acquire_u32(&sw->count) < target) {
-                if (ld_relaxed_i32(&sw->err) != 0) { ok = 0; break; }
-                if (++spins > CGP_BARRIER_SPIN_LIMIT) {
-                    atomicCAS(&sw->err, 0, CGP_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                if (spins > 256) __nanosleep(64);
-            }
-            __threadfence();
+            ok = grid_poll(sw, epoch * nblocks);
         } else {
             ok = ld_relaxed_i32(&sw->err) == 0;
         }
@@ -76,10 +87,7 @@ __device__ __forceinline__ void grid_arrive(SyncWords* sw, unsigned int nblocks,
     __syncthreads();
     if (threadIdx.x == 0) {
         epoch += 1;
-        if (nblocks > 1) {
-            __threadfence();
-            red_release_add_u32(&sw->count, 1u);
-        }
+        if (nblocks > 1) red_release_add_u32(&sw->count, 1u);
     }
 }
 
@@ -89,18 +97,7 @@ __device__ __forceinline__ bool grid_wait(SyncWords* sw, unsigned int nblocks, u
     if (threadIdx.x == 0) {
         int ok = 1;
         if (nblocks > 1) {
-            const unsigned int target = epoch * nblocks;
-            unsigned int spins = 0;
-            while (ld_acquire_u32(&sw->count) < target) {
-                if (ld_relaxed_i32(&sw->err) != 0) { ok = 0; break; }
-                if (++spins > CGP_BARRIER_SPIN_LIMIT) {
-                    atomicCAS(&sw->err, 0, CGP_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                if (spins > 256) __nanosleep(64);
-            }
-            __threadfence();
+            ok = grid_poll(sw, epoch * nblocks);
         } else {
             ok = ld_relaxed_i32(&sw->err) == 0;
         }
