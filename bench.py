@@ -363,7 +363,7 @@ def run_gpu(args):
                      "note": "coarse matrix + vectors live in shared memory, registers and L2 (ncu: 0.1 % DRAM "
                              "throughput); the kernel is bound by barrier latency, so achieved is an effective rate: "
                              "the bytes a memory-streaming CG would move per iteration x iterations / time",
-                     "latency": {"us_per_iter": 1000.0 * pms / max(it, 1.0), "grid_barriers_per_iter": 3}},
+                     "latency": {"us_per_iter": 1000.0 * pms / max(it, 1.0), "grid_barriers_per_iter": 2}},
         "e2e": {"value": 1000.0 / statistics.mean(e2e_ms), "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": h2d},
         "gpu_launches": launches_per_step * args.steps,

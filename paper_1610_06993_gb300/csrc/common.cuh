@@ -274,7 +274,7 @@ __device__ __forceinline__ Grp group_of(const BatchMap& m) {
 // Maximum number of blocks of a persistent launch (partials are read 32 x 8 at a time).
 #define CGP_MAX_GRID 256
 // Partial-sum slots (of nblocks doubles each) of a single-instance context.
-#define CGP_PART_SLOTS 40
+#define CGP_PART_SLOTS 48
 
 // After a grid barrier: every block sums the nblocks partials of each of the K slots in the same
 // fixed order, so all blocks hold bit-identical totals. Slot k's partials start at

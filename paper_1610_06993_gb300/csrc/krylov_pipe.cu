@@ -457,7 +457,9 @@ struct SchwarzArgs {
 #endif
 
 enum { PS_P0 = 0, PS_O1 = 1 /* 2 slots */, PS_I0 = 3, PS_R = 4 /* SZ_NC SZ_SUB slots */,
-       PS_I = 4 + SZ_NC * SZ_SUB /* 2 x 3 */ };
+       PS_F = 4 + SZ_NC * SZ_SUB /* 3 products, then 3 SZ_NC SZ_SUB moments */,
+       PS_END = PS_F + 3 + 3 * SZ_NC * SZ_SUB };
+static_assert(PS_END <= CGP_PART_SLOTS, "partial-sum slots");
 
 // Subdomain of every renumbered row: the part of its block's slice of rpb rows.
 std::vector<int> onchip_subdomains(int n, int rpb) {
@@ -474,27 +476,37 @@ template <> struct __align__(16) LocEnt<double> { int c; int pad; double v; };
 
 // Dynamic shared memory of k_pcg_schwarz: the block's ELL slice of A (values in TI, global
 // columns), the compact ELL slice of A_aa (local columns, values in TP), two Chebyshev buffers,
-// the FP64 reduction buffer (three values per thread), the block's SZ_NC rows of A_0^-1 and the
-// gathered R_0 r. T is a multiple of 32, so every region before the TP arrays ends on a 128-byte
-// boundary.
+// the FP64 reduction buffer (three values per thread), the block's SZ_NC SZ_SUB rows of A_0^-1,
+// R_0 r, the gathered moments R_0 w, R_0 r, R_0 s of the last reduction and the per-thread
+// moments of that reduction (9 per thread). T is a multiple of 32, so every region before the TP
+// arrays ends on a 128-byte boundary.
 size_t schwarz_smem(int width, int T, int nb, size_t sti, size_t stp) {
     const size_t wt = (size_t)width * T;
     const size_t ncs = (size_t)SZ_NC * SZ_SUB * nb;
     const size_t loc = stp == sizeof(float) ? sizeof(LocEnt<float>) : sizeof(LocEnt<double>);
     return wt * (sti + sizeof(int)) + wt * loc + 2 * (size_t)T * stp + 3 * (size_t)T * sizeof(double) +
-           (SZ_NC * SZ_SUB + 1) * ncs * stp;
+           (SZ_NC * SZ_SUB + 1 + 3) * ncs * stp + 3 * SZ_NC * (size_t)T * stp;
 }
 
+// Iteration (Chronopoulos-Gear CG with the two-level Schwarz preconditioner M^-1 = local
+// Chebyshev solves + R_0^T A_0^-1 R_0; two grid barriers per iteration):
+//   reduction of (r,u), (r,r), (w,u) and of the coarse moments R_0 w, R_0 r, R_0 s | barrier
+//   totals and every block's moments; alpha, beta (thread 0)
+//   p = u + beta p,  s = w + beta s,  d += alpha p,  r -= alpha s                         (local)
+//   R_0 s <- R_0 w + beta R_0 s,  R_0 r <- R_0 r - alpha R_0 s  (one step from exact moments)
+//   u = Chebyshev(A_aa, r) + R_0^T A_0^-1 R_0 r;  publish u | barrier | w = A u
+// The moments of the new residual follow from the exact moments of the vectors it is formed
+// from, so the coarse correction needs no reduction of its own, and they never drift: each
+// reduction recomputes them from the vectors.
 template <typename TI, typename TP>
 __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ TI s_redT[32 * 4];
     __shared__ TP s_redP[32 * SZ_NC * SZ_SUB];
     __shared__ double s_bc[4];
-    __shared__ TI s_ctl[2];
+    __shared__ double s_ctl[2];
     __shared__ int s_flag;
     __shared__ TP s_y[SZ_NC * SZ_SUB];   // [f][h]
-    const int T = blockDim.x, t = threadIdx.x;
+    const int T = blockDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = T >> 5;
     const unsigned int nb = gridDim.x;
     unsigned int epoch = 0;
     const int r0 = min(a.n, (int)blockIdx.x * a.rows_per_block);
@@ -509,8 +521,13 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
     double* s_lean = reinterpret_cast<double*>(s_z + 2 * T);                      // [3][T]
     const unsigned int nsub = SZ_SUB * nb, ncs = SZ_NC * nsub;
     TP* s_ainv = reinterpret_cast<TP*>(s_lean + 3 * T);   // [SZ_NC SZ_SUB][ncs]: rows (f, h)
-    TP* s_rc = s_ainv + SZ_NC * SZ_SUB * ncs;             // [ncs]
-    const int hh = t / ((a.rows_per_block + SZ_SUB - 1) / SZ_SUB);   // this row's part of the slice
+    TP* s_rc = s_ainv + SZ_NC * SZ_SUB * ncs;             // [ncs] R_0 r of the current residual
+    TP* s_Rw = s_rc + ncs;                                // [ncs] moments of the last reduction
+    TP* s_Rr = s_Rw + ncs;
+    TP* s_Rs = s_Rr + ncs;
+    TP* s_mom = s_Rs + ncs;                               // [3 SZ_NC][T] this thread's moments
+    const int hs = (a.rows_per_block + SZ_SUB - 1) / SZ_SUB;   // rows per part of the slice
+    const int hh = t / hs;                                     // this row's part
     int wl, wloc;   // longest row / longest A_aa row among this warp's rows (warp-uniform loop ends)
     {
         int k0 = 0, len = 0, m = 0;
@@ -553,22 +570,8 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
     const TP sigma = theta / delta;
     __syncthreads();
 
-    // u = M^-1 r on the block's rows; every thread of every block calls it the same number of
-    // times. False if the grid barrier inside failed.
-    auto precondition = [&](TI rI, TI& u) -> bool {
-        {
-            // moments in the preconditioner's precision (they only feed the coarse correction)
-            // slot PS_R + 3 h + f holds function f on part h of every block
-            const TP r = (TP)rI, rf[SZ_NC] = {r, fx * r, fy * r};
-            TP v[SZ_NC * SZ_SUB];
-#pragma unroll
-            for (int h = 0; h < SZ_SUB; ++h)
-#pragma unroll
-                for (int f = 0; f < SZ_NC; ++f) v[SZ_NC * h + f] = hh == h ? rf[f] : (TP)0;
-            block_partials_t<SZ_NC * SZ_SUB, TP>(v, a.part + PS_R * nb, nb, s_redP);
-        }
-        grid_arrive(a.sw, nb, epoch);
-        // local part: Chebyshev iteration on A_aa z = r from z = 0, s_z double buffered
+    // local part: Chebyshev iteration on A_aa z = r from z = 0 (s_z double buffered)
+    auto chebyshev = [&](TI rI) -> TP {
         const TP r = (TP)rI;
         TP rho = (TP)1 / sigma;
         TP d = di * r / theta;
@@ -590,29 +593,155 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
             z += d;
             rho = rn;
         }
+        return z;
+    };
+    // coarse part: s_y = the block's SZ_NC SZ_SUB entries of A_0^-1 (R_0 r) from s_rc, warp w
+    // taking entries w, w + warps, ... (a 128-thread block has fewer warps than entries)
+    auto coarse_solve = [&]() {
+        for (int k = warp; k < SZ_NC * SZ_SUB; k += nwarps) {
+            const TP* arow = s_ainv + k * ncs;
+            TP acc = (TP)0;
+            for (unsigned int j = lane; j < ncs; j += 32) acc += arow[j] * s_rc[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) s_y[k] = acc;
+        }
+        __syncthreads();
+    };
+    auto coarse_value = [&]() -> TP { return s_y[hh] + fx * s_y[SZ_SUB + hh] + fy * s_y[2 * SZ_SUB + hh]; };
+
+    // u = M^-1 r with the moments of r reduced explicitly (the refinement pass); every thread of
+    // every block calls it the same number of times. False if the grid barrier inside failed.
+    auto precondition = [&](TI rI, TI& u) -> bool {
+        {
+            // slot PS_R + 3 h + f holds function f on part h of every block
+            const TP r = (TP)rI, rf[SZ_NC] = {r, fx * r, fy * r};
+            TP v[SZ_NC * SZ_SUB];
+#pragma unroll
+            for (int h = 0; h < SZ_SUB; ++h)
+#pragma unroll
+                for (int f = 0; f < SZ_NC; ++f) v[SZ_NC * h + f] = hh == h ? rf[f] : (TP)0;
+            block_partials_t<SZ_NC * SZ_SUB, TP>(v, a.part + PS_R * nb, nb, s_redP);
+        }
+        grid_arrive(a.sw, nb, epoch);
+        const TP z = chebyshev(rI);
         if (!grid_wait(a.sw, nb, epoch)) return false;
-        // coarse part: y = the block's SZ_NC SZ_SUB entries of A_0^-1 R_0 r, warp w taking entries
-        // w, w + warps, ... (a 128-thread block has fewer warps than entries); R_0 r gathered into
-        // coarse-index order
         for (unsigned int j = t; j < ncs; j += T) {
             const unsigned int f = j / nsub, rem = j - f * nsub, b = rem / SZ_SUB, h = rem - b * SZ_SUB;
             s_rc[j] = (TP)__ldcg(a.part + (size_t)(PS_R + SZ_NC * h + f) * nb + b);
         }
         __syncthreads();
+        coarse_solve();
+        u = own ? (TI)(z + coarse_value()) : (TI)0;
+        return true;
+    };
+
+    // One reduction of the products (r,u), (r,r), (w,u) and the moments of w, r, s on this
+    // block's parts: slot PS_F + q for product q; from slot PS_F + 3 on, the moments in coarse
+    // order, entry (3 v + f) nsub + SZ_SUB b + h for function f of vector v (w, r, s) on part h of
+    // block b, so that every block gathers them with one contiguous copy. Warp w sums tasks w,
+    // w + warps, ...: a product over the whole block (FP64 for FP64 iterations), a moment over one
+    // part (in TP); fixed order.
+    auto reduce_fused = [&](TI rI, TI uI, TI wI, TI sI) {
+        __syncthreads();   // earlier readers of s_lean / s_mom are done
+        if constexpr (sizeof(TI) == sizeof(double)) {
+            s_lean[t] = (double)(rI * uI);
+            s_lean[T + t] = (double)(rI * rI);
+            s_lean[2 * T + t] = (double)(wI * uI);
+        } else {
+            TI* sl = reinterpret_cast<TI*>(s_lean);
+            sl[t] = rI * uI;
+            sl[T + t] = rI * rI;
+            sl[2 * T + t] = wI * uI;
+        }
         {
-            const int warp = t >> 5, lane = t & 31;
-            for (int k = warp; k < SZ_NC * SZ_SUB; k += T >> 5) {
-                const TP* arow = s_ainv + k * ncs;
-                TP acc = (TP)0;
-                for (unsigned int j = lane; j < ncs; j += 32) acc += arow[j] * s_rc[j];
+            const TP vec[3] = {(TP)wI, (TP)rI, (TP)sI};
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0) s_y[k] = acc;
+            for (int v = 0; v < 3; ++v) {
+                s_mom[(3 * v) * T + t] = vec[v];
+                s_mom[(3 * v + 1) * T + t] = fx * vec[v];
+                s_mom[(3 * v + 2) * T + t] = fy * vec[v];
             }
         }
         __syncthreads();
-        u = own ? (TI)(z + s_y[hh] + fx * s_y[SZ_SUB + hh] + fy * s_y[2 * SZ_SUB + hh]) : (TI)0;
-        return true;
+        for (int q = warp; q < 3 + 3 * SZ_NC * SZ_SUB; q += nwarps) {
+            double tot;
+            if (q < 3) {
+                if constexpr (sizeof(TI) == sizeof(double)) {
+                    const double* b = s_lean + q * T;
+                    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+                    int j = lane;
+                    for (; j + 96 < T; j += 128) {
+                        a0 += b[j];
+                        a1 += b[j + 32];
+                        a2 += b[j + 64];
+                        a3 += b[j + 96];
+                    }
+                    for (; j < T; j += 32) a0 += b[j];
+                    double acc = (a0 + a1) + (a2 + a3);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    tot = acc;
+                } else {
+                    const TI* b = reinterpret_cast<const TI*>(s_lean) + q * T;
+                    TI acc = (TI)0;
+                    for (int j = lane; j < T; j += 32) acc += b[j];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                    tot = (double)acc;
+                }
+            } else {
+                const int m = q - 3, k = m / SZ_SUB, h = m - k * SZ_SUB;
+                const TP* b = s_mom + k * T;
+                const int j1 = min(T, (h + 1) * hs);
+                TP acc = (TP)0;
+                for (int j = h * hs + lane; j < j1; j += 32) acc += b[j];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0)
+                    a.part[(size_t)(PS_F + 3) * nb + (size_t)k * nsub + SZ_SUB * blockIdx.x + h] = (double)acc;
+                continue;
+            }
+            if (lane == 0) a.part[(size_t)(PS_F + q) * nb + blockIdx.x] = tot;
+        }
+    };
+    // after the barrier: the three totals into s_bc, every block's moments into s_Rw, s_Rr, s_Rs
+    // in coarse order (index f nsub + SZ_SUB b + h)
+    auto gather_fused = [&]() {
+        if (warp < 3) {
+            const double* pp = a.part + (size_t)(PS_F + warp) * nb;
+            double v[CGP_MAX_GRID / 32];
+#pragma unroll
+            for (int q = 0; q < CGP_MAX_GRID / 32; ++q) {
+                const unsigned int b = lane + 32u * q;
+                v[q] = b < nb ? __ldcg(pp + b) : 0.0;
+            }
+            double tt = 0.0;
+#pragma unroll
+            for (int q = 0; q < CGP_MAX_GRID / 32; ++q) tt += v[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tt += __shfl_xor_sync(0xffffffffu, tt, o);
+            if (lane == 0) s_bc[warp] = tt;
+        }
+        // the moments: a contiguous copy into s_Rw, s_Rr, s_Rs (consecutive [3][ncs]), all loads
+        // of a round in flight before the first store
+        const double* src = a.part + (size_t)(PS_F + 3) * nb;
+        const unsigned int lim = 3 * ncs;
+        constexpr int GQ = 10;
+        for (unsigned int i0 = t; i0 < lim; i0 += GQ * T) {
+            double m[GQ];
+#pragma unroll
+            for (int q = 0; q < GQ; ++q) {
+                const unsigned int i = i0 + q * T;
+                m[q] = i < lim ? __ldcg(src + i) : 0.0;
+            }
+#pragma unroll
+            for (int q = 0; q < GQ; ++q) {
+                const unsigned int i = i0 + q * T;
+                if (i < lim) s_Rw[i] = (TP)m[q];
+            }
+        }
+        __syncthreads();
     };
 
     double bb;
@@ -641,69 +770,41 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
             r = (TI)r64;
         }
         if (!precondition(r, u)) return record_failure(a.sw, a.st_barrier);
-        double gam;
         {
+            // publish u in the same barrier as the FP64 residual norm
             if (own) a.ubuf[row] = u;
-            double v[2] = {r64 * r64, (double)(r * u)}, tt[2];
-            block_partials_lean<2>(v, a.part + PS_O1 * nb, nb, blockIdx.x, s_lean);
+            double v[1] = {r64 * r64}, tt[1];
+            block_partials_lean<1>(v, a.part + PS_O1 * nb, nb, blockIdx.x, s_lean);
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-            grid_totals<2>(a.part + PS_O1 * nb, nb, tt, s_bc);
+            grid_totals<1>(a.part + PS_O1 * nb, nb, tt, s_bc);
             rr64 = tt[0];
-            gam = tt[1];
         }
-        if (bad(rr64) || bad(gam)) { status = CGP_ERR_NAN; break; }
+        if (bad(rr64)) { status = CGP_ERR_NAN; break; }
         if (bb == 0.0 || rr64 <= rtol2 * bb) break;
         if (outer >= a.max_outer || iters >= a.max_iter) { status = CGP_ERR_NOT_CONVERGED; break; }
         const double tgt = fmax(itol2 * rr64, floor2 * bb);
-        // ---- w = A u, delta = (w, u)
         TI w = own ? ell_row<TI, TI>(s_ci, s_val, T, t, wl, a.ubuf) : (TI)0;
-        double alpha;
-        {
-            double v[1] = {(double)(w * u)}, tt[1];
-            block_partials_lean<1>(v, a.part + PS_I0 * nb, nb, blockIdx.x, s_lean);
-            if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-            grid_totals<1>(a.part + PS_I0 * nb, nb, tt, s_bc);
-            if (bad(tt[0])) { status = CGP_ERR_NAN; break; }
-            alpha = tt[0] != 0.0 ? gam / tt[0] : 0.0;
-        }
         TI d = (TI)0, p = (TI)0, s = (TI)0;
-        TI A = (TI)alpha, B = (TI)0;
-        double beta = 0.0;
-        int par = 0;
+        double alpha = 0.0, beta = 0.0, gam = 0.0;
         bool first = true, nan = false, fail = false;
-        // every thread leaves this loop on the same broadcast flag (or the same initial alpha)
-        while (alpha != 0.0 || !first) {
-            p = first ? u : u + B * p;
-            s = first ? w : w + B * s;
-            d += A * p;
-            r -= A * s;
-            if (!precondition(r, u)) { fail = true; break; }
-            // publish u (a pure barrier), then w = A u and all three inner products in one
-            // reduction
-            if (own) a.ubuf[row] = u;
-            const int base = PS_I + 3 * par;
+        for (;;) {
+            reduce_fused(r, u, w, s);
             if (!grid_sync(a.sw, nb, epoch)) { fail = true; break; }
-            w = own ? ell_row<TI, TI>(s_ci, s_val, T, t, wl, a.ubuf) : (TI)0;
-            if constexpr (sizeof(TI) == sizeof(double)) {
-                const double v[3] = {(double)(r * u), (double)(r * r), (double)(w * u)};
-                block_partials_lean<3>(v, a.part + base * nb, nb, blockIdx.x, s_lean);
-            } else {
-                const TI v[3] = {r * u, r * r, w * u};
-                block_partials_t<3, TI>(v, a.part + base * nb, nb, s_redT);
-            }
-            if (!grid_sync(a.sw, nb, epoch)) { fail = true; break; }
-            {
-                const int slot[3] = {base, base + 1, base + 2};
-                grid_totals_shared<3>(a.part, slot, nb, s_bc);
-            }
-            iters += 1;
-            first = false;
-            par ^= 1;
+            gather_fused();
+            if (!first) iters += 1;
             if (t == 0) {
                 const double gnew = s_bc[0], rho = s_bc[1], del = s_bc[2];
                 int flag = 0;
                 if (bad(gnew) || bad(rho) || bad(del)) {
                     flag = 2;
+                } else if (first) {
+                    if (del == 0.0 || gnew == 0.0) {
+                        flag = 1;
+                    } else {
+                        gam = gnew;
+                        alpha = gnew / del;
+                        beta = 0.0;
+                    }
                 } else if (rho <= tgt || iters >= a.max_iter || gam == 0.0) {
                     flag = 1;
                 } else {
@@ -720,16 +821,37 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
                         gam = gnew;
                     }
                 }
-                s_ctl[0] = (TI)alpha;
-                s_ctl[1] = (TI)beta;
+                s_ctl[0] = alpha;
+                s_ctl[1] = beta;
                 s_flag = flag;
             }
             __syncthreads();
             const int flag = s_flag;
-            A = s_ctl[0];
-            B = s_ctl[1];
+            alpha = s_ctl[0];
+            beta = s_ctl[1];
             if (flag == 2) { nan = true; break; }
             if (flag == 1) break;
+            const TI A = (TI)alpha, B = (TI)beta;
+            p = first ? u : u + B * p;
+            s = first ? w : w + B * s;
+            d += A * p;
+            r -= A * s;
+            {
+                const TP Ap = (TP)alpha, Bp = (TP)beta;
+                for (unsigned int j = t; j < ncs; j += T) {
+                    const TP rs = first ? s_Rw[j] : s_Rw[j] + Bp * s_Rs[j];
+                    s_rc[j] = s_Rr[j] - Ap * rs;
+                }
+            }
+            __syncthreads();
+            coarse_solve();
+            const TP z = chebyshev(r);
+            u = own ? (TI)(z + coarse_value()) : (TI)0;
+            // publish u (a pure barrier), then w = A u
+            if (own) a.ubuf[row] = u;
+            if (!grid_sync(a.sw, nb, epoch)) { fail = true; break; }
+            w = own ? ell_row<TI, TI>(s_ci, s_val, T, t, wl, a.ubuf) : (TI)0;
+            first = false;
         }
         if (fail) return record_failure(a.sw, a.st_barrier);
         if (nan) { status = CGP_ERR_NAN; break; }
