@@ -257,7 +257,8 @@ def run_gpu(args):
              block_threads=args.threads, spmv_lanes=args.lanes, coarse_solver=args.coarse_solver,
              precond_degree=args.precond_degree, precond_ratio=args.precond_ratio,
              **({"warm_start": args.warm_start} if args.warm_start >= 0 else {}),
-             **({"inner_rtol": args.inner_rtol} if args.inner_rtol > 0 else {}))
+             **({"inner_rtol": args.inner_rtol} if args.inner_rtol > 0 else {}),
+             **({"mass_degree": args.mass_degree} if args.mass_degree > 0 else {}))
     stream = torch.cuda.current_stream()
     flush = L2Flush(f"cuda:{local}")
     bc = torch.empty_like(f.pc)
@@ -557,7 +558,8 @@ def main():
     ap.add_argument("--precond-degree", type=int, default=0)
     ap.add_argument("--precond-ratio", type=float, default=0.0)
     ap.add_argument("--warm-start", type=int, default=-1)
-    ap.add_argument("--inner-rtol", type=float, default=0.0)   # 0: the library default (1e-4)   # -1: the library default (1, extrapolation)
+    ap.add_argument("--inner-rtol", type=float, default=0.0)   # 0: the library default (1e-4)
+    ap.add_argument("--mass-degree", type=int, default=0)      # 0: the library default (4)   # -1: the library default (1, extrapolation)
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spmv", action="store_true")

@@ -95,6 +95,10 @@ typedef struct {
                           2 v^n - v^(n-1) of p and w, history kept by the context (cgp_step, the
                           batched step, cgp_momentum_solve, cgp_prolong_correct for w,
                           cgp_predict_pressure for p). cgp_set_bc clears the history */
+    int mass_degree;   /* preconditioner of the consistent-mass solve (Eq. 23): 1 = Jacobi, k >= 2 = the
+                          degree-k Chebyshev polynomial in D^-1 M on [1/2, 2] (its spectrum for P1
+                          triangles), applied in FP32 inside the CG; 0 (default) = 4, except Jacobi
+                          for CGP_MIXED on fine meshes of more than 2048 rows per block */
 } cgp_params;
 
 /* A coarse mesh: n_nodes points xy_host[n][2] and n_tris counter-clockwise triangles
@@ -130,7 +134,7 @@ typedef struct {
 
 /* Fill *p with the defaults: rho = 1, mu = 0.01, dt = 0.01, levels = 1, CGP_FP64, rtol = 1e-8,
  * inner_rtol = 1e-4, max_iter = 20000, max_outer = 30, spmv_lanes = 0, block_threads = 0,
- * coarse_solver = 0, spmv_format = 0, precond_degree = 0, precond_ratio = 0, warm_start = 1. */
+ * coarse_solver = 0, spmv_format = 0, precond_degree = 0, precond_ratio = 0, warm_start = 1, mass_degree = 0. */
 void cgp_default_params(cgp_params* p);
 
 /* Preprocessing (the paper's C_pre, Sect. 2.4): validates the coarse mesh, refines it

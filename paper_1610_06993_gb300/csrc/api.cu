@@ -81,6 +81,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     if (P.coarse_solver < 0 || P.coarse_solver > 5) return CGP_ERR_ARG;
     if (P.precond_degree < 0 || P.precond_degree > 64 || P.precond_ratio < 0.0) return CGP_ERR_ARG;
     if (P.warm_start < 0 || P.warm_start > 1) return CGP_ERR_ARG;
+    if (P.mass_degree < 0 || P.mass_degree > 16) return CGP_ERR_ARG;
     if (P.spmv_format < 0 || P.spmv_format > 2) return CGP_ERR_ARG;
     if (P.inner_rtol <= 0.0) P.inner_rtol = 1e-4;
     if (P.max_iter <= 0) P.max_iter = 20000;
@@ -213,6 +214,12 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     const int lanes = P.spmv_lanes ? P.spmv_lanes : 1;
     c->sh_f = make_shape(c->nf, threads, lanes, c->num_sms, bps);
     c->sh_c = make_shape(c->nc, threads, lanes, c->num_sms, bps);
+    if (P.mass_degree == 0) {
+        // the polynomial trades FP64 (or FP32) CG iterations for FP32 products; on a fine mesh
+        // of more than 2048 rows per block those leave L2 and FP32 iterations are cheaper
+        const long long rpb = ((long long)c->nf + c->sh_f.blocks - 1) / std::max(c->sh_f.blocks, 1);
+        P.mass_degree = (P.precision == CGP_MIXED && rpb > 2048) ? 1 : 4;
+    }
     c->width_c = 0;
     for (int i = 0; i < H.coarse.n; ++i) c->width_c = std::max(c->width_c, H.coarse.rp[i + 1] - H.coarse.rp[i]);
     CK(pipe_prepare(c));
@@ -255,6 +262,7 @@ void cgp_default_params(cgp_params* p) {
     p->spmv_lanes = 0;
     p->block_threads = 0;
     p->warm_start = 1;
+    p->mass_degree = 0;
 }
 
 int cgp_mesh_create(const cgp_mesh_desc* coarse, const cgp_params* prm, cgp_ctx* out) {

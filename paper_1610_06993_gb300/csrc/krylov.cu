@@ -74,6 +74,16 @@ CgArgs<TI> mass_args(cgp_ctx_s* c, const double* b, double* x, SyncWords* sw, do
     a.max_iter = c->prm.max_iter; a.max_outer = c->prm.max_outer; a.lanes = c->sh_f.lanes;
     a.st_iters = &c->stats->mass_iters; a.st_outer = &c->stats->mass_outer; a.st_status = &c->stats->mass_status;
     a.st_rel = &c->stats->mass_rel; a.st_barrier = &c->stats->barrier_status;
+    // Chebyshev preconditioner: for P1 triangles every element matrix D_e^-1 M_e has the
+    // eigenvalues 1/2, 1/2, 2, so the spectrum of D^-1 M lies in [1/2, 2] on any mesh
+    a.pdeg = c->prm.mass_degree;
+    if (a.pdeg >= 2) {
+        a.plmin = 0.5;
+        a.plmax = 2.0;
+        a.valP = c->M32;
+        a.dinvP = c->dinvM32;
+        a.zc0 = carve<float>(p, n2); a.zc1 = carve<float>(p, n2); a.dc = carve<float>(p, n2);
+    }
     return a;
 }
 

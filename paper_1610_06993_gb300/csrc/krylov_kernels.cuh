@@ -151,6 +151,13 @@ struct CgArgs {
     int* st_status;
     double* st_rel;
     int* st_barrier;
+    // Chebyshev polynomial preconditioner (pdeg >= 2; else Jacobi): u = p(D^-1 A) D^-1 r for a
+    // spectrum of D^-1 A inside [plmin, plmax], applied in FP32
+    int pdeg = 0;
+    double plmin = 0.0, plmax = 0.0;
+    const float* valP = nullptr;    // FP32 matrix values and inverse diagonal
+    const float* dinvP = nullptr;
+    float *zc0 = nullptr, *zc1 = nullptr, *dc = nullptr;   // [n][NR] iterates (double buffered), direction
 };
 
 // partial-sum regions (units of nblocks doubles)
@@ -165,6 +172,9 @@ constexpr size_t cg_smem(int threads) {
 // Iteration (Chronopoulos-Gear form, two grid barriers per iteration, one of them a reduction):
 //   p = u + beta p,  s = w + beta s,  d += alpha p,  r -= alpha s,  u = D^-1 r     (local)
 //   publish u | barrier | w = A u; partials (r,u), (r,r), (w,u) | barrier
+// With the polynomial preconditioner, u = p(D^-1 A) D^-1 r is the Chebyshev iteration on A z = r
+// from z = 0 (pdeg - 1 products with the FP32 copy of A, a barrier before each), and (r, u) is
+// taken in the product w = A u.
 // MINB: resident blocks per SM the launch is compiled for: 1 for a single context (128 registers
 // per thread, no spills), 2 for batches, whose many small block groups gain more from twice the
 // threads per SM than from registers.
@@ -213,6 +223,42 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
     }
     const double rtol2 = a.rtol * a.rtol, itol2 = a.inner_rtol * a.inner_rtol;
     const double floor2 = 0.25 * rtol2;
+    const bool poly = a.pdeg >= 2;
+    const float thetaP = poly ? (float)(0.5 * (a.plmax + a.plmin)) : 1.f;
+    const float deltaP = poly ? (float)(0.5 * (a.plmax - a.plmin)) : 1.f;
+    const float sigmaP = thetaP / deltaP;
+    // Chebyshev steps 1 .. pdeg - 1 from the first iterate z_1 = D^-1 r / theta (in zc0 and dc,
+    // written by the caller before a barrier); the last step writes u. Every block calls it the
+    // same number of times; false if a barrier failed.
+    auto poly_apply = [&]() -> bool {
+        float rho = 1.f / sigmaP;
+        for (int j = 1; j < a.pdeg; ++j) {
+            const float* zin = (j & 1) ? a.zc0 : a.zc1;
+            float* zout = (j & 1) ? a.zc1 : a.zc0;
+            const bool last = j == a.pdeg - 1;
+            const float rn = 1.f / (2.f * sigmaP - rho);
+            const float c1 = rn * rho, c2 = 2.f * rn / deltaP;
+            if (!grid_sync(a.sw, nb, epoch)) return false;
+            spmv_block<NR, float, float>(rr, a.rp, a.ci, a.valP, zin, a.lanes, [&](int i, float s0, float s1) {
+                const float acc[2] = {s0, s1};
+                const float di = a.dinvP[i];
+#pragma unroll
+                for (int c = 0; c < NR; ++c) {
+                    const size_t idx = (size_t)i * NR + c;
+                    const float dn = c1 * a.dc[idx] + c2 * di * ((float)a.r[idx] - acc[c]);
+                    const float zn = zin[idx] + dn;
+                    if (last) {
+                        a.u[idx] = (TI)zn;
+                    } else {
+                        a.dc[idx] = dn;
+                        zout[idx] = zn;
+                    }
+                }
+            });
+            rho = rn;
+        }
+        return true;
+    };
 
     for (;;) {
         // ---- refinement pass: FP64 true residual, inner start r = (TI) r64, u = D^-1 r, d = 0
@@ -231,9 +277,15 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
                     v[c] += ri * ri;
                     const TI rI = (TI)ri, uI = di * rI;
                     a.r[idx] = rI;
-                    a.u[idx] = uI;
                     a.d[idx] = (TI)0;
-                    v[NR + c] += (double)(rI * uI);
+                    if (poly) {
+                        const float z1 = a.dinvP[i] * (float)ri / thetaP;
+                        a.zc0[idx] = z1;
+                        a.dc[idx] = z1;
+                    } else {
+                        a.u[idx] = uI;
+                        v[NR + c] += (double)(rI * uI);
+                    }
                 }
             });
             block_partials_lean<2 * NR>(v, a.part + CG_O1 * nb, nb, g.bid, s_lean);
@@ -255,24 +307,40 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
         if (!any) break;
         if (outer >= a.max_outer || iters >= a.max_iter) { status = CGP_ERR_NOT_CONVERGED; break; }
 
-        // ---- w = A u, delta = (w, u); alpha_0 = gamma_0 / delta_0
+        // ---- w = A u, delta = (w, u) (and gamma_0 = (r, u) with the polynomial); alpha_0
         {
-            TI vv[NR];
+            if (poly) {
+                if (!poly_apply()) return record_failure(a.sw, a.st_barrier);
+                if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
+            }
+            TI vv[2 * NR];
 #pragma unroll
-            for (int c = 0; c < NR; ++c) vv[c] = (TI)0;
+            for (int c = 0; c < 2 * NR; ++c) vv[c] = (TI)0;
             spmv_block<NR, TI, TI>(rr, a.rp, a.ci, a.valI, a.u, a.lanes, [&](int i, TI s0, TI s1) {
                 const TI acc[2] = {s0, s1};
 #pragma unroll
                 for (int c = 0; c < NR; ++c) {
                     const size_t idx = (size_t)i * NR + c;
+                    const TI ui = a.u[idx];
                     a.w[idx] = acc[c];
-                    vv[c] += acc[c] * a.u[idx];
+                    vv[c] += acc[c] * ui;
+                    if (poly) vv[NR + c] += a.r[idx] * ui;
                 }
             });
-            double t0[NR];
-            block_partials_it<NR, TI>(vv, a.part + CG_I0 * nb, nb, g.bid, s_lean, s_f32);
+            double t0[2 * NR];
+            block_partials_it<2 * NR, TI>(vv, a.part + CG_I1 * nb, nb, g.bid, s_lean, s_f32);
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-            grid_totals<NR>(a.part + CG_I0 * nb, nb, t0, s_bc);
+            grid_totals<2 * NR>(a.part + CG_I1 * nb, nb, t0, s_bc);
+            if (poly) {
+#pragma unroll
+                for (int c = 0; c < NR; ++c) {
+                    gam[c] = t0[NR + c];
+                    if (bad(gam[c])) {
+                        nan = true;
+                        act[c] = false;
+                    }
+                }
+            }
 #pragma unroll
             for (int c = 0; c < NR; ++c) {
                 if (act[c] && t0[c] != 0.0 && !bad(t0[c])) {
@@ -330,14 +398,21 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
                             a.d[idx] = dd[h][c] + al[c] * p;
                             const TI r = ro[h][c] - al[c] * sv;
                             a.r[idx] = r;
-                            const TI u = di[h] * r;
-                            a.u[idx] = u;
-                            vg[c] += r * u;
                             vr[c] += r * r;
+                            if (poly) {
+                                const float z1 = a.dinvP[row[h]] * (float)r / thetaP;
+                                a.zc0[idx] = z1;
+                                a.dc[idx] = z1;
+                            } else {
+                                const TI u = di[h] * r;
+                                a.u[idx] = u;
+                                vg[c] += r * u;
+                            }
                         }
                     }
                 }
             }
+            if (poly && !poly_apply()) return record_failure(a.sw, a.st_barrier);
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
             // ---- w = A u; (r, u), (r, r), (w, u) in one reduction
             spmv_block<NR, TI, TI>(rr, a.rp, a.ci, a.valI, a.u, a.lanes, [&](int i, TI s0, TI s1) {
@@ -345,8 +420,10 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
 #pragma unroll
                 for (int c = 0; c < NR; ++c) {
                     const size_t idx = (size_t)i * NR + c;
+                    const TI ui = a.u[idx];
                     a.w[idx] = acc[c];
-                    vd[c] += acc[c] * a.u[idx];
+                    vd[c] += acc[c] * ui;
+                    if (poly) vg[c] += a.r[idx] * ui;
                 }
             });
             {
