@@ -99,6 +99,10 @@ typedef struct {
                           degree-k Chebyshev polynomial in D^-1 M on [1/2, 2] (its spectrum for P1
                           triangles), applied in FP32 inside the CG; 0 (default) = 4, except Jacobi
                           for CGP_MIXED on fine meshes of more than 2048 rows per block */
+    int momentum_degree; /* preconditioner of the momentum BiCGStab (Eq. 19): 1 = Jacobi, k >= 2 = the
+                          degree-k Chebyshev polynomial in D^-1 A on [1/2, G], G the Gershgorin bound
+                          of D^-1 A taken by each cgp_assemble, applied in FP32; 0 (default) = 3
+                          for CGP_FP64, Jacobi for CGP_MIXED */
 } cgp_params;
 
 /* A coarse mesh: n_nodes points xy_host[n][2] and n_tris counter-clockwise triangles
@@ -134,7 +138,8 @@ typedef struct {
 
 /* Fill *p with the defaults: rho = 1, mu = 0.01, dt = 0.01, levels = 1, CGP_FP64, rtol = 1e-8,
  * inner_rtol = 1e-4, max_iter = 20000, max_outer = 30, spmv_lanes = 0, block_threads = 0,
- * coarse_solver = 0, spmv_format = 0, precond_degree = 0, precond_ratio = 0, warm_start = 1, mass_degree = 0. */
+ * coarse_solver = 0, spmv_format = 0, precond_degree = 0, precond_ratio = 0, warm_start = 1, mass_degree = 0,
+ * momentum_degree = 0. */
 void cgp_default_params(cgp_params* p);
 
 /* Preprocessing (the paper's C_pre, Sect. 2.4): validates the coarse mesh, refines it

@@ -35,7 +35,7 @@ class cgp_params(C.Structure):
                 ("max_iter", C.c_int), ("max_outer", C.c_int), ("spmv_lanes", C.c_int),
                 ("block_threads", C.c_int), ("coarse_solver", C.c_int), ("spmv_format", C.c_int),
                 ("precond_degree", C.c_int), ("precond_ratio", C.c_double), ("warm_start", C.c_int),
-                ("mass_degree", C.c_int)]
+                ("mass_degree", C.c_int), ("momentum_degree", C.c_int)]
 
 
 class cgp_mesh_desc(C.Structure):

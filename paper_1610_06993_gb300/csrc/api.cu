@@ -82,6 +82,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     if (P.precond_degree < 0 || P.precond_degree > 64 || P.precond_ratio < 0.0) return CGP_ERR_ARG;
     if (P.warm_start < 0 || P.warm_start > 1) return CGP_ERR_ARG;
     if (P.mass_degree < 0 || P.mass_degree > 16) return CGP_ERR_ARG;
+    if (P.momentum_degree < 0 || P.momentum_degree > 16) return CGP_ERR_ARG;
     if (P.spmv_format < 0 || P.spmv_format > 2) return CGP_ERR_ARG;
     if (P.inner_rtol <= 0.0) P.inner_rtol = 1e-4;
     if (P.max_iter <= 0) P.max_iter = 20000;
@@ -164,13 +165,16 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     TRY(dalloc(c, &c->w_flag, 1));
     TRY(dalloc(c, &c->mom_dx, 2 * nf));
     TRY(dalloc(c, &c->mom_flag, 1));
+    TRY(dalloc(c, &c->mom_bound, 1));
     CK(cudaMemset(c->pc_flag, 0, sizeof(int)));
     CK(cudaMemset(c->w_flag, 0, sizeof(int)));
     CK(cudaMemset(c->mom_flag, 0, sizeof(int)));
     TRY(dalloc(c, &c->u_stage, 2 * nf));
     TRY(dalloc(c, &c->pc_stage, nc));
-    // Krylov workspace: the largest of BiCGStab (9 pair vectors) and CG (6 vectors), 256-byte carved
-    const size_t need = std::max({9 * 2 * nf * sizeof(double), 6 * 2 * nf * sizeof(double),
+    // Krylov workspace: the largest of BiCGStab (9 pair vectors) and CG (6 vectors), each with
+    // the three FP32 pair vectors of its polynomial preconditioner, 256-byte carved
+    const size_t need = std::max({9 * 2 * nf * sizeof(double) + 3 * 2 * nf * sizeof(float),
+                                  6 * 2 * nf * sizeof(double) + 3 * 2 * nf * sizeof(float),
                                   6 * nc * sizeof(double)}) + 16 * 256;
     c->ws_bytes = need;
     char* ws = nullptr;
@@ -220,6 +224,9 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
         const long long rpb = ((long long)c->nf + c->sh_f.blocks - 1) / std::max(c->sh_f.blocks, 1);
         P.mass_degree = (P.precision == CGP_MIXED && rpb > 2048) ? 1 : 4;
     }
+    // FP32 BiCGStab iterations cost about as much as the polynomial's FP32 products they save
+    if (P.momentum_degree == 0) P.momentum_degree = P.precision == CGP_MIXED ? 1 : 3;
+    c->fp32_A = P.precision == CGP_MIXED || P.momentum_degree >= 2;
     c->width_c = 0;
     for (int i = 0; i < H.coarse.n; ++i) c->width_c = std::max(c->width_c, H.coarse.rp[i + 1] - H.coarse.rp[i]);
     CK(pipe_prepare(c));
@@ -263,6 +270,7 @@ void cgp_default_params(cgp_params* p) {
     p->block_threads = 0;
     p->warm_start = 1;
     p->mass_degree = 0;
+    p->momentum_degree = 0;
 }
 
 int cgp_mesh_create(const cgp_mesh_desc* coarse, const cgp_params* prm, cgp_ctx* out) {

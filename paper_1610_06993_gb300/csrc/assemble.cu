@@ -152,11 +152,11 @@ StepAsmArgs asm_args(cgp_ctx_s* c, const double* u, SyncWords* sw) {
     a.mask = c->vel_mask;
     a.g = c->g;
     a.A = c->A;
-    const bool mixed = c->prm.precision == CGP_MIXED;
-    a.A32 = mixed ? c->A32 : nullptr;
+    a.A32 = c->fp32_A ? c->A32 : nullptr;
     a.dinv = c->dinvA;
-    a.dinv32 = mixed ? c->dinvA32 : nullptr;
+    a.dinv32 = c->fp32_A ? c->dinvA32 : nullptr;
     a.b = c->b_mom;
+    a.bound = c->prm.momentum_degree >= 2 ? c->mom_bound : nullptr;
     a.rho = c->prm.rho;
     a.dtrho = c->prm.dt * c->prm.rho;
     a.sw = sw;
@@ -175,8 +175,10 @@ namespace {
 
 // ev[9 e + 3 r + q] = dt rho (|T|/12) ((u_sum + u_r) . grad phi_q)  (Eq. 16's N, element e)
 __global__ void k_conv_elements(int t, const int* __restrict__ tri, const double* __restrict__ geo,
-                                const double* __restrict__ u, double dtrho, double* __restrict__ ev) {
+                                const double* __restrict__ u, double dtrho, double* __restrict__ ev,
+                                unsigned int* __restrict__ bound) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (bound && e == 0) *bound = 0u;   // k_rows, launched after this kernel, takes the max
     if (e >= t) return;
     const double* g = geo + 8 * (size_t)e;
     const double area12 = g[0] / 12.0;
@@ -205,28 +207,42 @@ __global__ void k_gather_entries(int nnz, const int* __restrict__ ip, const int*
     if (A32) A32[k] = (float)v;
 }
 
-// Jacobi diagonals and the right-hand side b = rho M u^n (Dirichlet rows: prescribed values)
+// Jacobi diagonals and the right-hand side b = rho M u^n (Dirichlet rows: prescribed values);
+// with `bound`, the largest Gershgorin bound 1 + sum_j!=i |A_ij| / |A_ii| of D^-1 A over the rows
+// (from the FP32 copy; identity rows for Dirichlet components), as an atomic max of float bits
 __global__ void k_rows(int nf, const int* __restrict__ rp, const int* __restrict__ ci, const int* __restrict__ diag,
-                       const double* __restrict__ A, const double* __restrict__ M, const double* __restrict__ u,
-                       const unsigned char* __restrict__ mask, const double* __restrict__ g, double rho,
-                       double* __restrict__ dinv, float* __restrict__ dinv32, double* __restrict__ b) {
+                       const double* __restrict__ A, const float* __restrict__ A32, const double* __restrict__ M,
+                       const double* __restrict__ u, const unsigned char* __restrict__ mask,
+                       const double* __restrict__ g, double rho, double* __restrict__ dinv,
+                       float* __restrict__ dinv32, double* __restrict__ b, unsigned int* __restrict__ bound) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nf) return;
-    const unsigned char m = mask[i];
-    const double di = 1.0 / A[diag[i]];
-    const double dx = (m & CGP_BC_U) ? 1.0 : di, dy = (m & CGP_BC_V) ? 1.0 : di;
-    store2(dinv, i, dx, dy);
-    if (dinv32) store2(dinv32, i, (float)dx, (float)dy);
-    double mx = 0.0, my = 0.0;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) {
-        double ujx, ujy;
-        load2(u, ci[k], ujx, ujy);
-        mx += M[k] * ujx;
-        my += M[k] * ujy;
+    float gmax = 1.f;
+    if (i < nf) {
+        const unsigned char m = mask[i];
+        const int kd = diag[i];
+        const double di = 1.0 / A[kd];
+        const double dx = (m & CGP_BC_U) ? 1.0 : di, dy = (m & CGP_BC_V) ? 1.0 : di;
+        store2(dinv, i, dx, dy);
+        if (dinv32) store2(dinv32, i, (float)dx, (float)dy);
+        double mx = 0.0, my = 0.0;
+        float off = 0.f;
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            double ujx, ujy;
+            load2(u, ci[k], ujx, ujy);
+            mx += M[k] * ujx;
+            my += M[k] * ujy;
+            if (bound && k != kd) off += fabsf(A32[k]);
+        }
+        double gx, gy;
+        load2(g, i, gx, gy);
+        store2(b, i, (m & CGP_BC_U) ? gx : rho * mx, (m & CGP_BC_V) ? gy : rho * my);
+        if (bound && (m & (CGP_BC_U | CGP_BC_V)) != (CGP_BC_U | CGP_BC_V))
+            gmax = 1.f + off / fabsf(A32[kd]);
     }
-    double gx, gy;
-    load2(g, i, gx, gy);
-    store2(b, i, (m & CGP_BC_U) ? gx : rho * mx, (m & CGP_BC_V) ? gy : rho * my);
+    if (bound) {
+        const unsigned int gb = __reduce_max_sync(0xffffffffu, __float_as_uint(gmax));
+        if ((threadIdx.x & 31) == 0) atomicMax(bound, gb);
+    }
 }
 
 }  // namespace
@@ -258,13 +274,15 @@ int assemble_gather_build(cgp_ctx_s* c) {
 }
 
 cudaError_t launch_assemble_step(cgp_ctx_s* c, const double* u, cudaStream_t s) {
-    const bool mixed = c->prm.precision == CGP_MIXED;
     const int t = c->EF.t, nnz = c->F.nnz, nf = c->nf;
-    k_conv_elements<<<(t + 255) / 256, 256, 0, s>>>(t, c->EF.tri, c->EF.geo, u, c->prm.dt * c->prm.rho, c->asm_ev);
+    unsigned int* bound = c->prm.momentum_degree >= 2 ? c->mom_bound : nullptr;
+    k_conv_elements<<<(t + 255) / 256, 256, 0, s>>>(t, c->EF.tri, c->EF.geo, u, c->prm.dt * c->prm.rho, c->asm_ev,
+                                                    bound);
     k_gather_entries<<<(nnz + 255) / 256, 256, 0, s>>>(nnz, c->asm_ip, c->asm_idx, c->asm_ev, c->A0, c->A,
-                                                      mixed ? c->A32 : nullptr);
-    k_rows<<<(nf + 255) / 256, 256, 0, s>>>(nf, c->F.rp, c->F.ci, c->F.diag, c->A, c->M, u, c->vel_mask, c->g,
-                                          c->prm.rho, c->dinvA, mixed ? c->dinvA32 : nullptr, c->b_mom);
+                                                      c->fp32_A ? c->A32 : nullptr);
+    k_rows<<<(nf + 255) / 256, 256, 0, s>>>(nf, c->F.rp, c->F.ci, c->F.diag, c->A, c->A32, c->M, u, c->vel_mask,
+                                          c->g, c->prm.rho, c->dinvA, c->fp32_A ? c->dinvA32 : nullptr, c->b_mom,
+                                          bound);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@ struct StepAsmArgs {
     double* dinv;                // [nf][2]
     float* dinv32;
     double* b;                   // [nf][2]
+    unsigned int* bound;         // Gershgorin bound of D^-1 A (float bits, atomic max), or nullptr
     double rho, dtrho;
     SyncWords* sw;
     int* barrier_status;
@@ -41,6 +42,7 @@ __global__ void __launch_bounds__(1024) k_assemble_step(Launch<StepAsmArgs> L) {
     const unsigned int nb = grp.nb;
     const int tid = grp.bid * blockDim.x + threadIdx.x;
     const int nthreads = grp.nb * blockDim.x;
+    if (a.bound && tid == 0) *a.bound = 0u;
     for (int k = tid; k < a.nnz; k += nthreads) a.A[k] = a.A0[k];
     if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.barrier_status);
     for (int c = 0; c < a.ncol; ++c) {
@@ -63,25 +65,38 @@ __global__ void __launch_bounds__(1024) k_assemble_step(Launch<StepAsmArgs> L) {
         }
         if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.barrier_status);
     }
+    float gmax = 1.f;
     for (int i = tid; i < a.nf; i += nthreads) {
         const unsigned char m = a.mask[i];
-        const double dg = a.A[a.diag[i]];
+        const int kd = a.diag[i];
+        const double dg = a.A[kd];
         const double di = 1.0 / dg;
         double dx = (m & CGP_BC_U) ? 1.0 : di, dy = (m & CGP_BC_V) ? 1.0 : di;
         store2(a.dinv, i, dx, dy);
         double mx = 0.0, my = 0.0;
+        float off = 0.f;
         for (int k = a.rp[i]; k < a.rp[i + 1]; ++k) {
             double ujx, ujy;
             load2(a.u, a.ci[k], ujx, ujy);
             const double mv = a.M[k];
             mx += mv * ujx;
             my += mv * ujy;
-            if (a.A32) a.A32[k] = (float)a.A[k];
+            if (a.A32) {
+                const float av = (float)a.A[k];
+                a.A32[k] = av;
+                if (k != kd) off += fabsf(av);
+            }
         }
         double gx, gy;
         load2(a.g, i, gx, gy);
         store2(a.b, i, (m & CGP_BC_U) ? gx : a.rho * mx, (m & CGP_BC_V) ? gy : a.rho * my);
         if (a.dinv32) store2(a.dinv32, i, (float)dx, (float)dy);
+        // Gershgorin disc of row i of D^-1 A (identity rows for Dirichlet components)
+        if ((m & (CGP_BC_U | CGP_BC_V)) != (CGP_BC_U | CGP_BC_V)) gmax = fmaxf(gmax, 1.f + off / fabsf((float)dg));
+    }
+    if (a.bound) {
+        const unsigned int gb = __reduce_max_sync(0xffffffffu, __float_as_uint(gmax));
+        if ((threadIdx.x & 31) == 0) atomicMax(a.bound, gb);
     }
 }
 

@@ -111,6 +111,8 @@ struct cgp_ctx_s {
     int* w_flag = nullptr;
     double* mom_dx = nullptr;    // [nf][2] last momentum increment u~^n - u^(n-1) (warm_start = 1)
     int* mom_flag = nullptr;     // 1 once mom_dx holds an increment
+    unsigned int* mom_bound = nullptr;   // Gershgorin bound of the spectrum of D^-1 A (float bits)
+    bool fp32_A = false;         // the assembly writes A32 / dinvA32 (mixed, or momentum polynomial)
 
     // Krylov workspace and reductions
     void* ws = nullptr;

@@ -100,6 +100,7 @@ BicgArgs<TI> momentum_args(cgp_ctx_s* c, const double* u_in, double* x, SyncWord
     const bool pred = c->prm.warm_start == 1;
     a.dx = pred ? c->mom_dx : nullptr;
     a.dx_flag = pred ? c->mom_flag : nullptr;
+    a.pdeg = c->prm.momentum_degree;
     a.r = carve<TI>(p, n2); a.rh = carve<TI>(p, n2); a.p = carve<TI>(p, n2);
     a.v = carve<TI>(p, n2); a.y = carve<TI>(p, n2); a.s = carve<TI>(p, n2);
     a.z = carve<TI>(p, n2); a.t = carve<TI>(p, n2); a.d = carve<TI>(p, n2);
@@ -107,6 +108,16 @@ BicgArgs<TI> momentum_args(cgp_ctx_s* c, const double* u_in, double* x, SyncWord
     a.max_iter = c->prm.max_iter; a.max_outer = c->prm.max_outer; a.lanes = c->sh_f.lanes;
     a.st_iters = &c->stats->mom_iters; a.st_outer = &c->stats->mom_outer; a.st_status = &c->stats->mom_status;
     a.st_rel = &c->stats->mom_rel; a.st_barrier = &c->stats->barrier_status;
+    if (a.pdeg >= 2) {
+        // the real parts of the spectrum of D^-1 A lie near [1/2, 2] while the mass matrix
+        // dominates; the upper end is the assembly's Gershgorin bound, and an underestimated lower
+        // end only leaves those components to the Krylov iteration
+        a.plmin = 0.5;
+        a.pbound = c->mom_bound;
+        a.valP = c->A32;
+        a.dinvP = c->dinvA32;
+        a.zc0 = carve<float>(p, n2); a.zc1 = carve<float>(p, n2); a.dc = carve<float>(p, n2);
+    }
     return a;
 }
 

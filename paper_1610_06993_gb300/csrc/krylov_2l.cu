@@ -294,14 +294,16 @@ __global__ void __launch_bounds__(512, MINB) k_cg2l(Launch<Cg2Args<TI>> L) {
                 } else if (rho <= tgt || iters >= a.max_iter || gam == 0.0) {
                     flag = 1;
                 } else {
-                    const double rga = 1.0 / (gam * alpha);
-                    const double bnew = gnew * alpha * rga;
-                    const double den = del - gnew * gnew * rga;
+                    // beta = gnew / gam and alpha' = gnew / (del - gnew^2 / (gam alpha))
+                    // = gnew gam alpha / (del gam alpha - gnew^2): two independent divisions
+                    // (a dependent FP64 operation costs tens of cycles on this GPU)
+                    const double ga = gam * alpha;
+                    const double den = fma(del, ga, -gnew * gnew);
                     if (den == 0.0 || gnew == 0.0) {
                         flag = 1;
                     } else {
-                        beta = bnew;
-                        alpha = gnew / den;
+                        beta = gnew / gam;
+                        alpha = (gnew * ga) / den;
                         gam = gnew;
                     }
                 }

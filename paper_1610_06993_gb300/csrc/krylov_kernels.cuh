@@ -453,13 +453,14 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
                     bad_any |= bad(gnew) | bad(rho) | bad(del);
                     if (act[c] && rho <= tgt[c]) act[c] = false;
                     if (act[c]) {
-                        // beta = gnew / gam and beta gnew / alpha from one reciprocal
-                        const double rga = 1.0 / (gam[c] * alpha[c]);
-                        const double bnew = gnew * alpha[c] * rga;
-                        const double den = del - gnew * gnew * rga;
+                        // beta = gnew / gam and alpha' = gnew gam alpha / (del gam alpha - gnew^2):
+                        // two independent divisions (a dependent FP64 operation costs tens of
+                        // cycles on this GPU)
+                        const double ga = gam[c] * alpha[c];
+                        const double den = fma(del, ga, -gnew * gnew);
                         if (den != 0.0 && gam[c] != 0.0) {
-                            beta[c] = bnew;
-                            alpha[c] = gnew / den;
+                            beta[c] = gnew / gam[c];
+                            alpha[c] = (gnew * ga) / den;
                             gam[c] = gnew;
                         } else {
                             act[c] = false;
@@ -526,6 +527,14 @@ struct BicgArgs {
     double* x;                    // [n][2] solution (x == x_in gives a zero increment)
     double* dx;                   // [n][2] increment x - x_in of the last converged solve, or nullptr
     int* dx_flag;                 // 1 once dx holds an increment
+    // Chebyshev polynomial preconditioner (pdeg >= 2; else Jacobi): y = p(D^-1 A) D^-1 q for a
+    // spectrum of D^-1 A inside [plmin, the float bound at *pbound], applied in FP32
+    int pdeg = 0;
+    double plmin = 0.0;
+    const unsigned int* pbound = nullptr;
+    const float* valP = nullptr;  // FP32 matrix values and inverse diagonal ([n][2])
+    const float* dinvP = nullptr;
+    float *zc0 = nullptr, *zc1 = nullptr, *dc = nullptr;   // [n][2] iterates (double buffered), direction
     TI *r, *rh, *p, *v, *y, *s, *z, *t, *d;
     double* part;
     SyncWords* sw;
@@ -553,6 +562,9 @@ constexpr size_t bicg_smem(int threads) { return (size_t)10 * threads * sizeof(d
 //   rho' = (rh, s) - omega (rh, t),  (r, r) = (s, s) - 2 omega (t, s) + omega^2 (t, t)
 // The next rho and ||r||^2 follow from inner products of s and t taken in the same reduction
 // (exact identities for r = s - omega t), which saves the fifth barrier of the textbook form.
+// With the polynomial preconditioner, y = K^-1 p and z = K^-1 s are Chebyshev iterations on
+// A y = p and A z = s from zero (pdeg - 1 products with the FP32 copy of A, a barrier before
+// each; identity rows at Dirichlet components).
 template <typename TI, int MINB = 1>
 __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) {
     extern __shared__ double s_lean[];   // [10][blockDim.x]
@@ -571,6 +583,48 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
     // Initial guess u^n + (u~^n - u^(n-1)): the last step's increment, repeated. Every block reads
     // the flag before the first grid barrier; block 0 rewrites it only after the last one.
     const bool have_dx = a.dx != nullptr && *a.dx_flag != 0;
+    const bool poly = a.pdeg >= 2;
+    float thetaP = 1.f, deltaP = 1.f;
+    if (poly) {
+        const float lmax = fmaxf(__uint_as_float(*a.pbound), (float)a.plmin * 1.25f);
+        thetaP = 0.5f * (lmax + (float)a.plmin);
+        deltaP = 0.5f * (lmax - (float)a.plmin);
+    }
+    const float sigmaP = thetaP / deltaP;
+    // y <- K^-1 q: Chebyshev steps 1 .. pdeg - 1 from the first iterate D^-1 q / theta (in zc0 and
+    // dc, written by the caller before a barrier); the last step writes y. Every block calls it
+    // the same number of times; false if a barrier failed.
+    auto poly_apply = [&](const TI* q, TI* y) -> bool {
+        float rho = 1.f / sigmaP;
+        for (int j = 1; j < a.pdeg; ++j) {
+            const float* zin = (j & 1) ? a.zc0 : a.zc1;
+            float* zout = (j & 1) ? a.zc1 : a.zc0;
+            const bool last = j == a.pdeg - 1;
+            const float rn = 1.f / (2.f * sigmaP - rho);
+            const float c1 = rn * rho, c2 = 2.f * rn / deltaP;
+            if (!grid_sync(a.sw, nb, epoch)) return false;
+            spmv_block<2, float, float>(rr, a.rp, a.ci, a.valP, zin, a.lanes, [&](int i, float s0, float s1) {
+                const unsigned char m = a.mask[i];
+                float z0, z1, d0, d1, i0, i1;
+                load2(zin, i, z0, z1);
+                load2(a.dc, i, d0, d1);
+                load2(a.dinvP, i, i0, i1);
+                TI q0, q1;
+                load2(q, i, q0, q1);
+                const float a0 = (m & 1) ? z0 : s0, a1 = (m & 2) ? z1 : s1;
+                const float n0 = c1 * d0 + c2 * i0 * ((float)q0 - a0);
+                const float n1 = c1 * d1 + c2 * i1 * ((float)q1 - a1);
+                if (last) {
+                    store2(y, i, (TI)(z0 + n0), (TI)(z1 + n1));
+                } else {
+                    store2(a.dc, i, n0, n1);
+                    store2(zout, i, z0 + n0, z1 + n1);
+                }
+            });
+            rho = rn;
+        }
+        return true;
+    };
 
     // initial guess with prescribed values, ||b||^2
     {
@@ -694,12 +748,21 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
                         store2(a.d, row[h], dn[0], dn[1]);
                         store2(a.r, row[h], rn[0], rn[1]);
                     }
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) yn[c] = dg[h][c] * pn[c];
                     store2(a.p, row[h], pn[0], pn[1]);
-                    store2(a.y, row[h], yn[0], yn[1]);
+                    if (poly) {
+                        float i0, i1;
+                        load2(a.dinvP, row[h], i0, i1);
+                        const float z0 = i0 * (float)pn[0] / thetaP, z1 = i1 * (float)pn[1] / thetaP;
+                        store2(a.zc0, row[h], z0, z1);
+                        store2(a.dc, row[h], z0, z1);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) yn[c] = dg[h][c] * pn[c];
+                        store2(a.y, row[h], yn[0], yn[1]);
+                    }
                 }
             }
+            if (poly && !poly_apply(a.p, a.y)) return record_failure(a.sw, a.st_barrier);
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
             // ---- v = A y, sigma = (rh, v); alpha = rho / sigma (thread 0, broadcast)
             {
@@ -721,6 +784,7 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
                 grid_totals_shared<2>(a.part, slot, nb, s_bc);
                 if (threadIdx.x == 0) {
                     int fl = 0;
+#pragma unroll
                     for (int c = 0; c < 2; ++c) {
                         const double ts = s_bc[c];
                         fl |= bad(ts) ? 1 : 0;
@@ -759,10 +823,19 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
                         dn[c] = dv[h][c] + al[c] * yv[h][c];
                     }
                     store2(a.s, row[h], sn[0], sn[1]);
-                    store2(a.z, row[h], zn[0], zn[1]);
                     store2(a.d, row[h], dn[0], dn[1]);
+                    if (poly) {
+                        float i0, i1;
+                        load2(a.dinvP, row[h], i0, i1);
+                        const float z0 = i0 * (float)sn[0] / thetaP, z1 = i1 * (float)sn[1] / thetaP;
+                        store2(a.zc0, row[h], z0, z1);
+                        store2(a.dc, row[h], z0, z1);
+                    } else {
+                        store2(a.z, row[h], zn[0], zn[1]);
+                    }
                 }
             }
+            if (poly && !poly_apply(a.s, a.z)) return record_failure(a.sw, a.st_barrier);
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
             // ---- t = A z; (t, s), (t, t), (rh, t), (rh, s), (s, s) in one reduction
             {
@@ -800,6 +873,7 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
                 // omega, the next rho and beta, convergence: thread 0, broadcast
                 if (threadIdx.x == 0) {
                     int more = 0, fl = 0;
+#pragma unroll
                     for (int c = 0; c < 2; ++c) {
                         const double ts = s_bc[c], tt = s_bc[2 + c], ht = s_bc[4 + c], hs = s_bc[6 + c];
                         const double ss = s_bc[8 + c];
@@ -814,13 +888,16 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
                             omega[c] = 0.0;
                         }
                         if (act[c]) {
-                            const double rnew = hs - omega[c] * ht;
-                            const double rr2 = ss - 2.0 * omega[c] * ts + omega[c] * omega[c] * tt;
-                            if (rr2 <= tgt[c]) {
+                            // with omega = ts / tt (tt = (t, t) > 0): rnew tt = hs tt - ts ht,
+                            // ||r||^2 tt = ss tt - ts^2 and beta = (rnew / rho)(alpha / omega) =
+                            // rnew tt alpha / (rho ts); the three divisions are independent
+                            const double q = fma(hs, tt, -ts * ht);
+                            const double rr2t = fma(ss, tt, -ts * ts);
+                            if (rr2t <= tgt[c] * tt) {
                                 act[c] = false;
-                            } else if (rnew != 0.0 && omega[c] != 0.0 && rho[c] != 0.0) {
-                                beta[c] = (rnew / rho[c]) * (alpha[c] / omega[c]);
-                                rho[c] = rnew;
+                            } else if (q != 0.0 && ts != 0.0 && rho[c] != 0.0) {
+                                beta[c] = (q * alpha[c]) / (rho[c] * ts);
+                                rho[c] = q / tt;
                             } else {
                                 act[c] = false;            // breakdown: restart in the next pass
                             }

@@ -637,9 +637,9 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
     };
 
     // One reduction of the products (r,u), (r,r), (w,u) and the moments of w, r, s on this
-    // block's parts: slot PS_F + q for product q; from slot PS_F + 3 on, the moments in coarse
-    // order, entry (3 v + f) nsub + SZ_SUB b + h for function f of vector v (w, r, s) on part h of
-    // block b, so that every block gathers them with one contiguous copy. Warp w sums tasks w,
+    // block's parts: slot PS_F + q for product q; from slot PS_F + 3 on, the moments (stored in
+    // TP) in coarse order, entry (3 v + f) nsub + SZ_SUB b + h for function f of vector v (w, r,
+    // s) on part h of block b, so that every block gathers them with one contiguous copy. Warp w sums tasks w,
     // w + warps, ...: a product over the whole block (FP64 for FP64 iterations), a moment over one
     // part (in TP); fixed order.
     auto reduce_fused = [&](TI rI, TI uI, TI wI, TI sI) {
@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                 if (lane == 0)
-                    a.part[(size_t)(PS_F + 3) * nb + (size_t)k * nsub + SZ_SUB * blockIdx.x + h] = (double)acc;
+                    reinterpret_cast<TP*>(a.part + (size_t)(PS_F + 3) * nb)[(size_t)k * nsub + SZ_SUB * blockIdx.x + h] = acc;
                 continue;
             }
             if (lane == 0) a.part[(size_t)(PS_F + q) * nb + blockIdx.x] = tot;
@@ -724,21 +724,47 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
             if (lane == 0) s_bc[warp] = tt;
         }
         // the moments: a contiguous copy into s_Rw, s_Rr, s_Rs (consecutive [3][ncs]), all loads
-        // of a round in flight before the first store
-        const double* src = a.part + (size_t)(PS_F + 3) * nb;
+        // of a round in flight before the first store (16-byte loads for FP32 moments: the
+        // region starts at a multiple of 128 nb bytes)
+        const TP* src = reinterpret_cast<const TP*>(a.part + (size_t)(PS_F + 3) * nb);
         const unsigned int lim = 3 * ncs;
-        constexpr int GQ = 10;
-        for (unsigned int i0 = t; i0 < lim; i0 += GQ * T) {
-            double m[GQ];
+        if constexpr (sizeof(TP) == sizeof(float)) {
+            const unsigned int n4 = lim / 4;
+            const float4* s4 = reinterpret_cast<const float4*>(src);
+            constexpr int GQ = 4;
+            for (unsigned int i0 = t; i0 < n4; i0 += GQ * T) {
+                float4 m[GQ];
 #pragma unroll
-            for (int q = 0; q < GQ; ++q) {
-                const unsigned int i = i0 + q * T;
-                m[q] = i < lim ? __ldcg(src + i) : 0.0;
+                for (int q = 0; q < GQ; ++q) {
+                    const unsigned int i = i0 + q * T;
+                    m[q] = i < n4 ? __ldcg(s4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int q = 0; q < GQ; ++q) {
+                    const unsigned int i = i0 + q * T;
+                    if (i < n4) {
+                        s_Rw[4 * i] = m[q].x;
+                        s_Rw[4 * i + 1] = m[q].y;
+                        s_Rw[4 * i + 2] = m[q].z;
+                        s_Rw[4 * i + 3] = m[q].w;
+                    }
+                }
             }
+            for (unsigned int i = 4 * n4 + t; i < lim; i += T) s_Rw[i] = __ldcg(src + i);
+        } else {
+            constexpr int GQ = 10;
+            for (unsigned int i0 = t; i0 < lim; i0 += GQ * T) {
+                TP m[GQ];
 #pragma unroll
-            for (int q = 0; q < GQ; ++q) {
-                const unsigned int i = i0 + q * T;
-                if (i < lim) s_Rw[i] = (TP)m[q];
+                for (int q = 0; q < GQ; ++q) {
+                    const unsigned int i = i0 + q * T;
+                    m[q] = i < lim ? __ldcg(src + i) : (TP)0;
+                }
+#pragma unroll
+                for (int q = 0; q < GQ; ++q) {
+                    const unsigned int i = i0 + q * T;
+                    if (i < lim) s_Rw[i] = m[q];
+                }
             }
         }
         __syncthreads();
@@ -808,16 +834,16 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
                 } else if (rho <= tgt || iters >= a.max_iter || gam == 0.0) {
                     flag = 1;
                 } else {
-                    // beta = gnew / gam and beta gnew / alpha = gnew^2 / (gam alpha) from one
-                    // reciprocal: FP64 division is slow on this GPU
-                    const double rga = 1.0 / (gam * alpha);
-                    const double bnew = gnew * alpha * rga;
-                    const double den = del - gnew * gnew * rga;
+                    // beta = gnew / gam and alpha' = gnew / (del - gnew^2 / (gam alpha))
+                    // = gnew gam alpha / (del gam alpha - gnew^2): two independent divisions
+                    // (a dependent FP64 operation costs tens of cycles on this GPU)
+                    const double ga = gam * alpha;
+                    const double den = fma(del, ga, -gnew * gnew);
                     if (den == 0.0 || gnew == 0.0) {
                         flag = 1;
                     } else {
-                        beta = bnew;
-                        alpha = gnew / den;
+                        beta = gnew / gam;
+                        alpha = (gnew * ga) / den;
                         gam = gnew;
                     }
                 }
