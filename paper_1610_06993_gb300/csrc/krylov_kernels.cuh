@@ -196,31 +196,10 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
 #pragma unroll
     for (int c = 0; c < NR; ++c) rr64[c] = 0.0;
 
-    // ||b||^2 per right-hand side; a zero right-hand side has the zero solution
-    {
-        double v[NR];
+    // ||b||^2 per right-hand side is taken in the first refinement pass's reduction (bb < 0 until
+    // then); a zero right-hand side has the zero solution
 #pragma unroll
-        for (int c = 0; c < NR; ++c) v[c] = 0.0;
-        for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb)
-#pragma unroll
-            for (int c = 0; c < NR; ++c) {
-                const double bi = a.b[(size_t)i * NR + c];
-                v[c] += bi * bi;
-            }
-        block_partials_lean<NR>(v, a.part + CG_P0 * nb, nb, g.bid, s_lean);
-        if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-        grid_totals<NR>(a.part + CG_P0 * nb, nb, bb, s_bc);
-        bool any_zero = false;
-#pragma unroll
-        for (int c = 0; c < NR; ++c) any_zero |= (bb[c] == 0.0);
-        if (any_zero) {
-            for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb)
-#pragma unroll
-                for (int c = 0; c < NR; ++c)
-                    if (bb[c] == 0.0) a.x[(size_t)i * NR + c] = 0.0;
-            if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-        }
-    }
+    for (int c = 0; c < NR; ++c) bb[c] = -1.0;
     const double rtol2 = a.rtol * a.rtol, itol2 = a.inner_rtol * a.inner_rtol;
     const double floor2 = 0.25 * rtol2;
     const bool poly = a.pdeg >= 2;
@@ -262,19 +241,21 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
 
     for (;;) {
         // ---- refinement pass: FP64 true residual, inner start r = (TI) r64, u = D^-1 r, d = 0
-        double t1[2 * NR];
+        double t1[3 * NR];
         {
-            double v[2 * NR];
+            double v[3 * NR];
 #pragma unroll
-            for (int k = 0; k < 2 * NR; ++k) v[k] = 0.0;
+            for (int k = 0; k < 3 * NR; ++k) v[k] = 0.0;
             spmv_block<NR, double, double>(rr, a.rp, a.ci, a.val64, a.x, a.lanes, [&](int i, double s0, double s1) {
                 const double acc[2] = {s0, s1};
                 const TI di = a.dinvI[i];
 #pragma unroll
                 for (int c = 0; c < NR; ++c) {
                     const size_t idx = (size_t)i * NR + c;
-                    const double ri = a.b[idx] - acc[c];
+                    const double bi = a.b[idx];
+                    const double ri = bi - acc[c];
                     v[c] += ri * ri;
+                    v[2 * NR + c] += bi * bi;
                     const TI rI = (TI)ri, uI = di * rI;
                     a.r[idx] = rI;
                     a.d[idx] = (TI)0;
@@ -288,9 +269,19 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
                     }
                 }
             });
-            block_partials_lean<2 * NR>(v, a.part + CG_O1 * nb, nb, g.bid, s_lean);
+            block_partials_lean<3 * NR>(v, a.part + CG_O1 * nb, nb, g.bid, s_lean);
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-            grid_totals<2 * NR>(a.part + CG_O1 * nb, nb, t1, s_bc);
+            grid_totals<3 * NR>(a.part + CG_O1 * nb, nb, t1, s_bc);
+            if (bb[0] < 0.0) {
+#pragma unroll
+                for (int c = 0; c < NR; ++c) bb[c] = t1[2 * NR + c];
+                // zero right-hand sides: x = 0 (those components stay inactive, so no other
+                // row's update reads the old values)
+                for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb)
+#pragma unroll
+                    for (int c = 0; c < NR; ++c)
+                        if (bb[c] == 0.0) a.x[(size_t)i * NR + c] = 0.0;
+            }
         }
         bool act[NR], any = false, nan = false;
         double tgt[NR], gam[NR], alpha[NR], beta[NR];

@@ -626,9 +626,21 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
         grid_arrive(a.sw, nb, epoch);
         const TP z = chebyshev(rI);
         if (!grid_wait(a.sw, nb, epoch)) return false;
-        for (unsigned int j = t; j < ncs; j += T) {
-            const unsigned int f = j / nsub, rem = j - f * nsub, b = rem / SZ_SUB, h = rem - b * SZ_SUB;
-            s_rc[j] = (TP)__ldcg(a.part + (size_t)(PS_R + SZ_NC * h + f) * nb + b);
+        constexpr int GQ = 4;   // all loads of a round in flight before the first store
+        for (unsigned int j0 = t; j0 < ncs; j0 += GQ * T) {
+            double m[GQ];
+#pragma unroll
+            for (int q = 0; q < GQ; ++q) {
+                const unsigned int j = j0 + q * T;
+                m[q] = 0.0;
+                if (j < ncs) {
+                    const unsigned int f = j / nsub, rem = j - f * nsub, b = rem / SZ_SUB, h = rem - b * SZ_SUB;
+                    m[q] = __ldcg(a.part + (size_t)(PS_R + SZ_NC * h + f) * nb + b);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < GQ; ++q)
+                if (j0 + q * T < ncs) s_rc[j0 + q * T] = (TP)m[q];
         }
         __syncthreads();
         coarse_solve();
@@ -664,7 +676,12 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
             }
         }
         __syncthreads();
-        for (int q = warp; q < 3 + 3 * SZ_NC * SZ_SUB; q += nwarps) {
+        // with 8 or more warps the three products (the longer sums) go to the last three warps
+        // and the moments to the others; fewer warps take the tasks in order
+        const bool split = nwarps >= 8;
+        const int w0 = split ? (warp >= nwarps - 3 ? warp - (nwarps - 3) : 3 + warp) : warp;
+        const int stride = split ? (warp >= nwarps - 3 ? 1 << 30 : nwarps - 3) : nwarps;
+        for (int q = w0; q < 3 + 3 * SZ_NC * SZ_SUB; q += stride) {
             double tot;
             if (q < 3) {
                 if constexpr (sizeof(TI) == sizeof(double)) {
@@ -770,20 +787,12 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
         __syncthreads();
     };
 
-    double bb;
-    {
-        double v[1] = {bi * bi}, tt[1];
-        block_partials_lean<1>(v, a.part + PS_P0 * nb, nb, blockIdx.x, s_lean);
-        if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-        grid_totals<1>(a.part + PS_P0 * nb, nb, tt, s_bc);
-        bb = tt[0];
-    }
-    if (bb == 0.0) xi = 0.0;
     const double rtol2 = a.rtol * a.rtol, itol2 = a.inner_rtol * a.inner_rtol, floor2 = 0.25 * rtol2;
     int iters = 0, outer = 0, status = CGP_OK;
-    double rr64 = 0.0;
+    double rr64 = 0.0, bb = -1.0;   // ||b||^2, taken in the first pass's reduction
     for (;;) {
-        // ---- refinement pass: publish x, FP64 true residual, u = M^-1 r
+        // ---- refinement pass: publish x, FP64 true residual and its norm (with ||b||^2), stop if
+        // converged; else u = M^-1 r, published for w = A u
         if (own) a.xp[row] = xi;
         if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
         TI r, u;
@@ -795,20 +804,26 @@ __global__ void __launch_bounds__(512) k_pcg_schwarz(SchwarzArgs<TI, TP> a) {
             r64 = own ? bi - ax : 0.0;
             r = (TI)r64;
         }
-        if (!precondition(r, u)) return record_failure(a.sw, a.st_barrier);
         {
-            // publish u in the same barrier as the FP64 residual norm
-            if (own) a.ubuf[row] = u;
-            double v[1] = {r64 * r64}, tt[1];
-            block_partials_lean<1>(v, a.part + PS_O1 * nb, nb, blockIdx.x, s_lean);
+            double v[2] = {r64 * r64, bi * bi}, tt[2];
+            block_partials_lean<2>(v, a.part + PS_O1 * nb, nb, blockIdx.x, s_lean);
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
-            grid_totals<1>(a.part + PS_O1 * nb, nb, tt, s_bc);
+            grid_totals<2>(a.part + PS_O1 * nb, nb, tt, s_bc);
             rr64 = tt[0];
+            if (bb < 0.0) bb = tt[1];
+        }
+        if (bb == 0.0) {   // zero right-hand side: the zero solution
+            xi = 0.0;
+            rr64 = 0.0;
+            break;
         }
         if (bad(rr64)) { status = CGP_ERR_NAN; break; }
-        if (bb == 0.0 || rr64 <= rtol2 * bb) break;
+        if (rr64 <= rtol2 * bb) break;
         if (outer >= a.max_outer || iters >= a.max_iter) { status = CGP_ERR_NOT_CONVERGED; break; }
         const double tgt = fmax(itol2 * rr64, floor2 * bb);
+        if (!precondition(r, u)) return record_failure(a.sw, a.st_barrier);
+        if (own) a.ubuf[row] = u;
+        if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
         TI w = own ? ell_row<TI, TI>(s_ci, s_val, T, t, wl, a.ubuf) : (TI)0;
         TI d = (TI)0, p = (TI)0, s = (TI)0;
         double alpha = 0.0, beta = 0.0, gam = 0.0;
