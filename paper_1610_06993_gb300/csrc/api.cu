@@ -60,6 +60,7 @@ int upload_elems(cgp_ctx_s* c, const HostLevel& L, const HostElems& h, DevElems&
     TRY(upload(c, &d.slot, h.slot));
     TRY(upload(c, &d.perm, h.perm));
     TRY(dalloc(c, &d.geo, 8 * (size_t)L.t));
+    TRY(dalloc(c, &d.conv, 6 * (size_t)L.t));
     return CGP_OK;
 }
 
@@ -203,6 +204,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
         if ((e = cudaMemsetAsync(c->Dc_xy, 0, 2 * nnzc * sizeof(double), s)) != cudaSuccess) break;
         if ((e = launch_geometry(c->xy_f, c->EF.tri, c->EF.t, c->EF.geo, s)) != cudaSuccess) break;
         if ((e = launch_geometry(c->xy_c, c->EC.tri, c->EC.t, c->EC.geo, s)) != cudaSuccess) break;
+        if ((e = launch_conv_scale(c->EF.geo, c->EF.t, c->prm.dt * c->prm.rho, c->EF.conv, s)) != cudaSuccess) break;
         if ((e = launch_const_assembly(c->EF, c->M, Kf, c->Gxy, s)) != cudaSuccess) break;
         if ((e = launch_const_assembly(c->EC, nullptr, c->Kc_raw, c->Dc_xy, s)) != cudaSuccess) break;
         if ((e = launch_make_A0(c, Kf, s)) != cudaSuccess) break;

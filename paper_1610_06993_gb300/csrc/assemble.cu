@@ -105,6 +105,26 @@ cudaError_t launch_geometry(const double* xy, const int* tri, int t, double* geo
     return cudaGetLastError();
 }
 
+namespace {
+// The element gradients scaled once by dt rho |T| / 12, the factor of every convection entry
+// (Eq. 16's N; A carries dt rho N), so the per-step kernels need no division and fewer FP64
+// products (this GPU issues FP64 at a small fraction of its FP32 rate).
+__global__ void k_conv_scale(const double* __restrict__ geo, int t, double dtrho, double* __restrict__ conv) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= t) return;
+    const double* g = geo + 8 * (size_t)e;
+    const double c = dtrho * (g[0] / 12.0);
+    double* o = conv + 6 * (size_t)e;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) o[k] = c * g[1 + k];
+}
+}  // namespace
+
+cudaError_t launch_conv_scale(const double* geo, int t, double dtrho, double* conv, cudaStream_t s) {
+    k_conv_scale<<<(t + 255) / 256, 256, 0, s>>>(geo, t, dtrho, conv);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_const_assembly(const DevElems& E, double* M, double* K, double* Dxy, cudaStream_t s) {
     for (int c = 0; c < E.ncol; ++c) {
         int k0 = E.colptr[c], k1 = E.colptr[c + 1];
@@ -141,7 +161,7 @@ StepAsmArgs asm_args(cgp_ctx_s* c, const double* u, SyncWords* sw) {
     a.colptr = c->EF.colptr_dev;
     a.perm = c->EF.perm;
     a.slot = c->EF.slot;
-    a.geo = c->EF.geo;
+    a.conv = c->EF.conv;
     a.tri = c->EF.tri;
     a.rp = c->F.rp;
     a.ci = c->F.ci;
@@ -173,26 +193,33 @@ StepAsmArgs asm_args(cgp_ctx_s* c, const double* u, SyncWords* sw) {
 // once, in element order, so the sum is deterministic): three plain launches, no barrier.
 namespace {
 
-// ev[9 e + 3 r + q] = dt rho (|T|/12) ((u_sum + u_r) . grad phi_q)  (Eq. 16's N, element e)
-__global__ void k_conv_elements(int t, const int* __restrict__ tri, const double* __restrict__ geo,
-                                const double* __restrict__ u, double dtrho, double* __restrict__ ev,
+// ev[9 e + 3 r + q] = dt rho (|T|/12) ((u_sum + u_r) . grad phi_q)  (Eq. 16's N, element e), from
+// the pre-scaled gradients: S_q + u_r . (c grad phi_q) with S_q = u_sum . (c grad phi_q)
+__global__ void k_conv_elements(int t, const int* __restrict__ tri, const double* __restrict__ conv,
+                                const double* __restrict__ u, double* __restrict__ ev,
                                 unsigned int* __restrict__ bound) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (bound && e == 0) *bound = 0u;   // k_rows, launched after this kernel, takes the max
     if (e >= t) return;
-    const double* g = geo + 8 * (size_t)e;
-    const double area12 = g[0] / 12.0;
+    const double* g = conv + 6 * (size_t)e;
+    double gx[3], gy[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        gx[q] = g[q];
+        gy[q] = g[3 + q];
+    }
     double ux[3], uy[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) load2(u, tri[3 * e + q], ux[q], uy[q]);
     const double sx = ux[0] + ux[1] + ux[2], sy = uy[0] + uy[1] + uy[2];
+    double S[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) S[q] = fma(sy, gy[q], sx * gx[q]);
     double* o = ev + 9 * (size_t)e;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        const double cx = area12 * (sx + ux[r]), cy = area12 * (sy + uy[r]);
+    for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) o[r * 3 + q] = dtrho * (cx * g[1 + q] + cy * g[4 + q]);
-    }
+        for (int q = 0; q < 3; ++q) o[r * 3 + q] = fma(ux[r], gx[q], fma(uy[r], gy[q], S[q]));
 }
 
 // A[k] = A0[k] + the element contributions of entry k (and its FP32 copy)
@@ -276,8 +303,7 @@ int assemble_gather_build(cgp_ctx_s* c) {
 cudaError_t launch_assemble_step(cgp_ctx_s* c, const double* u, cudaStream_t s) {
     const int t = c->EF.t, nnz = c->F.nnz, nf = c->nf;
     unsigned int* bound = c->prm.momentum_degree >= 2 ? c->mom_bound : nullptr;
-    k_conv_elements<<<(t + 255) / 256, 256, 0, s>>>(t, c->EF.tri, c->EF.geo, u, c->prm.dt * c->prm.rho, c->asm_ev,
-                                                    bound);
+    k_conv_elements<<<(t + 255) / 256, 256, 0, s>>>(t, c->EF.tri, c->EF.conv, u, c->asm_ev, bound);
     k_gather_entries<<<(nnz + 255) / 256, 256, 0, s>>>(nnz, c->asm_ip, c->asm_idx, c->asm_ev, c->A0, c->A,
                                                       c->fp32_A ? c->A32 : nullptr);
     k_rows<<<(nf + 255) / 256, 256, 0, s>>>(nf, c->F.rp, c->F.ci, c->F.diag, c->A, c->A32, c->M, u, c->vel_mask,

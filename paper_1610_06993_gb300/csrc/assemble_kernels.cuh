@@ -11,7 +11,7 @@ struct StepAsmArgs {
     const int* colptr;           // device copy of the colour offsets
     const int* perm;
     const int* slot;
-    const double* geo;
+    const double* conv;          // [t][6] gradients scaled by dt rho |T| / 12
     const int* tri;
     const int* rp;
     const int* ci;
@@ -49,19 +49,19 @@ __global__ void __launch_bounds__(1024) k_assemble_step(Launch<StepAsmArgs> L) {
         const int k0 = a.colptr[c], k1 = a.colptr[c + 1];
         for (int k = k0 + tid; k < k1; k += nthreads) {
             const int e = a.perm[k];
-            const double* g = a.geo + 8 * (size_t)e;
-            const double area12 = g[0] / 12.0;
+            const double* g = a.conv + 6 * (size_t)e;
             double ux[3], uy[3];
 #pragma unroll
             for (int q = 0; q < 3; ++q) load2(a.u, a.tri[3 * e + q], ux[q], uy[q]);
             const double sx = ux[0] + ux[1] + ux[2], sy = uy[0] + uy[1] + uy[2];
+            double S[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) S[q] = fma(sy, g[3 + q], sx * g[q]);
             const int* sl = a.slot + 9 * (size_t)e;
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                const double cx = area12 * (sx + ux[r]), cy = area12 * (sy + uy[r]);
+            for (int r = 0; r < 3; ++r)
 #pragma unroll
-                for (int q = 0; q < 3; ++q) a.A[sl[r * 3 + q]] += a.dtrho * (cx * g[1 + q] + cy * g[4 + q]);
-            }
+                for (int q = 0; q < 3; ++q) a.A[sl[r * 3 + q]] += fma(ux[r], g[q], fma(uy[r], g[3 + q], S[q]));
         }
         if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.barrier_status);
     }

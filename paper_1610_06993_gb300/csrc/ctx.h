@@ -32,6 +32,7 @@ struct DevElems {
     int* slot = nullptr;       // [t][9]
     int* perm = nullptr;       // [t]
     double* geo = nullptr;     // [t][8]: area, gx[3], gy[3], pad
+    double* conv = nullptr;    // [t][6]: c gx[3], c gy[3] with c = dt rho |T| / 12 (fine set)
 };
 
 // Launch shape of one persistent (cooperative) kernel family.
@@ -201,6 +202,7 @@ int persistent_blocks_per_sm(int threads, bool batch);
 
 // assemble.cu
 cudaError_t launch_geometry(const double* xy, const int* tri, int t, double* geo, cudaStream_t s);
+cudaError_t launch_conv_scale(const double* geo, int t, double dtrho, double* conv, cudaStream_t s);
 cudaError_t launch_const_assembly(const DevElems& E, double* M, double* K, double* Dxy, cudaStream_t s);
 cudaError_t launch_apply_pressure_bc(cgp_ctx_s* c, cudaStream_t s);
 cudaError_t launch_make_A0(cgp_ctx_s* c, const double* K, cudaStream_t s);
