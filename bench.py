@@ -155,8 +155,9 @@ def dist_env():
     return ws, rank, local
 
 
-def oracle_sample(n_steps: int):
-    """Time the CPU oracle on the same workload: setup once, then ``n_steps`` steps from rest."""
+def oracle_sample(n_steps: int, n_warmup: int = 0):
+    """Time the CPU oracle on the same workload: setup once, ``n_warmup`` untimed steps from rest,
+    then ``n_steps`` timed steps."""
     from oracle import cgp as ocgp
     coarse, prob, _ = ci.workload(WORKLOAD)
     t0 = time.perf_counter()
@@ -165,10 +166,11 @@ def oracle_sample(n_steps: int):
     mask, g = orc.dirichlet(0.0)
     u = prob.u0(orc.fine.xy, mask, g)
     times = []
-    for k in range(n_steps):
+    for k in range(n_warmup + n_steps):
         t0 = time.perf_counter()
         r = orc.step(u, (k + 1) * prob.dt)
-        times.append(time.perf_counter() - t0)
+        if k >= n_warmup:
+            times.append(time.perf_counter() - t0)
         u = r.u
     try:
         from threadpoolctl import threadpool_info
@@ -182,16 +184,19 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    times, t_setup, cores = oracle_sample(max(1, min(args.steps, 10)))
+    # about 3 s per oracle step: at most 3 warm-up and 10 timed steps keep the run near a minute
+    n_warm, n_steps = min(args.warmup, 3), max(1, min(args.steps, 10))
+    times, t_setup, cores = oracle_sample(n_steps, n_warm)
     ms = 1000.0 * statistics.mean(times)
     v = 1000.0 / ms
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": 0, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "steps": n_steps, "warmup": n_warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: backward-facing step 65,308/259,117 nodes, Re=400, dt=0.005",
-                       "levels": 1, "rtol": "direct LU"},
+            "config": {"workload": f"{WORKLOAD}: {DESCR[WORKLOAD]}, coarse 65,308 / fine 259,117 nodes, l=1, "
+                                   f"Re=400, dt=0.005", "rtol": "direct LU (the oracle)"},
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{len(times)} oracle steps from rest after a {t_setup:.1f}s setup"},
+                             "sample": f"{len(times)} oracle steps after {n_warm} untimed steps from rest and a "
+                                       f"{t_setup:.1f}s setup (requested: {args.steps} steps, {args.warmup} warm-up)"},
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
