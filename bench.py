@@ -274,7 +274,7 @@ def run_gpu(args):
         L.cgp_assemble(f.ctx, f.u, stream)
         L.cgp_momentum_solve(f.ctx, f.u, ut, stream)
         L.cgp_restrict(f.ctx, ut, bc, stream)
-        if f.params.warm_start == 1:
+        if f.params.warm_start >= 1:
             L.cgp_predict_pressure(f.ctx, f.pc, stream)
         ev[0].record(stream)
         L.cgp_poisson_solve(f.ctx, bc, f.pc, stream)
@@ -344,7 +344,7 @@ def run_gpu(args):
         cpu = {"value": 1.0 / statistics.mean(times), "unit": "steps/s", "cores": cores, "kind": "oracle",
                "sample": f"{len(times)} oracle steps of the same workload from rest (setup {t_setup:.1f}s excluded)"}
 
-    launches_per_step = 9 + f.info.levels + (4 if f.params.warm_start == 1 else 0)
+    launches_per_step = 9 + f.info.levels + (4 if f.params.warm_start >= 1 else 0)
     tname = "double" if prec == L.CGP_FP64 else "float"
     kname = {0: f"k_cg<{tname}, 1>", 1: f"k_pcg_onchip<{tname}>", 2: f"k_pcg_pipe<{tname}>",
              3: "k_pcg_schwarz<double, float>", 4: f"k_pcg_schwarz<{tname}, {tname}>"}[f.info.coarse_kernel]
@@ -359,7 +359,8 @@ def run_gpu(args):
                    "block_threads": f.info.block_threads, "grid_blocks": f.info.grid_blocks,
                    "spmv_lanes": f.info.spmv_lanes, "coarse_kernel": kname,
                    "precond_degree": args.precond_degree,
-                   "coarse_initial_guess": "2 p^n - p^(n-1)" if f.params.warm_start == 1 else "p^n"},
+                   "coarse_initial_guess": {0: "p^n", 1: "2 p^n - p^(n-1)",
+                                            2: "3 p^n - 3 p^(n-1) + p^(n-2)"}[f.params.warm_start]},
         "coarse_solves_per_s": 1000.0 / pms,
         "poisson_ms": pms, "poisson_iters": it, "poisson_outer": outer,
         "momentum_iters": statistics.mean(mom_iters), "mass_iters": statistics.mean(mass_iters),

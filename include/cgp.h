@@ -90,11 +90,14 @@ typedef struct {
     int precond_degree;
     double precond_ratio;
     int warm_start;    /* initial guesses of the solves of a step: 0 = u^n (momentum), p^n, w^n
-                          (coarse Poisson, mass); 1 (default) = u^n + (u~^n - u^(n-1)) (the last
-                          converged momentum increment, repeated) and the linear extrapolations
-                          2 v^n - v^(n-1) of p and w, history kept by the context (cgp_step, the
-                          batched step, cgp_momentum_solve, cgp_prolong_correct for w,
-                          cgp_predict_pressure for p). cgp_set_bc clears the history */
+                          (coarse Poisson, mass); 1 = u^n + (u~^n - u^(n-1)) (the last converged
+                          momentum increment, repeated) and the linear extrapolations
+                          2 v^n - v^(n-1) of p and w; 2 (default) = the same with the quadratic
+                          extrapolations 3 v^n - 3 v^(n-1) + v^(n-2) once three values exist (the
+                          second step after cgp_set_bc extrapolates linearly); history kept by the
+                          context (cgp_step, the batched step, cgp_momentum_solve,
+                          cgp_prolong_correct for w, cgp_predict_pressure for p). cgp_set_bc clears
+                          the history */
     int mass_degree;   /* preconditioner of the consistent-mass solve (Eq. 23): 1 = Jacobi, k >= 2 = the
                           degree-k Chebyshev polynomial in D^-1 M on [1/2, 2] (its spectrum for P1
                           triangles), applied in FP32 inside the CG; 0 (default) = 4, except Jacobi
@@ -138,7 +141,7 @@ typedef struct {
 
 /* Fill *p with the defaults: rho = 1, mu = 0.01, dt = 0.01, levels = 1, CGP_FP64, rtol = 1e-8,
  * inner_rtol = 1e-4, max_iter = 20000, max_outer = 30, spmv_lanes = 0, block_threads = 0,
- * coarse_solver = 0, spmv_format = 0, precond_degree = 0, precond_ratio = 0, warm_start = 1, mass_degree = 0,
+ * coarse_solver = 0, spmv_format = 0, precond_degree = 0, precond_ratio = 0, warm_start = 2, mass_degree = 0,
  * momentum_degree = 0. */
 void cgp_default_params(cgp_params* p);
 
@@ -163,11 +166,12 @@ int cgp_mesh_create(const cgp_mesh_desc* coarse, const cgp_params* prm, cgp_ctx*
 int cgp_refine(const cgp_mesh_desc* coarse, int levels, int* n_fine, int* n_tris_fine, double* xy_host,
                int* tri_host, int* sp_host, int* colour_host);
 
-/* Coarse-pressure predictor for time stepping: pc <- 2 pc - pc_prev, where pc_prev is the pc the
- * context saw at its previous call (the previous step's pressure when pc holds the latest one);
- * then pc_prev <- the incoming pc. The first call after cgp_set_bc only records pc. pc_dev:
- * [n_coarse] float64, device. Stream-ordered; cgp_step calls it when warm_start = 1. Errors:
- * CGP_ERR_ARG, CGP_ERR_STATE, CGP_ERR_CUDA. */
+/* Coarse-pressure predictor for time stepping: pc <- 2 pc - pc_prev (warm_start = 1, or the second
+ * call) or pc <- 3 pc - 3 pc_prev + pc_prev2 (warm_start = 2, from the third call on), where
+ * pc_prev, pc_prev2 are the pc the context saw at its previous calls (the previous steps'
+ * pressures when pc holds the latest one); then the history shifts by the incoming pc. The first
+ * call after cgp_set_bc only records pc. pc_dev: [n_coarse] float64, device. Stream-ordered;
+ * cgp_step calls it when warm_start >= 1. Errors: CGP_ERR_ARG, CGP_ERR_STATE, CGP_ERR_CUDA. */
 int cgp_predict_pressure(cgp_ctx ctx, double* pc_dev, void* stream);
 
 /* Sizes and launch shapes of the context. */
@@ -200,7 +204,7 @@ int cgp_assemble(cgp_ctx ctx, const double* u_dev, void* stream);
 /* Step 1, Eq. 19: solve A u~ = b (per component, Dirichlet rows replaced by identity rows) by
  * Jacobi-preconditioned BiCGStab on both components at once (CGP_MIXED: FP32 BiCGStab inside FP64
  * iterative refinement). Requires cgp_assemble() on the same u^n first. u_dev: u^n, the initial
- * guess, plus the previous converged increment when warm_start = 1; ut_dev: [n_fine][2] output
+ * guess, plus the previous converged increment when warm_start >= 1; ut_dev: [n_fine][2] output
  * u~^{n+1}. ut_dev may equal u_dev (the increment kept for the next guess is then zero). */
 int cgp_momentum_solve(cgp_ctx ctx, const double* u_dev, double* ut_dev, void* stream);
 

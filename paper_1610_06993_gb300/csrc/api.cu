@@ -81,7 +81,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     if (P.precision != CGP_FP64 && P.precision != CGP_MIXED) return CGP_ERR_ARG;
     if (P.coarse_solver < 0 || P.coarse_solver > 5) return CGP_ERR_ARG;
     if (P.precond_degree < 0 || P.precond_degree > 64 || P.precond_ratio < 0.0) return CGP_ERR_ARG;
-    if (P.warm_start < 0 || P.warm_start > 1) return CGP_ERR_ARG;
+    if (P.warm_start < 0 || P.warm_start > 2) return CGP_ERR_ARG;
     if (P.mass_degree < 0 || P.mass_degree > 16) return CGP_ERR_ARG;
     if (P.momentum_degree < 0 || P.momentum_degree > 16) return CGP_ERR_ARG;
     if (P.spmv_format < 0 || P.spmv_format > 2) return CGP_ERR_ARG;
@@ -163,6 +163,8 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     TRY(dalloc(c, &c->pc_prev, nc));
     TRY(dalloc(c, &c->pc_flag, 1));
     TRY(dalloc(c, &c->w_prev, 2 * nf));
+    TRY(dalloc(c, &c->w_prev2, 2 * nf));
+    TRY(dalloc(c, &c->pc_prev2, nc));
     TRY(dalloc(c, &c->w_flag, 1));
     TRY(dalloc(c, &c->mom_dx, 2 * nf));
     TRY(dalloc(c, &c->mom_flag, 1));
@@ -238,10 +240,12 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
 }
 
 // Mass solve of the correction (Eq. 23), M w = G p_f, from the previous step's w, or with
-// warm_start = 1 from its extrapolation 2 w^n - w^(n-1) (w is linear in the pressure).
+// warm_start = 1 / 2 from its linear / quadratic extrapolation in time (w is linear in the
+// pressure).
 cudaError_t mass_stage(cgp_ctx_s* c, cudaStream_t s) {
-    if (c->prm.warm_start == 1) {
-        cudaError_t e = launch_predict_vec(c->w, c->w, c->w_prev, c->w_flag, 2 * c->nf, s);
+    if (c->prm.warm_start >= 1) {
+        cudaError_t e = launch_predict_vec(c->w, c->w, c->w_prev, c->w_prev2, c->w_flag, 2 * c->nf,
+                                           c->prm.warm_start, s);
         if (e != cudaSuccess) return e;
     }
     return launch_mass_cg(c, c->grad, c->w, s);
@@ -270,7 +274,7 @@ void cgp_default_params(cgp_params* p) {
     p->max_outer = 30;
     p->spmv_lanes = 0;
     p->block_threads = 0;
-    p->warm_start = 1;
+    p->warm_start = 2;
     p->mass_degree = 0;
     p->momentum_degree = 0;
 }
@@ -420,7 +424,7 @@ int cgp_step(cgp_ctx c, double* u_dev, double* pc_dev, void* stream) {
     CK(launch_assemble_step(c, u_dev, s));
     CK(launch_momentum_bicgstab(c, u_dev, c->ut, s));
     CK(launch_restrict_rhs(c, c->ut, c->bc, s));
-    if (c->prm.warm_start == 1) CK(launch_predict(c, pc_dev, s));
+    if (c->prm.warm_start >= 1) CK(launch_predict(c, pc_dev, s));
     CK(launch_poisson_cg(c, c->bc, pc_dev, s));
     CK(launch_prolong(c, pc_dev, c->pf, s));
     CK(launch_gradient(c, c->pf, c->grad, s));

@@ -105,7 +105,9 @@ struct cgp_ctx_s {
     double* bc = nullptr;        // [nc] coarse right-hand side for cgp_step
     double* pc_prev = nullptr;   // [nc] pressure seen by the previous predictor call
     int* pc_flag = nullptr;      // 1 once pc_prev holds a pressure
-    double* w_prev = nullptr;    // [nf][2] previous mass-solve solution (warm_start = 1)
+    double* w_prev = nullptr;    // [nf][2] previous mass-solve solution (warm_start >= 1)
+    double* w_prev2 = nullptr;   // [nf][2] the one before (warm_start = 2)
+    double* pc_prev2 = nullptr;  // [nc] the pressure before pc_prev
     int* asm_ip = nullptr;       // [nnz_f + 1] per CSR entry: offsets into asm_idx
     int* asm_idx = nullptr;      // [9 t_f] element contributions of each entry, element order
     double* asm_ev = nullptr;    // [9 t_f] the step's element contributions
@@ -233,7 +235,8 @@ cudaError_t launch_correct(cgp_ctx_s* c, const double* ut, const double* w, doub
                            cudaStream_t s);
 cudaError_t launch_copy_pairs(const double* src, double* dst, int n, cudaStream_t s);
 cudaError_t launch_predict(cgp_ctx_s* c, double* pc, cudaStream_t s);
-cudaError_t launch_predict_vec(const double* in, double* out, double* prev, int* flag, int n, cudaStream_t s);
+cudaError_t launch_predict_vec(const double* in, double* out, double* prev, double* prev2, int* flag, int n,
+                               int order, cudaStream_t s);
 cudaError_t batch_predict_launch(cgp_batch_s* b, cudaStream_t s);
 cudaError_t batch_predict_build(cgp_batch_s* b);
 

@@ -97,7 +97,7 @@ BicgArgs<TI> momentum_args(cgp_ctx_s* c, const double* u_in, double* x, SyncWord
     a.valI = mixed ? (const TI*)(const void*)c->A32 : (const TI*)(const void*)c->A;
     a.dinvI = mixed ? (const TI*)(const void*)c->dinvA32 : (const TI*)(const void*)c->dinvA;
     a.mask = c->vel_mask; a.diag = c->F.diag; a.g = c->g; a.b = c->b_mom; a.x_in = u_in; a.x = x;
-    const bool pred = c->prm.warm_start == 1;
+    const bool pred = c->prm.warm_start >= 1;
     a.dx = pred ? c->mom_dx : nullptr;
     a.dx_flag = pred ? c->mom_flag : nullptr;
     a.pdeg = c->prm.momentum_degree;
