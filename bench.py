@@ -360,7 +360,8 @@ def run_gpu(args):
                    "spmv_lanes": f.info.spmv_lanes, "coarse_kernel": kname,
                    "precond_degree": args.precond_degree,
                    "coarse_initial_guess": {0: "p^n", 1: "2 p^n - p^(n-1)",
-                                            2: "3 p^n - 3 p^(n-1) + p^(n-2)"}[f.params.warm_start]},
+                                            2: "3 p^n - 3 p^(n-1) + p^(n-2)",
+                                            3: "4 p^n - 6 p^(n-1) + 4 p^(n-2) - p^(n-3)"}[f.params.warm_start]},
         "coarse_solves_per_s": 1000.0 / pms,
         "poisson_ms": pms, "poisson_iters": it, "poisson_outer": outer,
         "momentum_iters": statistics.mean(mom_iters), "mass_iters": statistics.mean(mass_iters),

@@ -92,9 +92,12 @@ typedef struct {
     int warm_start;    /* initial guesses of the solves of a step: 0 = u^n (momentum), p^n, w^n
                           (coarse Poisson, mass); 1 = u^n + (u~^n - u^(n-1)) (the last converged
                           momentum increment, repeated) and the linear extrapolations
-                          2 v^n - v^(n-1) of p and w; 2 (default) = the same with the quadratic
-                          extrapolations 3 v^n - 3 v^(n-1) + v^(n-2) once three values exist (the
-                          second step after cgp_set_bc extrapolates linearly); history kept by the
+                          2 v^n - v^(n-1) of p and w; 2 = the same with the quadratic
+                          extrapolations 3 v^n - 3 v^(n-1) + v^(n-2) once three values exist; 3
+                          (default) = the cubic extrapolations 4 v^n - 6 v^(n-1) + 4 v^(n-2) -
+                          v^(n-3) once four exist and the momentum guess u^n + 2 dx^n - dx^(n-1)
+                          (dx the converged increments) once two exist; lower orders until the
+                          history is long enough; history kept by the
                           context (cgp_step, the batched step, cgp_momentum_solve,
                           cgp_prolong_correct for w, cgp_predict_pressure for p). cgp_set_bc clears
                           the history */
@@ -141,7 +144,7 @@ typedef struct {
 
 /* Fill *p with the defaults: rho = 1, mu = 0.01, dt = 0.01, levels = 1, CGP_FP64, rtol = 1e-8,
  * inner_rtol = 1e-4, max_iter = 20000, max_outer = 30, spmv_lanes = 0, block_threads = 0,
- * coarse_solver = 0, spmv_format = 0, precond_degree = 0, precond_ratio = 0, warm_start = 2, mass_degree = 0,
+ * coarse_solver = 0, spmv_format = 0, precond_degree = 0, precond_ratio = 0, warm_start = 3, mass_degree = 0,
  * momentum_degree = 0. */
 void cgp_default_params(cgp_params* p);
 
@@ -167,8 +170,9 @@ int cgp_refine(const cgp_mesh_desc* coarse, int levels, int* n_fine, int* n_tris
                int* tri_host, int* sp_host, int* colour_host);
 
 /* Coarse-pressure predictor for time stepping: pc <- 2 pc - pc_prev (warm_start = 1, or the second
- * call) or pc <- 3 pc - 3 pc_prev + pc_prev2 (warm_start = 2, from the third call on), where
- * pc_prev, pc_prev2 are the pc the context saw at its previous calls (the previous steps'
+ * call), pc <- 3 pc - 3 pc_prev + pc_prev2 (warm_start = 2, or the third call) or
+ * pc <- 4 pc - 6 pc_prev + 4 pc_prev2 - pc_prev3 (warm_start = 3, from the fourth call on), where
+ * pc_prev, pc_prev2, pc_prev3 are the pc the context saw at its previous calls (the previous steps'
  * pressures when pc holds the latest one); then the history shifts by the incoming pc. The first
  * call after cgp_set_bc only records pc. pc_dev: [n_coarse] float64, device. Stream-ordered;
  * cgp_step calls it when warm_start >= 1. Errors: CGP_ERR_ARG, CGP_ERR_STATE, CGP_ERR_CUDA. */

@@ -81,7 +81,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     if (P.precision != CGP_FP64 && P.precision != CGP_MIXED) return CGP_ERR_ARG;
     if (P.coarse_solver < 0 || P.coarse_solver > 5) return CGP_ERR_ARG;
     if (P.precond_degree < 0 || P.precond_degree > 64 || P.precond_ratio < 0.0) return CGP_ERR_ARG;
-    if (P.warm_start < 0 || P.warm_start > 2) return CGP_ERR_ARG;
+    if (P.warm_start < 0 || P.warm_start > 3) return CGP_ERR_ARG;
     if (P.mass_degree < 0 || P.mass_degree > 16) return CGP_ERR_ARG;
     if (P.momentum_degree < 0 || P.momentum_degree > 16) return CGP_ERR_ARG;
     if (P.spmv_format < 0 || P.spmv_format > 2) return CGP_ERR_ARG;
@@ -164,7 +164,10 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     TRY(dalloc(c, &c->pc_flag, 1));
     TRY(dalloc(c, &c->w_prev, 2 * nf));
     TRY(dalloc(c, &c->w_prev2, 2 * nf));
+    TRY(dalloc(c, &c->w_prev3, 2 * nf));
     TRY(dalloc(c, &c->pc_prev2, nc));
+    TRY(dalloc(c, &c->pc_prev3, nc));
+    TRY(dalloc(c, &c->mom_dx2, 2 * nf));
     TRY(dalloc(c, &c->w_flag, 1));
     TRY(dalloc(c, &c->mom_dx, 2 * nf));
     TRY(dalloc(c, &c->mom_flag, 1));
@@ -244,7 +247,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
 // pressure).
 cudaError_t mass_stage(cgp_ctx_s* c, cudaStream_t s) {
     if (c->prm.warm_start >= 1) {
-        cudaError_t e = launch_predict_vec(c->w, c->w, c->w_prev, c->w_prev2, c->w_flag, 2 * c->nf,
+        cudaError_t e = launch_predict_vec(c->w, c->w, c->w_prev, c->w_prev2, c->w_prev3, c->w_flag, 2 * c->nf,
                                            c->prm.warm_start, s);
         if (e != cudaSuccess) return e;
     }
@@ -274,7 +277,7 @@ void cgp_default_params(cgp_params* p) {
     p->max_outer = 30;
     p->spmv_lanes = 0;
     p->block_threads = 0;
-    p->warm_start = 2;
+    p->warm_start = 3;
     p->mass_degree = 0;
     p->momentum_degree = 0;
 }

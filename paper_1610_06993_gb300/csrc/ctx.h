@@ -106,14 +106,17 @@ struct cgp_ctx_s {
     double* pc_prev = nullptr;   // [nc] pressure seen by the previous predictor call
     int* pc_flag = nullptr;      // 1 once pc_prev holds a pressure
     double* w_prev = nullptr;    // [nf][2] previous mass-solve solution (warm_start >= 1)
-    double* w_prev2 = nullptr;   // [nf][2] the one before (warm_start = 2)
-    double* pc_prev2 = nullptr;  // [nc] the pressure before pc_prev
+    double* w_prev2 = nullptr;   // [nf][2] the two before (warm_start >= 2, 3)
+    double* w_prev3 = nullptr;
+    double* pc_prev2 = nullptr;  // [nc] the two pressures before pc_prev
+    double* pc_prev3 = nullptr;
+    double* mom_dx2 = nullptr;   // [nf][2] the momentum increment before mom_dx (warm_start = 3)
     int* asm_ip = nullptr;       // [nnz_f + 1] per CSR entry: offsets into asm_idx
     int* asm_idx = nullptr;      // [9 t_f] element contributions of each entry, element order
     double* asm_ev = nullptr;    // [9 t_f] the step's element contributions
     int* w_flag = nullptr;
     double* mom_dx = nullptr;    // [nf][2] last momentum increment u~^n - u^(n-1) (warm_start = 1)
-    int* mom_flag = nullptr;     // 1 once mom_dx holds an increment
+    int* mom_flag = nullptr;     // number of increments recorded, 0 .. 2
     unsigned int* mom_bound = nullptr;   // Gershgorin bound of the spectrum of D^-1 A (float bits)
     bool fp32_A = false;         // the assembly writes A32 / dinvA32 (mixed, or momentum polynomial)
 
@@ -235,8 +238,8 @@ cudaError_t launch_correct(cgp_ctx_s* c, const double* ut, const double* w, doub
                            cudaStream_t s);
 cudaError_t launch_copy_pairs(const double* src, double* dst, int n, cudaStream_t s);
 cudaError_t launch_predict(cgp_ctx_s* c, double* pc, cudaStream_t s);
-cudaError_t launch_predict_vec(const double* in, double* out, double* prev, double* prev2, int* flag, int n,
-                               int order, cudaStream_t s);
+cudaError_t launch_predict_vec(const double* in, double* out, double* prev, double* prev2, double* prev3, int* flag,
+                               int n, int order, cudaStream_t s);
 cudaError_t batch_predict_launch(cgp_batch_s* b, cudaStream_t s);
 cudaError_t batch_predict_build(cgp_batch_s* b);
 

@@ -100,6 +100,7 @@ BicgArgs<TI> momentum_args(cgp_ctx_s* c, const double* u_in, double* x, SyncWord
     const bool pred = c->prm.warm_start >= 1;
     a.dx = pred ? c->mom_dx : nullptr;
     a.dx_flag = pred ? c->mom_flag : nullptr;
+    a.dx2 = c->prm.warm_start >= 3 ? c->mom_dx2 : nullptr;
     a.pdeg = c->prm.momentum_degree;
     a.r = carve<TI>(p, n2); a.rh = carve<TI>(p, n2); a.p = carve<TI>(p, n2);
     a.v = carve<TI>(p, n2); a.y = carve<TI>(p, n2); a.s = carve<TI>(p, n2);

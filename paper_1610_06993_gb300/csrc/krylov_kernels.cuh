@@ -517,7 +517,8 @@ struct BicgArgs {
     const double* x_in;           // [n][2] u^n (Dirichlet entries of the guess are replaced by g)
     double* x;                    // [n][2] solution (x == x_in gives a zero increment)
     double* dx;                   // [n][2] increment x - x_in of the last converged solve, or nullptr
-    int* dx_flag;                 // 1 once dx holds an increment
+    double* dx2 = nullptr;        // [n][2] the increment before it (second-order guess), or nullptr
+    int* dx_flag;                 // number of increments recorded, 0 .. 2
     // Chebyshev polynomial preconditioner (pdeg >= 2; else Jacobi): y = p(D^-1 A) D^-1 q for a
     // spectrum of D^-1 A inside [plmin, the float bound at *pbound], applied in FP32
     int pdeg = 0;
@@ -571,9 +572,11 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
     const int tpb = blockDim.x;
     double bb[2], rr64[2] = {0.0, 0.0};
     int iters = 0, outer = 0, status = CGP_OK;
-    // Initial guess u^n + (u~^n - u^(n-1)): the last step's increment, repeated. Every block reads
-    // the flag before the first grid barrier; block 0 rewrites it only after the last one.
-    const bool have_dx = a.dx != nullptr && *a.dx_flag != 0;
+    // Initial guess u^n + (u~^n - u^(n-1)): the last step's increment, repeated, or with dx2 its
+    // linear extrapolation u^n + 2 dx^n - dx^(n-1) once two are recorded. Every block reads the
+    // flag before the first grid barrier; block 0 rewrites it only after the last one.
+    const int n_dx = a.dx != nullptr ? *a.dx_flag : 0;
+    const bool have_dx = n_dx > 0, have_dx2 = a.dx2 != nullptr && n_dx >= 2;
     const bool poly = a.pdeg >= 2;
     float thetaP = 1.f, deltaP = 1.f;
     if (poly) {
@@ -627,6 +630,12 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
             if (have_dx) {
                 double d0, d1;
                 load2(a.dx, i, d0, d1);
+                if (have_dx2) {
+                    double e0, e1;
+                    load2(a.dx2, i, e0, e1);
+                    d0 = 2.0 * d0 - e0;
+                    d1 = 2.0 * d1 - e1;
+                }
                 x0 += d0;
                 x1 += d1;
             }
@@ -936,9 +945,14 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
                 double x0, x1, u0, u1;
                 load2(a.x, i, x0, x1);
                 load2(a.x_in, i, u0, u1);
+                if (a.dx2) {
+                    double d0, d1;
+                    load2(a.dx, i, d0, d1);
+                    store2(a.dx2, i, d0, d1);
+                }
                 store2(a.dx, i, x0 - u0, x1 - u1);
             }
-        if (g.bid == 0 && threadIdx.x == 0) *a.dx_flag = status == CGP_OK ? 1 : 0;
+        if (g.bid == 0 && threadIdx.x == 0) *a.dx_flag = status == CGP_OK ? min(n_dx + 1, 2) : 0;
     }
     if (g.bid == 0 && threadIdx.x == 0) {
         double rel = 0.0;

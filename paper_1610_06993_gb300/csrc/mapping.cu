@@ -127,46 +127,51 @@ struct PredictArgs {
     double* out;        // the prediction (may be `in`)
     double* prev;       // v^(n-1), replaced by v^n
     double* prev2;      // v^(n-2), replaced by v^(n-1)
-    int* flag;          // number of recorded values, 0 .. 2
-    int n, order;       // order 1: linear, 2: quadratic extrapolation
+    double* prev3;      // v^(n-3), replaced by v^(n-2)
+    int* flag;          // number of recorded values, 0 .. 3
+    int n, order;       // order 1: linear, 2: quadratic, 3: cubic extrapolation
 };
 
-// Extrapolation in time of a solver's initial guess from the values the previous calls recorded:
-// out <- 3 v^n - 3 v^(n-1) + v^(n-2) (order 2, two values recorded), 2 v^n - v^(n-1) (one value
-// recorded, or order 1), v^n (none); then prev2 <- prev, prev <- v^n. blockIdx.y selects the
-// vector of a batch. The flag is only read here; k_predict_flag, launched after this kernel,
-// counts it up.
+// Extrapolation in time of a solver's initial guess from the values the previous calls recorded,
+// the polynomial through the last min(order, recorded) + 1 values taken one step on:
+// 4 v^n - 6 v^(n-1) + 4 v^(n-2) - v^(n-3), 3 v^n - 3 v^(n-1) + v^(n-2), 2 v^n - v^(n-1) or v^n;
+// then the history shifts by v^n. blockIdx.y selects the vector of a batch. The flag is only read
+// here; k_predict_flag, launched after this kernel, counts it up.
 __global__ void k_predict(const PredictArgs* __restrict__ tab, PredictArgs single) {
     const PredictArgs a = tab ? tab[blockIdx.y] : single;
     const int have = *a.flag;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    const double vn = a.in[i], v1 = a.prev[i];
+    const int k = min(have, a.order);
+    const double vn = a.in[i], v1 = a.prev[i], v2 = a.prev2[i];
     double o = vn;
-    if (have >= 2 && a.order >= 2) o = fma(3.0, vn - v1, a.prev2[i]);
-    else if (have >= 1) o = 2.0 * vn - v1;
+    if (k >= 3) o = 4.0 * (vn + v2) - 6.0 * v1 - a.prev3[i];
+    else if (k == 2) o = fma(3.0, vn - v1, v2);
+    else if (k == 1) o = 2.0 * vn - v1;
     a.out[i] = o;
+    a.prev3[i] = v2;
     a.prev2[i] = v1;
     a.prev[i] = vn;
 }
 
 __global__ void k_predict_flag(const PredictArgs* __restrict__ tab, PredictArgs single) {
     const PredictArgs a = tab ? tab[blockIdx.x] : single;
-    if (threadIdx.x == 0) *a.flag = min(*a.flag + 1, 2);
+    if (threadIdx.x == 0) *a.flag = min(*a.flag + 1, 3);
 }
 
 }  // namespace
 
-cudaError_t launch_predict_vec(const double* in, double* out, double* prev, double* prev2, int* flag, int n,
-                               int order, cudaStream_t s) {
-    const PredictArgs a{in, out, prev, prev2, flag, n, order};
+cudaError_t launch_predict_vec(const double* in, double* out, double* prev, double* prev2, double* prev3, int* flag,
+                               int n, int order, cudaStream_t s) {
+    const PredictArgs a{in, out, prev, prev2, prev3, flag, n, order};
     k_predict<<<dim3((n + 255) / 256, 1), 256, 0, s>>>(nullptr, a);
     k_predict_flag<<<1, 32, 0, s>>>(nullptr, a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_predict(cgp_ctx_s* c, double* pc, cudaStream_t s) {
-    return launch_predict_vec(pc, pc, c->pc_prev, c->pc_prev2, c->pc_flag, c->nc, std::max(1, c->prm.warm_start), s);
+    return launch_predict_vec(pc, pc, c->pc_prev, c->pc_prev2, c->pc_prev3, c->pc_flag, c->nc,
+                              std::max(1, c->prm.warm_start), s);
 }
 
 // Batched predictors of every instance with warm_start >= 1 (coarse pressure and mass-solve initial
@@ -180,8 +185,8 @@ cudaError_t batch_predict_build(cgp_batch_s* b) {
         cgp_ctx_s* c = b->ctx[i];
         if (c->prm.warm_start < 1) continue;
         const int n2 = 2 * c->nf, order = c->prm.warm_start;
-        tab.push_back(PredictArgs{b->pc[i], b->pc[i], c->pc_prev, c->pc_prev2, c->pc_flag, c->nc, order});
-        tab.push_back(PredictArgs{c->w, c->w, c->w_prev, c->w_prev2, c->w_flag, n2, order});
+        tab.push_back(PredictArgs{b->pc[i], b->pc[i], c->pc_prev, c->pc_prev2, c->pc_prev3, c->pc_flag, c->nc, order});
+        tab.push_back(PredictArgs{c->w, c->w, c->w_prev, c->w_prev2, c->w_prev3, c->w_flag, n2, order});
         nmax = std::max({nmax, c->nc, n2});
     }
     if (tab.empty()) return cudaSuccess;

@@ -325,7 +325,8 @@ def test_schwarz_cuts_iterations(L, bfs_full, precision):
 def test_pressure_predictor(L, cavity_state):
     """warm_start = 1 starts the coarse Poisson and mass solves of cgp_step from the linear
     extrapolations 2 v^n - v^(n-1) (warm_start = 2: 3 v^n - 3 v^(n-1) + v^(n-2) once three
-    values exist) instead of v^n, and the momentum solve from u^n plus the last
+    values exist; warm_start = 3: the cubic extrapolation, and the momentum increment extrapolated
+    linearly) instead of v^n, and the momentum solve from u^n plus the last
     converged increment u~^n - u^(n-1) instead of u^n. The initial guess does not change what a
     solve converges to, so 30 cavity steps still match the oracle at the parity bar (1e-10 relative
     L2 in u), while from step 3 on (two previous values exist, the start-up transient has passed)
@@ -334,7 +335,7 @@ def test_pressure_predictor(L, cavity_state):
     coarse, prob, _, _ = cavity_state
     steps, its, mom = 30, {}, {}
     ref = ocgp.run(coarse, prob, steps).u
-    for ws in (0, 1, 2):
+    for ws in (0, 1, 2, 3):
         f = flow(coarse, prob, rtol=1e-13, warm_start=ws)
         tot = tm = 0
         for k in range(steps):
@@ -347,7 +348,7 @@ def test_pressure_predictor(L, cavity_state):
         u = f.u.cpu().numpy()
         f.close()
         assert rel(u, ref) < 1e-10, (ws, rel(u, ref))
-    assert its[1] < its[0] and its[2] < its[0], its
+    assert its[1] < its[0] and its[2] < its[0] and its[3] < its[0], its
     assert mom[1] < mom[0], mom
 
 
