@@ -43,6 +43,41 @@ def test_binding_declares_every_entry_point(L):
     assert not missing, missing
 
 
+def _header_structs():
+    """Field lists (C type, name) of the header's typedef structs, comments removed."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "cgp.h")).read(), flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct \{(.*?)\}\s*(\w+);", text, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            m = re.match(r"((?:const )?\w+\s*\**)\s*(.*)", decl)
+            ctype = m.group(1).replace(" ", "")
+            for nm in m.group(2).split(","):
+                nm = nm.strip()
+                stars = len(nm) - len(nm.lstrip("*"))
+                fields.append((ctype + "*" * stars, nm.lstrip("*")))
+        out[name] = fields
+    return out
+
+
+def test_binding_structs_match_header(L):
+    """The ctypes mirrors of the header's structs list the same fields, in the same order, with the
+    same C types: a field added to one side only would shift every later field across the ABI."""
+    import ctypes as C
+    ctype_of = {"double": C.c_double, "int": C.c_int, "constdouble*": C.POINTER(C.c_double),
+                "constint*": C.POINTER(C.c_int)}
+    structs = _header_structs()
+    for name in ("cgp_params", "cgp_mesh_desc", "cgp_info", "cgp_stats"):
+        hdr = structs[name]
+        py = getattr(L, name)._fields_
+        assert [n for _, n in hdr] == [n for n, _ in py], name
+        for (ct, n), (_, pt) in zip(hdr, py):
+            assert ctype_of[ct] == pt, (name, n, ct, pt)
+
+
 @pytest.mark.parametrize("mesh", [ci.cavity_mesh(9, 3), ci.bfs_mesh(2, 4)], ids=["cavity", "bfs"])
 @pytest.mark.parametrize("levels", [0, 1, 2])
 def test_native_refinement_matches_oracle(L, mesh, levels):
