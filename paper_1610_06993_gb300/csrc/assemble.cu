@@ -178,7 +178,6 @@ StepAsmArgs asm_args(cgp_ctx_s* c, const double* u, SyncWords* sw) {
     a.b = c->b_mom;
     a.bound = c->prm.momentum_degree >= 2 ? c->mom_bound : nullptr;
     a.rho = c->prm.rho;
-    a.dtrho = c->prm.dt * c->prm.rho;
     a.sw = sw;
     a.barrier_status = &c->stats->barrier_status;
     return a;

@@ -27,7 +27,7 @@ struct StepAsmArgs {
     float* dinv32;
     double* b;                   // [nf][2]
     unsigned int* bound;         // Gershgorin bound of D^-1 A (float bits, atomic max), or nullptr
-    double rho, dtrho;
+    double rho;
     SyncWords* sw;
     int* barrier_status;
 };

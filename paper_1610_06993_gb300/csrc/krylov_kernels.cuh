@@ -161,7 +161,7 @@ struct CgArgs {
 };
 
 // partial-sum regions (units of nblocks doubles)
-enum { CG_P0 = 0, CG_O1 = 2, CG_I0 = 8, CG_I1 = 10 /* 3 NR */ };
+enum { CG_O1 = 2 /* 3 NR: residual norms, (r, u), ||b||^2 */, CG_I1 = 10 /* 3 NR */ };
 
 // Dynamic shared memory of k_cg: the lean FP64 reduction buffer, 3 NR doubles per thread.
 template <int NR>
