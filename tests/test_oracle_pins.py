@@ -76,6 +76,45 @@ def test_jacobi_scaled_mass_spectrum(mesh):
     np.testing.assert_allclose(np.sort(np.linalg.eigvals(de @ me).real), [0.5, 0.5, 2.0], rtol=0, atol=1e-14)
 
 
+def _kovasznay(xy, re):
+    """Kovasznay's closed-form steady Navier-Stokes flow (rho = 1, mu = 1/Re): u = 1 - e^(lx)
+    cos(2 pi y), v = l/(2 pi) e^(lx) sin(2 pi y), p = (1 - e^(2lx))/2, l = Re/2 - sqrt(Re^2/4 + 4 pi^2)."""
+    lam = re / 2 - math.sqrt(re * re / 4 + 4 * math.pi ** 2)
+    x, y = xy[:, 0], xy[:, 1]
+    e = np.exp(lam * x)
+    u = np.stack([1 - e * np.cos(2 * np.pi * y), lam / (2 * np.pi) * e * np.sin(2 * np.pi * y)], axis=1)
+    return u, 0.5 * (1 - np.exp(2 * lam * x))
+
+
+def test_kovasznay_steady_residual_converges():
+    """The nodal interpolants of Kovasznay's exact steady flow (Re = 40 on [-1/2, 1] x [-1/2, 3/2],
+    jittered meshes, h = 1/8, 1/16, 1/32) nearly satisfy the discrete steady momentum equations
+    N(u) u + mu K u + G p = 0 at interior nodes (the convection, stiffness and gradient matrices of
+    Eqs. 16-18 and 23): the residual in the discrete H^-1 norm (R^T K_0^-1 R, K_0 the interior
+    stiffness) falls at better than first order, and the weak divergence D u at first order. A
+    wrong sign or factor in N, a missing viscous term or swapped gradient components leave an O(1)
+    residual that does not fall."""
+    import scipy.sparse.linalg as spla
+    re = 40.0
+    res, div = [], []
+    for k in (4, 8, 16):
+        m = ci.jittered_grid(-0.5, 1.0, -0.5, 1.5, 3 * k, 4 * k, 50 + k)
+        ops = fem.P1Operators(m.xy, m.tri)
+        onb = refine.boundary_nodes(m.tri.astype(np.int64), m.n_nodes)
+        u, p = _kovasznay(ops.xy, re)
+        R = ops.convection(u) @ u + (1.0 / re) * (ops.K @ u) + np.stack([ops.Dx @ p, ops.Dy @ p], axis=1)
+        inner = ~onb
+        z = spla.spsolve(ops.K[inner][:, inner].tocsc(), R[inner])
+        res.append(math.sqrt(float(np.sum(R[inner] * z))))
+        d = ops.Dx @ u[:, 0] + ops.Dy @ u[:, 1]
+        lumped = np.asarray(ops.M.sum(axis=1)).ravel()
+        div.append(math.sqrt(float(np.sum(d * d / lumped))))
+    rate_res = [math.log2(res[i] / res[i + 1]) for i in range(2)]
+    rate_div = [math.log2(div[i] / div[i + 1]) for i in range(2)]
+    assert min(rate_res) > 1.3 and res[-1] < 1e-2, (res, rate_res)
+    assert min(rate_div) > 0.8, (div, rate_div)
+
+
 def test_stiffness_annihilates_linear_fields(jmesh):
     ops, onb = jmesh
     x, y = ops.xy[:, 0], ops.xy[:, 1]
