@@ -401,6 +401,16 @@ def test_taylor_green_first_order_in_time():
     assert ((rates > 0.75) & (rates < 1.25)).all(), (e, rates)
 
 
+@pytest.mark.parametrize("levels", [0, 1])
+def test_taylor_green_second_order_in_space(levels):
+    """Taylor-Green velocity (Eqs. 34-35) over 10 steps of dt = 1e-4, where the first-order
+    splitting error is small: the nodal velocity error falls at second order in h, the P1 rate, for
+    the standard scheme (l = 0) and for CGP (l = 1), on 9-, 17- and 33-node coarse grids."""
+    es = [_tg_error(ci.cavity_mesh(n, 43), 1e-4, 1e-3, levels)[0] for n in (9, 17, 33)]
+    rates = np.log2(np.array(es[:-1]) / np.array(es[1:]))
+    assert ((rates > 1.7) & (rates < 2.5)).all(), (es, rates)
+
+
 def test_taylor_green_cgp_close_to_standard():
     """One level of CGP on a 65x65-node fine mesh stays within 15 % of the standard scheme's
     velocity error (Table 1: the l = 1 velocity error grows only mildly over l = 0)."""
