@@ -206,8 +206,9 @@ int cgp_set_dirichlet_values(cgp_ctx ctx, const double* g_dev, void* stream);
 int cgp_assemble(cgp_ctx ctx, const double* u_dev, void* stream);
 
 /* Step 1, Eq. 19: solve A u~ = b (per component, Dirichlet rows replaced by identity rows) by
- * Jacobi-preconditioned BiCGStab on both components at once (CGP_MIXED: FP32 BiCGStab inside FP64
- * iterative refinement). Requires cgp_assemble() on the same u^n first. u_dev: u^n, the initial
+ * BiCGStab on both components at once, preconditioned by Jacobi or by the FP32 Chebyshev
+ * polynomial of cgp_params.momentum_degree (CGP_MIXED: FP32 BiCGStab inside FP64 iterative
+ * refinement). Requires cgp_assemble() on the same u^n first. u_dev: u^n, the initial
  * guess, plus the previous converged increment when warm_start >= 1; ut_dev: [n_fine][2] output
  * u~^{n+1}. ut_dev may equal u_dev (the increment kept for the next guess is then zero). */
 int cgp_momentum_solve(cgp_ctx ctx, const double* u_dev, double* ut_dev, void* stream);
@@ -218,14 +219,17 @@ int cgp_momentum_solve(cgp_ctx ctx, const double* u_dev, double* ut_dev, void* s
 int cgp_restrict(cgp_ctx ctx, const double* ut_dev, double* bc_dev, void* stream);
 
 /* Step 3, Eq. 21: solve K_c p_c = b_c (K_c = coarse stiffness, +(-Laplacian), after symmetric
- * elimination of masked nodes) by Jacobi-preconditioned conjugate gradients in a single
- * persistent kernel (CGP_MIXED: FP32 CG inside FP64 iterative refinement). pc_dev [n_coarse] is
+ * elimination of masked nodes) by conjugate gradients in a single persistent kernel, preconditioned
+ * as cgp_params.coarse_solver selects (default: two-level additive Schwarz; 5: Jacobi) (CGP_MIXED:
+ * FP32 CG inside FP64 iterative refinement). pc_dev [n_coarse] is
  * the initial guess on entry (warm start) and the solution on exit. bc_dev [n_coarse], or NULL
  * for the context's own right-hand side of its latest cgp_step. */
 int cgp_poisson_solve(cgp_ctx ctx, const double* bc_dev, double* pc_dev, void* stream);
 
 /* Steps 4-5, Eqs. 22-23 with Eq. 29: p_f = P p_c level by level, g = G p_f (G_ij = int phi_i
- * d psi_j), w = M^{-1} g by FP64 Jacobi-CG on the consistent mass matrix, then
+ * d psi_j), w = M^{-1} g by CG on the consistent mass matrix (FP64, or FP32 inside FP64 refinement
+ * with CGP_MIXED), preconditioned by Jacobi or the FP32 Chebyshev polynomial of
+ * cgp_params.mass_degree, then
  * u = u~ - (dt/rho) w and Dirichlet nodes reset to their prescribed values.
  * pc_dev [n_coarse], ut_dev [n_fine][2] inputs; u_dev [n_fine][2] output (may equal ut_dev);
  * pf_dev [n_fine] and gp_dev [n_fine][2] optional outputs (NULL to skip): p_f and w. */
