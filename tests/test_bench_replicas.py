@@ -56,3 +56,34 @@ def test_single_rank_is_identity():
     import bench
     assert bench.job_time_ms(12.5, 1, "cpu") == 12.5
     assert bench.job_rate(1.0, 4.0, 1) == pytest.approx(250.0)
+
+
+def _run_bench(args, env_extra):
+    import json
+    import subprocess
+    env = dict(os.environ)
+    env.update(env_extra)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    return r.returncode, [json.loads(l) for l in lines]
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` times the CPU oracle on the headline workload (no GPU) and prints
+    one JSON line with the contract's keys, its own sample sizes and a zero-copy e2e entry."""
+    code, lines = _run_bench(["--impl", "reference", "--steps", "1", "--warmup", "1"],
+                             {"RANK": "0", "WORLD_SIZE": "1", "LOCAL_RANK": "0"})
+    assert code == 0 and len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["unit"] == "steps/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["ms_per_step"] == pytest.approx(1000.0 / d["value"])
+    assert d["steps"] == 1 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["config"]["workload"].startswith("bfs33: backward-facing step, coarse 65,308 / fine 259,117 nodes")
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    code, lines = _run_bench(["--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1"],
+                             {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert code == 0 and lines == []
