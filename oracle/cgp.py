@@ -15,6 +15,19 @@ One time step follows the paper's five steps, Eqs. 19-23, with the density carri
    to their boundary values (Eq. 3).
 
 f = 0 in every workload here. All systems are solved by sparse LU.
+
+Options beyond the paper's scheme (the paper's Sect. 4 and its comparison of restriction forms
+leave these open; each is defined here in plain terms and checked by the pins in ``tests/``):
+
+* ``restrict_mode = "galerkin"``: the coarse right-hand side restricts the fine divergence instead
+  of injecting the velocity, b_c = -(rho/dt) P^T (Dx_f u~_x + Dy_f u~_y), i.e. the coarse test
+  functions integrated against the divergence of the fine intermediate velocity;
+* ``projection = "incremental"``: the momentum right-hand side carries the previous pressure,
+  rho M u^n - dt G_f P p_c^n, the coarse Poisson solve gives the increment phi (same matrix and
+  right-hand side as Eq. 21), the correction applies phi, and p_c^{n+1} = p_c^n + phi;
+* ``projection = "rotational"``: as incremental, with p_c^{n+1} = p_c^n + phi - mu chi, where
+  chi = M_L^-1 D_c u~_c is the divergence of the injected intermediate velocity divided by the
+  lumped coarse mass (chi = 0 where the pressure is held).
 """
 from __future__ import annotations
 
@@ -52,7 +65,13 @@ class StepResult:
 class CGPOracle:
     """The CGP method on one coarse mesh refined ``levels`` times (``levels = 0``: standard scheme)."""
 
-    def __init__(self, coarse_xy, coarse_tri, rho, mu, dt, levels, vel_bc, p_bc):
+    def __init__(self, coarse_xy, coarse_tri, rho, mu, dt, levels, vel_bc, p_bc, restrict_mode="injection",
+                 projection="standard"):
+        if restrict_mode not in ("injection", "galerkin"):
+            raise ValueError(restrict_mode)
+        if projection not in ("standard", "incremental", "rotational"):
+            raise ValueError(projection)
+        self.restrict_mode, self.projection = restrict_mode, projection
         self.rho, self.mu, self.dt = float(rho), float(mu), float(dt)
         self.h = refine.build_hierarchy(coarse_xy, coarse_tri, levels)
         fine, coarse = self.h.fine, self.h.coarse
@@ -79,11 +98,19 @@ class CGPOracle:
         return np.asarray(mask, dtype=np.uint8), np.asarray(g, dtype=np.float64)
 
     # --- the five steps ------------------------------------------------------------------
-    def momentum(self, u_n: np.ndarray, t_next: float) -> np.ndarray:
-        """Step 1, Eq. 19: the intermediate velocity u~^{n+1}."""
+    def pressure_gradient(self, p_c: np.ndarray) -> np.ndarray:
+        """G_f P p_c: the fine gradient (G = D on V_f) of the prolonged coarse pressure, [N_f, 2]."""
+        p_f = refine.prolong(self.h, p_c)
+        return np.stack([self.fine.Dx @ p_f, self.fine.Dy @ p_f], axis=1)
+
+    def momentum(self, u_n: np.ndarray, t_next: float, p_c_n: np.ndarray | None = None) -> np.ndarray:
+        """Step 1, Eq. 19: the intermediate velocity u~^{n+1}. With ``p_c_n`` (incremental forms)
+        the right-hand side also carries -dt G_f P p_c^n."""
         mask, g = self.dirichlet(t_next)
         A = self.A0 + (self.dt * self.rho) * self.fine.convection(u_n)
         rhs = self.rho * (self.fine.M @ u_n)
+        if p_c_n is not None:
+            rhs = rhs - self.dt * self.pressure_gradient(p_c_n)
         ut = np.empty_like(u_n)
         for c in range(2):
             d = (mask & (1 << c)) != 0
@@ -92,11 +119,28 @@ class CGPOracle:
         return ut
 
     def restrict_rhs(self, ut: np.ndarray) -> np.ndarray:
-        """Steps 2-3 right-hand side: Eq. 20 then -(rho/dt) D_c u~_c with pressure BC rows zeroed."""
-        uc = refine.restrict(self.h, ut)
-        b = -(self.rho / self.dt) * (self.coarse.Dx @ uc[:, 0] + self.coarse.Dy @ uc[:, 1])
+        """Steps 2-3 right-hand side: Eq. 20 then -(rho/dt) D_c u~_c with pressure BC rows zeroed;
+        with restrict_mode "galerkin", -(rho/dt) P^T D_f u~_f instead."""
+        if self.restrict_mode == "galerkin":
+            div_f = self.fine.Dx @ ut[:, 0] + self.fine.Dy @ ut[:, 1]
+            b = -(self.rho / self.dt) * refine.restrict_transpose(self.h, div_f)
+        else:
+            uc = refine.restrict(self.h, ut)
+            b = -(self.rho / self.dt) * (self.coarse.Dx @ uc[:, 0] + self.coarse.Dy @ uc[:, 1])
         b[self.p_mask] = 0.0
         return b
+
+    def pressure_update(self, p_c_n: np.ndarray, phi: np.ndarray, ut: np.ndarray) -> np.ndarray:
+        """Incremental forms: p^{n+1} = p^n + phi, and for the rotational form also - mu chi with
+        chi = (D_c u~_c) / (lumped coarse mass), zero where the pressure is held."""
+        p = p_c_n + phi
+        if self.projection == "rotational":
+            uc = refine.restrict(self.h, ut)
+            d = self.coarse.Dx @ uc[:, 0] + self.coarse.Dy @ uc[:, 1]
+            chi = d / np.asarray(self.coarse.M.sum(axis=1)).ravel()
+            chi[self.p_mask] = 0.0
+            p = p - self.mu * chi
+        return p
 
     def poisson(self, b_c: np.ndarray) -> np.ndarray:
         """Step 3, Eq. 21 (exact solve)."""
@@ -114,30 +158,42 @@ class CGPOracle:
             u[d, c] = gd[d, c]
         return u, p_f, w
 
-    def step(self, u_n: np.ndarray, t_next: float) -> StepResult:
-        ut = self.momentum(u_n, t_next)
+    def step(self, u_n: np.ndarray, t_next: float, p_c_n: np.ndarray | None = None) -> StepResult:
+        """One step. The incremental forms need the previous coarse pressure ``p_c_n`` (zero if
+        omitted); StepResult.p_c is then the new pressure and p_f, gp belong to the increment."""
+        if self.projection == "standard":
+            ut = self.momentum(u_n, t_next)
+            b_c = self.restrict_rhs(ut)
+            p_c = self.poisson(b_c)
+            u, p_f, gp = self.prolong_correct(p_c, ut, t_next)
+            return StepResult(u, ut, b_c, p_c, p_f, gp)
+        p_n = np.zeros(self.n_coarse) if p_c_n is None else np.asarray(p_c_n, dtype=np.float64)
+        ut = self.momentum(u_n, t_next, p_n)
         b_c = self.restrict_rhs(ut)
-        p_c = self.poisson(b_c)
-        u, p_f, gp = self.prolong_correct(p_c, ut, t_next)
-        return StepResult(u, ut, b_c, p_c, p_f, gp)
+        phi = self.poisson(b_c)
+        u, p_f, gp = self.prolong_correct(phi, ut, t_next)
+        return StepResult(u, ut, b_c, self.pressure_update(p_n, phi, ut), p_f, gp)
 
 
 def run(coarse, problem, n_steps: int, levels: int | None = None, u0=None, t0: float = 0.0,
-        return_oracle: bool = False):
+        return_oracle: bool = False, restrict_mode: str = "injection", projection: str = "standard",
+        p0=None):
     """Advance ``problem`` on the coarse mesh ``coarse`` (a ``cgp_inputs.CoarseMesh``) by ``n_steps``.
 
-    Returns the last :class:`StepResult` (and the :class:`CGPOracle` if asked).
+    Returns the last :class:`StepResult` (and the :class:`CGPOracle` if asked). The incremental
+    forms start from the coarse pressure ``p0`` (zero if omitted).
     """
     lv = problem.levels if levels is None else levels
     orc = CGPOracle(coarse.xy, coarse.tri, problem.rho, problem.mu, problem.dt, lv,
-                    problem.vel_bc, problem.p_bc)
+                    problem.vel_bc, problem.p_bc, restrict_mode=restrict_mode, projection=projection)
     if u0 is None:
         mask, g = orc.dirichlet(t0)
         u = problem.u0(orc.fine.xy, mask, g)
     else:
         u = np.array(u0, dtype=np.float64)
+    p = None if p0 is None else np.array(p0, dtype=np.float64)
     res = None
     for n in range(n_steps):
-        res = orc.step(u, t0 + (n + 1) * problem.dt)
-        u = res.u
+        res = orc.step(u, t0 + (n + 1) * problem.dt, p)
+        u, p = res.u, res.p_c
     return (res, orc) if return_oracle else res

@@ -8,6 +8,9 @@ into four, and Remark 2.2 replaces the prolongation and restriction matrices by 
 * s^u (Eq. 30): for each node eta of the coarser mesh the index xi of the same point on the finer
   mesh, with U_c(eta) = U_f(xi).
 
+Besides the injection R of Eq. 30 this module gives the transpose P^T of the prolongation, which
+the Galerkin reading of the restriction uses (b_c = P^T applied to a fine-mesh load vector).
+
 Numbering convention (shared with the CUDA library by specification, not by code): the parent
 nodes keep their indices 0..N_k-1; every edge gets one midpoint, appended in order of first visit
 (triangles in order, local edges (a,b), (b,c), (c,a)); triangle (a,b,c) becomes the four children
@@ -127,3 +130,22 @@ def prolong(h: Hierarchy, p_c: np.ndarray) -> np.ndarray:
 def restrict(h: Hierarchy, u_f: np.ndarray) -> np.ndarray:
     """Injection R (Eq. 20 through the table of Eq. 30)."""
     return np.asarray(u_f)[h.su]
+
+
+def restrict_transpose(h: Hierarchy, r_f: np.ndarray) -> np.ndarray:
+    """P^T applied level by level, from the fine mesh down to the coarse mesh.
+
+    Row alpha of P_k^{k+1} (Eq. 29) holds the weight 1/2 at columns beta_alpha and gamma_alpha
+    (a single weight 1 when beta = gamma = alpha), so P^T r gives every coarser node beta half of
+    r[alpha] for each finer node alpha whose pair contains beta, plus r[beta] itself from its
+    parent-coincident row. For a fine-mesh load vector r_i = int phi_i f, (P^T r)_j = int psi_j f
+    with psi_j the coarse shape function, since psi_j = sum_i P_ij phi_i on nested meshes.
+    """
+    r = np.asarray(r_f, dtype=np.float64)
+    for k in range(len(h.sp) - 1, -1, -1):
+        sp = h.sp[k]
+        out = np.zeros(h.levels[k].xy.shape[0])
+        np.add.at(out, sp[:, 0], 0.5 * r)
+        np.add.at(out, sp[:, 1], 0.5 * r)
+        r = out
+    return r

@@ -1,0 +1,205 @@
+"""Pins of the oracle's options beyond the paper's scheme (CPU, no GPU).
+
+Galerkin restriction: b_c = -(rho/dt) P^T D_f u~_f, the coarse test functions integrated against
+the divergence of the fine intermediate velocity (the paper restricts by injecting u~ and applying
+the coarse D, Eqs. 20-21 with Eq. 30). Pinned by quadrature with brute-force point location, by
+its agreement with injection on velocity fields of the coarse space (P^T D_f P = D_c on nested P1
+spaces), and by its Taylor-Green accuracy next to injection (Eqs. 34-36).
+
+Incremental and rotational pressure correction (the paper's Sect. 4 names them as the way to
+remove the damping of its non-incremental scheme near walls): the momentum right-hand side carries
+-dt G_f P p_c^n, the coarse Poisson solve gives the increment, and p_c^{n+1} = p_c^n + phi (minus
+mu chi in the rotational form). Pinned by a dense brute-force recomputation, by the first step from
+a zero pressure equalling the standard step, and by Taylor-Green: with the Galerkin restriction the
+incremental CGP step is stable as dt -> 0 and its velocity error is several times below the
+non-incremental scheme's; with injection it is not stable (the recorded reading for the option).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import cgp_inputs as ci
+from oracle import cgp, refine
+from test_oracle_pins import _dense_ops, _interp_matrix, _shape_coeffs
+
+
+def _coarse_test_quadrature(coarse_xy, coarse_tri, fine_xy, fine_tri, u):
+    """int psi_i div(u_f) by brute force: on every fine triangle div(u_f) is constant and the coarse
+    shape function psi_i is linear (the fine triangle lies inside one coarse triangle), so the
+    integral is |T| psi_i(centroid) div; the coarse triangle is found by point location."""
+    b = np.zeros(coarse_xy.shape[0])
+    coeffs = [_shape_coeffs(coarse_xy[t])[0] for t in coarse_tri]
+    for t in fine_tri:
+        C, area = _shape_coeffs(fine_xy[t])
+        div = C[1, :] @ u[t, 0] + C[2, :] @ u[t, 1]
+        c = fine_xy[t].mean(axis=0)
+        for tc, Cc in zip(coarse_tri, coeffs):
+            lam = np.array([1.0, c[0], c[1]]) @ Cc
+            if lam.min() > -1e-12:
+                b[tc] += area * lam * div
+                break
+        else:
+            raise AssertionError("centroid outside the coarse mesh")
+    return b
+
+
+@pytest.mark.parametrize("case,levels", [("cavity", 1), ("cavity", 2), ("bfs", 1)])
+def test_galerkin_restriction_equals_quadrature(case, levels):
+    if case == "cavity":
+        coarse, prob = ci.cavity_mesh(5, 51), ci.cavity_problem(100.0, 0.01, levels)
+    else:
+        coarse, prob = ci.bfs_mesh(2, 52), ci.bfs_problem(400.0, 0.005, levels)
+    orc = cgp.CGPOracle(coarse.xy, coarse.tri, prob.rho, prob.mu, prob.dt, levels, prob.vel_bc, prob.p_bc,
+                        restrict_mode="galerkin")
+    ut = np.random.default_rng(5).standard_normal((orc.n_fine, 2))
+    ref = -(prob.rho / prob.dt) * _coarse_test_quadrature(coarse.xy, coarse.tri.astype(np.int64), orc.fine.xy,
+                                                          orc.fine.tri, ut)
+    ref[orc.p_mask] = 0.0
+    got = orc.restrict_rhs(ut)
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_galerkin_equals_injection_on_coarse_fields(levels):
+    """For u~_f = P u~_c (a velocity of the coarse space) both restrictions give the same b_c."""
+    coarse, prob = ci.bfs_mesh(3, 53), ci.bfs_problem(400.0, 0.005, levels)
+    og = cgp.CGPOracle(coarse.xy, coarse.tri, prob.rho, prob.mu, prob.dt, levels, prob.vel_bc, prob.p_bc,
+                       restrict_mode="galerkin")
+    oi = cgp.CGPOracle(coarse.xy, coarse.tri, prob.rho, prob.mu, prob.dt, levels, prob.vel_bc, prob.p_bc)
+    uc = np.random.default_rng(6).standard_normal((og.n_coarse, 2))
+    uf = np.stack([refine.prolong(og.h, uc[:, 0]), refine.prolong(og.h, uc[:, 1])], axis=1)
+    a, b = og.restrict_rhs(uf), oi.restrict_rhs(uf)
+    assert np.linalg.norm(a - b) <= 1e-13 * np.linalg.norm(b)
+    # and for a general fine field they differ (the option is not the identity)
+    uf2 = np.random.default_rng(7).standard_normal((og.n_fine, 2))
+    assert np.linalg.norm(og.restrict_rhs(uf2) - oi.restrict_rhs(uf2)) > 1e-3 * np.linalg.norm(oi.restrict_rhs(uf2))
+
+
+def _tg(coarse, dt, t_end, levels, **kw):
+    """Taylor-Green (Eqs. 34-36) from the exact fields at t = 0: relative nodal L2 error of u at
+    t_end. The incremental forms start from the exact coarse pressure (zero at the pin)."""
+    mu = 0.01
+    prob = ci.taylor_green_problem(mu, dt, levels)
+    n = int(round(t_end / dt))
+    orc = cgp.CGPOracle(coarse.xy, coarse.tri, prob.rho, prob.mu, prob.dt, levels, prob.vel_bc, prob.p_bc, **kw)
+    mask, g = orc.dirichlet(0.0)
+    u = prob.u0(orc.fine.xy, mask, g)
+    p = ci.taylor_green_pressure(orc.coarse.xy, 0.0, mu)
+    p = p - p[orc.p_mask].mean()
+    for k in range(n):
+        r = orc.step(u, (k + 1) * dt, p)
+        u, p = r.u, r.p_c
+    ue = ci.taylor_green_velocity(orc.fine.xy, n * dt, mu)
+    return float(np.linalg.norm(u - ue) / np.linalg.norm(ue))
+
+
+def test_galerkin_restriction_taylor_green_accuracy():
+    """With the paper's non-incremental step, the Galerkin restriction's Taylor-Green velocity error
+    stays within 10 % of injection's (observed slightly below it), and stays first order in dt."""
+    coarse = ci.cavity_mesh(33, 41)
+    eg = [_tg(coarse, dt, 0.2, 1, restrict_mode="galerkin") for dt in (0.04, 0.02, 0.01)]
+    ei = [_tg(coarse, dt, 0.2, 1) for dt in (0.04, 0.02, 0.01)]
+    rates = np.log2(np.array(eg[:-1]) / np.array(eg[1:]))
+    assert all(a < 1.1 * b for a, b in zip(eg, ei)), (eg, ei)
+    assert ((rates > 0.75) & (rates < 1.25)).all(), rates
+
+
+def _dense_incremental_step(prob, coarse, fine_xy, fine_tri, onb_f, onb_c, u_n, p_n, t_next, rotational, galerkin):
+    """The incremental / rotational CGP step with dense matrices built by quadrature, point-location
+    prolongation and coordinate-matching restriction (no code shared with the oracle)."""
+    rho, mu, dt = prob.rho, prob.mu, prob.dt
+    M, K, Dx, Dy, N = _dense_ops(fine_xy, fine_tri, u_n)
+    Mc, Kc, Dxc, Dyc, _ = _dense_ops(coarse.xy, coarse.tri.astype(np.int64))
+    R = np.zeros((coarse.n_nodes, fine_xy.shape[0]))
+    for eta, q in enumerate(coarse.xy):
+        R[eta, np.flatnonzero((fine_xy == q).all(axis=1))[0]] = 1.0
+    P = _interp_matrix(coarse.xy, coarse.tri.astype(np.int64), fine_xy)
+    mask, g = prob.vel_bc(fine_xy, onb_f, t_next)
+    A = rho * M + dt * (rho * N + mu * K)
+    pf_n = P @ p_n
+    b = rho * M @ u_n - dt * np.stack([Dx @ pf_n, Dy @ pf_n], 1)
+    ut = np.zeros_like(u_n)
+    for c in range(2):
+        d = (mask & (1 << c)) != 0
+        Ac, bc = A.copy(), b[:, c].copy()
+        Ac[d, :] = 0.0
+        Ac[d, d] = 1.0
+        bc[d] = g[d, c]
+        ut[:, c] = np.linalg.solve(Ac, bc)
+    uc = R @ ut
+    if galerkin:
+        bcoarse = -(rho / dt) * (P.T @ (Dx @ ut[:, 0] + Dy @ ut[:, 1]))
+    else:
+        bcoarse = -(rho / dt) * (Dxc @ uc[:, 0] + Dyc @ uc[:, 1])
+    pm = prob.p_bc(coarse.xy, onb_c).astype(bool)
+    Kb = Kc.copy()
+    Kb[pm, :] = 0.0
+    Kb[:, pm] = 0.0
+    Kb[pm, pm] = 1.0
+    bcoarse[pm] = 0.0
+    phi = np.linalg.solve(Kb, bcoarse)
+    phif = P @ phi
+    w = np.linalg.solve(M, np.stack([Dx @ phif, Dy @ phif], 1))
+    u = ut - dt / rho * w
+    for c in range(2):
+        d = (mask & (1 << c)) != 0
+        u[d, c] = g[d, c]
+    p = p_n + phi
+    if rotational:
+        chi = (Dxc @ uc[:, 0] + Dyc @ uc[:, 1]) / Mc.sum(axis=1)
+        chi[pm] = 0.0
+        p = p - mu * chi
+    return dict(ut=ut, b_c=bcoarse, p_c=p, gp=w, u=u)
+
+
+@pytest.mark.parametrize("projection", ["incremental", "rotational"])
+@pytest.mark.parametrize("restrict_mode", ["injection", "galerkin"])
+@pytest.mark.parametrize("case,levels", [("cavity", 1), ("bfs", 1), ("tg", 2)])
+def test_incremental_step_matches_bruteforce_dense(projection, restrict_mode, case, levels):
+    if case == "cavity":
+        coarse, prob = ci.cavity_mesh(5, 31), ci.cavity_problem(100.0, 0.01, levels)
+    elif case == "tg":
+        coarse, prob = ci.cavity_mesh(4, 32), ci.taylor_green_problem(0.01, 0.01, levels)
+    else:
+        coarse, prob = ci.bfs_mesh(2, 33), ci.bfs_problem(400.0, 0.005, levels)
+    orc = cgp.CGPOracle(coarse.xy, coarse.tri, prob.rho, prob.mu, prob.dt, levels, prob.vel_bc, prob.p_bc,
+                        restrict_mode=restrict_mode, projection=projection)
+    rng = np.random.default_rng(8)
+    u_n = 0.5 * rng.standard_normal((orc.n_fine, 2))
+    p_n = rng.standard_normal(orc.n_coarse)
+    p_n[orc.p_mask] = 0.0
+    got = orc.step(u_n, 0.37, p_n)
+    ref = _dense_incremental_step(prob, coarse, orc.fine.xy, orc.fine.tri, orc.onb_f, orc.onb_c, u_n, p_n, 0.37,
+                                  projection == "rotational", restrict_mode == "galerkin")
+    for k, v in ref.items():
+        err = np.linalg.norm(getattr(got, k) - v) / max(np.linalg.norm(v), 1e-300)
+        assert err < 1e-11, (k, err)
+
+
+def test_incremental_first_step_from_zero_pressure_is_standard():
+    coarse, prob, _ = ci.workload("cavity33")
+    a = cgp.run(coarse, prob, 1)
+    b = cgp.run(coarse, prob, 1, projection="incremental")
+    assert np.array_equal(a.u, b.u) and np.array_equal(a.p_c, b.p_c)
+
+
+def test_incremental_galerkin_taylor_green_stable_and_accurate():
+    """Incremental CGP (l = 1) with the Galerkin restriction on a 17 x 17-node coarse grid: the
+    velocity error stays at the spatial level as dt falls from 0.04 to 0.0025 (no growth), and at
+    dt = 0.01 it is below a third of the non-incremental scheme's."""
+    coarse = ci.cavity_mesh(17, 41)
+    e = [_tg(coarse, dt, 0.2, 1, projection="incremental", restrict_mode="galerkin") for dt in (0.04, 0.01, 0.0025)]
+    es = _tg(coarse, 0.01, 0.2, 1)
+    assert max(e) < 1.25 * min(e) and e[-1] <= 1.1 * e[1], e
+    assert e[1] < es / 3.0, (e, es)
+
+
+def test_incremental_injection_taylor_green_grows_as_dt_falls():
+    """The recorded reading for the incremental forms: with the paper's injection restriction the
+    coarse Laplacian of Eq. 21 does not match the divergence it corrects, the pressure increments
+    accumulate that mismatch, and the Taylor-Green error grows as dt falls (here more than tenfold
+    from dt = 0.04 to 0.005 on the 17 x 17-node grid) instead of settling at the spatial error."""
+    coarse = ci.cavity_mesh(17, 41)
+    e = [_tg(coarse, dt, 0.2, 1, projection="incremental") for dt in (0.04, 0.005)]
+    assert e[1] > 10.0 * e[0], e
