@@ -26,8 +26,9 @@ leave these open; each is defined here in plain terms and checked by the pins in
   rho M u^n - dt G_f P p_c^n, the coarse Poisson solve gives the increment phi (same matrix and
   right-hand side as Eq. 21), the correction applies phi, and p_c^{n+1} = p_c^n + phi;
 * ``projection = "rotational"``: as incremental, with p_c^{n+1} = p_c^n + phi - mu chi, where
-  chi = M_L^-1 D_c u~_c is the divergence of the injected intermediate velocity divided by the
-  lumped coarse mass (chi = 0 where the pressure is held).
+  chi = -(dt/rho) M_L^-1 b_c is the discrete divergence the coarse right-hand side was built
+  from (D_c u~_c with injection, P^T D_f u~_f with the Galerkin restriction) divided by the
+  lumped coarse mass M_L (chi = 0 where the pressure is held, as b_c is).
 """
 from __future__ import annotations
 
@@ -130,14 +131,13 @@ class CGPOracle:
         b[self.p_mask] = 0.0
         return b
 
-    def pressure_update(self, p_c_n: np.ndarray, phi: np.ndarray, ut: np.ndarray) -> np.ndarray:
+    def pressure_update(self, p_c_n: np.ndarray, phi: np.ndarray, b_c: np.ndarray) -> np.ndarray:
         """Incremental forms: p^{n+1} = p^n + phi, and for the rotational form also - mu chi with
-        chi = (D_c u~_c) / (lumped coarse mass), zero where the pressure is held."""
+        chi = -(dt/rho) b_c / (lumped coarse mass): the restricted divergence of u~ that b_c was
+        built from, as a nodal field (zero where the pressure is held)."""
         p = p_c_n + phi
         if self.projection == "rotational":
-            uc = refine.restrict(self.h, ut)
-            d = self.coarse.Dx @ uc[:, 0] + self.coarse.Dy @ uc[:, 1]
-            chi = d / np.asarray(self.coarse.M.sum(axis=1)).ravel()
+            chi = -(self.dt / self.rho) * b_c / np.asarray(self.coarse.M.sum(axis=1)).ravel()
             chi[self.p_mask] = 0.0
             p = p - self.mu * chi
         return p
@@ -172,7 +172,7 @@ class CGPOracle:
         b_c = self.restrict_rhs(ut)
         phi = self.poisson(b_c)
         u, p_f, gp = self.prolong_correct(phi, ut, t_next)
-        return StepResult(u, ut, b_c, self.pressure_update(p_n, phi, ut), p_f, gp)
+        return StepResult(u, ut, b_c, self.pressure_update(p_n, phi, b_c), p_f, gp)
 
 
 def run(coarse, problem, n_steps: int, levels: int | None = None, u0=None, t0: float = 0.0,

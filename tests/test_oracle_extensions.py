@@ -9,7 +9,8 @@ spaces), and by its Taylor-Green accuracy next to injection (Eqs. 34-36).
 Incremental and rotational pressure correction (the paper's Sect. 4 names them as the way to
 remove the damping of its non-incremental scheme near walls): the momentum right-hand side carries
 -dt G_f P p_c^n, the coarse Poisson solve gives the increment, and p_c^{n+1} = p_c^n + phi (minus
-mu chi in the rotational form). Pinned by a dense brute-force recomputation, by the first step from
+mu chi in the rotational form, chi the restricted divergence over the lumped coarse mass). Pinned
+by a dense brute-force recomputation, by the first step from
 a zero pressure equalling the standard step, and by Taylor-Green: with the Galerkin restriction the
 incremental CGP step is stable as dt -> 0 and its velocity error is several times below the
 non-incremental scheme's; with injection it is not stable (the recorded reading for the option).
@@ -147,7 +148,8 @@ def _dense_incremental_step(prob, coarse, fine_xy, fine_tri, onb_f, onb_c, u_n, 
         u[d, c] = g[d, c]
     p = p_n + phi
     if rotational:
-        chi = (Dxc @ uc[:, 0] + Dyc @ uc[:, 1]) / Mc.sum(axis=1)
+        div = P.T @ (Dx @ ut[:, 0] + Dy @ ut[:, 1]) if galerkin else Dxc @ uc[:, 0] + Dyc @ uc[:, 1]
+        chi = div / Mc.sum(axis=1)
         chi[pm] = 0.0
         p = p - mu * chi
     return dict(ut=ut, b_c=bcoarse, p_c=p, gp=w, u=u)
