@@ -11,7 +11,10 @@ Modules
 -------
 ``refine``  nested 1:4 refinement and the s^p / s^u mapping tables (Sect. 2.2, Eqs. 29-30).
 ``fem``     closed-form P1 element matrices and global assembly (Eqs. 16-18).
-``cgp``     the five-step IFE-CGP time step (Eqs. 19-23) with direct sparse solves.
+``cgp``     the five-step IFE-CGP time step (Eqs. 19-23) with direct sparse solves, plus the
+            Galerkin restriction and the incremental / rotational forms (options, Sect. 4).
+``diagnostics``  body forces (drag, lift), wall shear, reattachment length and Strouhal number
+            of the benchmark flows (Sect. 3.2-3.3).
 
 Every linear system is solved by a sparse direct LU (SuperLU through ``scipy``), so the oracle's
 results carry only rounding error; the CUDA path's Krylov solvers are compared against it within
