@@ -109,6 +109,25 @@ typedef struct {
                           degree-k Chebyshev polynomial in D^-1 A on [1/2, G], G the Gershgorin bound
                           of D^-1 A taken by each cgp_assemble, applied in FP32; 0 (default) = 3
                           for CGP_FP64, Jacobi for CGP_MIXED */
+    int solver_format; /* matrix layout of the fine-mesh solvers' products (momentum and mass, Eqs. 19
+                          and 23): 0 (default) = automatic (CSR until cgp_autotune times the
+                          alternatives), 1 = sliced ELL of the natural row order (32-row slices, slot
+                          k of a slice's rows contiguous, so each warp load is coalesced), 2 = CSR
+                          with spmv_lanes lanes per row. Batched steps always use CSR */
+    int restrict_mode; /* coarse right-hand side of the Poisson solve (Eq. 21): 0 (default) = the
+                          paper's injection u~_c = u~_f[xi] (Eqs. 20, 30) and b_c = -(rho/dt) D_c u~_c;
+                          1 = Galerkin restriction of the fine divergence, b_c = -(rho/dt) P^T D_f u~_f
+                          with P the prolongation of Eq. 29 (the coarse test functions integrated
+                          against div u~_f); not in the paper */
+    int projection;    /* pressure-correction form: 0 (default) = the paper's non-incremental scheme
+                          (Eqs. 9-15); 1 = incremental: the momentum right-hand side carries
+                          -dt G_f P p_c^n, the Poisson solve of Eq. 21 gives the increment phi, the
+                          correction applies phi and p_c^{n+1} = p_c^n + phi; 2 = rotational: as 1 with
+                          p_c^{n+1} = p_c^n + phi - mu chi, chi = -(dt/rho) b_c / (lumped coarse mass).
+                          The paper's Sect. 4 names these forms as future work; with restrict_mode 0
+                          they drift as dt falls (the coarse Laplacian does not match the injected
+                          divergence), with restrict_mode 1 they are stable. Single contexts only:
+                          cgp_batch_create rejects contexts with projection != 0 */
 } cgp_params;
 
 /* A coarse mesh: n_nodes points xy_host[n][2] and n_tris counter-clockwise triangles
@@ -128,6 +147,7 @@ typedef struct {
     int coarse_kernel;   /* 0 generic classical CG, 1 on-chip classical CG, 2 on-chip pipelined CG,
                             3 on-chip two-level Schwarz CG, preconditioner in FP32,
                             4 the same, preconditioner in the iteration precision */
+    int solver_format;   /* layout of the fine solvers' products: 1 sliced ELL, 2 CSR */
 } cgp_info;
 
 /* Per-solve statistics of the most recent step (read back by cgp_get_stats, which synchronises
@@ -145,7 +165,7 @@ typedef struct {
 /* Fill *p with the defaults: rho = 1, mu = 0.01, dt = 0.01, levels = 1, CGP_FP64, rtol = 1e-8,
  * inner_rtol = 1e-4, max_iter = 20000, max_outer = 30, spmv_lanes = 0, block_threads = 0,
  * coarse_solver = 0, spmv_format = 0, precond_degree = 0, precond_ratio = 0, warm_start = 3, mass_degree = 0,
- * momentum_degree = 0. */
+ * momentum_degree = 0, solver_format = 0, restrict_mode = 0, projection = 0. */
 void cgp_default_params(cgp_params* p);
 
 /* Preprocessing (the paper's C_pre, Sect. 2.4): validates the coarse mesh, refines it
@@ -215,7 +235,9 @@ int cgp_momentum_solve(cgp_ctx ctx, const double* u_dev, double* ut_dev, void* s
 
 /* Steps 2-3 right-hand side, Eqs. 20-21 with Eq. 30: u~_c = u~_f[xi] (injection), then
  * b_c = -(rho/dt) (Dx_c u~_c,x + Dy_c u~_c,y) with D_ij = int psi_i d phi_j on the coarse mesh,
- * zero at p-masked nodes. ut_dev: [n_fine][2]; bc_dev: [n_coarse] output. */
+ * zero at p-masked nodes; with restrict_mode = 1, b_c = -(rho/dt) P^T (Dx_f u~_x + Dy_f u~_y)
+ * instead (P^T level by level through inverse child lists of the s^p tables of Eq. 29).
+ * ut_dev: [n_fine][2]; bc_dev: [n_coarse] output. */
 int cgp_restrict(cgp_ctx ctx, const double* ut_dev, double* bc_dev, void* stream);
 
 /* Step 3, Eq. 21: solve K_c p_c = b_c (K_c = coarse stiffness, +(-Laplacian), after symmetric
@@ -238,8 +260,36 @@ int cgp_prolong_correct(cgp_ctx ctx, const double* pc_dev, const double* ut_dev,
 
 /* One whole time step (Eqs. 19-23): assemble, momentum, restrict, Poisson (warm-started from
  * pc_dev), prolong-correct. u_dev [n_fine][2] holds u^n on entry and u^{n+1} on exit; pc_dev
- * [n_coarse] holds p_c^n on entry and p_c^{n+1} on exit. Stream-ordered, no host sync. */
+ * [n_coarse] holds p_c^n on entry and p_c^{n+1} on exit. With projection = 1 or 2 the step is
+ * cgp_assemble_incremental with p_c^n, the momentum solve, the restriction, the Poisson solve for
+ * the increment (warm-started from the extrapolated previous increments), prolong-correct with
+ * the increment and cgp_pressure_update. Stream-ordered, no host sync. */
 int cgp_step(cgp_ctx ctx, double* u_dev, double* pc_dev, void* stream);
+
+/* Many coarse Poisson solves (Eq. 21) with the context's matrix in one call: nrhs right-hand
+ * sides b_dev [nrhs][n_coarse] and initial guesses / solutions x_dev [nrhs][n_coarse], each solved
+ * to the context's rtol by the two-level preconditioned CG of the batched step (Jacobi plus three
+ * coarse functions per 256-row subdomain of a Hilbert-curve renumbering), one block per right-hand
+ * side, as many right-hand sides per cooperative launch as the GPU holds blocks of that kernel
+ * (about two per SM; larger counts go in successive launches). For independent solves of one mesh:
+ * the learned warm start's evaluation, or many instances that share a coarse mesh. iters_dev,
+ * rel_dev, status_dev [nrhs] (optional): per right-hand side iteration count, final FP64 relative
+ * residual and CGP_* status. The first call builds the two-level structures and workspace
+ * (synchronously). Coarse meshes of at most 131,072 nodes (else CGP_ERR_ARG). Not in the paper. */
+int cgp_poisson_solve_many(cgp_ctx ctx, int nrhs, const double* b_dev, double* x_dev, int* iters_dev, double* rel_dev,
+                           int* status_dev, void* stream);
+
+/* Incremental forms, step 1: as cgp_assemble, with the momentum right-hand side
+ * rho M u^n - dt G_f P p_c^n (the previous pressure prolonged by Eq. 29 and its fine gradient)
+ * at rows that are not velocity-Dirichlet. pc_dev: [n_coarse] p_c^n. Stream-ordered. Not in the
+ * paper (its Sect. 4 names the incremental form as future work). */
+int cgp_assemble_incremental(cgp_ctx ctx, const double* u_dev, const double* pc_dev, void* stream);
+
+/* Incremental forms, last step: pc_dev += phi_dev (projection 1), and for projection 2 also
+ * - mu chi with chi = -(dt/rho) bc_dev / (lumped coarse mass) (the restricted divergence of u~
+ * that the right-hand side bc_dev of the increment's Poisson solve was built from). bc_dev,
+ * phi_dev, pc_dev: [n_coarse]. Stream-ordered. Errors: CGP_ERR_ARG, CGP_ERR_STATE (projection 0). */
+int cgp_pressure_update(cgp_ctx ctx, const double* bc_dev, const double* phi_dev, double* pc_dev, void* stream);
 
 /* y = A0 x with A0 = rho M + dt mu K (the constant part of the momentum matrix of Eq. 19) on the
  * fine mesh, for two interleaved right-hand sides: x_dev, y_dev [n_fine][2]. The SpMV kernel of
@@ -267,7 +317,8 @@ int cgp_get_stats(cgp_ctx ctx, void* stream, cgp_stats* st);
  * inside a group. The coarse solve uses the generic classical CG kernel. The gathers between
  * stages are launched per instance. Not in the paper: a systems pattern for many small problems.
  * u_devs[i] [n_fine_i][2] and pc_devs[i] [n_coarse_i] are the instances' state, caller-owned
- * device buffers that must stay valid until cgp_batch_destroy. */
+ * device buffers that must stay valid until cgp_batch_destroy. Contexts with projection != 0 are
+ * rejected (CGP_ERR_ARG). */
 typedef struct cgp_batch_s* cgp_batch;
 int cgp_batch_create(cgp_ctx* ctxs, int n, double* const* u_devs, double* const* pc_devs, cgp_batch* out);
 /* Launch shape: total blocks and each instance's group sizes (arrays of n, may be NULL). */
@@ -322,29 +373,96 @@ int cgp_ws_train_step(cgp_ws w, const double* b_dev, const double* p_dev, int B,
 int cgp_ws_status(cgp_ws w, void* stream);
 int cgp_ws_destroy(cgp_ws w);
 
-/* Time the SpMV lane counts {1, 2, 4, 8} on the fine and coarse matrices and keep the fastest
- * for the solver kernels (a project-written autotuner, not in the paper). Synchronous. */
+/* Residual form of the learned warm start: the network corrects a base guess x_base (for example
+ * the previous step's pressure or its extrapolation) instead of predicting p itself. Inference:
+ * r = b - K_c x_base (the coarse matrix of Eq. 21 after elimination, from ctx), then
+ * p = x_base + ||r|| NN(r / ||r||). Training on pairs (b, p): the same r as input and the
+ * correction p - x_base as target (loss as in cgp_ws_train_step). b_dev, base_dev, p_dev: [B][n]
+ * float64 with n = the context's n_coarse (else CGP_ERR_ARG). The first call allocates two
+ * [batch_max][n] buffers. Stream-ordered. */
+int cgp_ws_forward_residual(cgp_ws w, cgp_ctx ctx, const double* b_dev, const double* base_dev, int B, double* p_dev,
+                            void* stream);
+int cgp_ws_train_step_residual(cgp_ws w, cgp_ctx ctx, const double* b_dev, const double* p_dev, const double* base_dev,
+                               int B, float lr, float* loss_dev, void* stream);
+
+/* out = the extrapolation in time of order 0..3 through the values v0 (newest) .. v3 of n doubles:
+ * v0, 2 v0 - v1, 3 v0 - 3 v1 + v2, 4 v0 - 6 v1 + 4 v2 - v3 (the initial-guess predictors of
+ * warm_start, without a history); unused inputs may be NULL. Stream-ordered. */
+int cgp_extrapolate(long long n, int order, const double* v0_dev, const double* v1_dev, const double* v2_dev,
+                    const double* v3_dev, double* out_dev, void* stream);
+
+/* Project-written autotuner (not in the paper). Times the SpMV lane counts {1, 2, 4, 8} on the
+ * fine and coarse matrices and keeps the fastest for the solver kernels; the stand-alone SpMV's
+ * layout (CSR or sliced ELL, spmv_format 0); and, for the fine-mesh solvers (solver_format 0 and/or
+ * block_threads 0), the product layout (CSR or sliced ELL) and the threads per block of their
+ * persistent kernels (the default or 256, i.e. rows per thread), by timing the consistent-mass CG
+ * on a fixed right-hand side. Overwrites the statistics and the context's intermediate-velocity
+ * and gradient buffers (not the solution histories). Synchronous. */
 int cgp_autotune(cgp_ctx ctx, void* stream);
 
 /* Allocation-free conjugate-gradient solve of one symmetric positive definite CSR system
  * A x = b (no counterpart in the paper: it exists for callers that must not allocate device
  * memory, such as code embedded in a host program whose allocator owns every device byte, or code
  * running where a cudaMalloc would synchronise or fail). It runs the same persistent
- * Jacobi-preconditioned CG kernel inside FP64 refinement that the library uses for Eq. 21, but
- * takes its scratch from a fixed static device array of about 3.6 MB instead of a context.
+ * Jacobi-preconditioned CG kernel inside FP64 refinement that cgp_poisson_solve uses for its
+ * generic coarse solver (CSR products with 4 lanes per row, at most 30 FP64 refinement passes),
+ * but takes its scratch from a fixed static device array of about 3.6 MB instead of a context.
  * Arguments: n rows (1 <= n <= 65536; larger n returns CGP_ERR_ARG), rp_dev [n+1], ci_dev [nnz]
  * (0-based columns), val_dev [nnz] float64, all device memory; b_dev [n]; x_dev [n] initial
  * guess in, solution out; stop at ||b - A x|| <= rtol ||b||; max_iter caps CG iterations.
  * status_dev, iters_dev, rel_res_dev: optional device outputs (NULL to skip) receiving the
- * CGP_* status, the iteration count and the final true relative residual.
+ * CGP_* status, the iteration count and the final true relative residual. Device-side statuses:
+ * CGP_ERR_ARG when a row has no positive finite stored diagonal (that row's preconditioner entry
+ * is taken as 0); CGP_ERR_NOT_CONVERGED when max_iter or the 30 refinement passes run out (x and
+ * the residual are still written, so a caller seeing fewer than max_iter iterations knows the
+ * pass cap ended the solve); CGP_ERR_NAN on a non-finite residual or inner product;
+ * CGP_ERR_TIMEOUT when a grid barrier gave up (then rel_res reads NaN, iters holds what the
+ * solver had recorded, and x is unspecified).
  * The call is stream-ordered and asynchronous and allocates nothing (no cudaMalloc, no
  * cudaFree). The first call on each device looks up the scratch array's device address with that
  * device current; make that first call before any stream capture. All calls share the one
  * scratch array, so calls whose kernels overlap on the GPU race with each other: serialise them
- * (one stream, or events). Errors: CGP_ERR_ARG, CGP_ERR_CUDA. */
+ * (one stream, or events). Host-side errors (returned): CGP_ERR_ARG, CGP_ERR_CUDA. */
 int cgp_cg_solve_noalloc(int n, const int* rp_dev, const int* ci_dev, const double* val_dev, const double* b_dev,
                          double* x_dev, double rtol, int max_iter, int* status_dev, int* iters_dev,
                          double* rel_res_dev, void* stream);
+
+/* ---- diagnostics of the benchmark flows (Sect. 3.2 reattachment length, Sect. 3.3 drag and lift) ----
+ * Standard definitions (the paper prints none for the forces): the force on a body is the sum over
+ * its boundary edges of int sigma n_b, sigma = -p I + mu (grad u + grad u^T), n_b the unit normal
+ * from the body into the fluid, p = P p_c on the fine mesh (Eq. 29, trapezoid rule along the edge),
+ * grad u the P1 gradient of the fluid triangle owning the edge; C_D = 2 F_x / (rho u_inf^2 d),
+ * C_L = 2 F_y / (rho u_inf^2 d). Wall shear tau = mu t . (grad u) n_f per wall edge (t the unit
+ * tangent towards larger x, n_f the unit normal into the fluid). */
+
+/* Surface of a diagnostic: which = 0 the body of cgp_body_force, 1 the wall of cgp_reattachment;
+ * node_mask_host [n_fine]: nonzero on the surface's fine nodes; the surface is every boundary edge
+ * of the fine mesh whose two end nodes are marked (wall edges are kept sorted by midpoint x).
+ * *n_edges (optional) receives the edge count. Synchronous. Errors: CGP_ERR_ARG, CGP_ERR_NOMEM,
+ * CGP_ERR_CUDA. */
+int cgp_set_surface(cgp_ctx ctx, int which, const unsigned char* node_mask_host, int* n_edges);
+
+/* Force on the body for velocity u_dev [n_fine][2] and coarse pressure pc_dev [n_coarse]:
+ * force_dev [4] = pressure force (x, y), viscous force (x, y). One block, fixed-order sums
+ * (deterministic). Stream-ordered. Errors: CGP_ERR_ARG, CGP_ERR_STATE (no body set). */
+int cgp_body_force(cgp_ctx ctx, const double* u_dev, const double* pc_dev, double* force_dev, void* stream);
+
+/* Reattachment point on the wall: the first x >= x_start at which the wall shear turns from
+ * negative to non-negative, linear between edge midpoints; *xr_dev = NaN if there is none.
+ * x_dev, tau_dev [n_edges] (optional): each wall edge's midpoint x and shear. Stream-ordered.
+ * Errors: CGP_ERR_ARG, CGP_ERR_STATE (no wall set). */
+int cgp_reattachment(cgp_ctx ctx, const double* u_dev, double x_start, double* xr_dev, double* x_dev, double* tau_dev,
+                     void* stream);
+
+/* Check of the bounded device waits (not in the paper; for tests of failure detection): launches,
+ * on the context's persistent launch shape (grid_blocks blocks, cooperative), one grid barrier
+ * whose target is grid_blocks + missing_blocks arrivals, with a wait bound of limit_ms
+ * (0 < limit_ms <= 10000) instead of the library's 250 ms. With missing_blocks = 0 every block
+ * passes and *status_dev receives CGP_OK; with missing_blocks > 0 (at most 1024) the barrier can
+ * never complete, every block gives up after limit_ms and *status_dev receives CGP_ERR_TIMEOUT.
+ * The context's own statistics are not touched and it stays usable. status_dev: one int of
+ * device memory. Stream-ordered. Errors: CGP_ERR_ARG, CGP_ERR_CUDA. */
+int cgp_wait_probe(cgp_ctx ctx, int missing_blocks, double limit_ms, int* status_dev, void* stream);
 
 /* Free everything the context owns. NULL is accepted. */
 int cgp_mesh_destroy(cgp_ctx ctx);

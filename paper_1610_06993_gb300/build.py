@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcgp.so")
 SOURCES = ["api.cu", "assemble.cu", "krylov.cu", "krylov_pipe.cu", "krylov_2l.cu", "mapping.cu", "batch.cu", "mlp.cu",
-           "host_mesh.cpp"]
+           "diagnostics.cu", "host_mesh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

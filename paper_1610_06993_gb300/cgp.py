@@ -35,7 +35,8 @@ class cgp_params(C.Structure):
                 ("max_iter", C.c_int), ("max_outer", C.c_int), ("spmv_lanes", C.c_int),
                 ("block_threads", C.c_int), ("coarse_solver", C.c_int), ("spmv_format", C.c_int),
                 ("precond_degree", C.c_int), ("precond_ratio", C.c_double), ("warm_start", C.c_int),
-                ("mass_degree", C.c_int), ("momentum_degree", C.c_int)]
+                ("mass_degree", C.c_int), ("momentum_degree", C.c_int), ("solver_format", C.c_int),
+                ("restrict_mode", C.c_int), ("projection", C.c_int)]
 
 
 class cgp_mesh_desc(C.Structure):
@@ -46,7 +47,7 @@ class cgp_mesh_desc(C.Structure):
 class cgp_info(C.Structure):
     _fields_ = [(k, C.c_int) for k in ("n_fine", "n_coarse", "tris_fine", "tris_coarse", "nnz_fine",
                                        "nnz_coarse", "levels", "n_colours", "grid_blocks",
-                                       "block_threads", "spmv_lanes", "coarse_kernel")]
+                                       "block_threads", "spmv_lanes", "coarse_kernel", "solver_format")]
 
 
 class cgp_stats(C.Structure):
@@ -75,11 +76,18 @@ _SIGNATURES = {
     "cgp_poisson_solve": (C.c_int, [_VP, _VP, _VP, _VP]),
     "cgp_prolong_correct": (C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "cgp_step": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "cgp_assemble_incremental": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "cgp_poisson_solve_many": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "cgp_pressure_update": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "cgp_step_host": (C.c_int, [_VP, _VP, _VP, _VP]),
     "cgp_get_stats": (C.c_int, [_VP, _VP, C.POINTER(cgp_stats)]),
     "cgp_autotune": (C.c_int, [_VP, _VP]),
     "cgp_cg_solve_noalloc": (C.c_int, [C.c_int, _VP, _VP, _VP, _VP, _VP, C.c_double, C.c_int, _VP, _VP, _VP,
                                        _VP]),
+    "cgp_wait_probe": (C.c_int, [_VP, C.c_int, C.c_double, _VP, _VP]),
+    "cgp_set_surface": (C.c_int, [_VP, C.c_int, _VP, C.POINTER(C.c_int)]),
+    "cgp_body_force": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "cgp_reattachment": (C.c_int, [_VP, _VP, C.c_double, _VP, _VP, _VP, _VP]),
     "cgp_batch_create": (C.c_int, [_VP, C.c_int, _VP, _VP, C.POINTER(_VP)]),
     "cgp_batch_info": (C.c_int, [_VP, _VP, _VP, _VP]),
     "cgp_batch_step": (C.c_int, [_VP, _VP]),
@@ -100,6 +108,9 @@ _SIGNATURES = {
     "cgp_ws_train_step": (C.c_int, [_VP, _VP, _VP, C.c_int, C.c_float, _VP, _VP]),
     "cgp_ws_status": (C.c_int, [_VP, _VP]),
     "cgp_ws_destroy": (C.c_int, [_VP]),
+    "cgp_ws_forward_residual": (C.c_int, [_VP, _VP, _VP, _VP, C.c_int, _VP, _VP]),
+    "cgp_ws_train_step_residual": (C.c_int, [_VP, _VP, _VP, _VP, _VP, C.c_int, C.c_float, _VP, _VP]),
+    "cgp_extrapolate": (C.c_int, [C.c_longlong, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP]),
     "cgp_mesh_destroy": (C.c_int, [_VP]),
     "cgp_status_str": (C.c_char_p, [C.c_int]),
 }
@@ -243,6 +254,23 @@ def cgp_step(ctx: int, u_dev, pc_dev, stream=None) -> None:
     _check(load().cgp_step(ctx, _ptr(u_dev), _ptr(pc_dev), _stream(stream)), "cgp_step")
 
 
+def cgp_poisson_solve_many(ctx: int, b_dev, x_dev, iters_dev=None, rel_dev=None, status_dev=None, stream=None) -> None:
+    """Solve the coarse Poisson system for every row of b_dev [nrhs][n_coarse] into x_dev."""
+    nrhs = int(b_dev.shape[0])
+    _check(load().cgp_poisson_solve_many(ctx, nrhs, _ptr(b_dev), _ptr(x_dev), _ptr(iters_dev), _ptr(rel_dev),
+                                         _ptr(status_dev), _stream(stream)), "cgp_poisson_solve_many")
+
+
+def cgp_assemble_incremental(ctx: int, u_dev, pc_dev, stream=None) -> None:
+    _check(load().cgp_assemble_incremental(ctx, _ptr(u_dev), _ptr(pc_dev), _stream(stream)),
+           "cgp_assemble_incremental")
+
+
+def cgp_pressure_update(ctx: int, bc_dev, phi_dev, pc_dev, stream=None) -> None:
+    _check(load().cgp_pressure_update(ctx, _ptr(bc_dev), _ptr(phi_dev), _ptr(pc_dev), _stream(stream)),
+           "cgp_pressure_update")
+
+
 def cgp_step_host(ctx: int, u_host, pc_host, stream=None) -> None:
     """``u_host``/``pc_host``: contiguous float64 host buffers (numpy arrays or pinned CPU tensors)."""
     _check(load().cgp_step_host(ctx, _ptr(u_host), _ptr(pc_host), _stream(stream)), "cgp_step_host")
@@ -268,6 +296,29 @@ def cgp_cg_solve_noalloc(rp_dev, ci_dev, val_dev, b_dev, x_dev, rtol: float, max
     _check(load().cgp_cg_solve_noalloc(n, _ptr(rp_dev), _ptr(ci_dev), _ptr(val_dev), _ptr(b_dev), _ptr(x_dev),
                                        float(rtol), int(max_iter), _ptr(status_dev), _ptr(iters_dev),
                                        _ptr(rel_res_dev), _stream(stream)), "cgp_cg_solve_noalloc")
+
+
+def cgp_wait_probe(ctx: int, missing_blocks: int, limit_ms: float, status_dev, stream=None) -> None:
+    """One bounded grid barrier that waits for ``missing_blocks`` more blocks than were launched."""
+    _check(load().cgp_wait_probe(ctx, int(missing_blocks), float(limit_ms), _ptr(status_dev), _stream(stream)),
+           "cgp_wait_probe")
+
+
+def cgp_set_surface(ctx: int, which: int, node_mask: np.ndarray) -> int:
+    """Body (which = 0) or wall (which = 1) of the diagnostics; returns its edge count."""
+    m = np.ascontiguousarray(node_mask, dtype=np.uint8)
+    n = C.c_int(0)
+    _check(load().cgp_set_surface(ctx, int(which), _ptr(m), C.byref(n)), "cgp_set_surface")
+    return n.value
+
+
+def cgp_body_force(ctx: int, u_dev, pc_dev, force_dev, stream=None) -> None:
+    _check(load().cgp_body_force(ctx, _ptr(u_dev), _ptr(pc_dev), _ptr(force_dev), _stream(stream)), "cgp_body_force")
+
+
+def cgp_reattachment(ctx: int, u_dev, x_start: float, xr_dev, x_dev=None, tau_dev=None, stream=None) -> None:
+    _check(load().cgp_reattachment(ctx, _ptr(u_dev), float(x_start), _ptr(xr_dev), _ptr(x_dev), _ptr(tau_dev),
+                                   _stream(stream)), "cgp_reattachment")
 
 
 def cgp_batch_create(ctxs, u_devs, pc_devs) -> int:
@@ -377,6 +428,24 @@ def cgp_ws_train_step(w: int, b_dev, p_dev, lr: float, loss_dev=None, stream=Non
 
 def cgp_ws_status(w: int, stream=None) -> int:
     return load().cgp_ws_status(w, _stream(stream))
+
+
+def cgp_ws_forward_residual(w: int, ctx: int, b_dev, base_dev, p_dev, stream=None) -> None:
+    _check(load().cgp_ws_forward_residual(w, ctx, _ptr(b_dev), _ptr(base_dev), int(b_dev.shape[0]), _ptr(p_dev),
+                                          _stream(stream)), "cgp_ws_forward_residual")
+
+
+def cgp_ws_train_step_residual(w: int, ctx: int, b_dev, p_dev, base_dev, lr: float, loss_dev=None,
+                               stream=None) -> None:
+    _check(load().cgp_ws_train_step_residual(w, ctx, _ptr(b_dev), _ptr(p_dev), _ptr(base_dev), int(b_dev.shape[0]),
+                                             float(lr), _ptr(loss_dev), _stream(stream)), "cgp_ws_train_step_residual")
+
+
+def cgp_extrapolate(order: int, v, out_dev, stream=None) -> None:
+    """out = extrapolation of order ``order`` through the tensors v[0] (newest) .. v[order]."""
+    vs = [_ptr(x) for x in v] + [None] * (4 - len(v))
+    _check(load().cgp_extrapolate(int(out_dev.numel()), int(order), *vs, _ptr(out_dev), _stream(stream)),
+           "cgp_extrapolate")
 
 
 def cgp_ws_destroy(w: int) -> None:

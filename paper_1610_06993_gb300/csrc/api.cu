@@ -85,6 +85,9 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     if (P.mass_degree < 0 || P.mass_degree > 16) return CGP_ERR_ARG;
     if (P.momentum_degree < 0 || P.momentum_degree > 16) return CGP_ERR_ARG;
     if (P.spmv_format < 0 || P.spmv_format > 2) return CGP_ERR_ARG;
+    if (P.solver_format < 0 || P.solver_format > 2) return CGP_ERR_ARG;
+    if (P.restrict_mode < 0 || P.restrict_mode > 1) return CGP_ERR_ARG;
+    if (P.projection < 0 || P.projection > 2) return CGP_ERR_ARG;
     if (P.inner_rtol <= 0.0) P.inner_rtol = 1e-4;
     if (P.max_iter <= 0) P.max_iter = 20000;
     if (P.max_outer <= 0) P.max_outer = 30;
@@ -122,6 +125,28 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
         TRY(upload(c, &c->sell_src, hs.src));
         TRY(upload(c, &c->sell_perm, hs.perm));
         TRY(dalloc(c, &c->sell_val, (size_t)c->sell_total));
+    }
+    {
+        // sliced ELL of the natural row order (sigma = 1: no sorting) for the fine solvers
+        HostSell he;
+        build_sell(H.fine, 32, 1, he);
+        c->ell_nslices = he.nslices;
+        c->ell_total = he.ptr[he.nslices];
+        std::vector<int> pos(H.fine.nnz, -1);
+        for (int p = 0; p < c->ell_total; ++p)
+            if (he.src[p] >= 0) pos[he.src[p]] = p;
+        TRY(upload(c, &c->ell_ptr, he.ptr));
+        TRY(upload(c, &c->ell_col, he.col));
+        TRY(upload(c, &c->ell_src, he.src));
+        TRY(upload(c, &c->ell_pos, pos));
+        TRY(dalloc(c, &c->ell_A, (size_t)c->ell_total));
+        TRY(dalloc(c, &c->ell_M, (size_t)c->ell_total));
+        TRY(dalloc(c, &c->ell_A32, (size_t)c->ell_total));
+        TRY(dalloc(c, &c->ell_M32, (size_t)c->ell_total));
+        // padding slots stay zero; the assembly rewrites only the matrix entries of ell_A
+        CK(cudaMemset(c->ell_A, 0, sizeof(double) * (size_t)c->ell_total));
+        CK(cudaMemset(c->ell_A32, 0, sizeof(float) * (size_t)c->ell_total));
+        c->ell_on = P.solver_format == 1;   // automatic: CSR until cgp_autotune times both
     }
     c->lv_n.clear();
     for (auto& L : H.lv) c->lv_n.push_back(L.n);
@@ -175,6 +200,11 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     CK(cudaMemset(c->pc_flag, 0, sizeof(int)));
     CK(cudaMemset(c->w_flag, 0, sizeof(int)));
     CK(cudaMemset(c->mom_flag, 0, sizeof(int)));
+    TRY(dalloc(c, &c->gal_div, nf));
+    TRY(dalloc(c, &c->grad_n, 2 * nf));
+    TRY(dalloc(c, &c->phi, nc));
+    TRY(dalloc(c, &c->mlump_c, nc));
+    CK(cudaMemset(c->phi, 0, nc * sizeof(double)));
     TRY(dalloc(c, &c->u_stage, 2 * nf));
     TRY(dalloc(c, &c->pc_stage, nc));
     // Krylov workspace: the largest of BiCGStab (9 pair vectors) and CG (6 vectors), each with
@@ -213,7 +243,9 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
         if ((e = launch_const_assembly(c->EF, c->M, Kf, c->Gxy, s)) != cudaSuccess) break;
         if ((e = launch_const_assembly(c->EC, nullptr, c->Kc_raw, c->Dc_xy, s)) != cudaSuccess) break;
         if ((e = launch_make_A0(c, Kf, s)) != cudaSuccess) break;
+        if ((e = launch_lumped_mass(c, Kf, s)) != cudaSuccess) break;   // Kf (nnz_f >= nnz_c) reused as scratch
         if ((e = sell_fill(c, c->A0, s)) != cudaSuccess) break;
+        if ((e = ell_fill(c->ell_total, c->ell_src, c->M, c->ell_M, c->ell_M32, s)) != cudaSuccess) break;
         e = cudaStreamSynchronize(s);
     } while (0);
     cudaFree(Kf);
@@ -238,6 +270,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     for (int i = 0; i < H.coarse.n; ++i) c->width_c = std::max(c->width_c, H.coarse.rp[i + 1] - H.coarse.rp[i]);
     CK(pipe_prepare(c));
     TRY(assemble_gather_build(c));
+    TRY(galerkin_build(c));
     c->spmv_sell = P.spmv_format == 1;
     return CGP_OK;
 }
@@ -257,6 +290,31 @@ cudaError_t mass_stage(cgp_ctx_s* c, cudaStream_t s) {
 void destroy_impl(cgp_ctx_s* c) {
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
+    for (auto& S : c->surf) {
+        if (S.e) cudaFree(S.e);
+        if (S.xs) cudaFree(S.xs);
+        S = cgp_ctx_s::Surface();
+    }
+}
+
+// One grid barrier of every block of a cooperative launch, waiting for `expect` arrivals with the
+// wait bounded by limit_ns (cgp_wait_probe): more arrivals than blocks can never come, so the
+// wait runs out and the first block to give up records CGP_ERR_TIMEOUT.
+__global__ void k_wait_probe(SyncWords* sw, unsigned int expect, unsigned long long limit_ns, int* status) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        red_release_add_u32(&sw->count, 1u);
+        if (!grid_poll(sw, expect, limit_ns)) {
+            const int e = ld_relaxed_i32(&sw->err);
+            atomicCAS(status, 0, e != 0 ? e : CGP_ERR_TIMEOUT);
+        }
+    }
+}
+
+// A fixed smooth right-hand side for the autotuner's timed solves.
+__global__ void k_fill_wave(size_t n, double* b) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = sin(1e-3 * (double)i) + 0.5;
 }
 
 }  // namespace
@@ -338,6 +396,7 @@ int cgp_mesh_info(cgp_ctx c, cgp_info* info) {
     info->spmv_lanes = c->sh_f.lanes;
     info->coarse_kernel = c->use_schwarz ? (c->schwarz_fp32 && c->prm.precision == CGP_FP64 ? 3 : 4)
                                          : c->use_pipe ? (c->onchip_pipelined ? 2 : 1) : 0;
+    info->solver_format = c->ell_on ? 1 : 2;
     return CGP_OK;
 }
 
@@ -420,10 +479,42 @@ int cgp_prolong_correct(cgp_ctx c, const double* pc_dev, const double* ut_dev, d
     return CGP_OK;
 }
 
+int cgp_assemble_incremental(cgp_ctx c, const double* u_dev, const double* pc_dev, void* stream) {
+    if (!c || !u_dev || !pc_dev) return CGP_ERR_ARG;
+    if (!c->bc_set) return CGP_ERR_STATE;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(launch_pressure_term(c, pc_dev, s));
+    CK(launch_assemble_step(c, u_dev, s, c->grad_n));
+    return CGP_OK;
+}
+
+int cgp_pressure_update(cgp_ctx c, const double* bc_dev, const double* phi_dev, double* pc_dev, void* stream) {
+    if (!c || !bc_dev || !phi_dev || !pc_dev) return CGP_ERR_ARG;
+    if (!c->bc_set || c->prm.projection == 0) return CGP_ERR_STATE;
+    CK(launch_pressure_update(c, bc_dev, phi_dev, pc_dev, (cudaStream_t)stream));
+    return CGP_OK;
+}
+
 int cgp_step(cgp_ctx c, double* u_dev, double* pc_dev, void* stream) {
     if (!c || !u_dev || !pc_dev) return CGP_ERR_ARG;
     if (!c->bc_set) return CGP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
+    if (c->prm.projection != 0) {
+        // incremental forms: pressure term of p^n, momentum, restriction, Poisson for the
+        // increment (its own extrapolated history), correction by the increment, p += phi (- mu chi)
+        CK(launch_pressure_term(c, pc_dev, s));
+        CK(launch_assemble_step(c, u_dev, s, c->grad_n));
+        CK(launch_momentum_bicgstab(c, u_dev, c->ut, s));
+        CK(launch_restrict_rhs(c, c->ut, c->bc, s));
+        if (c->prm.warm_start >= 1) CK(launch_predict(c, c->phi, s));
+        CK(launch_poisson_cg(c, c->bc, c->phi, s));
+        CK(launch_prolong(c, c->phi, c->pf, s));
+        CK(launch_gradient(c, c->pf, c->grad, s));
+        CK(mass_stage(c, s));
+        CK(launch_correct(c, c->ut, c->w, u_dev, nullptr, s));
+        CK(launch_pressure_update(c, c->bc, c->phi, pc_dev, s));
+        return CGP_OK;
+    }
     CK(launch_assemble_step(c, u_dev, s));
     CK(launch_momentum_bicgstab(c, u_dev, c->ut, s));
     CK(launch_restrict_rhs(c, c->ut, c->bc, s));
@@ -522,6 +613,76 @@ int cgp_autotune(cgp_ctx c, void* stream) {
             if (c->prm.spmv_format == 0) c->spmv_sell = t / 20 < best;
         }
     }
+    // fine-mesh solvers: the layout (CSR with the chosen lanes, or sliced ELL) and the threads per
+    // block of their persistent kernels, timed on the consistent-mass CG (the same kernel family
+    // and pattern as the momentum solve) from a zero guess on a fixed right-hand side
+    if (c->prm.solver_format == 0 || c->prm.block_threads == 0) {
+        const bool fmts[2] = {false, true};
+        const int thr[2] = {c->sh_f.threads, 256};
+        double* b = c->grad;
+        double* x = c->ut;
+        k_fill_wave<<<(2 * c->nf + 255) / 256, 256, 0, s>>>(2 * (size_t)c->nf, b);
+        CK(cudaGetLastError());
+        float best = 1e30f;
+        bool best_ell = c->ell_on;
+        int best_thr = c->sh_f.threads;
+        const Shape keep = c->sh_f;
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        for (int fi = 0; fi < 2; ++fi) {
+            if (c->prm.solver_format != 0 && fmts[fi] != (c->prm.solver_format == 1)) continue;
+            for (int ti = 0; ti < 2; ++ti) {
+                if (ti == 1 && (thr[1] == thr[0] || c->prm.block_threads != 0)) continue;
+                c->ell_on = fmts[fi];
+                c->sh_f.threads = thr[ti];
+                float tot = 0.f;
+                for (int rep = 0; rep < 4; ++rep) {
+                    CK(cudaMemsetAsync(x, 0, 2 * sizeof(double) * (size_t)c->nf, s));
+                    CK(cudaEventRecord(e0, s));
+                    CK(launch_mass_cg(c, b, x, s));
+                    CK(cudaEventRecord(e1, s));
+                    CK(cudaEventSynchronize(e1));
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    if (rep > 0) tot += t;
+                }
+                if (tot < best) {
+                    best = tot;
+                    best_ell = fmts[fi];
+                    best_thr = thr[ti];
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->sh_f = keep;
+        c->sh_f.threads = best_thr;
+        c->ell_on = best_ell;
+        CK(cudaMemset(c->stats, 0, sizeof(DevStats)));
+    }
+    return CGP_OK;
+}
+
+int cgp_poisson_solve_many(cgp_ctx c, int nrhs, const double* b_dev, double* x_dev, int* iters_dev, double* rel_dev,
+                           int* status_dev, void* stream) {
+    if (!c || nrhs <= 0 || !b_dev || !x_dev) return CGP_ERR_ARG;
+    if (!c->bc_set) return CGP_ERR_STATE;
+    return many_solve(c, nrhs, b_dev, x_dev, iters_dev, rel_dev, status_dev, (cudaStream_t)stream);
+}
+
+int cgp_wait_probe(cgp_ctx c, int missing, double limit_ms, int* status_dev, void* stream) {
+    if (!c || !status_dev || missing < 0 || missing > 1024 || !(limit_ms > 0.0) || limit_ms > 10000.0)
+        return CGP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    SyncWords* sw = c->sync + SYNC_ASM;
+    CK(cudaMemsetAsync(sw, 0, sizeof(SyncWords), s));
+    CK(cudaMemsetAsync(status_dev, 0, sizeof(int), s));
+    const int blocks = std::max(1, c->sh_f.blocks);
+    unsigned int expect = (unsigned int)(blocks + missing);
+    unsigned long long ns = (unsigned long long)(limit_ms * 1e6);
+    void* kargs[] = {(void*)&sw, (void*)&expect, (void*)&ns, (void*)&status_dev};
+    CK(cudaLaunchCooperativeKernel((const void*)k_wait_probe, dim3(blocks), dim3(32), kargs, 0, s));
     return CGP_OK;
 }
 

@@ -221,26 +221,35 @@ __global__ void k_conv_elements(int t, const int* __restrict__ tri, const double
         for (int q = 0; q < 3; ++q) o[r * 3 + q] = fma(ux[r], gx[q], fma(uy[r], gy[q], S[q]));
 }
 
-// A[k] = A0[k] + the element contributions of entry k (and its FP32 copy)
+// A[k] = A0[k] + the element contributions of entry k (and its FP32 copy); with `pos`, the same
+// value also goes to the entry's slot of the solvers' sliced-ELL copies
 __global__ void k_gather_entries(int nnz, const int* __restrict__ ip, const int* __restrict__ idx,
                                  const double* __restrict__ ev, const double* __restrict__ A0, double* __restrict__ A,
-                                 float* __restrict__ A32) {
+                                 float* __restrict__ A32, const int* __restrict__ pos, double* __restrict__ Aell,
+                                 float* __restrict__ A32ell) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nnz) return;
     double v = A0[k];
     for (int m = ip[k]; m < ip[k + 1]; ++m) v += ev[idx[m]];
     A[k] = v;
     if (A32) A32[k] = (float)v;
+    if (pos) {
+        const int p = pos[k];
+        Aell[p] = v;
+        if (A32ell) A32ell[p] = (float)v;
+    }
 }
 
-// Jacobi diagonals and the right-hand side b = rho M u^n (Dirichlet rows: prescribed values);
-// with `bound`, the largest Gershgorin bound 1 + sum_j!=i |A_ij| / |A_ii| of D^-1 A over the rows
-// (from the FP32 copy; identity rows for Dirichlet components), as an atomic max of float bits
+// Jacobi diagonals and the right-hand side b = rho M u^n (Dirichlet rows: prescribed values), with
+// `gpn` (incremental forms) b = rho M u^n - dt gpn, gpn = G_f P p_c^n; with `bound`, the largest
+// Gershgorin bound 1 + sum_j!=i |A_ij| / |A_ii| of D^-1 A over the rows (from the FP32 copy;
+// identity rows for Dirichlet components), as an atomic max of float bits
 __global__ void k_rows(int nf, const int* __restrict__ rp, const int* __restrict__ ci, const int* __restrict__ diag,
                        const double* __restrict__ A, const float* __restrict__ A32, const double* __restrict__ M,
                        const double* __restrict__ u, const unsigned char* __restrict__ mask,
                        const double* __restrict__ g, double rho, double* __restrict__ dinv,
-                       float* __restrict__ dinv32, double* __restrict__ b, unsigned int* __restrict__ bound) {
+                       float* __restrict__ dinv32, double* __restrict__ b, unsigned int* __restrict__ bound,
+                       const double* __restrict__ gpn, double dt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float gmax = 1.f;
     if (i < nf) {
@@ -259,9 +268,15 @@ __global__ void k_rows(int nf, const int* __restrict__ rp, const int* __restrict
             my += M[k] * ujy;
             if (bound && k != kd) off += fabsf(A32[k]);
         }
-        double gx, gy;
+        double gx, gy, bx = rho * mx, by = rho * my;
+        if (gpn) {
+            double px, py;
+            load2(gpn, i, px, py);
+            bx -= dt * px;
+            by -= dt * py;
+        }
         load2(g, i, gx, gy);
-        store2(b, i, (m & CGP_BC_U) ? gx : rho * mx, (m & CGP_BC_V) ? gy : rho * my);
+        store2(b, i, (m & CGP_BC_U) ? gx : bx, (m & CGP_BC_V) ? gy : by);
         if (bound && (m & (CGP_BC_U | CGP_BC_V)) != (CGP_BC_U | CGP_BC_V))
             gmax = 1.f + off / fabsf(A32[kd]);
     }
@@ -299,15 +314,16 @@ int assemble_gather_build(cgp_ctx_s* c) {
     return CGP_OK;
 }
 
-cudaError_t launch_assemble_step(cgp_ctx_s* c, const double* u, cudaStream_t s) {
+cudaError_t launch_assemble_step(cgp_ctx_s* c, const double* u, cudaStream_t s, const double* gpn) {
     const int t = c->EF.t, nnz = c->F.nnz, nf = c->nf;
     unsigned int* bound = c->prm.momentum_degree >= 2 ? c->mom_bound : nullptr;
     k_conv_elements<<<(t + 255) / 256, 256, 0, s>>>(t, c->EF.tri, c->EF.conv, u, c->asm_ev, bound);
     k_gather_entries<<<(nnz + 255) / 256, 256, 0, s>>>(nnz, c->asm_ip, c->asm_idx, c->asm_ev, c->A0, c->A,
-                                                      c->fp32_A ? c->A32 : nullptr);
+                                                      c->fp32_A ? c->A32 : nullptr, c->ell_on ? c->ell_pos : nullptr,
+                                                      c->ell_A, c->fp32_A ? c->ell_A32 : nullptr);
     k_rows<<<(nf + 255) / 256, 256, 0, s>>>(nf, c->F.rp, c->F.ci, c->F.diag, c->A, c->A32, c->M, u, c->vel_mask,
                                           c->g, c->prm.rho, c->dinvA, c->fp32_A ? c->dinvA32 : nullptr, c->b_mom,
-                                          bound);
+                                          bound, gpn, c->prm.dt);
     return cudaGetLastError();
 }
 

@@ -99,6 +99,7 @@ int create_impl(cgp_ctx* ctxs, int n, double* const* u, double* const* pc, cgp_b
         if (!ctxs[i]->bc_set) return CGP_ERR_STATE;
         if (ctxs[i]->prm.precision != b->precision) return CGP_ERR_ARG;
         if (ctxs[i]->device != ctxs[0]->device) return CGP_ERR_ARG;
+        if (ctxs[i]->prm.projection != 0) return CGP_ERR_ARG;   // incremental forms: single contexts only
     }
     const int sms = ctxs[0]->num_sms;
     const int bps = std::min(2, persistent_blocks_per_sm(b->threads, true));

@@ -5,11 +5,17 @@
 #include <stdint.h>
 #include "cgp.h"
 
+#ifndef CGP_BARRIER_TIMEOUT_NS
+// Wall-clock bound of one grid-barrier wait before it gives up with CGP_ERR_TIMEOUT: 250 ms,
+// read from the GPU's global nanosecond timer every 32 polls. A barrier of a healthy persistent
+// launch completes within microseconds (every block is co-resident by the cooperative launch),
+// so the bound only ends a wait that can never complete.
+#define CGP_BARRIER_TIMEOUT_NS 250000000ull
+#endif
 #ifndef CGP_BARRIER_SPIN_LIMIT
-// Upper bound on polls of one grid barrier before it gives up with CGP_ERR_TIMEOUT. A poll is
-// one L2 round trip (under a microsecond), with a short sleep every 32 polls once the wait has
-// passed a few milliseconds, so the bound is some tens of seconds of wall time.
-#define CGP_BARRIER_SPIN_LIMIT (1u << 25)
+// Backstop on the number of polls (one L2 round trip each, with a short sleep every 32 polls
+// once the wait is long): the time bound above normally ends the wait long before this.
+#define CGP_BARRIER_SPIN_LIMIT (1u << 24)
 #endif
 
 namespace cgp {
@@ -36,16 +42,26 @@ __device__ __forceinline__ void red_release_add_u32(unsigned int* p, unsigned in
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Bounded wait of thread 0 until the arrival counter reaches `target`: polls with acquire loads
-// and, every 32 polls, looks for an error raised by another block and counts against
-// CGP_BARRIER_SPIN_LIMIT. Returns 0 on an error or when it gives up (then it records
-// CGP_ERR_TIMEOUT), 1 once every block has arrived.
-__device__ __forceinline__ int grid_poll(SyncWords* sw, unsigned int target) {
+// and, every 32 polls, looks for an error raised by another block and checks the elapsed time
+// against `limit_ns` (and the poll count against CGP_BARRIER_SPIN_LIMIT). Returns 0 on an error
+// or when it gives up (then it records CGP_ERR_TIMEOUT), 1 once every block has arrived.
+__device__ __forceinline__ int grid_poll(SyncWords* sw, unsigned int target,
+                                         unsigned long long limit_ns = CGP_BARRIER_TIMEOUT_NS) {
     unsigned int spins = 0;
+    unsigned long long t0 = 0;
     while (ld_acquire_u32(&sw->count) < target) {
         if ((++spins & 31u) == 0) {
             if (ld_relaxed_i32(&sw->err) != 0) return 0;
-            if (spins > CGP_BARRIER_SPIN_LIMIT) {
+            const unsigned long long now = global_ns();
+            if (t0 == 0) t0 = now;
+            if (now - t0 > limit_ns || spins > CGP_BARRIER_SPIN_LIMIT) {
                 atomicCAS(&sw->err, 0, CGP_ERR_TIMEOUT);
                 return 0;
             }
@@ -60,9 +76,9 @@ __device__ __forceinline__ int grid_poll(SyncWords* sw, unsigned int target) {
 // earlier writes, which the block barrier made visible to thread 0, before the arrival) and polls
 // with acquire loads (they order the block's later reads after every arrival, again through the
 // trailing block barrier); no further fence is needed. The poll is bounded: after
-// CGP_BARRIER_SPIN_LIMIT polls, or as soon as another block has raised an error, it returns false
-// (and records CGP_ERR_TIMEOUT if it was the one to give up). Callers must stop their work and
-// return when it is false. `epoch` is thread 0's count of barriers passed.
+// CGP_BARRIER_TIMEOUT_NS of waiting, or as soon as another block has raised an error, it returns
+// false (and records CGP_ERR_TIMEOUT if it was the one to give up). Callers must stop their work
+// and return when it is false. `epoch` is thread 0's count of barriers passed.
 __device__ __forceinline__ bool grid_sync(SyncWords* sw, unsigned int nblocks, unsigned int& epoch) {
     __shared__ int s_ok;
     __syncthreads();
@@ -362,6 +378,17 @@ __device__ __forceinline__ RowRange block_rows(int n) {
 __device__ __forceinline__ RowRange group_rows(int n, const Grp& g) {
     const long long per = ((long long)n + g.nb - 1) / g.nb;
     long long r0 = per * g.bid, r1 = r0 + per;
+    if (r0 > n) r0 = n;
+    if (r1 > n) r1 = n;
+    return {(int)r0, (int)r1};
+}
+
+// Rows owned by a block of a block group when rows go in 32-row slices (the sliced-ELL layout):
+// whole slices per block, so every slice's rows belong to one block.
+__device__ __forceinline__ RowRange group_rows_aligned(int n, const Grp& g) {
+    const long long ns = ((long long)n + 31) >> 5;
+    const long long per = (ns + g.nb - 1) / g.nb;
+    long long r0 = per * g.bid * 32, r1 = r0 + per * 32;
     if (r0 > n) r0 = n;
     if (r1 > n) r1 = n;
     return {(int)r0, (int)r1};

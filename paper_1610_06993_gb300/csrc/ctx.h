@@ -53,6 +53,18 @@ struct TwoLevel {
     float *val32 = nullptr, *dinv32 = nullptr, *fxy32 = nullptr, *ainv32 = nullptr;
 };
 
+// Workspace of the multi-right-hand-side coarse solve (cgp_poisson_solve_many): one block per
+// right-hand side, up to `wave` right-hand sides per cooperative launch.
+struct ManyRhs {
+    int wave = 0;               // right-hand sides per launch (resident blocks of the kernel)
+    size_t per_rhs = 0;         // workspace bytes per right-hand side
+    void* ws = nullptr;         // [wave][per_rhs]
+    void* tab = nullptr;        // [wave] kernel arguments, filled on the device per launch
+    int* stats = nullptr;       // [wave][8] iteration count, outer passes, status, barrier, rel (2 ints)
+    int *map_ib = nullptr, *map_b0 = nullptr, *map_nb = nullptr;   // identity block-group map
+    size_t smem = 0;
+};
+
 }  // namespace cgp
 
 struct cgp_ctx_s {
@@ -138,6 +150,33 @@ struct cgp_ctx_s {
     double* sell_val = nullptr;  // A0 values in SELL slot order
     bool spmv_sell = false;      // cgp_spmv uses the SELL kernel (cgp_autotune decides)
 
+    // sliced ELL of the fine pattern in the natural row order (32-row slices, slot k of a slice's
+    // rows contiguous), the layout of the fine-mesh Krylov solvers' products when ell_on
+    bool ell_on = false;
+    int ell_nslices = 0, ell_total = 0;
+    int *ell_ptr = nullptr, *ell_col = nullptr, *ell_pos = nullptr;   // ell_pos: CSR entry -> slot
+    int* ell_src = nullptr;                                            // slot -> CSR entry or -1
+    double *ell_A = nullptr, *ell_M = nullptr;
+    float *ell_A32 = nullptr, *ell_M32 = nullptr;
+
+    // Galerkin restriction (restrict_mode 1): per level k the inverse child lists of the s^p
+    // table (for each level-k node the finer nodes whose (beta, gamma) pair contains it) and the
+    // fine divergence D_f u~_f
+    std::vector<int*> gal_ptr, gal_idx;
+    double* gal_div = nullptr;   // [nf]
+    // incremental / rotational pressure correction (projection 1, 2)
+    double* grad_n = nullptr;    // [nf][2] G_f P p_c^n, the momentum right-hand side's pressure term
+    double* phi = nullptr;       // [nc] the pressure increment of the latest step
+    double* mlump_c = nullptr;   // [nc] lumped coarse mass (row sums of the coarse P1 mass matrix)
+
+    // diagnostic surfaces (cgp_set_surface): 0 the body of cgp_body_force, 1 the wall of
+    // cgp_reattachment; boundary edges (a, b, owning fine triangle) and the wall's shear scratch
+    struct Surface {
+        int n = 0;
+        int4* e = nullptr;
+        double* xs = nullptr;    // [2 n]: edge midpoints x, then shear
+    } surf[2];
+
     cgp::Shape sh_f, sh_c;       // persistent shapes for fine and coarse problems
     int width_c = 0;             // longest coarse CSR row
     bool use_pipe = false;       // coarse Poisson on an on-chip CG kernel
@@ -160,6 +199,7 @@ struct cgp_ctx_s {
     std::vector<double> sz_fxy_h;
     size_t sz_smem = 0;
     cgp::TwoLevel tl;            // batched two-level coarse CG
+    cgp::ManyRhs many;           // multi-right-hand-side coarse solve
     std::vector<void*> allocs;   // everything to free
 };
 
@@ -204,6 +244,9 @@ int twolevel_build(cgp_ctx_s* c);
 bool batch_poisson2l_build(cgp_batch_s* b);
 cudaError_t batch_poisson2l_launch(cgp_batch_s* b, cudaStream_t s);
 int persistent_blocks_per_sm(int threads, bool batch);
+int many_prepare(cgp_ctx_s* c);
+int many_solve(cgp_ctx_s* c, int nrhs, const double* b, double* x, int* iters, double* rel, int* status,
+               cudaStream_t s);
 
 // assemble.cu
 cudaError_t launch_geometry(const double* xy, const int* tri, int t, double* geo, cudaStream_t s);
@@ -211,7 +254,7 @@ cudaError_t launch_conv_scale(const double* geo, int t, double dtrho, double* co
 cudaError_t launch_const_assembly(const DevElems& E, double* M, double* K, double* Dxy, cudaStream_t s);
 cudaError_t launch_apply_pressure_bc(cgp_ctx_s* c, cudaStream_t s);
 cudaError_t launch_make_A0(cgp_ctx_s* c, const double* K, cudaStream_t s);
-cudaError_t launch_assemble_step(cgp_ctx_s* c, const double* u, cudaStream_t s);
+cudaError_t launch_assemble_step(cgp_ctx_s* c, const double* u, cudaStream_t s, const double* gpn = nullptr);
 cudaError_t launch_assemble_step_coloured(cgp_ctx_s* c, const double* u, cudaStream_t s);
 int assemble_gather_build(cgp_ctx_s* c);
 
@@ -223,6 +266,7 @@ cudaError_t time_spmv_lanes(cgp_ctx_s* c, bool fine, int lanes, cudaStream_t s, 
 cudaError_t launch_spmv_fine(cgp_ctx_s* c, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_spmv_sell(cgp_ctx_s* c, const double* x, double* y, cudaStream_t s);
 cudaError_t sell_fill(cgp_ctx_s* c, const double* csr_val, cudaStream_t s);
+cudaError_t ell_fill(int total, const int* src, const double* csr_val, double* val, float* val32, cudaStream_t s);
 
 // krylov_pipe.cu
 bool pipe_shape(int n, int width, int num_sms, size_t elem, int* blocks, int* threads, size_t* smem);
@@ -237,6 +281,10 @@ cudaError_t launch_gradient(cgp_ctx_s* c, const double* pf, double* grad, cudaSt
 cudaError_t launch_correct(cgp_ctx_s* c, const double* ut, const double* w, double* u, double* gp_out,
                            cudaStream_t s);
 cudaError_t launch_copy_pairs(const double* src, double* dst, int n, cudaStream_t s);
+cudaError_t launch_pressure_term(cgp_ctx_s* c, const double* pc, cudaStream_t s);
+cudaError_t launch_pressure_update(cgp_ctx_s* c, const double* bc, const double* phi, double* pc, cudaStream_t s);
+cudaError_t launch_lumped_mass(cgp_ctx_s* c, double* tmp_nnzc, cudaStream_t s);
+int galerkin_build(cgp_ctx_s* c);
 cudaError_t launch_predict(cgp_ctx_s* c, double* pc, cudaStream_t s);
 cudaError_t launch_predict_vec(const double* in, double* out, double* prev, double* prev2, double* prev3, int* flag,
                                int n, int order, cudaStream_t s);

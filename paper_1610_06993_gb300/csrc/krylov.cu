@@ -59,7 +59,7 @@ CgArgs<TI> poisson_args(cgp_ctx_s* c, const double* b, double* x, SyncWords* sw,
 }
 
 template <typename TI>
-CgArgs<TI> mass_args(cgp_ctx_s* c, const double* b, double* x, SyncWords* sw, double* part) {
+CgArgs<TI> mass_args(cgp_ctx_s* c, const double* b, double* x, SyncWords* sw, double* part, bool ell) {
     const bool mixed = sizeof(TI) == sizeof(float);
     const size_t n2 = 2 * (size_t)c->nf;
     char* p = (char*)c->ws;
@@ -84,11 +84,18 @@ CgArgs<TI> mass_args(cgp_ctx_s* c, const double* b, double* x, SyncWords* sw, do
         a.dinvP = c->dinvM32;
         a.zc0 = carve<float>(p, n2); a.zc1 = carve<float>(p, n2); a.dc = carve<float>(p, n2);
     }
+    if (ell) {
+        a.eptr = c->ell_ptr;
+        a.ecol = c->ell_col;
+        a.eval64 = c->ell_M;
+        a.evalI = mixed ? (const TI*)(const void*)c->ell_M32 : (const TI*)(const void*)c->ell_M;
+        a.evalP = c->ell_M32;
+    }
     return a;
 }
 
 template <typename TI>
-BicgArgs<TI> momentum_args(cgp_ctx_s* c, const double* u_in, double* x, SyncWords* sw, double* part) {
+BicgArgs<TI> momentum_args(cgp_ctx_s* c, const double* u_in, double* x, SyncWords* sw, double* part, bool ell) {
     const bool mixed = sizeof(TI) == sizeof(float);
     const size_t n2 = 2 * (size_t)c->nf;
     char* p = (char*)c->ws;
@@ -118,6 +125,13 @@ BicgArgs<TI> momentum_args(cgp_ctx_s* c, const double* u_in, double* x, SyncWord
         a.valP = c->A32;
         a.dinvP = c->dinvA32;
         a.zc0 = carve<float>(p, n2); a.zc1 = carve<float>(p, n2); a.dc = carve<float>(p, n2);
+    }
+    if (ell) {
+        a.eptr = c->ell_ptr;
+        a.ecol = c->ell_col;
+        a.eval64 = c->ell_A;
+        a.evalI = mixed ? (const TI*)(const void*)c->ell_A32 : (const TI*)(const void*)c->ell_A;
+        a.evalP = c->ell_A32;
     }
     return a;
 }
@@ -150,24 +164,30 @@ cudaError_t launch_mass_cg(cgp_ctx_s* c, const double* b, double* x, cudaStream_
     SyncWords* sw = c->sync + SYNC_MASS;
     cudaError_t e = cudaMemsetAsync(sw, 0, sizeof(SyncWords), s);
     if (e != cudaSuccess) return e;
+    const int B = c->sh_f.blocks, T = c->sh_f.threads;
     if (c->prm.precision == CGP_MIXED) {
-        auto L = single_launch(mass_args<float>(c, b, x, sw, c->part));
-        return coop_launch(k_cg<float, 2>, c->sh_f.blocks, c->sh_f.threads, L, s, cg_smem<2>(c->sh_f.threads));
+        auto L = single_launch(mass_args<float>(c, b, x, sw, c->part, c->ell_on));
+        if (c->ell_on) return coop_launch(k_cg<float, 2, 1, true>, B, T, L, s, cg_smem<2>(T));
+        return coop_launch(k_cg<float, 2>, B, T, L, s, cg_smem<2>(T));
     }
-    auto L = single_launch(mass_args<double>(c, b, x, sw, c->part));
-    return coop_launch(k_cg<double, 2>, c->sh_f.blocks, c->sh_f.threads, L, s, cg_smem<2>(c->sh_f.threads));
+    auto L = single_launch(mass_args<double>(c, b, x, sw, c->part, c->ell_on));
+    if (c->ell_on) return coop_launch(k_cg<double, 2, 1, true>, B, T, L, s, cg_smem<2>(T));
+    return coop_launch(k_cg<double, 2>, B, T, L, s, cg_smem<2>(T));
 }
 
 cudaError_t launch_momentum_bicgstab(cgp_ctx_s* c, const double* u_in, double* x, cudaStream_t s) {
     SyncWords* sw = c->sync + SYNC_MOM;
     cudaError_t e = cudaMemsetAsync(sw, 0, sizeof(SyncWords), s);
     if (e != cudaSuccess) return e;
+    const int B = c->sh_f.blocks, T = c->sh_f.threads;
     if (c->prm.precision == CGP_MIXED) {
-        auto L = single_launch(momentum_args<float>(c, u_in, x, sw, c->part));
-        return coop_launch(k_bicgstab<float>, c->sh_f.blocks, c->sh_f.threads, L, s, bicg_smem(c->sh_f.threads));
+        auto L = single_launch(momentum_args<float>(c, u_in, x, sw, c->part, c->ell_on));
+        if (c->ell_on) return coop_launch(k_bicgstab<float, 1, true>, B, T, L, s, bicg_smem(T));
+        return coop_launch(k_bicgstab<float>, B, T, L, s, bicg_smem(T));
     }
-    auto L = single_launch(momentum_args<double>(c, u_in, x, sw, c->part));
-    return coop_launch(k_bicgstab<double>, c->sh_f.blocks, c->sh_f.threads, L, s, bicg_smem(c->sh_f.threads));
+    auto L = single_launch(momentum_args<double>(c, u_in, x, sw, c->part, c->ell_on));
+    if (c->ell_on) return coop_launch(k_bicgstab<double, 1, true>, B, T, L, s, bicg_smem(T));
+    return coop_launch(k_bicgstab<double>, B, T, L, s, bicg_smem(T));
 }
 
 // ---- batched solver stages: one cooperative launch per stage for all instances ----------------
@@ -193,9 +213,9 @@ cudaError_t build_typed(cgp_batch_s* b) {
     std::vector<CgArgs<TI>> mass(b->n);
     for (int i = 0; i < b->n; ++i) {
         cgp_ctx_s* c = b->ctx[i];
-        mom[i] = momentum_args<TI>(c, b->u[i], c->ut, bsync(b, i, SYNC_MOM), bpart(b, i));
+        mom[i] = momentum_args<TI>(c, b->u[i], c->ut, bsync(b, i, SYNC_MOM), bpart(b, i), false);
         poi[i] = poisson_args<TI>(c, c->bc, b->pc[i], bsync(b, i, SYNC_POI), bpart(b, i));
-        mass[i] = mass_args<TI>(c, c->grad, c->w, bsync(b, i, SYNC_MASS), bpart(b, i));
+        mass[i] = mass_args<TI>(c, c->grad, c->w, bsync(b, i, SYNC_MASS), bpart(b, i), false);
     }
     cudaError_t e = upload_table(b, mom, &b->tab_mom);
     if (e == cudaSuccess) e = upload_table(b, poi, &b->tab_poi);
@@ -253,14 +273,17 @@ int persistent_blocks_per_sm(int threads, bool batch) {
     int m = 1 << 30, v = 0;
     const void* single[] = {(const void*)k_cg<double, 1>, (const void*)k_cg<float, 1>, (const void*)k_cg<double, 2>,
                             (const void*)k_cg<float, 2>, (const void*)k_bicgstab<double>,
-                            (const void*)k_bicgstab<float>};
+                            (const void*)k_bicgstab<float>, (const void*)k_cg<double, 2, 1, true>,
+                            (const void*)k_cg<float, 2, 1, true>, (const void*)k_bicgstab<double, 1, true>,
+                            (const void*)k_bicgstab<float, 1, true>};
     const void* batched[] = {(const void*)k_cg<double, 1, 2>, (const void*)k_cg<float, 1, 2>,
                              (const void*)k_cg<double, 2, 2>, (const void*)k_cg<float, 2, 2>,
                              (const void*)k_bicgstab<double, 2>, (const void*)k_bicgstab<float, 2>};
     const size_t smem[] = {cg_smem<1>(threads), cg_smem<1>(threads), cg_smem<2>(threads),
-                           cg_smem<2>(threads), bicg_smem(threads), bicg_smem(threads)};
+                           cg_smem<2>(threads), bicg_smem(threads), bicg_smem(threads),
+                           cg_smem<2>(threads), cg_smem<2>(threads), bicg_smem(threads), bicg_smem(threads)};
     const void* const* fns = batch ? batched : single;
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < (batch ? 6 : 10); ++k) {
         if (cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem[k]) != cudaSuccess)
             return 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, fns[k], threads, smem[k]) != cudaSuccess) return 0;
@@ -318,6 +341,24 @@ __global__ void __launch_bounds__(256) k_spmv_sell2(int nslices, const int* __re
 }
 
 }  // namespace
+
+namespace {
+__global__ void k_ell_fill(int total, const int* __restrict__ src, const double* __restrict__ csr_val, double* val,
+                           float* val32) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    const double v = src[p] >= 0 ? csr_val[src[p]] : 0.0;
+    val[p] = v;
+    if (val32) val32[p] = (float)v;
+}
+}  // namespace
+
+// Copy CSR values into sliced-ELL slot order (padding slots get 0), with an FP32 copy if asked.
+cudaError_t ell_fill(int total, const int* src, const double* csr_val, double* val, float* val32, cudaStream_t s) {
+    if (total <= 0) return cudaSuccess;
+    k_ell_fill<<<(total + 255) / 256, 256, 0, s>>>(total, src, csr_val, val, val32);
+    return cudaGetLastError();
+}
 
 cudaError_t sell_fill(cgp_ctx_s* c, const double* csr_val, cudaStream_t s) {
     k_sell_fill<<<(c->sell_total + 255) / 256, 256, 0, s>>>(c->sell_total, c->sell_src, csr_val, c->sell_val);
@@ -384,6 +425,8 @@ constexpr int NOALLOC_MAX_ROWS = 65536;
 constexpr size_t NOALLOC_VEC_BYTES = (size_t)NOALLOC_MAX_ROWS * sizeof(double);
 constexpr size_t NOALLOC_PART_BYTES = 32 * (size_t)CGP_MAX_GRID * sizeof(double);
 constexpr size_t NOALLOC_BYTES = 7 * NOALLOC_VEC_BYTES + NOALLOC_PART_BYTES + 512;
+// FP64 refinement passes of one allocation-free solve (each ends with an FP64 true residual)
+constexpr int NOALLOC_MAX_OUTER = 30;
 
 // All scratch of cgp_cg_solve_noalloc: seven vectors of NOALLOC_MAX_ROWS doubles (r, u, w, p,
 // s, d and the inverse diagonal), the per-block partial sums, the grid-barrier words and a
@@ -393,6 +436,7 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 struct NoallocStats {
     int iters, outer, status, barrier;
     double rel;
+    int arg;   // CGP_ERR_ARG when a row has no positive finite stored diagonal
 };
 
 struct NoallocDevice {
@@ -403,14 +447,32 @@ struct NoallocDevice {
 std::mutex g_noalloc_mu;
 NoallocDevice g_noalloc_dev[64];
 
+// Jacobi inverse diagonal. A row without a positive finite stored diagonal cannot belong to an
+// SPD matrix: it gets 0 (so the solve stays finite) and the call's status becomes CGP_ERR_ARG.
 __global__ void k_noalloc_dinv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                               const double* __restrict__ val, double* dinv) {
+                               const double* __restrict__ val, double* dinv, NoallocStats* st) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double d = 0.0;
     for (int k = rp[i]; k < rp[i + 1]; ++k)
         if (ci[k] == i) d = val[k];
-    dinv[i] = 1.0 / d;
+    if (d > 0.0 && d <= 1.7976931348623157e308) {
+        dinv[i] = 1.0 / d;
+    } else {
+        dinv[i] = 0.0;
+        st->arg = CGP_ERR_ARG;
+    }
+}
+
+// Folds the solve's statistics into the caller's outputs: an argument error first, then a grid
+// barrier that gave up (the solver's own status and residual are then meaningless: the residual
+// reads NaN and the iteration count is what the solver had recorded, 0 if nothing), then the
+// solver's status.
+__global__ void k_noalloc_finish(const NoallocStats* st, int* status, int* iters, double* rel) {
+    const int s = st->arg != 0 ? st->arg : (st->barrier != 0 ? st->barrier : st->status);
+    if (status) *status = s;
+    if (iters) *iters = st->iters;
+    if (rel) *rel = st->barrier != 0 ? __longlong_as_double(0x7ff8000000000000ll) : st->rel;
 }
 
 }  // namespace
@@ -452,8 +514,7 @@ extern "C" int cgp_cg_solve_noalloc(int n, const int* rp_dev, const int* ci_dev,
     NoallocStats* st = (NoallocStats*)(base + 7 * NOALLOC_VEC_BYTES + NOALLOC_PART_BYTES + 256);
     // the scratch keeps the previous call's contents: clear the barrier words and statistics
     if (cudaMemsetAsync(sw, 0, 512, s) != cudaSuccess) return CGP_ERR_CUDA;
-    if (status_dev && cudaMemsetAsync(status_dev, 0, sizeof(int), s) != cudaSuccess) return CGP_ERR_CUDA;
-    k_noalloc_dinv<<<(n + 255) / 256, 256, 0, s>>>(n, rp_dev, ci_dev, val_dev, vec[6]);
+    k_noalloc_dinv<<<(n + 255) / 256, 256, 0, s>>>(n, rp_dev, ci_dev, val_dev, vec[6], st);
     if (cudaGetLastError() != cudaSuccess) return CGP_ERR_CUDA;
     CgArgs<double> a;
     a.n = n;
@@ -475,17 +536,22 @@ extern "C" int cgp_cg_solve_noalloc(int n, const int* rp_dev, const int* ci_dev,
     a.rtol = rtol;
     a.inner_rtol = 0.0;
     a.max_iter = max_iter;
-    a.max_outer = 30;
+    a.max_outer = NOALLOC_MAX_OUTER;
     a.lanes = 4;
-    a.st_iters = iters_dev ? iters_dev : &st->iters;
+    // every statistic goes to the scratch record first, the barrier status in its own word, so a
+    // barrier failure recorded by one block is never overwritten by another block's final status
+    a.st_iters = &st->iters;
     a.st_outer = &st->outer;
-    a.st_status = status_dev ? status_dev : &st->status;
-    a.st_rel = rel_res_dev ? rel_res_dev : &st->rel;
-    a.st_barrier = status_dev ? status_dev : &st->barrier;
+    a.st_status = &st->status;
+    a.st_rel = &st->rel;
+    a.st_barrier = &st->barrier;
     const int threads = 512;
     int blocks = (n + threads - 1) / threads;
     blocks = std::max(1, std::min(std::min(blocks, nd->num_sms), CGP_MAX_GRID));
     auto La = single_launch(a);
     cudaError_t e = coop_launch(k_cg<double, 1>, blocks, threads, La, s, cg_smem<1>(threads));
+    if (e != cudaSuccess) return CGP_ERR_CUDA;
+    k_noalloc_finish<<<1, 1, 0, s>>>(st, status_dev, iters_dev, rel_res_dev);
+    e = cudaGetLastError();
     return e == cudaSuccess ? CGP_OK : CGP_ERR_CUDA;
 }

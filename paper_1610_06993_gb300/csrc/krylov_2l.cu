@@ -478,6 +478,109 @@ bool batch_poisson2l_build(cgp_batch_s* b) {
     return true;
 }
 
+// ---- many right-hand sides of one coarse matrix (cgp_poisson_solve_many) ----------------------
+namespace {
+
+// Per-right-hand-side workspace layout (256-byte carved): xp (n doubles), r u w p s d (n TI each),
+// mom (9 nsub doubles), part (32 doubles), sync words.
+template <typename TI>
+size_t many_bytes(int n, int nsub) {
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    return al(sizeof(double) * n) + 6 * al(sizeof(TI) * n) + al(sizeof(double) * 9 * nsub) + al(32 * sizeof(double)) +
+           al(sizeof(SyncWords));
+}
+
+// Arguments of right-hand side i of the launch: the context's shared template with the
+// per-right-hand-side vectors, workspace and statistics (one block per right-hand side).
+template <typename TI>
+__global__ void k_many_table(int cnt, Cg2Args<TI> tmpl, const double* b, double* x, size_t n, char* ws, size_t per,
+                             int* stats, int* rhs_iters, double* rhs_rel, int* rhs_status, int first,
+                             Cg2Args<TI>* tab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    auto al = [](size_t v) { return (v + 255) / 256 * 256; };
+    Cg2Args<TI> a = tmpl;
+    char* p = ws + (size_t)i * per;
+    a.b = b + (size_t)(first + i) * n;
+    a.x = x + (size_t)(first + i) * n;
+    a.xp = (double*)p; p += al(sizeof(double) * n);
+    a.r = (TI*)p; p += al(sizeof(TI) * n);
+    a.u = (TI*)p; p += al(sizeof(TI) * n);
+    a.w = (TI*)p; p += al(sizeof(TI) * n);
+    a.p = (TI*)p; p += al(sizeof(TI) * n);
+    a.s = (TI*)p; p += al(sizeof(TI) * n);
+    a.d = (TI*)p; p += al(sizeof(TI) * n);
+    a.mom = (double*)p; p += al(sizeof(double) * 9 * tmpl.nsub);
+    a.part = (double*)p; p += al(32 * sizeof(double));
+    a.sw = (SyncWords*)p;
+    a.sw->count = 0;
+    a.sw->err = 0;
+    int* st = stats + 8 * (size_t)i;
+    st[3] = 0;
+    a.st_iters = rhs_iters ? rhs_iters + first + i : st;
+    a.st_outer = st + 1;
+    a.st_status = rhs_status ? rhs_status + first + i : st + 2;
+    a.st_barrier = st + 3;   // one block per right-hand side: its barriers never wait
+    a.st_rel = rhs_rel ? rhs_rel + first + i : (double*)(st + 4);
+    tab[i] = a;
+}
+
+template <typename TI>
+int many_launch(cgp_ctx_s* c, int nrhs, const double* b, double* x, int* iters, double* rel, int* status,
+                cudaStream_t s) {
+    ManyRhs& m = c->many;
+    const int n = c->nc;
+    Cg2Args<TI> tmpl = cg2_args<TI>(c, x, nullptr, nullptr);
+    for (int w0 = 0; w0 < nrhs; w0 += m.wave) {
+        const int cnt = std::min(m.wave, nrhs - w0);
+        k_many_table<TI><<<(cnt + 127) / 128, 128, 0, s>>>(cnt, tmpl, b, x, (size_t)n, (char*)m.ws, m.per_rhs, m.stats,
+                                                          iters, rel, status, w0, (Cg2Args<TI>*)m.tab);
+        if (cudaGetLastError() != cudaSuccess) return CGP_ERR_CUDA;
+        Launch<Cg2Args<TI>> L;
+        L.single = Cg2Args<TI>();
+        L.table = (const Cg2Args<TI>*)m.tab;
+        L.map = {m.map_ib, m.map_b0, m.map_nb};
+        if (coop_launch(k_cg2l<TI, 2>, cnt, 2 * CG2_S, L, s, m.smem) != cudaSuccess) return CGP_ERR_CUDA;
+    }
+    return CGP_OK;
+}
+
+}  // namespace
+
+// Set-up of the multi-right-hand-side solve: the two-level structures and the per-wave workspace.
+int many_prepare(cgp_ctx_s* c) {
+    ManyRhs& m = c->many;
+    if (m.ws) return CGP_OK;
+    int st = c->tl.ready ? CGP_OK : twolevel_build(c);
+    if (st != CGP_OK) return st;
+    const bool mixed = c->prm.precision == CGP_MIXED;
+    const void* fn = mixed ? (const void*)k_cg2l<float, 2> : (const void*)k_cg2l<double, 2>;
+    m.smem = cg2_smem(2 * CG2_S, c->tl.nsub);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m.smem) != cudaSuccess)
+        return CGP_ERR_CUDA;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 2 * CG2_S, m.smem) != cudaSuccess || occ < 1)
+        return CGP_ERR_CUDA;
+    m.wave = std::min(occ * c->num_sms, CGP_MAX_GRID * 4);
+    m.per_rhs = mixed ? many_bytes<float>(c->nc, c->tl.nsub) : many_bytes<double>(c->nc, c->tl.nsub);
+    const size_t tab_bytes = (mixed ? sizeof(Cg2Args<float>) : sizeof(Cg2Args<double>)) * (size_t)m.wave;
+    std::vector<int> ib(m.wave), b0(m.wave), nb(m.wave, 1);
+    for (int i = 0; i < m.wave; ++i) ib[i] = b0[i] = i;
+    if ((st = tl_alloc(c, (char**)&m.ws, m.per_rhs * (size_t)m.wave)) || (st = tl_alloc(c, (char**)&m.tab, tab_bytes)) ||
+        (st = tl_alloc(c, &m.stats, 8 * (size_t)m.wave)) || (st = tl_upload(c, &m.map_ib, ib)) ||
+        (st = tl_upload(c, &m.map_b0, b0)) || (st = tl_upload(c, &m.map_nb, nb)))
+        return st;
+    return CGP_OK;
+}
+
+int many_solve(cgp_ctx_s* c, int nrhs, const double* b, double* x, int* iters, double* rel, int* status,
+               cudaStream_t s) {
+    int st = many_prepare(c);
+    if (st != CGP_OK) return st;
+    return c->prm.precision == CGP_MIXED ? many_launch<float>(c, nrhs, b, x, iters, rel, status, s)
+                                         : many_launch<double>(c, nrhs, b, x, iters, rel, status, s);
+}
+
 cudaError_t batch_poisson2l_launch(cgp_batch_s* b, cudaStream_t s) {
     if (b->precision == CGP_MIXED) {
         Launch<Cg2Args<float>> L;

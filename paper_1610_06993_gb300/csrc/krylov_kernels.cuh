@@ -3,83 +3,94 @@
 #pragma once
 #include "ctx.h"
 
+#ifndef CGP_ROWS_F32
+#define CGP_ROWS_F32 4        // rows in flight per thread in the FP32 CSR product
+#endif
+#ifndef CGP_ELL_CHUNK_F32
+#define CGP_ELL_CHUNK_F32 4   // slots per load group of the FP32 sliced-ELL product
+#endif
+
 namespace cgp {
 
 namespace {
 
-// CNT consecutive entries (from k) of row pair (a, b): column and value loads first, then the x
-// gathers and products; entries past a row's end are skipped per lane.
-template <int CNT, int NR, typename TV, typename TX>
-__device__ __forceinline__ void spmv_pair_chunk(int k, int ka, int na, int kb, int nbr, const int* __restrict__ ci,
-                                                const TV* __restrict__ val, const TX* x, TX& a0, TX& a1, TX& b0,
-                                                TX& b1) {
-    int ja[CNT], jb[CNT];
-    TX va[CNT], vb[CNT];
+// CNT consecutive entries (from k) of R rows (row q starts at ka[q] and has na[q] entries): all
+// column and value loads first, then the x gathers and products; entries past a row's end are
+// skipped per lane.
+template <int R, int CNT, int NR, typename TV, typename TX>
+__device__ __forceinline__ void spmv_rows_chunk(int k, const int (&ka)[R], const int (&na)[R],
+                                                const int* __restrict__ ci, const TV* __restrict__ val, const TX* x,
+                                                TX (&acc0)[R], TX (&acc1)[R]) {
+    int j[R][CNT];
+    TX v[R][CNT];
 #pragma unroll
-    for (int q = 0; q < CNT; ++q) {
-        const bool ia = k + q < na, ib = k + q < nbr;
-        ja[q] = ia ? __ldg(ci + ka + k + q) : -1;
-        va[q] = ia ? (TX)__ldg(val + ka + k + q) : (TX)0;
-        jb[q] = ib ? __ldg(ci + kb + k + q) : -1;
-        vb[q] = ib ? (TX)__ldg(val + kb + k + q) : (TX)0;
-    }
+    for (int q = 0; q < R; ++q)
 #pragma unroll
-    for (int q = 0; q < CNT; ++q) {
-        if (ja[q] >= 0) {
-            if (NR == 1) {
-                a0 += va[q] * x[ja[q]];
-            } else {
-                TX x0, x1;
-                load2(x, ja[q], x0, x1);
-                a0 += va[q] * x0;
-                a1 += va[q] * x1;
+        for (int e = 0; e < CNT; ++e) {
+            const bool in = k + e < na[q];
+            j[q][e] = in ? __ldg(ci + ka[q] + k + e) : -1;
+            v[q][e] = in ? (TX)__ldg(val + ka[q] + k + e) : (TX)0;
+        }
+#pragma unroll
+    for (int q = 0; q < R; ++q)
+#pragma unroll
+        for (int e = 0; e < CNT; ++e) {
+            if (j[q][e] >= 0) {
+                if (NR == 1) {
+                    acc0[q] += v[q][e] * x[j[q][e]];
+                } else {
+                    TX x0, x1;
+                    load2(x, j[q][e], x0, x1);
+                    acc0[q] += v[q][e] * x0;
+                    acc1[q] += v[q][e] * x1;
+                }
             }
         }
-        if (jb[q] >= 0) {
-            if (NR == 1) {
-                b0 += vb[q] * x[jb[q]];
-            } else {
-                TX x0, x1;
-                load2(x, jb[q], x0, x1);
-                b0 += vb[q] * x0;
-                b1 += vb[q] * x1;
-            }
-        }
-    }
 }
 
-// y = A x over the block's rows with one thread per row, two rows per thread in flight: row i of
-// the first half of the block's range together with row i + H of the second half, so that every
-// pass but the last has both rows in all lanes. The entries of a row pair go four at a time
-// (loads of a group before its x gathers: about three dependent memory round trips per four
-// entries instead of two per entry), and the warp stops at its longest row exactly: the FP64
-// products of a warp issue once per entry slot that some lane needs, which on a part with few
-// FP64 units per SM is what an FP64 product costs. x is written by other blocks during the
-// launch, so it is read with ordinary (coherent) loads; the matrix goes through the read-only
-// path.
-template <int NR, typename TV, typename TX, typename Emit>
+// y = A x over the block's rows with one thread per row and R rows per thread in flight: the
+// block's range is cut into R equal parts and a thread takes row i of every part at once, so that
+// every pass but the last has all R rows in all lanes. The entries of the R rows go CNT at a time
+// (all column and value loads of a group before its x gathers), and the warp stops at its longest
+// row exactly: the products of a warp issue once per entry slot that some lane needs. A product is
+// bound by the dependent column -> x round trips of a thread, so R rows in flight divide their
+// number by R. x is written by other blocks during the launch, so it is read with ordinary
+// (coherent) loads; the matrix goes through the read-only path. The single-context kernels take
+// four FP32 rows per thread (CGP_ROWS_F32), the rest two (registers).
+template <int NR, typename TV, typename TX, int R = 2, typename Emit>
 __device__ __forceinline__ void spmv_rows(RowRange rr, const int* __restrict__ rp, const int* __restrict__ ci,
                                           const TV* __restrict__ val, const TX* x, Emit emit) {
     const int T = blockDim.x;
-    const int H = (rr.r1 - rr.r0 + 1) >> 1;
-    for (int i0 = rr.r0 + threadIdx.x; i0 < rr.r0 + H; i0 += T) {
-        const int i1 = i0 + H;
-        const bool h1 = i1 < rr.r1;
-        const int ka = __ldg(rp + i0), na = __ldg(rp + i0 + 1) - ka;
-        const int kb = h1 ? __ldg(rp + i1) : 0, nbr = h1 ? __ldg(rp + i1 + 1) - kb : 0;
+    const int Q = (rr.r1 - rr.r0 + R - 1) / R;
+    for (int i0 = rr.r0 + threadIdx.x; i0 < rr.r0 + Q; i0 += T) {
+        int ka[R], na[R];
+        int mx = 0;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = i0 + q * Q;
+            const bool h = i < rr.r1;
+            ka[q] = h ? __ldg(rp + i) : 0;
+            na[q] = h ? __ldg(rp + i + 1) - ka[q] : 0;
+            mx = max(mx, na[q]);
+        }
         // the longest row among the lanes here; each lane's own rows are no longer than that
-        const int mw = (int)__reduce_max_sync(__activemask(), (unsigned)max(na, nbr));
-        TX a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+        const int mw = (int)__reduce_max_sync(__activemask(), (unsigned)mx);
+        TX a0[R], a1[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) a0[q] = a1[q] = (TX)0;
         int k = 0;
-        for (; k + 4 <= mw; k += 4) spmv_pair_chunk<4, NR, TV, TX>(k, ka, na, kb, nbr, ci, val, x, a0, a1, b0, b1);
+        for (; k + 4 <= mw; k += 4) spmv_rows_chunk<R, 4, NR, TV, TX>(k, ka, na, ci, val, x, a0, a1);
         switch (mw - k) {
-            case 3: spmv_pair_chunk<3, NR, TV, TX>(k, ka, na, kb, nbr, ci, val, x, a0, a1, b0, b1); break;
-            case 2: spmv_pair_chunk<2, NR, TV, TX>(k, ka, na, kb, nbr, ci, val, x, a0, a1, b0, b1); break;
-            case 1: spmv_pair_chunk<1, NR, TV, TX>(k, ka, na, kb, nbr, ci, val, x, a0, a1, b0, b1); break;
+            case 3: spmv_rows_chunk<R, 3, NR, TV, TX>(k, ka, na, ci, val, x, a0, a1); break;
+            case 2: spmv_rows_chunk<R, 2, NR, TV, TX>(k, ka, na, ci, val, x, a0, a1); break;
+            case 1: spmv_rows_chunk<R, 1, NR, TV, TX>(k, ka, na, ci, val, x, a0, a1); break;
             default: break;
         }
-        emit(i0, a0, a1);
-        if (h1) emit(i1, b0, b1);
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = i0 + q * Q;
+            if (i < rr.r1) emit(i, a0[q], a1[q]);
+        }
     }
 }
 
@@ -119,11 +130,104 @@ __device__ __forceinline__ void spmv_lanes(RowRange rr, const int* __restrict__ 
 
 // The product of the persistent Krylov kernels (one block per SM): one lane per row takes the
 // spmv_rows path, more lanes the group loop.
-template <int NR, typename TV, typename TX, typename Emit>
+template <int NR, typename TV, typename TX, int R = 2, typename Emit>
 __device__ __forceinline__ void spmv_block(RowRange rr, const int* __restrict__ rp, const int* __restrict__ ci,
                                            const TV* __restrict__ val, const TX* x, int lanes, Emit emit) {
-    if (lanes == 1) spmv_rows<NR, TV, TX>(rr, rp, ci, val, x, emit);
+    if (lanes == 1) spmv_rows<NR, TV, TX, R>(rr, rp, ci, val, x, emit);
     else spmv_lanes<NR, TV, TX>(rr, rp, ci, val, x, lanes, emit);
+}
+
+// CNT consecutive slots (from k) of two 32-row slices of the sliced-ELL layout (slot k of a slice's
+// rows contiguous, so every column and value load of a warp is one coalesced access): column and
+// value loads of both slices first, then the x gathers. Slice widths are warp-uniform, so the
+// bounds below never diverge. pa, pb: the lane's first slot in slices a and b.
+template <int CNT, int NR, typename TV, typename TX>
+__device__ __forceinline__ void ell_pair_chunk(int k, int pa, int wa, int pb, int wb, const int* __restrict__ col,
+                                               const TV* __restrict__ val, const TX* x, TX& a0, TX& a1, TX& b0,
+                                               TX& b1) {
+    int ja[CNT], jb[CNT];
+    TX va[CNT], vb[CNT];
+#pragma unroll
+    for (int q = 0; q < CNT; ++q) {
+        const int o = (k + q) << 5;
+        const bool ia = k + q < wa, ib = k + q < wb;
+        ja[q] = ia ? __ldcs(col + pa + o) : 0;
+        va[q] = ia ? (TX)__ldcs(val + pa + o) : (TX)0;
+        jb[q] = ib ? __ldcs(col + pb + o) : 0;
+        vb[q] = ib ? (TX)__ldcs(val + pb + o) : (TX)0;
+    }
+#pragma unroll
+    for (int q = 0; q < CNT; ++q) {
+        if (k + q < wa) {
+            if (NR == 1) {
+                a0 += va[q] * x[ja[q]];
+            } else {
+                TX x0, x1;
+                load2(x, ja[q], x0, x1);
+                a0 += va[q] * x0;
+                a1 += va[q] * x1;
+            }
+        }
+        if (k + q < wb) {
+            if (NR == 1) {
+                b0 += vb[q] * x[jb[q]];
+            } else {
+                TX x0, x1;
+                load2(x, jb[q], x0, x1);
+                b0 += vb[q] * x0;
+                b1 += vb[q] * x1;
+            }
+        }
+    }
+}
+
+// y = A x over the block's rows in the sliced-ELL layout of the natural row order: 32-row slices,
+// the slots of slice s at ptr[s] .. ptr[s + 1], slot k of its rows contiguous (padding slots hold
+// a zero value and a valid column). The block's rows are whole slices (group_rows_aligned). One
+// warp takes two slices at a time (the first half of the block's slices paired with the second),
+// one lane per row, four slots of both slices per load group: the matrix streams in 128-byte
+// (FP32, columns) or 256-byte (FP64) coalesced accesses, with the evict-first hint so the vectors
+// keep their place in L2. emit(row, acc0, acc1) runs once per row.
+template <int NR, typename TV, typename TX, typename Emit>
+__device__ __forceinline__ void spmv_ell(RowRange rr, const int* __restrict__ ptr, const int* __restrict__ col,
+                                         const TV* __restrict__ val, const TX* x, Emit emit) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int s0 = rr.r0 >> 5, s1 = (rr.r1 + 31) >> 5;
+    const int half = (s1 - s0 + 1) >> 1;
+    for (int sa = s0 + warp; sa < s0 + half; sa += nw) {
+        const int sb = sa + half;
+        const bool hb = sb < s1;
+        const int qa = __ldg(ptr + sa), wa = (__ldg(ptr + sa + 1) - qa) >> 5;
+        const int qb = hb ? __ldg(ptr + sb) : 0, wb = hb ? (__ldg(ptr + sb + 1) - qb) >> 5 : 0;
+        const int pa = qa + lane, pb = qb + lane;
+        const int mw = max(wa, wb);
+        TX a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+        // CH slots of both slices per load group (the guards inside skip slots past a slice's
+        // width, warp-uniformly); 4 measured faster than 8 on the 1M-row cylinder mesh
+        constexpr int CH = sizeof(TX) == sizeof(float) ? CGP_ELL_CHUNK_F32 : 4;
+        for (int k = 0; k < mw; k += CH) ell_pair_chunk<CH, NR, TV, TX>(k, pa, wa, pb, wb, col, val, x, a0, a1, b0, b1);
+        const int ia = (sa << 5) + lane, ib = (sb << 5) + lane;
+        if (ia < rr.r1) emit(ia, a0, a1);
+        if (hb && ib < rr.r1) emit(ib, b0, b1);
+    }
+}
+
+// The product of a persistent Krylov kernel on the layout it was compiled for: sliced ELL (ELL,
+// the launch's eptr / ecol / eval arrays) or CSR through spmv_block. One layout per instantiation
+// keeps each kernel within its register budget.
+template <bool ELL, int NR, typename TV, typename TX, int R = 2, typename Emit>
+__device__ __forceinline__ void spmv_sel(RowRange rr, const int* eptr, const int* ecol, const TV* eval,
+                                         const int* __restrict__ rp, const int* __restrict__ ci,
+                                         const TV* __restrict__ val, const TX* x, int lanes, Emit emit) {
+    if constexpr (ELL) spmv_ell<NR, TV, TX>(rr, eptr, ecol, eval, x, emit);
+    else spmv_block<NR, TV, TX, R>(rr, rp, ci, val, x, lanes, emit);
+}
+
+// Rows of the persistent kernels: whole 32-row slices per block with the sliced-ELL layout.
+template <bool ELL>
+__device__ __forceinline__ RowRange solver_rows(int n, const Grp& g) {
+    if constexpr (ELL) return group_rows_aligned(n, g);
+    else return group_rows(n, g);
 }
 
 __device__ __forceinline__ bool bad(double v) { return !(fabs(v) <= 1.7976931348623157e308); }
@@ -158,6 +262,13 @@ struct CgArgs {
     const float* valP = nullptr;    // FP32 matrix values and inverse diagonal
     const float* dinvP = nullptr;
     float *zc0 = nullptr, *zc1 = nullptr, *dc = nullptr;   // [n][NR] iterates (double buffered), direction
+    // sliced-ELL copy of the matrix (eptr != nullptr selects it for every product): slice offsets,
+    // columns, and the values matching val64, valI and valP
+    const int* eptr = nullptr;
+    const int* ecol = nullptr;
+    const double* eval64 = nullptr;
+    const TI* evalI = nullptr;
+    const float* evalP = nullptr;
 };
 
 // partial-sum regions (units of nblocks doubles)
@@ -177,9 +288,13 @@ constexpr size_t cg_smem(int threads) {
 // taken in the product w = A u.
 // MINB: resident blocks per SM the launch is compiled for: 1 for a single context (128 registers
 // per thread, no spills), 2 for batches, whose many small block groups gain more from twice the
-// threads per SM than from registers.
-template <typename TI, int NR, int MINB = 1>
+// threads per SM than from registers. ELL: products in the sliced-ELL layout (the launch's eptr,
+// ecol and eval* arrays; rows in whole 32-row slices per block) instead of CSR.
+template <typename TI, int NR, int MINB = 1, bool ELL = false>
 __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
+    // rows in flight per thread of the CSR products: more for FP32 in the single-context kernels
+    constexpr int RP = MINB == 1 ? CGP_ROWS_F32 : 2;
+    constexpr int RI = sizeof(TI) == sizeof(float) ? RP : 2;
     extern __shared__ double s_lean[];   // [3 NR][blockDim.x]
     __shared__ double s_bc[8];
     __shared__ float s_f32[32 * 3 * NR];
@@ -189,7 +304,7 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
     const CgArgs<TI>& a = L.table ? L.table[g.inst] : L.single;
     const unsigned int nb = g.nb;
     unsigned int epoch = 0;
-    const RowRange rr = group_rows(a.n, g);
+    const RowRange rr = solver_rows<ELL>(a.n, g);
     const int tpb = blockDim.x;
     double bb[NR], rr64[NR];
     int iters = 0, outer = 0, status = CGP_OK;
@@ -218,7 +333,7 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
             const float rn = 1.f / (2.f * sigmaP - rho);
             const float c1 = rn * rho, c2 = 2.f * rn / deltaP;
             if (!grid_sync(a.sw, nb, epoch)) return false;
-            spmv_block<NR, float, float>(rr, a.rp, a.ci, a.valP, zin, a.lanes, [&](int i, float s0, float s1) {
+            spmv_sel<ELL, NR, float, float, RP>(rr, a.eptr, a.ecol, a.evalP, a.rp, a.ci, a.valP, zin, a.lanes, [&](int i, float s0, float s1) {
                 const float acc[2] = {s0, s1};
                 const float di = a.dinvP[i];
 #pragma unroll
@@ -246,7 +361,7 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
             double v[3 * NR];
 #pragma unroll
             for (int k = 0; k < 3 * NR; ++k) v[k] = 0.0;
-            spmv_block<NR, double, double>(rr, a.rp, a.ci, a.val64, a.x, a.lanes, [&](int i, double s0, double s1) {
+            spmv_sel<ELL, NR, double, double, 2>(rr, a.eptr, a.ecol, a.eval64, a.rp, a.ci, a.val64, a.x, a.lanes, [&](int i, double s0, double s1) {
                 const double acc[2] = {s0, s1};
                 const TI di = a.dinvI[i];
 #pragma unroll
@@ -307,7 +422,7 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
             TI vv[2 * NR];
 #pragma unroll
             for (int c = 0; c < 2 * NR; ++c) vv[c] = (TI)0;
-            spmv_block<NR, TI, TI>(rr, a.rp, a.ci, a.valI, a.u, a.lanes, [&](int i, TI s0, TI s1) {
+            spmv_sel<ELL, NR, TI, TI, RI>(rr, a.eptr, a.ecol, a.evalI, a.rp, a.ci, a.valI, a.u, a.lanes, [&](int i, TI s0, TI s1) {
                 const TI acc[2] = {s0, s1};
 #pragma unroll
                 for (int c = 0; c < NR; ++c) {
@@ -406,7 +521,7 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
             if (poly && !poly_apply()) return record_failure(a.sw, a.st_barrier);
             if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
             // ---- w = A u; (r, u), (r, r), (w, u) in one reduction
-            spmv_block<NR, TI, TI>(rr, a.rp, a.ci, a.valI, a.u, a.lanes, [&](int i, TI s0, TI s1) {
+            spmv_sel<ELL, NR, TI, TI, RI>(rr, a.eptr, a.ecol, a.evalI, a.rp, a.ci, a.valI, a.u, a.lanes, [&](int i, TI s0, TI s1) {
                 const TI acc[2] = {s0, s1};
 #pragma unroll
                 for (int c = 0; c < NR; ++c) {
@@ -537,6 +652,12 @@ struct BicgArgs {
     int* st_status;
     double* st_rel;
     int* st_barrier;
+    // sliced-ELL copy of the matrix, as in CgArgs
+    const int* eptr = nullptr;
+    const int* ecol = nullptr;
+    const double* eval64 = nullptr;
+    const TI* evalI = nullptr;
+    const float* evalP = nullptr;
 };
 
 enum { BI_P0 = 0, BI_O1 = 2, BI_B2 = 6, BI_B4 = 8 /* 10 slots */ };
@@ -557,8 +678,10 @@ constexpr size_t bicg_smem(int threads) { return (size_t)10 * threads * sizeof(d
 // With the polynomial preconditioner, y = K^-1 p and z = K^-1 s are Chebyshev iterations on
 // A y = p and A z = s from zero (pdeg - 1 products with the FP32 copy of A, a barrier before
 // each; identity rows at Dirichlet components).
-template <typename TI, int MINB = 1>
+template <typename TI, int MINB = 1, bool ELL = false>
 __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) {
+    constexpr int RP = MINB == 1 ? CGP_ROWS_F32 : 2;
+    constexpr int RI = sizeof(TI) == sizeof(float) ? RP : 2;
     extern __shared__ double s_lean[];   // [10][blockDim.x]
     __shared__ double s_bc[10];
     __shared__ float s_f32[32 * 10];
@@ -568,7 +691,7 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
     const BicgArgs<TI>& a = L.table ? L.table[g.inst] : L.single;
     const unsigned int nb = g.nb;
     unsigned int epoch = 0;
-    const RowRange rr = group_rows(a.n, g);
+    const RowRange rr = solver_rows<ELL>(a.n, g);
     const int tpb = blockDim.x;
     double bb[2], rr64[2] = {0.0, 0.0};
     int iters = 0, outer = 0, status = CGP_OK;
@@ -597,7 +720,7 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
             const float rn = 1.f / (2.f * sigmaP - rho);
             const float c1 = rn * rho, c2 = 2.f * rn / deltaP;
             if (!grid_sync(a.sw, nb, epoch)) return false;
-            spmv_block<2, float, float>(rr, a.rp, a.ci, a.valP, zin, a.lanes, [&](int i, float s0, float s1) {
+            spmv_sel<ELL, 2, float, float, RP>(rr, a.eptr, a.ecol, a.evalP, a.rp, a.ci, a.valP, zin, a.lanes, [&](int i, float s0, float s1) {
                 const unsigned char m = a.mask[i];
                 float z0, z1, d0, d1, i0, i1;
                 load2(zin, i, z0, z1);
@@ -670,7 +793,7 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
         double t1[4];
         {
             double v[4] = {0.0, 0.0, 0.0, 0.0};
-            spmv_block<2, double, double>(rr, a.rp, a.ci, a.val64, a.x, a.lanes, [&](int i, double s0, double s1) {
+            spmv_sel<ELL, 2, double, double, 2>(rr, a.eptr, a.ecol, a.eval64, a.rp, a.ci, a.val64, a.x, a.lanes, [&](int i, double s0, double s1) {
                 const double acc[2] = {s0, s1};
                 const unsigned char m = a.mask[i];
 #pragma unroll
@@ -767,7 +890,7 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
             // ---- v = A y, sigma = (rh, v); alpha = rho / sigma (thread 0, broadcast)
             {
                 TI vs[2] = {(TI)0, (TI)0};
-                spmv_block<2, TI, TI>(rr, a.rp, a.ci, a.valI, a.y, a.lanes, [&](int i, TI s0, TI s1) {
+                spmv_sel<ELL, 2, TI, TI, RI>(rr, a.eptr, a.ecol, a.evalI, a.rp, a.ci, a.valI, a.y, a.lanes, [&](int i, TI s0, TI s1) {
                     const TI acc[2] = {s0, s1};
                     TI r0, r1, y0 = (TI)0, y1 = (TI)0;
                     load2(a.rh, i, r0, r1);
@@ -842,7 +965,7 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
                 TI q[10];
 #pragma unroll
                 for (int k = 0; k < 10; ++k) q[k] = (TI)0;
-                spmv_block<2, TI, TI>(rr, a.rp, a.ci, a.valI, a.z, a.lanes, [&](int i, TI s0, TI s1) {
+                spmv_sel<ELL, 2, TI, TI, RI>(rr, a.eptr, a.ecol, a.evalI, a.rp, a.ci, a.valI, a.z, a.lanes, [&](int i, TI s0, TI s1) {
                     const TI acc[2] = {s0, s1};
                     TI z0 = (TI)0, z1 = (TI)0, sv[2], hv[2];
                     const unsigned char m = a.mask[i];

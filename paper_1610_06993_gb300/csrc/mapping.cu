@@ -82,13 +82,90 @@ __global__ void k_copy_pairs(const double2* __restrict__ src, double2* __restric
     if (i < n) dst[i] = src[i];
 }
 
+// Fine divergence d_i = sum_j Dx_f[i,j] u~_x[j] + Dy_f[i,j] u~_y[j] (D_f = G_f on the fine mesh,
+// where velocity and pressure share the P1 space), one thread per row.
+__global__ void k_divergence(int nf, const int* __restrict__ rp, const int* __restrict__ ci,
+                             const double* __restrict__ Gxy, const double* __restrict__ ut, double* __restrict__ d) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    double acc = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+        double gx, gy, ux, uy;
+        load2(Gxy, k, gx, gy);
+        load2(ut, ci[k], ux, uy);
+        acc += gx * ux + gy * uy;
+    }
+    d[i] = acc;
+}
+
+// One level of P^T (the transpose of Eq. 29's prolongation): r_k[i] = r_{k+1}[i] (the
+// parent-coincident row, weight 1) + 1/2 sum over the finer nodes alpha whose pair (beta, gamma)
+// contains i of r_{k+1}[alpha], in the fixed order of the inverse child list. With `pm` (the last
+// level) the result is scaled and zeroed at pressure-held rows: b_c = scale P^T d.
+__global__ void k_restrict_transpose(int n, const int* __restrict__ ptr, const int* __restrict__ idx,
+                                     const double* __restrict__ src, double* __restrict__ dst,
+                                     const unsigned char* __restrict__ pm, double scale) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double h = 0.0;
+    for (int m = ptr[i]; m < ptr[i + 1]; ++m) h += src[idx[m]];
+    const double r = src[i] + 0.5 * h;
+    dst[i] = pm ? (pm[i] ? 0.0 : scale * r) : r;
+}
+
+// Fine divergence scaled straight into b_c (no refinement: P = I).
+__global__ void k_scale_mask(int n, const double* __restrict__ src, const unsigned char* __restrict__ pm,
+                             double scale, double* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = pm[i] ? 0.0 : scale * src[i];
+}
+
+// Incremental forms: p += phi, and with the rotational term also - mu chi where
+// chi = -(dt/rho) b_c / m_i (m the lumped coarse mass), i.e. p += phi + c b_c / m_i, c = mu dt / rho.
+__global__ void k_pressure_update(int n, const double* __restrict__ bc, const double* __restrict__ phi,
+                                  const double* __restrict__ m, double c, double* __restrict__ p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = p[i] + phi[i];
+    if (m) v += c * bc[i] / m[i];
+    p[i] = v;
+}
+
+// Row sums of a CSR matrix (the lumped mass from the assembled coarse mass matrix).
+__global__ void k_row_sums(int n, const int* __restrict__ rp, const double* __restrict__ val, double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) s += val[k];
+    out[i] = s;
+}
+
 }  // namespace
 
 cudaError_t launch_restrict_rhs(cgp_ctx_s* c, const double* ut, double* bc, cudaStream_t s) {
+    const double scale = -(c->prm.rho / c->prm.dt);
+    if (c->prm.restrict_mode == 1) {
+        // b_c = -(rho/dt) P^T D_f u~_f: fine divergence, then P^T from the finest level down
+        k_divergence<<<(c->nf + 255) / 256, 256, 0, s>>>(c->nf, c->F.rp, c->F.ci, c->Gxy, ut, c->gal_div);
+        if (c->levels == 0) {
+            k_scale_mask<<<(c->nc + 255) / 256, 256, 0, s>>>(c->nc, c->gal_div, c->p_mask, scale, bc);
+            return cudaGetLastError();
+        }
+        const double* src = c->gal_div;
+        for (int k = c->levels - 1; k >= 0; --k) {
+            const int n = c->lv_n[k];
+            const bool last = k == 0;
+            double* dst = last ? bc : c->pl[k - 1];   // pl[k - 1] holds N_k values
+            k_restrict_transpose<<<(n + 255) / 256, 256, 0, s>>>(n, c->gal_ptr[k], c->gal_idx[k], src, dst,
+                                                                last ? c->p_mask : nullptr, scale);
+            src = dst;
+        }
+        return cudaGetLastError();
+    }
     const int lanes = c->sh_c.lanes, threads = 256;
     const long long tot = (long long)c->nc * lanes;
     k_restrict_rhs<<<(int)((tot + threads - 1) / threads), threads, 0, s>>>(
-        c->nc, c->C.rp, c->cif_su, c->Dc_xy, ut, c->p_mask, -(c->prm.rho / c->prm.dt), bc, lanes);
+        c->nc, c->C.rp, c->cif_su, c->Dc_xy, ut, c->p_mask, scale, bc, lanes);
     return cudaGetLastError();
 }
 
@@ -216,4 +293,86 @@ cudaError_t launch_copy_pairs(const double* src, double* dst, int n, cudaStream_
     return cudaGetLastError();
 }
 
+// G_f P p_c into grad_n: the pressure term of the incremental forms' momentum right-hand side.
+cudaError_t launch_pressure_term(cgp_ctx_s* c, const double* pc, cudaStream_t s) {
+    cudaError_t e = launch_prolong(c, pc, c->pf, s);
+    if (e != cudaSuccess) return e;
+    return launch_gradient(c, c->pf, c->grad_n, s);
+}
+
+cudaError_t launch_pressure_update(cgp_ctx_s* c, const double* bc, const double* phi, double* pc, cudaStream_t s) {
+    const bool rot = c->prm.projection == 2;
+    k_pressure_update<<<(c->nc + 255) / 256, 256, 0, s>>>(c->nc, bc, phi, rot ? c->mlump_c : nullptr,
+                                                          c->prm.mu * c->prm.dt / c->prm.rho, pc);
+    return cudaGetLastError();
+}
+
+// Lumped coarse mass: the coarse P1 mass matrix assembled into tmp (nnz_c doubles, zeroed here),
+// then its row sums.
+cudaError_t launch_lumped_mass(cgp_ctx_s* c, double* tmp, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(double) * (size_t)c->C.nnz, s);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_const_assembly(c->EC, tmp, nullptr, nullptr, s)) != cudaSuccess) return e;
+    k_row_sums<<<(c->nc + 255) / 256, 256, 0, s>>>(c->nc, c->C.rp, tmp, c->mlump_c);
+    return cudaGetLastError();
+}
+
+// Inverse child lists of the s^p tables (host, once per context): for level k, node i of level k
+// lists the nodes alpha >= N_k of level k + 1 whose pair (beta, gamma) contains i, in increasing
+// alpha (a node with beta = gamma = i only is the parent-coincident row, taken with weight 1).
+int galerkin_build(cgp_ctx_s* c) {
+    const HostMesh& H = c->hm;
+    for (int k = 0; k < c->levels; ++k) {
+        const int nk = H.lv[k].n, nk1 = H.lv[k + 1].n;
+        const std::vector<int>& sp = H.sp[k];   // [nk1][2]
+        std::vector<int> ptr(nk + 1, 0), idx;
+        for (int a = nk; a < nk1; ++a) {
+            ptr[sp[2 * a] + 1] += 1;
+            ptr[sp[2 * a + 1] + 1] += 1;
+        }
+        for (int i = 0; i < nk; ++i) ptr[i + 1] += ptr[i];
+        idx.assign(ptr[nk], 0);
+        std::vector<int> pos(ptr.begin(), ptr.end() - 1);
+        for (int a = nk; a < nk1; ++a) {
+            idx[pos[sp[2 * a]]++] = a;
+            idx[pos[sp[2 * a + 1]]++] = a;
+        }
+        void *dp = nullptr, *di = nullptr;
+        if (cudaMalloc(&dp, sizeof(int) * ptr.size()) != cudaSuccess) return CGP_ERR_NOMEM;
+        c->allocs.push_back(dp);
+        if (cudaMalloc(&di, sizeof(int) * std::max<size_t>(1, idx.size())) != cudaSuccess) return CGP_ERR_NOMEM;
+        c->allocs.push_back(di);
+        if (cudaMemcpy(dp, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            (!idx.empty() && cudaMemcpy(di, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice) != cudaSuccess))
+            return CGP_ERR_CUDA;
+        c->gal_ptr.push_back((int*)dp);
+        c->gal_idx.push_back((int*)di);
+    }
+    return CGP_OK;
+}
+
+namespace {
+// out = the extrapolation in time of order k through v0 (newest) .. vk: 2 v0 - v1, 3 v0 - 3 v1 + v2,
+// 4 v0 - 6 v1 + 4 v2 - v3 (the predictors of k_predict, without a history)
+__global__ void k_extrapolate(size_t n, int order, const double* __restrict__ v0, const double* __restrict__ v1,
+                              const double* __restrict__ v2, const double* __restrict__ v3, double* __restrict__ out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double o = v0[i];
+    if (order >= 3) o = 4.0 * (v0[i] + v2[i]) - 6.0 * v1[i] - v3[i];
+    else if (order == 2) o = fma(3.0, v0[i] - v1[i], v2[i]);
+    else if (order == 1) o = 2.0 * v0[i] - v1[i];
+    out[i] = o;
+}
+}  // namespace
+
 }  // namespace cgp
+
+extern "C" int cgp_extrapolate(long long n, int order, const double* v0, const double* v1, const double* v2,
+                               const double* v3, double* out, void* stream) {
+    if (n <= 0 || order < 0 || order > 3 || !v0 || !out) return CGP_ERR_ARG;
+    if ((order >= 1 && !v1) || (order >= 2 && !v2) || (order >= 3 && !v3)) return CGP_ERR_ARG;
+    cgp::k_extrapolate<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>((size_t)n, order, v0, v1, v2, v3,
+                                                                                      out);
+    return cudaGetLastError() == cudaSuccess ? CGP_OK : CGP_ERR_CUDA;
+}

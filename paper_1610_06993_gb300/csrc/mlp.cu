@@ -532,6 +532,32 @@ __global__ void k_to_bf16(size_t count, int C, int R, const float* __restrict__ 
     if (wt) wt[(size_t)c * R + r] = __float2bfloat16_rn(w[i]);
 }
 
+// Residual form: r[i] = b[i] - (K x_base)[i] for every right-hand side of the batch (row-major
+// [B][n], one thread per entry, the coarse CSR matrix after the elimination of held rows), and with
+// p the training target c[i] = p[i] - x_base[i].
+__global__ void k_base_residual(int B, int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                const double* __restrict__ K, const double* __restrict__ b,
+                                const double* __restrict__ base, const double* __restrict__ p, double* __restrict__ r,
+                                double* __restrict__ c) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)B * n) return;
+    const size_t r0 = i / n * n;
+    const int row = (int)(i - r0);
+    double kx = 0.0;
+    for (int k = rp[row]; k < rp[row + 1]; ++k) kx += K[k] * base[r0 + ci[k]];
+    r[i] = b[i] - kx;
+    if (p) c[i] = p[i] - base[i];
+}
+
+// Residual form output: p = x_base + S[r] Y[r][j] (x_base alone at pressure-held entries).
+__global__ void k_output_add(int B, int n, int np, const unsigned char* __restrict__ mask, const float* __restrict__ S,
+                             const float* __restrict__ Y, const double* __restrict__ base, double* p) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)B * n) return;
+    const int r = (int)(i / n), j = (int)(i % n);
+    p[i] = base[i] + (mask[j] ? 0.0 : (double)S[r] * (double)Y[(size_t)r * np + j]);
+}
+
 // p[r][j] = S[r] * Y[r][j] (0 at pressure-held entries), r < B, j < n.
 __global__ void k_output(int B, int n, int np, const unsigned char* __restrict__ mask, const float* __restrict__ S,
                          const float* __restrict__ Y, double* p) {
@@ -565,6 +591,8 @@ struct cgp_ws_s {
     float *gW1, *gb1, *gW2, *gb2, *gW3, *gb3;
     double* loss_part;
     float* loss;
+    // residual form: r = b - K_c x_base and the correction target p - x_base, [bmax][n] (lazily)
+    double *res = nullptr, *cor = nullptr;
     unsigned char *mask, *keep_n, *keep_all;
     // split-K workspace of the GEMMs with few output tiles
     float* work = nullptr;
@@ -851,6 +879,46 @@ int cgp_ws_train_step(cgp_ws w, const double* b_dev, const double* p_dev, int B,
     if (!w || !b_dev || !p_dev || B <= 0 || B > w->bmax || !(lr >= 0.0f)) return CGP_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     if (train_step(w, b_dev, p_dev, B, lr, s) != cudaSuccess) return CGP_ERR_CUDA;
+    if (loss_dev && cudaMemcpyAsync(loss_dev, w->loss, sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return CGP_ERR_CUDA;
+    return CGP_OK;
+}
+
+namespace {
+int residual_prep(cgp_ws w, cgp_ctx c, const double* b, const double* base, const double* p, int B, cudaStream_t s) {
+    if (c->nc != w->n) return CGP_ERR_ARG;
+    if (!c->bc_set) return CGP_ERR_STATE;
+    if (!w->res) {
+        int st = CGP_OK;
+        if ((st = walloc(w, &w->res, (size_t)w->bmax * w->n)) || (st = walloc(w, &w->cor, (size_t)w->bmax * w->n)))
+            return st;
+    }
+    const size_t cnt = (size_t)B * w->n;
+    k_base_residual<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(B, w->n, c->C.rp, c->C.ci, c->Kc, b, base, p, w->res,
+                                                                  w->cor);
+    return cudaGetLastError() == cudaSuccess ? CGP_OK : CGP_ERR_CUDA;
+}
+}  // namespace
+
+int cgp_ws_forward_residual(cgp_ws w, cgp_ctx c, const double* b_dev, const double* base_dev, int B, double* p_dev,
+                            void* stream) {
+    if (!w || !c || !b_dev || !base_dev || !p_dev || B <= 0 || B > w->bmax) return CGP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = residual_prep(w, c, b_dev, base_dev, nullptr, B, s);
+    if (st != CGP_OK) return st;
+    if (forward(w, w->res, nullptr, B, s) != cudaSuccess) return CGP_ERR_CUDA;
+    const size_t cnt = (size_t)B * w->n;
+    k_output_add<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(B, w->n, w->np, w->mask, w->S, w->Y, base_dev, p_dev);
+    return cudaGetLastError() == cudaSuccess ? CGP_OK : CGP_ERR_CUDA;
+}
+
+int cgp_ws_train_step_residual(cgp_ws w, cgp_ctx c, const double* b_dev, const double* p_dev, const double* base_dev,
+                               int B, float lr, float* loss_dev, void* stream) {
+    if (!w || !c || !b_dev || !p_dev || !base_dev || B <= 0 || B > w->bmax || !(lr >= 0.0f)) return CGP_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st = residual_prep(w, c, b_dev, base_dev, p_dev, B, s);
+    if (st != CGP_OK) return st;
+    if (train_step(w, w->res, w->cor, B, lr, s) != cudaSuccess) return CGP_ERR_CUDA;
     if (loss_dev && cudaMemcpyAsync(loss_dev, w->loss, sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return CGP_ERR_CUDA;
     return CGP_OK;

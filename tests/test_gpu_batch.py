@@ -129,3 +129,28 @@ def test_batch_two_level_coarse_solver(L):
         for f in flows:
             f.close()
     assert all(2 * a <= j for a, j in zip(its[0], its[5])), its
+
+
+def test_batch_workload_full_size_matches_oracle(L):
+    """The 64-cavity batch at full size (coarse sizes log-uniform in [2k, 50k], the bench's launch
+    shape) at rtol = 1e-12: a sample of eight instances spread over the size range (every eighth
+    by size, the largest included) matches the oracle's direct-solve run after 3 steps at 1e-10
+    relative L2 in u."""
+    from paper_1610_06993_gb300.flow import Batch, Flow
+    cases = ci.batch_cavities()
+    sizes = np.array([m.n_nodes for m, _ in cases])
+    order = np.argsort(sizes, kind="stable")
+    sample = [int(order[k]) for k in (0, 9, 18, 27, 36, 45, 54, 63)]
+    flows = [Flow(m, p, rtol=1e-12) for m, p in cases]
+    b = Batch(flows)
+    steps = 3
+    b.step(steps)
+    b.stats(check=True)
+    errs = {}
+    for i in sample:
+        m, p = cases[i]
+        errs[i] = rel(flows[i].u.cpu().numpy(), ocgp.run(m, p, steps).u)
+    b.close()
+    for f in flows:
+        f.close()
+    assert max(errs.values()) < 1e-10, errs
