@@ -425,9 +425,10 @@ def run_gpu(args):
     coarse, prob, _ = ci.workload(wname)
     prec = L.CGP_MIXED if args.precision == "mixed" else L.CGP_FP64
 
-    def make(precision):
+    def make(precision, coarse_solver=None):
         return Flow(coarse, prob, precision=precision, rtol=args.rtol, device=dev,
-                    block_threads=args.threads, spmv_lanes=args.lanes, coarse_solver=args.coarse_solver,
+                    block_threads=args.threads, spmv_lanes=args.lanes,
+                    coarse_solver=args.coarse_solver if coarse_solver is None else coarse_solver,
                     precond_degree=args.precond_degree, precond_ratio=args.precond_ratio,
                     **({"warm_start": args.warm_start} if args.warm_start >= 0 else {}),
                     **({"inner_rtol": args.inner_rtol} if args.inner_rtol > 0 else {}),
@@ -441,9 +442,18 @@ def run_gpu(args):
     if args.autotune:
         L.cgp_autotune(f.ctx, stream)      # lanes, fine-solver layout and threads per block
         f.info = L.cgp_mesh_info(f.ctx)
-    # developed state: args.develop steps from rest on the GPU path, outside the timed region
-    for _ in range(args.develop):
+    # developed state: args.develop steps from rest on the GPU path, outside the timed region; the
+    # coarse right-hand sides and pressures of its second half are logged for the coarse-solve
+    # throughput comparison
+    n_log = args.develop - args.develop // 2
+    B_log = torch.empty(max(n_log, 1), f.info.n_coarse, dtype=torch.float64, device=dev)
+    P_log = torch.empty_like(B_log)
+    for k in range(args.develop):
         f.step(1, stream)
+        j = k - args.develop // 2
+        if j >= 0:
+            L.cgp_copy_coarse_rhs(f.ctx, B_log[j], stream)
+            P_log[j].copy_(f.pc)
     L.cgp_get_stats(f.ctx, stream, check=True)
     for _ in range(args.warmup):
         f.step(1, stream)
@@ -472,6 +482,10 @@ def run_gpu(args):
         L.cgp_get_stats(g.ctx, stream, check=True)
         ro = timed_steps(L, g, args.steps, flush, stream)
         other = (g, ro)
+
+    coarse_tp = None
+    if args.coarse_throughput and ws == 1 and n_log >= 8:
+        coarse_tp = coarse_throughput(L, Flow, make, f, other, B_log, P_log, stream, args)
 
     # errors against the oracle: one step of each path from the same developed state
     errors, cpu = None, None
@@ -557,6 +571,8 @@ def run_gpu(args):
                                    "iterations": {"momentum": ro["mom_it"], "poisson": ro["poi_it"],
                                                   "mass": ro["mass_it"]}}
         g.close()
+    if coarse_tp is not None:
+        line["coarse_solve_throughput"] = coarse_tp
     if errors is not None:
         line["errors_vs_oracle"] = errors
     if cpu is not None:
@@ -570,6 +586,62 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def coarse_throughput(L, Flow, make, f, other, B_log, P_log, stream, args):
+    """Coarse Poisson solves/s (Eq. 21, rtol) on the workload's own logged right-hand sides, each
+    solve started from the previous logged pressure (the same initial-guess policy in every arm)
+    and, for the plain arm, also from zero:
+      plain   - FP64 Jacobi-preconditioned CG (the paper's PCG), one solve after another;
+      default - FP64 two-level Schwarz CG (this library's single-solve kernel), one after another;
+      batched - this run's precision, all right-hand sides together (cgp_poisson_solve_many,
+                one block per right-hand side, two-level preconditioner)."""
+    import torch
+    nrhs = B_log.shape[0] - 1
+    Bs, X0 = B_log[1:].contiguous(), P_log[:-1].contiguous()
+
+    def sequential(ctx, rows, zero):
+        X = torch.zeros_like(Bs[:rows]) if zero else X0[:rows].clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its = 0
+        for k in range(rows):
+            L.cgp_poisson_solve(ctx, Bs[k], X[k], stream)
+            its += L.cgp_get_stats(ctx, stream, check=True).poisson_iters
+        e1.record(stream)
+        e1.synchronize()
+        return rows * 1000.0 / e0.elapsed_time(e1), its / rows
+
+    jac = make(L.CGP_FP64, coarse_solver=5)
+    rows_plain = min(nrhs, 8)
+    plain, plain_it = sequential(jac.ctx, rows_plain, False)
+    plain0, plain0_it = sequential(jac.ctx, rows_plain, True)
+    jac.close()
+    fp64 = other[0] if (other is not None and other[0].params.precision == L.CGP_FP64) else f
+    dflt, dflt_it = sequential(fp64.ctx, min(nrhs, 64), False)
+    X = X0.clone()
+    its = torch.zeros(nrhs, dtype=torch.int32, device=Bs.device)
+    st = torch.zeros(nrhs, dtype=torch.int32, device=Bs.device)
+    L.cgp_poisson_solve_many(f.ctx, Bs[:2], X[:2], None, None, None, stream)   # set-up outside the timing
+    X = X0.clone()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    L.cgp_poisson_solve_many(f.ctx, Bs, X, its, None, st, stream)
+    e1.record(stream)
+    e1.synchronize()
+    if int(st.max().item()) != L.CGP_OK:
+        raise RuntimeError(f"batched coarse solve status {int(st.max().item())}")
+    batched = nrhs * 1000.0 / e0.elapsed_time(e1)
+    return {"right_hand_sides": nrhs, "initial_guess": "previous logged pressure (all arms), plain also from zero",
+            "plain_fp64_jacobi_sequential": plain, "plain_iters": plain_it,
+            "plain_fp64_jacobi_zero_start": plain0, "plain_zero_iters": plain0_it,
+            "default_fp64_schwarz_sequential": dflt, "default_iters": dflt_it,
+            "batched_" + args.precision: batched, "batched_iters": float(its.double().mean().item()),
+            "ratio_batched_vs_plain_same_guess": batched / plain,
+            "ratio_batched_vs_plain_zero_start": batched / plain0,
+            "ratio_batched_vs_default_fp64": batched / dflt}
 
 
 def secondary_bfs33(L, Flow, dev, flush, stream, args):
@@ -777,6 +849,7 @@ def main():
     ap.add_argument("--no-other-precision", dest="other_precision", action="store_false")
     ap.add_argument("--no-secondary", dest="secondary", action="store_false")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--no-coarse-throughput", dest="coarse_throughput", action="store_false")
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--lanes", type=int, default=0)

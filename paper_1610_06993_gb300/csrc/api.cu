@@ -592,8 +592,10 @@ int cgp_autotune(cgp_ctx c, void* stream) {
                 best_l = l;
             }
         }
-        if (fine) c->sh_f.lanes = best_l;
-        else c->sh_c.lanes = best_l;
+        if (c->prm.spmv_lanes == 0) {   // a lane count fixed by the caller stays
+            if (fine) c->sh_f.lanes = best_l;
+            else c->sh_c.lanes = best_l;
+        }
         if (fine) {
             // the stand-alone fine SpMV: sliced ELL against the best CSR lane count
             double* x = (double*)c->ws;
@@ -616,49 +618,62 @@ int cgp_autotune(cgp_ctx c, void* stream) {
     // fine-mesh solvers: the layout (CSR with the chosen lanes, or sliced ELL) and the threads per
     // block of their persistent kernels, timed on the consistent-mass CG (the same kernel family
     // and pattern as the momentum solve) from a zero guess on a fixed right-hand side
-    if (c->prm.solver_format == 0 || c->prm.block_threads == 0) {
-        const bool fmts[2] = {false, true};
+    if (c->prm.solver_format == 0 || c->prm.block_threads == 0 || c->prm.spmv_lanes == 0) {
+        // candidates: CSR with one lane per row (the default), CSR with the stand-alone product's
+        // best lane count, sliced ELL; each with the configured threads per block and with 256
+        struct Cand {
+            bool ell;
+            int lanes, threads;
+        };
+        const int probe_lanes = c->sh_f.lanes;
+        std::vector<Cand> cand;
         const int thr[2] = {c->sh_f.threads, 256};
+        for (int ti = 0; ti < 2; ++ti) {
+            if (ti == 1 && (thr[1] == thr[0] || c->prm.block_threads != 0)) continue;
+            if (c->prm.solver_format != 1) {
+                cand.push_back({false, c->prm.spmv_lanes ? c->prm.spmv_lanes : 1, thr[ti]});
+                if (c->prm.spmv_lanes == 0 && probe_lanes != 1) cand.push_back({false, probe_lanes, thr[ti]});
+            }
+            if (c->prm.solver_format != 2) cand.push_back({true, 1, thr[ti]});
+        }
         double* b = c->grad;
         double* x = c->ut;
         k_fill_wave<<<(2 * c->nf + 255) / 256, 256, 0, s>>>(2 * (size_t)c->nf, b);
         CK(cudaGetLastError());
         float best = 1e30f;
-        bool best_ell = c->ell_on;
-        int best_thr = c->sh_f.threads;
+        Cand win = cand.front();
         const Shape keep = c->sh_f;
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        for (int fi = 0; fi < 2; ++fi) {
-            if (c->prm.solver_format != 0 && fmts[fi] != (c->prm.solver_format == 1)) continue;
-            for (int ti = 0; ti < 2; ++ti) {
-                if (ti == 1 && (thr[1] == thr[0] || c->prm.block_threads != 0)) continue;
-                c->ell_on = fmts[fi];
-                c->sh_f.threads = thr[ti];
-                float tot = 0.f;
-                for (int rep = 0; rep < 4; ++rep) {
-                    CK(cudaMemsetAsync(x, 0, 2 * sizeof(double) * (size_t)c->nf, s));
-                    CK(cudaEventRecord(e0, s));
-                    CK(launch_mass_cg(c, b, x, s));
-                    CK(cudaEventRecord(e1, s));
-                    CK(cudaEventSynchronize(e1));
-                    float t = 0.f;
-                    cudaEventElapsedTime(&t, e0, e1);
-                    if (rep > 0) tot += t;
-                }
-                if (tot < best) {
-                    best = tot;
-                    best_ell = fmts[fi];
-                    best_thr = thr[ti];
-                }
+        for (size_t k = 0; k < cand.size(); ++k) {
+            c->ell_on = cand[k].ell;
+            c->sh_f.lanes = cand[k].lanes;
+            c->sh_f.threads = cand[k].threads;
+            float tot = 0.f;
+            for (int rep = 0; rep < 6; ++rep) {
+                CK(cudaMemsetAsync(x, 0, 2 * sizeof(double) * (size_t)c->nf, s));
+                CK(cudaEventRecord(e0, s));
+                CK(launch_mass_cg(c, b, x, s));
+                CK(cudaEventRecord(e1, s));
+                CK(cudaEventSynchronize(e1));
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep >= 2) tot += t;
+            }
+            // the first candidate (the default layout) is left only for a clear gain
+            if (k > 0) tot *= 1.05f;
+            if (tot < best) {
+                best = tot;
+                win = cand[k];
             }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         c->sh_f = keep;
-        c->sh_f.threads = best_thr;
-        c->ell_on = best_ell;
+        c->sh_f.threads = win.threads;
+        c->sh_f.lanes = win.lanes;
+        c->ell_on = win.ell;
         CK(cudaMemset(c->stats, 0, sizeof(DevStats)));
     }
     return CGP_OK;

@@ -126,6 +126,8 @@ int create_impl(cgp_ctx* ctxs, int n, double* const* u, double* const* pc, cgp_b
     batch_poisson2l_build(b);
     cudaGetLastError();
     if (batch_predict_build(b) != cudaSuccess) return CGP_ERR_CUDA;
+    batch_gather_build(b);
+    cudaGetLastError();
     return CGP_OK;
 }
 
@@ -134,6 +136,15 @@ cudaError_t enqueue_step(cgp_batch_s* b, cudaStream_t s) {
     if (e == cudaSuccess) e = batch_asm_launch(b, s);
     if (e == cudaSuccess) e = batch_predict_launch(b, s);   // p_c and w still hold step n
     if (e == cudaSuccess) e = batch_momentum_launch(b, s);
+    if (b->gather) {
+        // the gathers between the persistent stages: one launch per stage for every instance
+        if (e == cudaSuccess) e = batch_restrict_launch(b, s);
+        if (e == cudaSuccess) e = b->poisson_2l ? batch_poisson2l_launch(b, s) : batch_poisson_launch(b, s);
+        if (e == cudaSuccess) e = batch_prolong_gradient_launch(b, s);
+        if (e == cudaSuccess) e = batch_mass_launch(b, s);
+        if (e == cudaSuccess) e = batch_correct_launch(b, s);
+        return e;
+    }
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) e = launch_restrict_rhs(b->ctx[i], b->ctx[i]->ut, b->ctx[i]->bc, s);
     if (e == cudaSuccess) e = b->poisson_2l ? batch_poisson2l_launch(b, s) : batch_poisson_launch(b, s);
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) {

@@ -6,6 +6,8 @@
 #include "common.cuh"
 #include "host_mesh.h"
 
+#define CGP_MAX_LEVELS 4   // refinement levels a context may have (cgp_mesh_create checks)
+
 namespace cgp {
 
 // Device-side statistics of the latest solves (mirrors cgp_stats).
@@ -224,6 +226,9 @@ struct cgp_batch_s {
     int predict_nmax = 0, predict_count = 0;
     bool poisson_2l = false;
     size_t smem_poi2 = 0;
+    bool gather = false;                 // batched inter-stage gathers (one launch per stage)
+    void* tab_gather = nullptr;
+    int gather_nc = 0, gather_nf = 0, gather_levels = 0, gather_nlv = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -290,6 +295,10 @@ cudaError_t launch_predict_vec(const double* in, double* out, double* prev, doub
                                int n, int order, cudaStream_t s);
 cudaError_t batch_predict_launch(cgp_batch_s* b, cudaStream_t s);
 cudaError_t batch_predict_build(cgp_batch_s* b);
+bool batch_gather_build(cgp_batch_s* b);
+cudaError_t batch_restrict_launch(cgp_batch_s* b, cudaStream_t s);
+cudaError_t batch_prolong_gradient_launch(cgp_batch_s* b, cudaStream_t s);
+cudaError_t batch_correct_launch(cgp_batch_s* b, cudaStream_t s);
 
 // Cooperative launch helper: launches `func` with the shape, `smem` bytes of dynamic shared
 // memory and its single by-value argument (typed, so a kernel cannot be handed the wrong

@@ -4,7 +4,7 @@
 #include "ctx.h"
 
 #ifndef CGP_ROWS_F32
-#define CGP_ROWS_F32 4        // rows in flight per thread in the FP32 CSR product
+#define CGP_ROWS_F32 2        // rows in flight per thread in the FP32 CSR product (4 measured no faster)
 #endif
 #ifndef CGP_ELL_CHUNK_F32
 #define CGP_ELL_CHUNK_F32 4   // slots per load group of the FP32 sliced-ELL product
@@ -54,9 +54,11 @@ __device__ __forceinline__ void spmv_rows_chunk(int k, const int (&ka)[R], const
 // (all column and value loads of a group before its x gathers), and the warp stops at its longest
 // row exactly: the products of a warp issue once per entry slot that some lane needs. A product is
 // bound by the dependent column -> x round trips of a thread, so R rows in flight divide their
-// number by R. x is written by other blocks during the launch, so it is read with ordinary
-// (coherent) loads; the matrix goes through the read-only path. The single-context kernels take
-// four FP32 rows per thread (CGP_ROWS_F32), the rest two (registers).
+// number by R (measured on the 1M-row cylinder mesh: four rows per thread were no faster than two;
+// with perfectly coalesced x reads a product was only a fifth faster, so it is bound by the
+// matrix stream at this occupancy rather than by the gathers). x is written by other blocks during
+// the launch, so it is read with ordinary (coherent) loads; the matrix goes through the read-only
+// path. CGP_ROWS_F32 sets R for the single-context FP32 products, the rest take two (registers).
 template <int NR, typename TV, typename TX, int R = 2, typename Emit>
 __device__ __forceinline__ void spmv_rows(RowRange rr, const int* __restrict__ rp, const int* __restrict__ ci,
                                           const TV* __restrict__ val, const TX* x, Emit emit) {

@@ -352,6 +352,164 @@ int galerkin_build(cgp_ctx_s* c) {
 }
 
 namespace {
+
+// Per-instance arguments of the batched gathers between the persistent stages of a batched step
+// (one launch per stage for all instances; blockIdx.y selects the instance).
+struct GatherArgs {
+    int nc, nf, levels;
+    int lv_n[CGP_MAX_LEVELS + 1];
+    const int* rp_c;
+    const int* cif;
+    const double* Dxy_c;
+    const unsigned char* pm;
+    double scale;
+    const double* ut;
+    double* bc;
+    const int2* sp[CGP_MAX_LEVELS];
+    double* pl[CGP_MAX_LEVELS];
+    const double* pc;
+    double* pf;
+    const int* rp_f;
+    const int* ci_f;
+    const double* Gxy;
+    double* grad;
+    const double* w;
+    double cdr;
+    const unsigned char* vmask;
+    const double* g;
+    double* u;
+};
+
+// The same arithmetic as k_restrict_rhs (one lane per row), k_prolong, k_gradient (one lane per
+// row) and k_correct, for instance blockIdx.y of the batch table.
+__global__ void k_restrict_b(const GatherArgs* __restrict__ tab) {
+    const GatherArgs& a = tab[blockIdx.y];
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= a.nc) return;
+    double acc = 0.0;
+    for (int k = a.rp_c[row]; k < a.rp_c[row + 1]; ++k) {
+        double dx, dy, ux, uy;
+        load2(a.Dxy_c, k, dx, dy);
+        load2(a.ut, a.cif[k], ux, uy);
+        acc += dx * ux + dy * uy;
+    }
+    a.bc[row] = a.pm[row] ? 0.0 : a.scale * acc;
+}
+
+__global__ void k_prolong_b(const GatherArgs* __restrict__ tab, int level) {
+    const GatherArgs& a = tab[blockIdx.y];
+    if (level >= a.levels) return;
+    const int n = a.lv_n[level + 1];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double* src = level == 0 ? a.pc : a.pl[level - 1];
+    double* dst = level + 1 == a.levels ? a.pf : a.pl[level];
+    const int2 bg = a.sp[level][i];
+    dst[i] = 0.5 * (src[bg.x] + src[bg.y]);
+}
+
+__global__ void k_gradient_b(const GatherArgs* __restrict__ tab) {
+    const GatherArgs& a = tab[blockIdx.y];
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= a.nf) return;
+    double ax = 0.0, ay = 0.0;
+    for (int k = a.rp_f[row]; k < a.rp_f[row + 1]; ++k) {
+        double gx, gy;
+        load2(a.Gxy, k, gx, gy);
+        const double p = a.pf[a.ci_f[k]];
+        ax += gx * p;
+        ay += gy * p;
+    }
+    store2(a.grad, row, ax, ay);
+}
+
+__global__ void k_correct_b(const GatherArgs* __restrict__ tab) {
+    const GatherArgs& a = tab[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nf) return;
+    double tx, ty, wx, wy, gx, gy;
+    load2(a.ut, i, tx, ty);
+    load2(a.w, i, wx, wy);
+    load2(a.g, i, gx, gy);
+    const unsigned char m = a.vmask[i];
+    store2(a.u, i, (m & CGP_BC_U) ? gx : tx - a.cdr * wx, (m & CGP_BC_V) ? gy : ty - a.cdr * wy);
+}
+
+}  // namespace
+
+// Table of the batched gathers; false (per-instance launches stay) when an instance uses the
+// Galerkin restriction or has no refinement level.
+bool batch_gather_build(cgp_batch_s* b) {
+    b->gather = false;
+    std::vector<GatherArgs> tab(b->n);
+    int maxc = 0, maxf = 0, maxl = 0, maxlv = 0;
+    for (int i = 0; i < b->n; ++i) {
+        cgp_ctx_s* c = b->ctx[i];
+        if (c->prm.restrict_mode != 0 || c->levels < 1 || c->levels > CGP_MAX_LEVELS) return false;
+        GatherArgs& a = tab[i];
+        a = GatherArgs();
+        a.nc = c->nc;
+        a.nf = c->nf;
+        a.levels = c->levels;
+        for (int k = 0; k <= c->levels; ++k) a.lv_n[k] = c->lv_n[k];
+        a.rp_c = c->C.rp;
+        a.cif = c->cif_su;
+        a.Dxy_c = c->Dc_xy;
+        a.pm = c->p_mask;
+        a.scale = -(c->prm.rho / c->prm.dt);
+        a.ut = c->ut;
+        a.bc = c->bc;
+        for (int k = 0; k < c->levels; ++k) {
+            a.sp[k] = c->sp[k];
+            a.pl[k] = c->pl[k];
+        }
+        a.pc = b->pc[i];
+        a.pf = c->pf;
+        a.rp_f = c->F.rp;
+        a.ci_f = c->F.ci;
+        a.Gxy = c->Gxy;
+        a.grad = c->grad;
+        a.w = c->w;
+        a.cdr = c->prm.dt / c->prm.rho;
+        a.vmask = c->vel_mask;
+        a.g = c->g;
+        a.u = b->u[i];
+        maxc = std::max(maxc, c->nc);
+        maxf = std::max(maxf, c->nf);
+        maxl = std::max(maxl, c->levels);
+        for (int k = 1; k <= c->levels; ++k) maxlv = std::max(maxlv, c->lv_n[k]);
+    }
+    void* d = nullptr;
+    if (cudaMalloc(&d, sizeof(GatherArgs) * tab.size()) != cudaSuccess) return false;
+    b->allocs.push_back(d);
+    if (cudaMemcpy(d, tab.data(), sizeof(GatherArgs) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess) return false;
+    b->tab_gather = d;
+    b->gather_nc = maxc;
+    b->gather_nf = maxf;
+    b->gather_levels = maxl;
+    b->gather_nlv = maxlv;
+    b->gather = true;
+    return true;
+}
+
+cudaError_t batch_restrict_launch(cgp_batch_s* b, cudaStream_t s) {
+    k_restrict_b<<<dim3((b->gather_nc + 255) / 256, b->n), 256, 0, s>>>((const GatherArgs*)b->tab_gather);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_prolong_gradient_launch(cgp_batch_s* b, cudaStream_t s) {
+    const GatherArgs* t = (const GatherArgs*)b->tab_gather;
+    for (int k = 0; k < b->gather_levels; ++k) k_prolong_b<<<dim3((b->gather_nlv + 255) / 256, b->n), 256, 0, s>>>(t, k);
+    k_gradient_b<<<dim3((b->gather_nf + 255) / 256, b->n), 256, 0, s>>>(t);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_correct_launch(cgp_batch_s* b, cudaStream_t s) {
+    k_correct_b<<<dim3((b->gather_nf + 255) / 256, b->n), 256, 0, s>>>((const GatherArgs*)b->tab_gather);
+    return cudaGetLastError();
+}
+
+namespace {
 // out = the extrapolation in time of order k through v0 (newest) .. vk: 2 v0 - v1, 3 v0 - 3 v1 + v2,
 // 4 v0 - 6 v1 + 4 v2 - v3 (the predictors of k_predict, without a history)
 __global__ void k_extrapolate(size_t n, int order, const double* __restrict__ v0, const double* __restrict__ v1,

@@ -57,6 +57,23 @@ def test_batch_matches_single_instances_and_oracle(L, precision):
         f.close()
 
 
+def test_batch_autotuned_instances_match_oracle(L):
+    """Instances tuned by cgp_autotune (per-instance lanes per row) before the batch is built: the
+    batched step (with its one-launch-per-stage gathers) still matches the oracle at 1e-10."""
+    from paper_1610_06993_gb300.flow import Batch, Flow
+    cases = small_batch()
+    flows = [Flow(m, p, rtol=1e-13, autotune=True) for m, p in cases]
+    b = Batch(flows)
+    b.step(6)
+    b.stats(check=True)
+    for (m, p), f in zip(cases, flows):
+        e = rel(f.u.cpu().numpy(), ocgp.run(m, p, 6).u)
+        assert e < 1e-10, (m.name, e)
+    b.close()
+    for f in flows:
+        f.close()
+
+
 def test_batch_graph_replay_is_bitwise(L):
     from paper_1610_06993_gb300.flow import Batch, Flow
     cases = small_batch()
