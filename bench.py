@@ -645,19 +645,37 @@ def coarse_throughput(L, Flow, make, f, other, B_log, P_log, stream, args):
 
 
 def secondary_bfs33(L, Flow, dev, flush, stream, args):
-    """The backward-facing-step channel (65,308 / 259,117 nodes, l = 1) in FP64, after 100
-    developing steps: steps/s and coarse solves/s."""
+    """The backward-facing-step channel (config 1: 65,308 / 259,117 nodes, l = 1) in FP64 and in
+    FP32+IR side by side, each after 100 developing steps: steps/s, coarse solves/s, and the relative
+    L2 error of one more step of each from the FP64 state against one oracle step."""
+    import torch
     coarse, prob, _ = ci.workload("bfs33")
-    f = Flow(coarse, prob, precision=L.CGP_FP64, rtol=args.rtol, device=dev)
-    for _ in range(100):
-        f.step(1, stream)
-    L.cgp_get_stats(f.ctx, stream, check=True)
-    r = timed_steps(L, f, max(10, args.steps // 2), flush, stream)
-    f.close()
-    return {"workload": "bfs33 (65,308 / 259,117 nodes, l=1, Re=400, dt=0.005), FP64, state after 100 steps",
-            "steps_per_s": 1000.0 / r["step"], "coarse_solves_per_s": 1000.0 / r["poi"],
-            "e2e_steps_per_s": 1000.0 / r["e2e"], "iterations": {"momentum": r["mom_it"], "poisson": r["poi_it"],
-                                                                "mass": r["mass_it"]}}
+    out = {"workload": "bfs33 (65,308 / 259,117 nodes, l=1, Re=400, dt=0.005), state after 100 steps"}
+    flows = {}
+    for name, prec in (("fp64", L.CGP_FP64), ("mixed", L.CGP_MIXED)):
+        f = Flow(coarse, prob, precision=prec, rtol=args.rtol, device=dev)
+        for _ in range(100):
+            f.step(1, stream)
+        L.cgp_get_stats(f.ctx, stream, check=True)
+        r = timed_steps(L, f, max(10, args.steps // 2), flush, stream)
+        out[name] = {"steps_per_s": 1000.0 / r["step"], "coarse_solves_per_s": 1000.0 / r["poi"],
+                     "e2e_steps_per_s": 1000.0 / r["e2e"],
+                     "iterations": {"momentum": r["mom_it"], "poisson": r["poi_it"], "mass": r["mass_it"]}}
+        flows[name] = f
+    if not args.no_cpu_baseline:
+        from oracle import cgp as ocgp
+        f64 = flows["fp64"]
+        u0, p0, t0 = f64.u.cpu().numpy().copy(), f64.pc.clone(), f64.t
+        orc = ocgp.CGPOracle(coarse.xy, coarse.tri, prob.rho, prob.mu, prob.dt, prob.levels, prob.vel_bc, prob.p_bc)
+        ref = orc.step(u0, t0 + prob.dt)
+        errs = {"after": "one step from the FP64 path's state", "rtol": args.rtol}
+        for name, f in flows.items():
+            u1, gp1 = one_step_with_gradient(L, f, torch.from_numpy(u0).to(dev), p0, stream)
+            errs[name] = {"u_rel_l2": rel(u1, ref.u), "gradp_rel_l2": rel(gp1, ref.gp)}
+        out["errors_vs_oracle"] = errs
+    for f in flows.values():
+        f.close()
+    return out
 
 
 def run_batch(args):
@@ -744,6 +762,24 @@ def run_batch(args):
             g.close()
         plain[solver] = (t_plain, it_plain)
 
+    # per-instance error against the oracle: one more batched step from the current states of a
+    # sample of instances spread over the sizes, against one oracle step from the same states
+    errs = None
+    if rank == 0 and not args.no_cpu_baseline:
+        from oracle import cgp as ocgp
+        sizes = np.array([f.info.n_coarse for f in flows])
+        order = np.argsort(sizes, kind="stable")
+        sample = [int(order[k]) for k in np.linspace(0, n_inst - 1, 4).round().astype(int)]
+        states = {i: (flows[i].u.cpu().numpy().copy(), flows[i].t) for i in sample}
+        b.step(1, stream)
+        b.stats(check=True)
+        errs = {"after": "one batched step from the timed run's final states", "rtol": args.rtol}
+        for i in sample:
+            m, p = cases[i]
+            orc = ocgp.CGPOracle(m.xy, m.tri, p.rho, p.mu, p.dt, p.levels, p.vel_bc, p.p_bc)
+            ref = orc.step(states[i][0], states[i][1] + p.dt)
+            errs[f"instance {i} ({int(sizes[i])} coarse nodes)"] = rel(flows[i].u.cpu().numpy(), ref.u)
+
     line = {
         "metric": METRIC, "value": job_rate(n_inst, ms, ws), "unit": "instance-steps/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -763,6 +799,8 @@ def run_batch(args):
                                 "iters_plain_schwarz_mean": statistics.mean(plain[0][1])},
         "gpu_launches": None, "clocks": clk.summary(),
     }
+    if errs is not None:
+        line["errors_vs_oracle"] = errs
     b.close()
     for f in flows:
         f.close()

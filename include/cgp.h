@@ -314,8 +314,11 @@ int cgp_get_stats(cgp_ctx ctx, void* stream, cgp_stats* st);
  * cgp_step, with one cooperative launch per persistent stage for all instances: the grid (up to
  * two blocks per SM) is cut into per-instance block groups, sized by the instance's fine nnz for
  * the fine-mesh solves and by nnz_c * sqrt(n_c) for the coarse CG; barriers and reductions stay
- * inside a group. The coarse solve uses the generic classical CG kernel. The gathers between
- * stages are launched per instance. Not in the paper: a systems pattern for many small problems.
+ * inside a group. The coarse solve uses the batched two-level CG (Jacobi plus three coarse
+ * functions per 256-row subdomain) when every instance has coarse_solver 0 and fits it, else the
+ * generic Jacobi CG. The gathers between stages (restriction, prolongation, gradient, correction)
+ * are one launch per stage for all instances (per instance when one uses restrict_mode 1). Not in
+ * the paper: a systems pattern for many small problems.
  * u_devs[i] [n_fine_i][2] and pc_devs[i] [n_coarse_i] are the instances' state, caller-owned
  * device buffers that must stay valid until cgp_batch_destroy. Contexts with projection != 0 are
  * rejected (CGP_ERR_ARG). */

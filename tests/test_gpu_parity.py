@@ -446,3 +446,22 @@ def test_solver_formats_agree(L, fmt, precision):
     e = rel(f.u.cpu().numpy(), ocgp.run(coarse, prob, 20).u)
     f.close()
     assert e < 1e-9, e
+
+
+@pytest.fixture(scope="module")
+def cavity129_ref():
+    coarse, prob, _ = ci.workload("cavity129")
+    return coarse, prob, ocgp.run(coarse, prob, 100)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_cavity129_100_steps(L, cavity129_ref, precision):
+    """Config 4's mesh (129x129-node cavity, 16,641 coarse / 66,049 fine nodes, dt = 0.005): the
+    spec bar, 1e-10 relative L2 in u and in w = M^-1 G p_f after 100 steps at rtol 1e-13."""
+    coarse, prob, ref = cavity129_ref
+    f = flow(coarse, prob, rtol=1e-13, precision=precision)
+    gp = _steps_with_gradient(L, f, 100)
+    st = f.stats(check=True)
+    eu, eg = rel(f.u.cpu().numpy(), ref.u), rel(gp, ref.gp)
+    f.close()
+    assert eu < 1e-10 and eg < 1e-10, (eu, eg, st.as_dict())
