@@ -394,7 +394,7 @@ int cgp_ws_train_step_residual(cgp_ws w, cgp_ctx ctx, const double* b_dev, const
 int cgp_extrapolate(long long n, int order, const double* v0_dev, const double* v1_dev, const double* v2_dev,
                     const double* v3_dev, double* out_dev, void* stream);
 
-/* Project-written autotuner (not in the paper). Times the SpMV lane counts {1, 2, 4, 8} on the
+/* Project-written autotuner (not in the paper). Times the SpMV lane counts {1, 2, 4, 8, 16, 32} on the
  * fine and coarse matrices and keeps the fastest for the solver kernels; the stand-alone SpMV's
  * layout (CSR or sliced ELL, spmv_format 0); and, for the fine-mesh solvers (solver_format 0 and/or
  * block_threads 0), the product layout (CSR or sliced ELL) and the threads per block of their

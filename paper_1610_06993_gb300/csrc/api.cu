@@ -580,7 +580,7 @@ int cgp_get_stats(cgp_ctx c, void* stream, cgp_stats* st) {
 int cgp_autotune(cgp_ctx c, void* stream) {
     if (!c) return CGP_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    const int cand[] = {1, 2, 4, 8};
+    const int cand[] = {1, 2, 4, 8, 16, 32};
     for (int fine = 0; fine < 2; ++fine) {
         float best = 1e30f;
         int best_l = 4;

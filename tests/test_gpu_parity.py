@@ -236,7 +236,7 @@ def test_nan_input_status(L):
 def test_autotuned_lanes_same_answer(L):
     coarse, prob, _ = ci.workload("cavity33")
     f = flow(coarse, prob, rtol=1e-13, autotune=True)
-    assert f.info.spmv_lanes in (1, 2, 4, 8)
+    assert f.info.spmv_lanes in (1, 2, 4, 8, 16, 32)
     f.step(5)
     f.stats(check=True)
     e = rel(f.u.cpu().numpy(), ocgp.run(coarse, prob, 5).u)
