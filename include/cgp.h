@@ -399,8 +399,10 @@ int cgp_extrapolate(long long n, int order, const double* v0_dev, const double* 
  * layout (CSR or sliced ELL, spmv_format 0); and, for the fine-mesh solvers (solver_format 0 and/or
  * block_threads 0), the product layout (CSR or sliced ELL) and the threads per block of their
  * persistent kernels (the default or 256, i.e. rows per thread), by timing the consistent-mass CG
- * on a fixed right-hand side. Overwrites the statistics and the context's intermediate-velocity
- * and gradient buffers (not the solution histories). Synchronous. */
+ * on a fixed right-hand side and, after cgp_set_bc, the momentum BiCGStab on the matrix of a fluid
+ * at rest (the default is left only for a 5 % gain). Overwrites the statistics, the momentum
+ * matrix and right-hand side (rebuilt by the next cgp_assemble) and the context's intermediate-
+ * velocity, staging and gradient buffers (not the solution histories). Synchronous. */
 int cgp_autotune(cgp_ctx ctx, void* stream);
 
 /* Allocation-free conjugate-gradient solve of one symmetric positive definite CSR system

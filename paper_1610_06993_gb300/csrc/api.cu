@@ -616,8 +616,8 @@ int cgp_autotune(cgp_ctx c, void* stream) {
         }
     }
     // fine-mesh solvers: the layout (CSR with the chosen lanes, or sliced ELL) and the threads per
-    // block of their persistent kernels, timed on the consistent-mass CG (the same kernel family
-    // and pattern as the momentum solve) from a zero guess on a fixed right-hand side
+    // block of their persistent kernels, timed on the consistent-mass CG from a zero guess on a
+    // fixed right-hand side and, once boundary conditions are set, the momentum BiCGStab
     if (c->prm.solver_format == 0 || c->prm.block_threads == 0 || c->prm.spmv_lanes == 0) {
         // candidates: CSR with one lane per row (the default), CSR with the stand-alone product's
         // best lane count, sliced ELL; each with the configured threads per block and with 256
@@ -640,6 +640,20 @@ int cgp_autotune(cgp_ctx c, void* stream) {
         double* x = c->ut;
         k_fill_wave<<<(2 * c->nf + 255) / 256, 256, 0, s>>>(2 * (size_t)c->nf, b);
         CK(cudaGetLastError());
+        // with boundary conditions set, the momentum solve (Eq. 19) is timed too: its matrix
+        // assembled for a fluid at rest (into both layouts), started from rest, without the
+        // initial-guess history (the next cgp_assemble overwrites everything used here)
+        const bool mom = c->bc_set;
+        const int ws_keep = c->prm.warm_start;
+        double* u0 = c->u_stage;
+        if (mom) {
+            CK(cudaMemsetAsync(u0, 0, 2 * sizeof(double) * (size_t)c->nf, s));
+            const bool ell_keep = c->ell_on;
+            c->ell_on = true;
+            CK(launch_assemble_step(c, u0, s));
+            c->ell_on = ell_keep;
+            c->prm.warm_start = 0;
+        }
         float best = 1e30f;
         Cand win = cand.front();
         const Shape keep = c->sh_f;
@@ -655,6 +669,7 @@ int cgp_autotune(cgp_ctx c, void* stream) {
                 CK(cudaMemsetAsync(x, 0, 2 * sizeof(double) * (size_t)c->nf, s));
                 CK(cudaEventRecord(e0, s));
                 CK(launch_mass_cg(c, b, x, s));
+                if (mom) CK(launch_momentum_bicgstab(c, u0, x, s));
                 CK(cudaEventRecord(e1, s));
                 CK(cudaEventSynchronize(e1));
                 float t = 0.f;
@@ -674,6 +689,7 @@ int cgp_autotune(cgp_ctx c, void* stream) {
         c->sh_f.threads = win.threads;
         c->sh_f.lanes = win.lanes;
         c->ell_on = win.ell;
+        c->prm.warm_start = ws_keep;
         CK(cudaMemset(c->stats, 0, sizeof(DevStats)));
     }
     return CGP_OK;
