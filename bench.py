@@ -434,7 +434,7 @@ def run_gpu(args):
                     **({"inner_rtol": args.inner_rtol} if args.inner_rtol > 0 else {}),
                     **({"mass_degree": args.mass_degree} if args.mass_degree > 0 else {}),
                     **({"momentum_degree": args.momentum_degree} if args.momentum_degree > 0 else {}),
-                    solver_format=args.solver_format)
+                    solver_format=args.solver_format, fine_order=args.fine_order)
 
     stream = torch.cuda.current_stream()
     flush = L2Flush(dev)
@@ -533,6 +533,7 @@ def run_gpu(args):
                    "parallelism": "replicas" if ws > 1 else "1gpu",
                    "block_threads": info.block_threads, "grid_blocks": info.grid_blocks,
                    "fine_solver_format": {1: "sliced ELL", 2: "CSR"}.get(info.solver_format, "?"),
+                   "fine_node_order": {0: "Hilbert curve", 1: "refinement order"}.get(info.fine_order, "?"),
                    "autotuned": bool(args.autotune), "spmv_lanes": info.spmv_lanes,
                    "coarse_kernel": coarse_name, "momentum_degree": f.params.momentum_degree,
                    "mass_degree": f.params.mass_degree,
@@ -899,6 +900,7 @@ def main():
     ap.add_argument("--mass-degree", type=int, default=0)      # 0: the library default (4)   # -1: the library default (1, extrapolation)
     ap.add_argument("--momentum-degree", type=int, default=0)  # 0: the library default
     ap.add_argument("--solver-format", type=int, default=0)    # 0: automatic, 1: sliced ELL, 2: CSR
+    ap.add_argument("--fine-order", type=int, default=0)       # 0: Hilbert-curve storage, 1: refinement order
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spmv", action="store_true")
     args = ap.parse_args()

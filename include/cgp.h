@@ -128,6 +128,12 @@ typedef struct {
                           they drift as dt falls (the coarse Laplacian does not match the injected
                           divergence), with restrict_mode 1 they are stable. Single contexts only:
                           cgp_batch_create rejects contexts with projection != 0 */
+    int fine_order;    /* storage order of the fine nodes inside the library (levels >= 1): 0 (default)
+                          = along a Hilbert curve of their coordinates, so that neighbouring rows and
+                          the columns they gather lie close together in memory; 1 = the refinement
+                          order. Every fine-mesh array crossing this interface (cgp_fine_mesh,
+                          cgp_set_bc, velocities, pf, gp) is in the refinement order either way; the
+                          library permutes on the way in and out */
 } cgp_params;
 
 /* A coarse mesh: n_nodes points xy_host[n][2] and n_tris counter-clockwise triangles
@@ -148,6 +154,8 @@ typedef struct {
                             3 on-chip two-level Schwarz CG, preconditioner in FP32,
                             4 the same, preconditioner in the iteration precision */
     int solver_format;   /* layout of the fine solvers' products: 1 sliced ELL, 2 CSR */
+    int fine_order;      /* storage order of the fine nodes: 0 a Hilbert curve, 1 the refinement order
+                            (always 1 when levels = 0, where the fine mesh is the coarse one) */
 } cgp_info;
 
 /* Per-solve statistics of the most recent step (read back by cgp_get_stats, which synchronises
@@ -165,7 +173,7 @@ typedef struct {
 /* Fill *p with the defaults: rho = 1, mu = 0.01, dt = 0.01, levels = 1, CGP_FP64, rtol = 1e-8,
  * inner_rtol = 1e-4, max_iter = 20000, max_outer = 30, spmv_lanes = 0, block_threads = 0,
  * coarse_solver = 0, spmv_format = 0, precond_degree = 0, precond_ratio = 0, warm_start = 3, mass_degree = 0,
- * momentum_degree = 0, solver_format = 0, restrict_mode = 0, projection = 0. */
+ * momentum_degree = 0, solver_format = 0, restrict_mode = 0, projection = 0, fine_order = 0. */
 void cgp_default_params(cgp_params* p);
 
 /* Preprocessing (the paper's C_pre, Sect. 2.4): validates the coarse mesh, refines it

@@ -36,7 +36,7 @@ class cgp_params(C.Structure):
                 ("block_threads", C.c_int), ("coarse_solver", C.c_int), ("spmv_format", C.c_int),
                 ("precond_degree", C.c_int), ("precond_ratio", C.c_double), ("warm_start", C.c_int),
                 ("mass_degree", C.c_int), ("momentum_degree", C.c_int), ("solver_format", C.c_int),
-                ("restrict_mode", C.c_int), ("projection", C.c_int)]
+                ("restrict_mode", C.c_int), ("projection", C.c_int), ("fine_order", C.c_int)]
 
 
 class cgp_mesh_desc(C.Structure):
@@ -47,7 +47,8 @@ class cgp_mesh_desc(C.Structure):
 class cgp_info(C.Structure):
     _fields_ = [(k, C.c_int) for k in ("n_fine", "n_coarse", "tris_fine", "tris_coarse", "nnz_fine",
                                        "nnz_coarse", "levels", "n_colours", "grid_blocks",
-                                       "block_threads", "spmv_lanes", "coarse_kernel", "solver_format")]
+                                       "block_threads", "spmv_lanes", "coarse_kernel", "solver_format",
+                                       "fine_order")]
 
 
 class cgp_stats(C.Structure):

@@ -88,6 +88,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     if (P.solver_format < 0 || P.solver_format > 2) return CGP_ERR_ARG;
     if (P.restrict_mode < 0 || P.restrict_mode > 1) return CGP_ERR_ARG;
     if (P.projection < 0 || P.projection > 2) return CGP_ERR_ARG;
+    if (P.fine_order < 0 || P.fine_order > 1) return CGP_ERR_ARG;
     if (P.inner_rtol <= 0.0) P.inner_rtol = 1e-4;
     if (P.max_iter <= 0) P.max_iter = 20000;
     if (P.max_outer <= 0) P.max_outer = 30;
@@ -95,7 +96,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     if (P.block_threads < 256 || P.block_threads > 512 || (P.block_threads & 31)) return CGP_ERR_ARG;
     if (P.spmv_lanes != 0 && (P.spmv_lanes < 1 || P.spmv_lanes > 32 || (P.spmv_lanes & (P.spmv_lanes - 1))))
         return CGP_ERR_ARG;
-    TRY(build_host_mesh(d, P.levels, c->hm));
+    TRY(build_host_mesh(d, P.levels, c->hm, P.fine_order == 0));
     HostMesh& H = c->hm;
     c->levels = P.levels;
     c->nc = H.lv[0].n;
@@ -115,9 +116,23 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     std::vector<int> cif(H.coarse.nnz);
     for (int k = 0; k < H.coarse.nnz; ++k) cif[k] = H.su[H.coarse.ci[k]];
     TRY(upload(c, &c->cif_su, cif));
+    // The stand-alone product (cgp_spmv) takes its vectors in the refinement order: with another
+    // stored order it keeps its own copy of the fine pattern in that order (P, values P_A0
+    // gathered from A0 through p_src once A0 is assembled).
+    HostCsr Pf;
+    int* p_src = nullptr;
+    if (!H.fperm.empty()) {
+        TRY(upload(c, &c->fperm, H.fperm));
+        std::vector<int> src;
+        csr_to_refinement_order(H.fine, H.fperm, Pf, src);
+        TRY(upload_csr(c, Pf, c->P));
+        TRY(upload(c, &p_src, src));
+    } else {
+        c->P = c->F;
+    }
     {
         HostSell hs;
-        build_sell(H.fine, 32, 32, hs);
+        build_sell(c->fperm ? Pf : H.fine, 32, 32, hs);
         c->sell_nslices = hs.nslices;
         c->sell_total = hs.ptr[hs.nslices];
         TRY(upload(c, &c->sell_ptr, hs.ptr));
@@ -207,6 +222,12 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     CK(cudaMemset(c->phi, 0, nc * sizeof(double)));
     TRY(dalloc(c, &c->u_stage, 2 * nf));
     TRY(dalloc(c, &c->pc_stage, nc));
+    if (c->fperm) {
+        TRY(dalloc(c, &c->u_int, 2 * nf));
+        TRY(dalloc(c, &c->P_A0, nnzf));
+    } else {
+        c->P_A0 = c->A0;
+    }
     // Krylov workspace: the largest of BiCGStab (9 pair vectors) and CG (6 vectors), each with
     // the three FP32 pair vectors of its polynomial preconditioner, 256-byte carved
     const size_t need = std::max({9 * 2 * nf * sizeof(double) + 3 * 2 * nf * sizeof(float),
@@ -244,7 +265,8 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
         if ((e = launch_const_assembly(c->EC, nullptr, c->Kc_raw, c->Dc_xy, s)) != cudaSuccess) break;
         if ((e = launch_make_A0(c, Kf, s)) != cudaSuccess) break;
         if ((e = launch_lumped_mass(c, Kf, s)) != cudaSuccess) break;   // Kf (nnz_f >= nnz_c) reused as scratch
-        if ((e = sell_fill(c, c->A0, s)) != cudaSuccess) break;
+        if (p_src && (e = gather_values((int)nnzf, p_src, c->A0, c->P_A0, s)) != cudaSuccess) break;
+        if ((e = sell_fill(c, c->P_A0, s)) != cudaSuccess) break;
         if ((e = ell_fill(c->ell_total, c->ell_src, c->M, c->ell_M, c->ell_M32, s)) != cudaSuccess) break;
         e = cudaStreamSynchronize(s);
     } while (0);
@@ -359,7 +381,7 @@ int cgp_refine(const cgp_mesh_desc* coarse, int levels, int* n_fine, int* n_tris
                int* tri_host, int* sp_host, int* colour_host) {
     if (!coarse) return CGP_ERR_ARG;
     HostMesh H;
-    int s = build_host_mesh(coarse, levels, H);
+    int s = build_host_mesh(coarse, levels, H, false);
     if (s != CGP_OK) return s;
     const HostLevel& L = H.lv[levels];
     if (n_fine) *n_fine = L.n;
@@ -397,20 +419,50 @@ int cgp_mesh_info(cgp_ctx c, cgp_info* info) {
     info->coarse_kernel = c->use_schwarz ? (c->schwarz_fp32 && c->prm.precision == CGP_FP64 ? 3 : 4)
                                          : c->use_pipe ? (c->onchip_pipelined ? 2 : 1) : 0;
     info->solver_format = c->ell_on ? 1 : 2;
+    info->fine_order = c->fperm ? 0 : 1;
     return CGP_OK;
 }
 
 int cgp_fine_mesh(cgp_ctx c, double* xy_host, int* tri_host, unsigned char* onb_host) {
     if (!c) return CGP_ERR_ARG;
     const HostLevel& L = c->hm.lv[c->levels];
-    if (xy_host) std::copy(L.xy.begin(), L.xy.end(), xy_host);
-    if (tri_host) std::copy(L.tri.begin(), L.tri.end(), tri_host);
-    if (onb_host) std::copy(c->hm.onb_f.begin(), c->hm.onb_f.end(), onb_host);
+    const std::vector<int>& fp = c->hm.fperm;
+    if (fp.empty()) {
+        if (xy_host) std::copy(L.xy.begin(), L.xy.end(), xy_host);
+        if (tri_host) std::copy(L.tri.begin(), L.tri.end(), tri_host);
+        if (onb_host) std::copy(c->hm.onb_f.begin(), c->hm.onb_f.end(), onb_host);
+        return CGP_OK;
+    }
+    // stored order -> refinement order
+    for (int i = 0; i < L.n; ++i) {
+        const int q = fp[i];
+        if (xy_host) {
+            xy_host[2 * q] = L.xy[2 * i];
+            xy_host[2 * q + 1] = L.xy[2 * i + 1];
+        }
+        if (onb_host) onb_host[q] = c->hm.onb_f[i];
+    }
+    if (tri_host)
+        for (size_t k = 0; k < L.tri.size(); ++k) tri_host[k] = fp[L.tri[k]];
     return CGP_OK;
 }
 
 int cgp_set_bc(cgp_ctx c, const unsigned char* vel_mask, const unsigned char* p_mask, const double* g) {
     if (!c || !vel_mask || !p_mask || !g) return CGP_ERR_ARG;
+    std::vector<unsigned char> vm_st;
+    std::vector<double> g_st;
+    if (!c->hm.fperm.empty()) {   // refinement order -> stored order
+        const std::vector<int>& fp = c->hm.fperm;
+        vm_st.resize(c->nf);
+        g_st.resize(2 * (size_t)c->nf);
+        for (int i = 0; i < c->nf; ++i) {
+            vm_st[i] = vel_mask[fp[i]];
+            g_st[2 * (size_t)i] = g[2 * (size_t)fp[i]];
+            g_st[2 * (size_t)i + 1] = g[2 * (size_t)fp[i] + 1];
+        }
+        vel_mask = vm_st.data();
+        g = g_st.data();
+    }
     CK(cudaMemcpy(c->vel_mask, vel_mask, (size_t)c->nf, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->p_mask, p_mask, (size_t)c->nc, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->g, g, 2 * sizeof(double) * (size_t)c->nf, cudaMemcpyHostToDevice));
@@ -426,29 +478,47 @@ int cgp_set_bc(cgp_ctx c, const unsigned char* vel_mask, const unsigned char* p_
 
 int cgp_set_dirichlet_values(cgp_ctx c, const double* g_dev, void* stream) {
     if (!c || !g_dev) return CGP_ERR_ARG;
-    CK(cudaMemcpyAsync(c->g, g_dev, 2 * sizeof(double) * (size_t)c->nf, cudaMemcpyDeviceToDevice,
-                       (cudaStream_t)stream));
+    CK(fine_to_stored(c, g_dev, c->g, 2, (cudaStream_t)stream));
     return CGP_OK;
 }
 
 int cgp_assemble(cgp_ctx c, const double* u_dev, void* stream) {
     if (!c || !u_dev) return CGP_ERR_ARG;
     if (!c->bc_set) return CGP_ERR_STATE;
-    CK(launch_assemble_step(c, u_dev, (cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    const double* u = u_dev;
+    if (c->fperm) {
+        CK(fine_to_stored(c, u_dev, c->u_int, 2, s));
+        u = c->u_int;
+    }
+    CK(launch_assemble_step(c, u, s));
     return CGP_OK;
 }
 
 int cgp_momentum_solve(cgp_ctx c, const double* u_dev, double* ut_dev, void* stream) {
     if (!c || !u_dev || !ut_dev) return CGP_ERR_ARG;
     if (!c->bc_set) return CGP_ERR_STATE;
-    CK(launch_momentum_bicgstab(c, u_dev, ut_dev, (cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->fperm) {
+        CK(launch_momentum_bicgstab(c, u_dev, ut_dev, s));
+        return CGP_OK;
+    }
+    CK(fine_to_stored(c, u_dev, c->u_int, 2, s));
+    CK(launch_momentum_bicgstab(c, c->u_int, c->ut, s));
+    CK(fine_to_public(c, c->ut, ut_dev, 2, s));
     return CGP_OK;
 }
 
 int cgp_restrict(cgp_ctx c, const double* ut_dev, double* bc_dev, void* stream) {
     if (!c || !ut_dev || !bc_dev) return CGP_ERR_ARG;
     if (!c->bc_set) return CGP_ERR_STATE;
-    CK(launch_restrict_rhs(c, ut_dev, bc_dev, (cudaStream_t)stream));
+    cudaStream_t s = (cudaStream_t)stream;
+    const double* ut = ut_dev;
+    if (c->fperm) {
+        CK(fine_to_stored(c, ut_dev, c->ut, 2, s));
+        ut = c->ut;
+    }
+    CK(launch_restrict_rhs(c, ut, bc_dev, s));
     return CGP_OK;
 }
 
@@ -471,11 +541,17 @@ int cgp_prolong_correct(cgp_ctx c, const double* pc_dev, const double* ut_dev, d
     if (!c || !pc_dev || !ut_dev || !u_dev) return CGP_ERR_ARG;
     if (!c->bc_set) return CGP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
-    double* pf = pf_dev ? pf_dev : c->pf;
+    const double* ut = ut_dev;
+    if (c->fperm) {
+        CK(fine_to_stored(c, ut_dev, c->ut, 2, s));
+        ut = c->ut;
+    }
+    double* pf = (pf_dev && !c->fperm) ? pf_dev : c->pf;
     CK(launch_prolong(c, pc_dev, pf, s));
+    if (pf_dev && c->fperm) CK(fine_to_public(c, c->pf, pf_dev, 1, s));
     CK(launch_gradient(c, pf, c->grad, s));
     CK(mass_stage(c, s));
-    CK(launch_correct(c, ut_dev, c->w, u_dev, gp_dev, s));
+    CK(launch_correct(c, ut, c->w, u_dev, gp_dev, s, true));
     return CGP_OK;
 }
 
@@ -483,8 +559,13 @@ int cgp_assemble_incremental(cgp_ctx c, const double* u_dev, const double* pc_de
     if (!c || !u_dev || !pc_dev) return CGP_ERR_ARG;
     if (!c->bc_set) return CGP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
+    const double* u = u_dev;
+    if (c->fperm) {
+        CK(fine_to_stored(c, u_dev, c->u_int, 2, s));
+        u = c->u_int;
+    }
     CK(launch_pressure_term(c, pc_dev, s));
-    CK(launch_assemble_step(c, u_dev, s, c->grad_n));
+    CK(launch_assemble_step(c, u, s, c->grad_n));
     return CGP_OK;
 }
 
@@ -499,31 +580,37 @@ int cgp_step(cgp_ctx c, double* u_dev, double* pc_dev, void* stream) {
     if (!c || !u_dev || !pc_dev) return CGP_ERR_ARG;
     if (!c->bc_set) return CGP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
+    // u^n in the stored fine order; the correction writes u^(n+1) back in the refinement order
+    const double* u = u_dev;
+    if (c->fperm) {
+        CK(fine_to_stored(c, u_dev, c->u_int, 2, s));
+        u = c->u_int;
+    }
     if (c->prm.projection != 0) {
         // incremental forms: pressure term of p^n, momentum, restriction, Poisson for the
         // increment (its own extrapolated history), correction by the increment, p += phi (- mu chi)
         CK(launch_pressure_term(c, pc_dev, s));
-        CK(launch_assemble_step(c, u_dev, s, c->grad_n));
-        CK(launch_momentum_bicgstab(c, u_dev, c->ut, s));
+        CK(launch_assemble_step(c, u, s, c->grad_n));
+        CK(launch_momentum_bicgstab(c, u, c->ut, s));
         CK(launch_restrict_rhs(c, c->ut, c->bc, s));
         if (c->prm.warm_start >= 1) CK(launch_predict(c, c->phi, s));
         CK(launch_poisson_cg(c, c->bc, c->phi, s));
         CK(launch_prolong(c, c->phi, c->pf, s));
         CK(launch_gradient(c, c->pf, c->grad, s));
         CK(mass_stage(c, s));
-        CK(launch_correct(c, c->ut, c->w, u_dev, nullptr, s));
+        CK(launch_correct(c, c->ut, c->w, u_dev, nullptr, s, true));
         CK(launch_pressure_update(c, c->bc, c->phi, pc_dev, s));
         return CGP_OK;
     }
-    CK(launch_assemble_step(c, u_dev, s));
-    CK(launch_momentum_bicgstab(c, u_dev, c->ut, s));
+    CK(launch_assemble_step(c, u, s));
+    CK(launch_momentum_bicgstab(c, u, c->ut, s));
     CK(launch_restrict_rhs(c, c->ut, c->bc, s));
     if (c->prm.warm_start >= 1) CK(launch_predict(c, pc_dev, s));
     CK(launch_poisson_cg(c, c->bc, pc_dev, s));
     CK(launch_prolong(c, pc_dev, c->pf, s));
     CK(launch_gradient(c, c->pf, c->grad, s));
     CK(mass_stage(c, s));
-    CK(launch_correct(c, c->ut, c->w, u_dev, nullptr, s));
+    CK(launch_correct(c, c->ut, c->w, u_dev, nullptr, s, true));
     return CGP_OK;
 }
 

@@ -340,7 +340,7 @@ cudaError_t launch_assemble_step_coloured(cgp_ctx_s* c, const double* u, cudaStr
 
 cudaError_t batch_asm_build(cgp_batch_s* b) {
     std::vector<StepAsmArgs> tab(b->n);
-    for (int i = 0; i < b->n; ++i) tab[i] = asm_args(b->ctx[i], b->u[i], b->sync + (size_t)i * SYNC_COUNT + SYNC_ASM);
+    for (int i = 0; i < b->n; ++i) tab[i] = asm_args(b->ctx[i], batch_u_work(b, i), b->sync + (size_t)i * SYNC_COUNT + SYNC_ASM);
     void* d = nullptr;
     cudaError_t e = cudaMalloc(&d, sizeof(StepAsmArgs) * tab.size());
     if (e != cudaSuccess) return e;

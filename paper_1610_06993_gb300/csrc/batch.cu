@@ -125,7 +125,7 @@ int create_impl(cgp_ctx* ctxs, int n, double* const* u, double* const* pc, cgp_b
     // solver and fits it; otherwise the Jacobi kernel
     batch_poisson2l_build(b);
     cudaGetLastError();
-    if (batch_predict_build(b) != cudaSuccess) return CGP_ERR_CUDA;
+    if (batch_predict_build(b) != cudaSuccess || batch_perm_build(b) != cudaSuccess) return CGP_ERR_CUDA;
     batch_gather_build(b);
     cudaGetLastError();
     return CGP_OK;
@@ -133,6 +133,7 @@ int create_impl(cgp_ctx* ctxs, int n, double* const* u, double* const* pc, cgp_b
 
 cudaError_t enqueue_step(cgp_batch_s* b, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(b->sync, 0, sizeof(SyncWords) * (size_t)b->n * SYNC_COUNT, s);
+    if (e == cudaSuccess) e = batch_perm_launch(b, s);   // u^n into the instances' stored fine order
     if (e == cudaSuccess) e = batch_asm_launch(b, s);
     if (e == cudaSuccess) e = batch_predict_launch(b, s);   // p_c and w still hold step n
     if (e == cudaSuccess) e = batch_momentum_launch(b, s);
@@ -154,7 +155,7 @@ cudaError_t enqueue_step(cgp_batch_s* b, cudaStream_t s) {
     }
     if (e == cudaSuccess) e = batch_mass_launch(b, s);
     for (int i = 0; i < b->n && e == cudaSuccess; ++i)
-        e = launch_correct(b->ctx[i], b->ctx[i]->ut, b->ctx[i]->w, b->u[i], nullptr, s);
+        e = launch_correct(b->ctx[i], b->ctx[i]->ut, b->ctx[i]->w, b->u[i], nullptr, s, true);
     return e;
 }
 

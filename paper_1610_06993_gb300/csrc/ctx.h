@@ -146,6 +146,16 @@ struct cgp_ctx_s {
     double* u_stage = nullptr;
     double* pc_stage = nullptr;
 
+    // fine-node storage order (fine_order 0: a Hilbert curve, see host_mesh.h). Fine vectors
+    // cross the interface in the refinement order; fperm[i] is the refinement-order index of
+    // stored node i (nullptr: the two orders coincide). u_int: the velocity in the stored order.
+    int* fperm = nullptr;
+    double* u_int = nullptr;
+    // the stand-alone product (cgp_spmv) works on vectors in the refinement order: A0 in the CSR
+    // pattern of that order (P; its SELL copy below is built from it)
+    cgp::DevCsr P;
+    double* P_A0 = nullptr;
+
     // sliced-ELL (SELL-32-256) copy of the fine pattern for the stand-alone SpMV
     int sell_nslices = 0, sell_total = 0;
     int *sell_ptr = nullptr, *sell_col = nullptr, *sell_src = nullptr, *sell_perm = nullptr;
@@ -229,6 +239,8 @@ struct cgp_batch_s {
     bool gather = false;                 // batched inter-stage gathers (one launch per stage)
     void* tab_gather = nullptr;
     int gather_nc = 0, gather_nf = 0, gather_levels = 0, gather_nlv = 0;
+    void* tab_perm = nullptr;            // velocities gathered into the instances' stored fine order
+    int perm_nmax = 0, perm_count = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -270,6 +282,8 @@ cudaError_t launch_momentum_bicgstab(cgp_ctx_s* c, const double* u_in, double* x
 cudaError_t time_spmv_lanes(cgp_ctx_s* c, bool fine, int lanes, cudaStream_t s, float* ms);
 cudaError_t launch_spmv_fine(cgp_ctx_s* c, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_spmv_sell(cgp_ctx_s* c, const double* x, double* y, cudaStream_t s);
+// out[k] = in[src[k]] (src[k] >= 0) or 0, k < total
+cudaError_t gather_values(int total, const int* src, const double* in, double* out, cudaStream_t s);
 cudaError_t sell_fill(cgp_ctx_s* c, const double* csr_val, cudaStream_t s);
 cudaError_t ell_fill(int total, const int* src, const double* csr_val, double* val, float* val32, cudaStream_t s);
 
@@ -284,7 +298,11 @@ cudaError_t launch_restrict_rhs(cgp_ctx_s* c, const double* ut, double* bc, cuda
 cudaError_t launch_prolong(cgp_ctx_s* c, const double* pc, double* pf, cudaStream_t s);
 cudaError_t launch_gradient(cgp_ctx_s* c, const double* pf, double* grad, cudaStream_t s);
 cudaError_t launch_correct(cgp_ctx_s* c, const double* ut, const double* w, double* u, double* gp_out,
-                           cudaStream_t s);
+                           cudaStream_t s, bool to_public = false);
+// fine vectors between the refinement order (the interface) and the stored order (fperm);
+// comps = values per node (1 or 2); copies when the two orders coincide
+cudaError_t fine_to_stored(cgp_ctx_s* c, const double* pub, double* st, int comps, cudaStream_t s);
+cudaError_t fine_to_public(cgp_ctx_s* c, const double* st, double* pub, int comps, cudaStream_t s);
 cudaError_t launch_copy_pairs(const double* src, double* dst, int n, cudaStream_t s);
 cudaError_t launch_pressure_term(cgp_ctx_s* c, const double* pc, cudaStream_t s);
 cudaError_t launch_pressure_update(cgp_ctx_s* c, const double* bc, const double* phi, double* pc, cudaStream_t s);
@@ -299,6 +317,10 @@ bool batch_gather_build(cgp_batch_s* b);
 cudaError_t batch_restrict_launch(cgp_batch_s* b, cudaStream_t s);
 cudaError_t batch_prolong_gradient_launch(cgp_batch_s* b, cudaStream_t s);
 cudaError_t batch_correct_launch(cgp_batch_s* b, cudaStream_t s);
+cudaError_t batch_perm_build(cgp_batch_s* b);
+// The velocity an instance's batched kernels read: its stored-order copy when it renumbers.
+inline double* batch_u_work(const cgp_batch_s* b, int i) { return b->ctx[i]->fperm ? b->ctx[i]->u_int : b->u[i]; }
+cudaError_t batch_perm_launch(cgp_batch_s* b, cudaStream_t s);
 
 // Cooperative launch helper: launches `func` with the shape, `smem` bytes of dynamic shared
 // memory and its single by-value argument (typed, so a kernel cannot be handed the wrong

@@ -119,6 +119,8 @@ extern "C" {
 int cgp_set_surface(cgp_ctx c, int which, const unsigned char* mask, int* n_edges) {
     if (!c || !mask || which < 0 || which > 1) return CGP_ERR_ARG;
     const HostLevel& F = c->hm.lv[c->levels];
+    const std::vector<int>& fp = c->hm.fperm;   // the mask is in the refinement order
+    auto pub = [&](int v) { return fp.empty() ? v : fp[v]; };
     // boundary edges (one owning triangle), in the owner's CCW order
     std::vector<long long> key;
     std::vector<int4> loc;
@@ -139,7 +141,7 @@ int cgp_set_surface(cgp_ctx c, int which, const unsigned char* mask, int* n_edge
         while (j < ord.size() && key[ord[j]] == key[ord[i]]) ++j;
         if (j - i == 1) {
             const int4 q = loc[ord[i]];
-            if (mask[q.x] && mask[q.y]) sel.push_back(q);
+            if (mask[pub(q.x)] && mask[pub(q.y)]) sel.push_back(q);
         }
         i = j;
     }
@@ -168,8 +170,13 @@ int cgp_body_force(cgp_ctx c, const double* u_dev, const double* pc_dev, double*
     if (!c || !u_dev || !pc_dev || !force_dev) return CGP_ERR_ARG;
     if (c->surf[0].n == 0) return CGP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
+    const double* u = u_dev;
+    if (c->fperm) {
+        if (fine_to_stored(c, u_dev, c->u_int, 2, s) != cudaSuccess) return CGP_ERR_CUDA;
+        u = c->u_int;
+    }
     if (launch_prolong(c, pc_dev, c->pf, s) != cudaSuccess) return CGP_ERR_CUDA;
-    k_body_force<<<1, 256, 0, s>>>(c->surf[0].n, c->surf[0].e, c->xy_f, c->EF.tri, c->EF.geo, u_dev, c->pf,
+    k_body_force<<<1, 256, 0, s>>>(c->surf[0].n, c->surf[0].e, c->xy_f, c->EF.tri, c->EF.geo, u, c->pf,
                                    c->prm.mu, force_dev);
     return cudaGetLastError() == cudaSuccess ? CGP_OK : CGP_ERR_CUDA;
 }
@@ -182,7 +189,12 @@ int cgp_reattachment(cgp_ctx c, const double* u_dev, double x_start, double* xr_
     cudaStream_t s = (cudaStream_t)stream;
     double* xs = x_dev ? x_dev : S.xs;
     double* tau = tau_dev ? tau_dev : S.xs + S.n;
-    k_wall_shear<<<(S.n + 255) / 256, 256, 0, s>>>(S.n, S.e, c->xy_f, c->EF.tri, c->EF.geo, u_dev, c->prm.mu, xs, tau);
+    const double* u = u_dev;
+    if (c->fperm) {
+        if (fine_to_stored(c, u_dev, c->u_int, 2, s) != cudaSuccess) return CGP_ERR_CUDA;
+        u = c->u_int;
+    }
+    k_wall_shear<<<(S.n + 255) / 256, 256, 0, s>>>(S.n, S.e, c->xy_f, c->EF.tri, c->EF.geo, u, c->prm.mu, xs, tau);
     k_reattach<<<1, 32, 0, s>>>(S.n, xs, tau, x_start, xr_dev);
     return cudaGetLastError() == cudaSuccess ? CGP_OK : CGP_ERR_CUDA;
 }

@@ -4,6 +4,9 @@
 #include <algorithm>
 #include <cstdint>
 #include <unordered_map>
+#include <utility>
+
+#include "subdomain.h"
 
 namespace cgp {
 
@@ -165,7 +168,7 @@ void build_sell(const HostCsr& c, int C, int sigma, HostSell& out) {
     }
 }
 
-int build_host_mesh(const cgp_mesh_desc* d, int levels, HostMesh& out) {
+int build_host_mesh(const cgp_mesh_desc* d, int levels, HostMesh& out, bool renumber_fine) {
     if (!d || !d->xy_host || !d->tri_host || d->n_nodes <= 2 || d->n_tris <= 0) return CGP_ERR_ARG;
     if (levels < 0 || levels > 4) return CGP_ERR_ARG;
     HostLevel c;
@@ -230,6 +233,33 @@ int build_host_mesh(const cgp_mesh_desc* d, int levels, HostMesh& out) {
         // s^u: parents keep their indices, so the coarse node's fine index is unchanged
         out.lv.push_back(std::move(F));
     }
+    // Stored order of the fine nodes: along a Hilbert curve of their coordinates, so that the rows
+    // of a warp, and the columns they gather, lie close together (in the refinement order a
+    // parent's fine neighbours are midpoints created far apart). The s^p rows of the last level,
+    // s^u and the boundary flags follow; the coarser levels keep the refinement order.
+    if (renumber_fine && levels >= 1) {
+        HostLevel& F = out.lv[levels];
+        out.fperm = hilbert_order(F.xy, F.n);
+        std::vector<int> inv(F.n);
+        for (int i = 0; i < F.n; ++i) inv[out.fperm[i]] = i;
+        std::vector<double> xy(2 * (size_t)F.n);
+        std::vector<unsigned char> onb(F.n);
+        const std::vector<int>& sp0 = out.sp[levels - 1];
+        std::vector<int> sp(sp0.size());
+        for (int i = 0; i < F.n; ++i) {
+            const int p = out.fperm[i];
+            xy[2 * i] = F.xy[2 * p];
+            xy[2 * i + 1] = F.xy[2 * p + 1];
+            onb[i] = out.onb_f[p];
+            sp[2 * i] = sp0[2 * p];
+            sp[2 * i + 1] = sp0[2 * p + 1];
+        }
+        for (int& v : F.tri) v = inv[v];
+        for (int& x : out.su) x = inv[x];
+        F.xy.swap(xy);
+        out.onb_f.swap(onb);
+        out.sp[levels - 1].swap(sp);
+    }
     // CSR patterns and element data of the coarse and fine meshes
     {
         HostLevel& Lc = out.lv[0];
@@ -246,6 +276,35 @@ int build_host_mesh(const cgp_mesh_desc* d, int levels, HostMesh& out) {
         if (s != CGP_OK) return s;
     }
     return CGP_OK;
+}
+
+void csr_to_refinement_order(const HostCsr& in, const std::vector<int>& fperm, HostCsr& out, std::vector<int>& src) {
+    const int n = in.n;
+    std::vector<int> inv(n);
+    for (int i = 0; i < n; ++i) inv[fperm[i]] = i;
+    out = HostCsr();
+    out.n = n;
+    out.nnz = in.nnz;
+    out.rp.assign(n + 1, 0);
+    for (int q = 0; q < n; ++q) {
+        const int i = inv[q];
+        out.rp[q + 1] = out.rp[q] + (in.rp[i + 1] - in.rp[i]);
+    }
+    out.ci.assign(in.nnz, 0);
+    src.assign(in.nnz, 0);
+    out.diag.assign(n, 0);
+    std::vector<std::pair<int, int>> row;
+    for (int q = 0; q < n; ++q) {
+        const int i = inv[q];
+        row.clear();
+        for (int k = in.rp[i]; k < in.rp[i + 1]; ++k) row.push_back({fperm[in.ci[k]], k});
+        std::sort(row.begin(), row.end());
+        for (size_t e = 0; e < row.size(); ++e) {
+            out.ci[out.rp[q] + (int)e] = row[e].first;
+            src[out.rp[q] + (int)e] = row[e].second;
+            if (row[e].first == q) out.diag[q] = out.rp[q] + (int)e;
+        }
+    }
 }
 
 }  // namespace cgp

@@ -28,6 +28,10 @@ struct HostMesh {
     std::vector<HostLevel> lv;               // lv[0] coarse (pressure) ... lv[L] fine (velocity)
     std::vector<std::vector<int>> sp;        // sp[k]: [N_{k+1}][2] parent pair (beta, gamma)
     std::vector<int> su;                     // [N_c] fine index xi of each coarse node
+    // Fine-node storage order: fperm[i] is the refinement-order index of stored fine node i
+    // (empty: the refinement order itself). Everything of the fine level above (xy, tri, the last
+    // s^p table's rows, su, onb_f, the fine CSR and elements) is in the stored order.
+    std::vector<int> fperm;
     HostCsr fine, coarse;
     HostElems ef, ec;
     std::vector<unsigned char> onb_f, onb_c; // on-boundary flags
@@ -43,7 +47,13 @@ struct HostSell {
 };
 void build_sell(const HostCsr& c, int C, int sigma, HostSell& out);
 
-// Build everything from a coarse mesh. Returns CGP_OK, CGP_ERR_ARG or CGP_ERR_MESH.
-int build_host_mesh(const cgp_mesh_desc* d, int levels, HostMesh& out);
+// Build everything from a coarse mesh. With renumber_fine (and levels >= 1) the fine nodes are
+// stored in Hilbert-curve order of their coordinates (fperm). Returns CGP_OK, CGP_ERR_ARG or
+// CGP_ERR_MESH.
+int build_host_mesh(const cgp_mesh_desc* d, int levels, HostMesh& out, bool renumber_fine = false);
+
+// The CSR pattern `in` of the stored fine order, rows and columns mapped back to the refinement
+// order through fperm (columns sorted): out, and src[k] = the entry of `in` that entry k of out is.
+void csr_to_refinement_order(const HostCsr& in, const std::vector<int>& fperm, HostCsr& out, std::vector<int>& src);
 
 }  // namespace cgp

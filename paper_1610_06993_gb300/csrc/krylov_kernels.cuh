@@ -28,8 +28,8 @@ __device__ __forceinline__ void spmv_rows_chunk(int k, const int (&ka)[R], const
 #pragma unroll
         for (int e = 0; e < CNT; ++e) {
             const bool in = k + e < na[q];
-            j[q][e] = in ? __ldg(ci + ka[q] + k + e) : -1;
-            v[q][e] = in ? (TX)__ldg(val + ka[q] + k + e) : (TX)0;
+            j[q][e] = in ? __ldcs(ci + ka[q] + k + e) : -1;
+            v[q][e] = in ? (TX)__ldcs(val + ka[q] + k + e) : (TX)0;
         }
 #pragma unroll
     for (int q = 0; q < R; ++q)
@@ -57,8 +57,10 @@ __device__ __forceinline__ void spmv_rows_chunk(int k, const int (&ka)[R], const
 // number by R (measured on the 1M-row cylinder mesh: four rows per thread were no faster than two;
 // with perfectly coalesced x reads a product was only a fifth faster, so it is bound by the
 // matrix stream at this occupancy rather than by the gathers). x is written by other blocks during
-// the launch, so it is read with ordinary (coherent) loads; the matrix goes through the read-only
-// path. CGP_ROWS_F32 sets R for the single-context FP32 products, the rest take two (registers).
+// the launch, so it is read with ordinary (coherent) loads; the matrix is streamed with the
+// evict-first hint, so that it does not push the Krylov vectors out of L2 (on the 1M-row cylinder
+// mesh the momentum products fell from ~44 to ~35 us). CGP_ROWS_F32 sets R for the single-context
+// FP32 products, the rest take two (registers).
 template <int NR, typename TV, typename TX, int R = 2, typename Emit>
 __device__ __forceinline__ void spmv_rows(RowRange rr, const int* __restrict__ rp, const int* __restrict__ ci,
                                           const TV* __restrict__ val, const TX* x, Emit emit) {

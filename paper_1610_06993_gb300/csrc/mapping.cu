@@ -63,9 +63,11 @@ __global__ void k_gradient(int nf, const int* __restrict__ rp, const int* __rest
 
 // Eq. 23 with Eq. 15's dt/rho: u = u~ - (dt/rho) w, then prescribed velocity values at Dirichlet
 // nodes (Eq. 3). Optionally copies w out.
+// u = u~ - c w with Dirichlet values restored (Eq. 23); the outputs go to position perm[i] of the
+// refinement order when perm is given (the caller's arrays), else to i.
 __global__ void k_correct(int nf, const double* ut, const double* __restrict__ w, double c,
                           const unsigned char* __restrict__ mask, const double* __restrict__ gd, double* u,
-                          double* gp_out) {
+                          double* gp_out, const int* __restrict__ perm) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
     double tx, ty, wx, wy, gx, gy;
@@ -73,8 +75,26 @@ __global__ void k_correct(int nf, const double* ut, const double* __restrict__ w
     load2(w, i, wx, wy);
     load2(gd, i, gx, gy);
     const unsigned char m = mask[i];
-    store2(u, i, (m & CGP_BC_U) ? gx : tx - c * wx, (m & CGP_BC_V) ? gy : ty - c * wy);
-    if (gp_out) store2(gp_out, i, wx, wy);
+    const int o = perm ? perm[i] : i;
+    store2(u, o, (m & CGP_BC_U) ? gx : tx - c * wx, (m & CGP_BC_V) ? gy : ty - c * wy);
+    if (gp_out) store2(gp_out, o, wx, wy);
+}
+
+// Between the stored fine order and the refinement order: dst[i] = src[perm[i]] (to_stored) or
+// dst[perm[i]] = src[i], for `comps` interleaved values per node (1 or 2).
+__global__ void k_permute(int n, int comps, const int* __restrict__ perm, const double* __restrict__ src,
+                          double* __restrict__ dst, int to_stored) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = perm[i];
+    const int from = to_stored ? p : i, to = to_stored ? i : p;
+    if (comps == 2) {
+        double x, y;
+        load2(src, from, x, y);
+        store2(dst, to, x, y);
+    } else {
+        dst[to] = src[from];
+    }
 }
 
 __global__ void k_copy_pairs(const double2* __restrict__ src, double2* __restrict__ dst, int n) {
@@ -192,8 +212,27 @@ cudaError_t launch_gradient(cgp_ctx_s* c, const double* pf, double* grad, cudaSt
 }
 
 cudaError_t launch_correct(cgp_ctx_s* c, const double* ut, const double* w, double* u, double* gp_out,
-                           cudaStream_t s) {
-    k_correct<<<(c->nf + 255) / 256, 256, 0, s>>>(c->nf, ut, w, c->prm.dt / c->prm.rho, c->vel_mask, c->g, u, gp_out);
+                           cudaStream_t s, bool to_public) {
+    k_correct<<<(c->nf + 255) / 256, 256, 0, s>>>(c->nf, ut, w, c->prm.dt / c->prm.rho, c->vel_mask, c->g, u, gp_out,
+                                                  to_public ? c->fperm : nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t fine_to_stored(cgp_ctx_s* c, const double* pub, double* st, int comps, cudaStream_t s) {
+    if (!c->fperm) {
+        if (pub == st) return cudaSuccess;
+        return cudaMemcpyAsync(st, pub, sizeof(double) * comps * (size_t)c->nf, cudaMemcpyDeviceToDevice, s);
+    }
+    k_permute<<<(c->nf + 255) / 256, 256, 0, s>>>(c->nf, comps, c->fperm, pub, st, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t fine_to_public(cgp_ctx_s* c, const double* st, double* pub, int comps, cudaStream_t s) {
+    if (!c->fperm) {
+        if (pub == st) return cudaSuccess;
+        return cudaMemcpyAsync(pub, st, sizeof(double) * comps * (size_t)c->nf, cudaMemcpyDeviceToDevice, s);
+    }
+    k_permute<<<(c->nf + 255) / 256, 256, 0, s>>>(c->nf, comps, c->fperm, st, pub, 0);
     return cudaGetLastError();
 }
 
@@ -378,6 +417,7 @@ struct GatherArgs {
     const unsigned char* vmask;
     const double* g;
     double* u;
+    const int* perm;    // refinement-order position of stored fine node i (nullptr: i)
 };
 
 // The same arithmetic as k_restrict_rhs (one lane per row), k_prolong, k_gradient (one lane per
@@ -432,7 +472,25 @@ __global__ void k_correct_b(const GatherArgs* __restrict__ tab) {
     load2(a.w, i, wx, wy);
     load2(a.g, i, gx, gy);
     const unsigned char m = a.vmask[i];
-    store2(a.u, i, (m & CGP_BC_U) ? gx : tx - a.cdr * wx, (m & CGP_BC_V) ? gy : ty - a.cdr * wy);
+    store2(a.u, a.perm ? a.perm[i] : i, (m & CGP_BC_U) ? gx : tx - a.cdr * wx, (m & CGP_BC_V) ? gy : ty - a.cdr * wy);
+}
+
+// The velocities of the instances that store their fine nodes in another order, gathered into
+// that order (instance blockIdx.y of the table) at the start of a batched step.
+struct PermArgs {
+    int n;
+    const int* perm;
+    const double* pub;
+    double* st;
+};
+
+__global__ void k_permute_b(const PermArgs* __restrict__ tab) {
+    const PermArgs& a = tab[blockIdx.y];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    double x, y;
+    load2(a.pub, a.perm[i], x, y);
+    store2(a.st, i, x, y);
 }
 
 }  // namespace
@@ -474,6 +532,7 @@ bool batch_gather_build(cgp_batch_s* b) {
         a.vmask = c->vel_mask;
         a.g = c->g;
         a.u = b->u[i];
+        a.perm = c->fperm;
         maxc = std::max(maxc, c->nc);
         maxf = std::max(maxf, c->nf);
         maxl = std::max(maxl, c->levels);
@@ -506,6 +565,34 @@ cudaError_t batch_prolong_gradient_launch(cgp_batch_s* b, cudaStream_t s) {
 
 cudaError_t batch_correct_launch(cgp_batch_s* b, cudaStream_t s) {
     k_correct_b<<<dim3((b->gather_nf + 255) / 256, b->n), 256, 0, s>>>((const GatherArgs*)b->tab_gather);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_perm_build(cgp_batch_s* b) {
+    b->perm_count = 0;
+    std::vector<PermArgs> tab;
+    int nmax = 0;
+    for (int i = 0; i < b->n; ++i) {
+        cgp_ctx_s* c = b->ctx[i];
+        if (!c->fperm) continue;
+        tab.push_back(PermArgs{c->nf, c->fperm, b->u[i], c->u_int});
+        nmax = std::max(nmax, c->nf);
+    }
+    if (tab.empty()) return cudaSuccess;
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(PermArgs) * tab.size());
+    if (e != cudaSuccess) return e;
+    b->allocs.push_back(d);
+    if ((e = cudaMemcpy(d, tab.data(), sizeof(PermArgs) * tab.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    b->tab_perm = d;
+    b->perm_nmax = nmax;
+    b->perm_count = (int)tab.size();
+    return cudaSuccess;
+}
+
+cudaError_t batch_perm_launch(cgp_batch_s* b, cudaStream_t s) {
+    if (b->perm_count == 0) return cudaSuccess;
+    k_permute_b<<<dim3((b->perm_nmax + 255) / 256, b->perm_count), 256, 0, s>>>((const PermArgs*)b->tab_perm);
     return cudaGetLastError();
 }
 

@@ -145,6 +145,33 @@ def test_taylor_green_time_dependent_bc(L, levels):
     assert e < 1e-10, e
 
 
+@pytest.mark.parametrize("name", ["cylinder_small", "bfs4"])
+def test_fine_storage_orders_agree(L, name):
+    """The fine nodes stored along a Hilbert curve (default) or in the refinement order: both
+    orders give the oracle's step (Eqs. 19-23) to the parity bar after 20 steps, through the
+    interface's refinement-order vectors (velocity, and pf and gp from the stage entry points)."""
+    if name == "bfs4":
+        coarse, prob = ci.bfs_mesh(4, 1001), ci.bfs_problem(400.0, 0.005, 1)
+    else:
+        coarse, prob, _ = ci.workload(name)
+    ref = ocgp.run(coarse, prob, 20)
+    out = {}
+    for order in (0, 1):
+        f = flow(coarse, prob, rtol=1e-13, fine_order=order)
+        assert f.info.fine_order == order
+        gp = _steps_with_gradient(L, f, 20)
+        f.stats(check=True)
+        pf = torch.empty(f.info.n_fine, dtype=torch.float64, device="cuda")
+        u1 = torch.empty_like(f.u)
+        L.cgp_prolong_correct(f.ctx, f.pc, f.u, u1, pf, None)
+        out[order] = (f.u.cpu().numpy(), gp, pf.cpu().numpy())
+        f.close()
+        eu, eg = rel(out[order][0], ref.u), rel(gp, ref.gp)
+        assert eu < 1e-10 and eg < 1e-10, (order, eu, eg)
+    for k in range(3):
+        assert rel(out[0][k], out[1][k]) < 1e-10, k
+
+
 def _steps_with_gradient(L, f, n):
     """n steps; the last one through the stage entry points, returning w = M^-1 G p_f (the
     pressure gradient the correction applies) on the host."""
