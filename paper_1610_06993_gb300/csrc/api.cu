@@ -442,8 +442,11 @@ int cgp_fine_mesh(cgp_ctx c, double* xy_host, int* tri_host, unsigned char* onb_
         }
         if (onb_host) onb_host[q] = c->hm.onb_f[i];
     }
-    if (tri_host)
-        for (size_t k = 0; k < L.tri.size(); ++k) tri_host[k] = fp[L.tri[k]];
+    if (tri_host) {
+        const std::vector<int>& tp = c->hm.tperm;
+        for (int t = 0; t < L.t; ++t)
+            for (int a = 0; a < 3; ++a) tri_host[3 * (size_t)tp[t] + a] = fp[L.tri[3 * (size_t)t + a]];
+    }
     return CGP_OK;
 }
 

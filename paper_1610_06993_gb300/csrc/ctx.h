@@ -174,7 +174,7 @@ struct cgp_ctx_s {
     // Galerkin restriction (restrict_mode 1): per level k the inverse child lists of the s^p
     // table (for each level-k node the finer nodes whose (beta, gamma) pair contains it) and the
     // fine divergence D_f u~_f
-    std::vector<int*> gal_ptr, gal_idx;
+    std::vector<int*> gal_ptr, gal_idx, gal_self;   // gal_self: the coinciding finer node
     double* gal_div = nullptr;   // [nf]
     // incremental / rotational pressure correction (projection 1, 2)
     double* grad_n = nullptr;    // [nf][2] G_f P p_c^n, the momentum right-hand side's pressure term

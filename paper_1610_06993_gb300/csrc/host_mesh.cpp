@@ -259,6 +259,18 @@ int build_host_mesh(const cgp_mesh_desc* d, int levels, HostMesh& out, bool renu
         F.xy.swap(xy);
         out.onb_f.swap(onb);
         out.sp[levels - 1].swap(sp);
+        // triangles follow their nodes (the assembly's element loops then read and write nearby
+        // rows): stable sort by the smallest stored node index
+        std::vector<int> tkey(F.t);
+        for (int t = 0; t < F.t; ++t)
+            tkey[t] = std::min({F.tri[3 * t], F.tri[3 * t + 1], F.tri[3 * t + 2]});
+        out.tperm.resize(F.t);
+        for (int t = 0; t < F.t; ++t) out.tperm[t] = t;
+        std::stable_sort(out.tperm.begin(), out.tperm.end(), [&](int a, int b) { return tkey[a] < tkey[b]; });
+        std::vector<int> tri(F.tri.size());
+        for (int t = 0; t < F.t; ++t)
+            for (int a = 0; a < 3; ++a) tri[3 * (size_t)t + a] = F.tri[3 * (size_t)out.tperm[t] + a];
+        F.tri.swap(tri);
     }
     // CSR patterns and element data of the coarse and fine meshes
     {

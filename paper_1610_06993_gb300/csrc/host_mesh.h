@@ -32,6 +32,9 @@ struct HostMesh {
     // (empty: the refinement order itself). Everything of the fine level above (xy, tri, the last
     // s^p table's rows, su, onb_f, the fine CSR and elements) is in the stored order.
     std::vector<int> fperm;
+    // Stored order of the fine triangles when fperm is set: tperm[k] is the refinement-order index
+    // of stored triangle k (sorted by their smallest stored node index).
+    std::vector<int> tperm;
     HostCsr fine, coarse;
     HostElems ef, ec;
     std::vector<unsigned char> onb_f, onb_c; // on-boundary flags

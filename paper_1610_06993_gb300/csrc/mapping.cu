@@ -118,18 +118,19 @@ __global__ void k_divergence(int nf, const int* __restrict__ rp, const int* __re
     d[i] = acc;
 }
 
-// One level of P^T (the transpose of Eq. 29's prolongation): r_k[i] = r_{k+1}[i] (the
-// parent-coincident row, weight 1) + 1/2 sum over the finer nodes alpha whose pair (beta, gamma)
-// contains i of r_{k+1}[alpha], in the fixed order of the inverse child list. With `pm` (the last
-// level) the result is scaled and zeroed at pressure-held rows: b_c = scale P^T d.
+// One level of P^T (the transpose of Eq. 29's prolongation): r_k[i] = r_{k+1}[self[i]] (the
+// parent-coincident row alpha with beta = gamma = i, weight 1) + 1/2 sum over the finer nodes
+// alpha whose pair (beta, gamma) contains i with beta != gamma of r_{k+1}[alpha], in the fixed
+// order of the inverse child list. With `pm` (the last level) the result is scaled and zeroed at
+// pressure-held rows: b_c = scale P^T d.
 __global__ void k_restrict_transpose(int n, const int* __restrict__ ptr, const int* __restrict__ idx,
-                                     const double* __restrict__ src, double* __restrict__ dst,
-                                     const unsigned char* __restrict__ pm, double scale) {
+                                     const int* __restrict__ self, const double* __restrict__ src,
+                                     double* __restrict__ dst, const unsigned char* __restrict__ pm, double scale) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double h = 0.0;
     for (int m = ptr[i]; m < ptr[i + 1]; ++m) h += src[idx[m]];
-    const double r = src[i] + 0.5 * h;
+    const double r = src[self[i]] + 0.5 * h;
     dst[i] = pm ? (pm[i] ? 0.0 : scale * r) : r;
 }
 
@@ -176,8 +177,8 @@ cudaError_t launch_restrict_rhs(cgp_ctx_s* c, const double* ut, double* bc, cuda
             const int n = c->lv_n[k];
             const bool last = k == 0;
             double* dst = last ? bc : c->pl[k - 1];   // pl[k - 1] holds N_k values
-            k_restrict_transpose<<<(n + 255) / 256, 256, 0, s>>>(n, c->gal_ptr[k], c->gal_idx[k], src, dst,
-                                                                last ? c->p_mask : nullptr, scale);
+            k_restrict_transpose<<<(n + 255) / 256, 256, 0, s>>>(n, c->gal_ptr[k], c->gal_idx[k], c->gal_self[k], src,
+                                                                dst, last ? c->p_mask : nullptr, scale);
             src = dst;
         }
         return cudaGetLastError();
@@ -364,28 +365,41 @@ int galerkin_build(cgp_ctx_s* c) {
     for (int k = 0; k < c->levels; ++k) {
         const int nk = H.lv[k].n, nk1 = H.lv[k + 1].n;
         const std::vector<int>& sp = H.sp[k];   // [nk1][2]
-        std::vector<int> ptr(nk + 1, 0), idx;
-        for (int a = nk; a < nk1; ++a) {
+        // the finer node coinciding with each coarser one (beta = gamma) and the inverse lists of
+        // the midpoints (beta != gamma), in the order of the finer level's stored numbering
+        std::vector<int> ptr(nk + 1, 0), idx, self(nk, -1);
+        for (int a = 0; a < nk1; ++a) {
+            if (sp[2 * a] == sp[2 * a + 1]) {
+                self[sp[2 * a]] = a;
+                continue;
+            }
             ptr[sp[2 * a] + 1] += 1;
             ptr[sp[2 * a + 1] + 1] += 1;
         }
+        for (int i = 0; i < nk; ++i)
+            if (self[i] < 0) return CGP_ERR_MESH;
         for (int i = 0; i < nk; ++i) ptr[i + 1] += ptr[i];
         idx.assign(ptr[nk], 0);
         std::vector<int> pos(ptr.begin(), ptr.end() - 1);
-        for (int a = nk; a < nk1; ++a) {
+        for (int a = 0; a < nk1; ++a) {
+            if (sp[2 * a] == sp[2 * a + 1]) continue;
             idx[pos[sp[2 * a]]++] = a;
             idx[pos[sp[2 * a + 1]]++] = a;
         }
-        void *dp = nullptr, *di = nullptr;
+        void *dp = nullptr, *di = nullptr, *ds = nullptr;
         if (cudaMalloc(&dp, sizeof(int) * ptr.size()) != cudaSuccess) return CGP_ERR_NOMEM;
         c->allocs.push_back(dp);
         if (cudaMalloc(&di, sizeof(int) * std::max<size_t>(1, idx.size())) != cudaSuccess) return CGP_ERR_NOMEM;
         c->allocs.push_back(di);
+        if (cudaMalloc(&ds, sizeof(int) * self.size()) != cudaSuccess) return CGP_ERR_NOMEM;
+        c->allocs.push_back(ds);
         if (cudaMemcpy(dp, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-            (!idx.empty() && cudaMemcpy(di, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice) != cudaSuccess))
+            (!idx.empty() && cudaMemcpy(di, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice) != cudaSuccess) ||
+            cudaMemcpy(ds, self.data(), sizeof(int) * self.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return CGP_ERR_CUDA;
         c->gal_ptr.push_back((int*)dp);
         c->gal_idx.push_back((int*)di);
+        c->gal_self.push_back((int*)ds);
     }
     return CGP_OK;
 }

@@ -55,6 +55,7 @@ def test_fine_mesh_matches_oracle(L, cavity_state):
     coarse, prob, orc, _ = cavity_state
     f = flow(coarse, prob)
     assert np.array_equal(f.fine_xy, orc.fine.xy)
+    assert np.array_equal(f.fine_tri, orc.fine.tri)   # refinement order, whatever the stored order
     assert np.array_equal(f.onb_f, orc.onb_f)
     assert f.info.n_fine == 4225 and f.info.nnz_fine == 29057 and f.info.nnz_coarse == 7361
     f.close()
