@@ -237,15 +237,18 @@ int cgp_assemble(cgp_ctx ctx, const double* u_dev, void* stream);
  * BiCGStab on both components at once, preconditioned by Jacobi or by the FP32 Chebyshev
  * polynomial of cgp_params.momentum_degree (CGP_MIXED: FP32 BiCGStab inside FP64 iterative
  * refinement). Requires cgp_assemble() on the same u^n first. u_dev: u^n, the initial
- * guess, plus the previous converged increment when warm_start >= 1; ut_dev: [n_fine][2] output
- * u~^{n+1}. ut_dev may equal u_dev (the increment kept for the next guess is then zero). */
+ * guess, plus the previous converged increment when warm_start >= 1, or NULL for the velocity of
+ * the last cgp_assemble (no second copy into the library's fine order); ut_dev: [n_fine][2]
+ * output u~^{n+1}, or NULL to keep u~^{n+1} inside the context for cgp_restrict and
+ * cgp_prolong_correct (no copy out of the library's fine order). */
 int cgp_momentum_solve(cgp_ctx ctx, const double* u_dev, double* ut_dev, void* stream);
 
 /* Steps 2-3 right-hand side, Eqs. 20-21 with Eq. 30: u~_c = u~_f[xi] (injection), then
  * b_c = -(rho/dt) (Dx_c u~_c,x + Dy_c u~_c,y) with D_ij = int psi_i d phi_j on the coarse mesh,
  * zero at p-masked nodes; with restrict_mode = 1, b_c = -(rho/dt) P^T (Dx_f u~_x + Dy_f u~_y)
  * instead (P^T level by level through inverse child lists of the s^p tables of Eq. 29).
- * ut_dev: [n_fine][2]; bc_dev: [n_coarse] output. */
+ * ut_dev: [n_fine][2], or NULL for the context's u~ of the last cgp_momentum_solve; bc_dev:
+ * [n_coarse] output. */
 int cgp_restrict(cgp_ctx ctx, const double* ut_dev, double* bc_dev, void* stream);
 
 /* Step 3, Eq. 21: solve K_c p_c = b_c (K_c = coarse stiffness, +(-Laplacian), after symmetric
@@ -261,7 +264,8 @@ int cgp_poisson_solve(cgp_ctx ctx, const double* bc_dev, double* pc_dev, void* s
  * with CGP_MIXED), preconditioned by Jacobi or the FP32 Chebyshev polynomial of
  * cgp_params.mass_degree, then
  * u = u~ - (dt/rho) w and Dirichlet nodes reset to their prescribed values.
- * pc_dev [n_coarse], ut_dev [n_fine][2] inputs; u_dev [n_fine][2] output (may equal ut_dev);
+ * pc_dev [n_coarse], ut_dev [n_fine][2] inputs (ut_dev NULL: the context's u~ of the last
+ * cgp_momentum_solve); u_dev [n_fine][2] output (may equal ut_dev);
  * pf_dev [n_fine] and gp_dev [n_fine][2] optional outputs (NULL to skip): p_f and w. */
 int cgp_prolong_correct(cgp_ctx ctx, const double* pc_dev, const double* ut_dev, double* u_dev,
                         double* pf_dev, double* gp_dev, void* stream);

@@ -495,29 +495,35 @@ int cgp_assemble(cgp_ctx c, const double* u_dev, void* stream) {
         u = c->u_int;
     }
     CK(launch_assemble_step(c, u, s));
+    c->u_asm = u;
     return CGP_OK;
 }
 
 int cgp_momentum_solve(cgp_ctx c, const double* u_dev, double* ut_dev, void* stream) {
-    if (!c || !u_dev || !ut_dev) return CGP_ERR_ARG;
+    if (!c) return CGP_ERR_ARG;
     if (!c->bc_set) return CGP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
-    if (!c->fperm) {
-        CK(launch_momentum_bicgstab(c, u_dev, ut_dev, s));
-        return CGP_OK;
+    const double* u = c->u_asm;   // NULL u_dev: the velocity of the last cgp_assemble
+    if (u_dev) {
+        u = u_dev;
+        if (c->fperm) {
+            CK(fine_to_stored(c, u_dev, c->u_int, 2, s));
+            u = c->u_int;
+        }
     }
-    CK(fine_to_stored(c, u_dev, c->u_int, 2, s));
-    CK(launch_momentum_bicgstab(c, c->u_int, c->ut, s));
-    CK(fine_to_public(c, c->ut, ut_dev, 2, s));
+    if (!u) return CGP_ERR_STATE;
+    double* x = (ut_dev && !c->fperm) ? ut_dev : c->ut;   // NULL ut_dev: u~ stays in the context
+    CK(launch_momentum_bicgstab(c, u, x, s));
+    if (ut_dev && c->fperm) CK(fine_to_public(c, c->ut, ut_dev, 2, s));
     return CGP_OK;
 }
 
 int cgp_restrict(cgp_ctx c, const double* ut_dev, double* bc_dev, void* stream) {
-    if (!c || !ut_dev || !bc_dev) return CGP_ERR_ARG;
+    if (!c || !bc_dev) return CGP_ERR_ARG;
     if (!c->bc_set) return CGP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
-    const double* ut = ut_dev;
-    if (c->fperm) {
+    const double* ut = ut_dev ? ut_dev : c->ut;   // NULL: the context's u~ of cgp_momentum_solve
+    if (ut_dev && c->fperm) {
         CK(fine_to_stored(c, ut_dev, c->ut, 2, s));
         ut = c->ut;
     }
@@ -541,11 +547,11 @@ int cgp_poisson_solve(cgp_ctx c, const double* bc_dev, double* pc_dev, void* str
 
 int cgp_prolong_correct(cgp_ctx c, const double* pc_dev, const double* ut_dev, double* u_dev, double* pf_dev,
                         double* gp_dev, void* stream) {
-    if (!c || !pc_dev || !ut_dev || !u_dev) return CGP_ERR_ARG;
+    if (!c || !pc_dev || !u_dev) return CGP_ERR_ARG;
     if (!c->bc_set) return CGP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
-    const double* ut = ut_dev;
-    if (c->fperm) {
+    const double* ut = ut_dev ? ut_dev : c->ut;   // NULL: the context's u~ of cgp_momentum_solve
+    if (ut_dev && c->fperm) {
         CK(fine_to_stored(c, ut_dev, c->ut, 2, s));
         ut = c->ut;
     }

@@ -151,6 +151,7 @@ struct cgp_ctx_s {
     // stored node i (nullptr: the two orders coincide). u_int: the velocity in the stored order.
     int* fperm = nullptr;
     double* u_int = nullptr;
+    const double* u_asm = nullptr;   // the stored-order velocity of the last cgp_assemble
     // the stand-alone product (cgp_spmv) works on vectors in the refinement order: A0 in the CSR
     // pattern of that order (P; its SELL copy below is built from it)
     cgp::DevCsr P;

@@ -223,6 +223,20 @@ def test_deterministic_and_host_entry(L):
         L.cgp_step_host(f.ctx, uh, ph)
     f.close()
     assert np.array_equal(uh, outs[0])
+    # the stage entry points with the intermediate velocity kept inside the context (NULL u~)
+    f = flow(coarse, prob, rtol=1e-10)
+    bc = torch.empty_like(f.pc)
+    for _ in range(3):
+        L.cgp_assemble(f.ctx, f.u)
+        L.cgp_momentum_solve(f.ctx, None, None)
+        L.cgp_restrict(f.ctx, None, bc)
+        L.cgp_predict_pressure(f.ctx, f.pc)
+        L.cgp_poisson_solve(f.ctx, bc, f.pc)
+        L.cgp_prolong_correct(f.ctx, f.pc, None, f.u)
+    f.stats(check=True)
+    us = f.u.cpu().numpy()
+    f.close()
+    assert np.array_equal(us, outs[0])
 
 
 def test_zero_flow_stays_zero(L):
