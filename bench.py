@@ -433,7 +433,8 @@ def run_gpu(args):
                     **({"inner_rtol": args.inner_rtol} if args.inner_rtol > 0 else {}),
                     **({"mass_degree": args.mass_degree} if args.mass_degree > 0 else {}),
                     **({"momentum_degree": args.momentum_degree} if args.momentum_degree > 0 else {}),
-                    solver_format=args.solver_format, fine_order=args.fine_order)
+                    solver_format=args.solver_format, fine_order=args.fine_order,
+                    momentum_rtol=args.momentum_rtol)
 
     stream = torch.cuda.current_stream()
     flush = L2Flush(dev)
@@ -902,6 +903,7 @@ def main():
     ap.add_argument("--momentum-degree", type=int, default=0)  # 0: the library default
     ap.add_argument("--solver-format", type=int, default=0)    # 0: automatic, 1: sliced ELL, 2: CSR
     ap.add_argument("--fine-order", type=int, default=0)       # 0: Hilbert-curve storage, 1: refinement order
+    ap.add_argument("--momentum-rtol", type=float, default=0.0)   # 0: rtol
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spmv", action="store_true")
     args = ap.parse_args()

@@ -134,6 +134,9 @@ typedef struct {
                           order. Every fine-mesh array crossing this interface (cgp_fine_mesh,
                           cgp_set_bc, velocities, pf, gp) is in the refinement order either way; the
                           library permutes on the way in and out */
+    double momentum_rtol; /* tolerance of the momentum solve (Eq. 19) alone: 0 (default) = rtol; a
+                          smaller value leaves less solver error in u~, which the extrapolated guesses
+                          of the later solves carry forward */
 } cgp_params;
 
 /* A coarse mesh: n_nodes points xy_host[n][2] and n_tris counter-clockwise triangles
@@ -173,7 +176,8 @@ typedef struct {
 /* Fill *p with the defaults: rho = 1, mu = 0.01, dt = 0.01, levels = 1, CGP_FP64, rtol = 1e-8,
  * inner_rtol = 1e-4, max_iter = 20000, max_outer = 30, spmv_lanes = 0, block_threads = 0,
  * coarse_solver = 0, spmv_format = 0, precond_degree = 0, precond_ratio = 0, warm_start = 3, mass_degree = 0,
- * momentum_degree = 0, solver_format = 0, restrict_mode = 0, projection = 0, fine_order = 0. */
+ * momentum_degree = 0, solver_format = 0, restrict_mode = 0, projection = 0, fine_order = 0,
+ * momentum_rtol = 0. */
 void cgp_default_params(cgp_params* p);
 
 /* Preprocessing (the paper's C_pre, Sect. 2.4): validates the coarse mesh, refines it

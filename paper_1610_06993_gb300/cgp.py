@@ -36,7 +36,8 @@ class cgp_params(C.Structure):
                 ("block_threads", C.c_int), ("coarse_solver", C.c_int), ("spmv_format", C.c_int),
                 ("precond_degree", C.c_int), ("precond_ratio", C.c_double), ("warm_start", C.c_int),
                 ("mass_degree", C.c_int), ("momentum_degree", C.c_int), ("solver_format", C.c_int),
-                ("restrict_mode", C.c_int), ("projection", C.c_int), ("fine_order", C.c_int)]
+                ("restrict_mode", C.c_int), ("projection", C.c_int), ("fine_order", C.c_int),
+                ("momentum_rtol", C.c_double)]
 
 
 class cgp_mesh_desc(C.Structure):

@@ -89,6 +89,8 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     if (P.restrict_mode < 0 || P.restrict_mode > 1) return CGP_ERR_ARG;
     if (P.projection < 0 || P.projection > 2) return CGP_ERR_ARG;
     if (P.fine_order < 0 || P.fine_order > 1) return CGP_ERR_ARG;
+    if (!(P.momentum_rtol >= 0.0)) return CGP_ERR_ARG;
+    if (P.momentum_rtol == 0.0) P.momentum_rtol = P.rtol;
     if (P.inner_rtol <= 0.0) P.inner_rtol = 1e-4;
     if (P.max_iter <= 0) P.max_iter = 20000;
     if (P.max_outer <= 0) P.max_outer = 30;

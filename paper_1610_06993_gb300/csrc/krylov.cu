@@ -112,7 +112,7 @@ BicgArgs<TI> momentum_args(cgp_ctx_s* c, const double* u_in, double* x, SyncWord
     a.r = carve<TI>(p, n2); a.rh = carve<TI>(p, n2); a.p = carve<TI>(p, n2);
     a.v = carve<TI>(p, n2); a.y = carve<TI>(p, n2); a.s = carve<TI>(p, n2);
     a.z = carve<TI>(p, n2); a.t = carve<TI>(p, n2); a.d = carve<TI>(p, n2);
-    a.part = part; a.sw = sw; a.rtol = c->prm.rtol; a.inner_rtol = mixed ? c->prm.inner_rtol : 0.0;
+    a.part = part; a.sw = sw; a.rtol = c->prm.momentum_rtol; a.inner_rtol = mixed ? c->prm.inner_rtol : 0.0;
     a.max_iter = c->prm.max_iter; a.max_outer = c->prm.max_outer; a.lanes = c->sh_f.lanes;
     a.st_iters = &c->stats->mom_iters; a.st_outer = &c->stats->mom_outer; a.st_status = &c->stats->mom_status;
     a.st_rel = &c->stats->mom_rel; a.st_barrier = &c->stats->barrier_status;

@@ -132,6 +132,20 @@ def test_cavity33_default_tolerance_error_is_stated(L):
     assert errs[0] < 1e-6 and errs[1] < 1e-6, errs
 
 
+def test_momentum_tolerance_of_its_own(L):
+    """momentum_rtol: the momentum solve (Eq. 19) alone runs to its own tolerance (here 1e-11
+    under rtol = 1e-8 for the others)."""
+    coarse, prob, _ = ci.workload("cavity33")
+    f = flow(coarse, prob, rtol=1e-8, momentum_rtol=1e-11)
+    for _ in range(5):
+        f.step()
+        st = f.stats(check=True)
+        assert st.momentum_rel_res <= 1e-11 and st.poisson_rel_res <= 1e-8, st.as_dict()
+    e = rel(f.u.cpu().numpy(), ocgp.run(coarse, prob, 5).u)
+    f.close()
+    assert e < 1e-6, e
+
+
 @pytest.mark.parametrize("levels", [0, 2])
 def test_taylor_green_time_dependent_bc(L, levels):
     """Taylor-Green (Eqs. 34-36) with exact Dirichlet data at t^{n+1}, levels 0 and 2."""
