@@ -531,6 +531,7 @@ def run_gpu(args):
                                f", state developed by {args.develop} GPU steps from rest (t = {state_t - args.steps * prob.dt:.3f} "
                                f"at the first timed step)",
                    "rtol": args.rtol, "precision": args.precision,
+                   "momentum_rtol": args.momentum_rtol if args.momentum_rtol > 0 else min(args.rtol, max(0.1 * args.rtol, 1e-14)),
                    "l2": "flushed before every timed step (512 MB write, then 256 MB read)",
                    "parallelism": "replicas" if ws > 1 else "1gpu",
                    "block_threads": info.block_threads, "grid_blocks": info.grid_blocks,
