@@ -309,9 +309,15 @@ int cgp_assemble_incremental(cgp_ctx ctx, const double* u_dev, const double* pc_
  * phi_dev, pc_dev: [n_coarse]. Stream-ordered. Errors: CGP_ERR_ARG, CGP_ERR_STATE (projection 0). */
 int cgp_pressure_update(cgp_ctx ctx, const double* bc_dev, const double* phi_dev, double* pc_dev, void* stream);
 
+/* The library's storage order of the fine nodes: perm_host[n_fine] receives, for each stored node
+ * i, its index in the refinement order of cgp_fine_mesh (the identity with fine_order = 1 or
+ * levels = 0). Errors: CGP_ERR_ARG. */
+int cgp_fine_order(cgp_ctx ctx, int* perm_host);
+
 /* y = A0 x with A0 = rho M + dt mu K (the constant part of the momentum matrix of Eq. 19) on the
- * fine mesh, for two interleaved right-hand sides: x_dev, y_dev [n_fine][2]. The SpMV kernel of
- * the Krylov solvers as a stand-alone launch (lanes per row from cgp_autotune). Stream-ordered. */
+ * fine mesh, for two interleaved right-hand sides: x_dev, y_dev [n_fine][2] in the library's
+ * stored fine order (cgp_fine_order), the layout the Krylov solvers multiply in. The sliced-ELL
+ * or CSR SpMV kernel (cgp_autotune picks) as a stand-alone launch. Stream-ordered. */
 int cgp_spmv(cgp_ctx ctx, const double* x_dev, double* y_dev, void* stream);
 
 /* Copy the coarse right-hand side b_c of the context's latest cgp_step (or batched step) to

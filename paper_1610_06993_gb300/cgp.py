@@ -100,6 +100,7 @@ _SIGNATURES = {
     "cgp_copy_coarse_rhs": (C.c_int, [_VP, _VP, _VP]),
     "cgp_predict_pressure": (C.c_int, [_VP, _VP, _VP]),
     "cgp_spmv": (C.c_int, [_VP, _VP, _VP, _VP]),
+    "cgp_fine_order": (C.c_int, [_VP, _VP]),
     "cgp_gemm_bf16": (C.c_int, [C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP]),
     "cgp_ws_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_VP)]),
     "cgp_ws_set_params": (C.c_int, [_VP] + [_VP] * 6),
@@ -363,6 +364,13 @@ def cgp_batch_get_stats(b: int, n: int, stream=None, check: bool = False):
 
 def cgp_batch_destroy(b: int) -> None:
     _check(load().cgp_batch_destroy(b), "cgp_batch_destroy")
+
+
+def cgp_fine_order(ctx: int, n_fine: int) -> np.ndarray:
+    """Refinement-order index of every stored fine node (the library's storage order)."""
+    perm = np.empty(n_fine, dtype=np.int32)
+    _check(load().cgp_fine_order(ctx, _ptr(perm)), "cgp_fine_order")
+    return perm
 
 
 def cgp_spmv(ctx: int, x_dev, y_dev, stream=None) -> None:

@@ -122,23 +122,10 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     std::vector<int> cif(H.coarse.nnz);
     for (int k = 0; k < H.coarse.nnz; ++k) cif[k] = H.su[H.coarse.ci[k]];
     TRY(upload(c, &c->cif_su, cif));
-    // The stand-alone product (cgp_spmv) takes its vectors in the refinement order: with another
-    // stored order it keeps its own copy of the fine pattern in that order (P, values P_A0
-    // gathered from A0 through p_src once A0 is assembled).
-    HostCsr Pf;
-    int* p_src = nullptr;
-    if (!H.fperm.empty()) {
-        TRY(upload(c, &c->fperm, H.fperm));
-        std::vector<int> src;
-        csr_to_refinement_order(H.fine, H.fperm, Pf, src);
-        TRY(upload_csr(c, Pf, c->P));
-        TRY(upload(c, &p_src, src));
-    } else {
-        c->P = c->F;
-    }
+    if (!H.fperm.empty()) TRY(upload(c, &c->fperm, H.fperm));
     {
         HostSell hs;
-        build_sell(c->fperm ? Pf : H.fine, 32, 32, hs);
+        build_sell(H.fine, 32, 32, hs);
         c->sell_nslices = hs.nslices;
         c->sell_total = hs.ptr[hs.nslices];
         TRY(upload(c, &c->sell_ptr, hs.ptr));
@@ -228,12 +215,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     CK(cudaMemset(c->phi, 0, nc * sizeof(double)));
     TRY(dalloc(c, &c->u_stage, 2 * nf));
     TRY(dalloc(c, &c->pc_stage, nc));
-    if (c->fperm) {
-        TRY(dalloc(c, &c->u_int, 2 * nf));
-        TRY(dalloc(c, &c->P_A0, nnzf));
-    } else {
-        c->P_A0 = c->A0;
-    }
+    if (c->fperm) TRY(dalloc(c, &c->u_int, 2 * nf));
     // Krylov workspace: the largest of BiCGStab (9 pair vectors) and CG (6 vectors), each with
     // the three FP32 pair vectors of its polynomial preconditioner, 256-byte carved
     const size_t need = std::max({9 * 2 * nf * sizeof(double) + 3 * 2 * nf * sizeof(float),
@@ -271,8 +253,7 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
         if ((e = launch_const_assembly(c->EC, nullptr, c->Kc_raw, c->Dc_xy, s)) != cudaSuccess) break;
         if ((e = launch_make_A0(c, Kf, s)) != cudaSuccess) break;
         if ((e = launch_lumped_mass(c, Kf, s)) != cudaSuccess) break;   // Kf (nnz_f >= nnz_c) reused as scratch
-        if (p_src && (e = gather_values((int)nnzf, p_src, c->A0, c->P_A0, s)) != cudaSuccess) break;
-        if ((e = sell_fill(c, c->P_A0, s)) != cudaSuccess) break;
+        if ((e = sell_fill(c, c->A0, s)) != cudaSuccess) break;
         if ((e = ell_fill(c->ell_total, c->ell_src, c->M, c->ell_M, c->ell_M32, s)) != cudaSuccess) break;
         e = cudaStreamSynchronize(s);
     } while (0);
@@ -626,6 +607,12 @@ int cgp_step(cgp_ctx c, double* u_dev, double* pc_dev, void* stream) {
     CK(launch_gradient(c, c->pf, c->grad, s));
     CK(mass_stage(c, s));
     CK(launch_correct(c, c->ut, c->w, u_dev, nullptr, s, true));
+    return CGP_OK;
+}
+
+int cgp_fine_order(cgp_ctx c, int* perm_host) {
+    if (!c || !perm_host) return CGP_ERR_ARG;
+    for (int i = 0; i < c->nf; ++i) perm_host[i] = c->hm.fperm.empty() ? i : c->hm.fperm[i];
     return CGP_OK;
 }
 

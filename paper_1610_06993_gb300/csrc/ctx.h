@@ -152,10 +152,6 @@ struct cgp_ctx_s {
     int* fperm = nullptr;
     double* u_int = nullptr;
     const double* u_asm = nullptr;   // the stored-order velocity of the last cgp_assemble
-    // the stand-alone product (cgp_spmv) works on vectors in the refinement order: A0 in the CSR
-    // pattern of that order (P; its SELL copy below is built from it)
-    cgp::DevCsr P;
-    double* P_A0 = nullptr;
 
     // sliced-ELL (SELL-32-256) copy of the fine pattern for the stand-alone SpMV
     int sell_nslices = 0, sell_total = 0;
@@ -283,8 +279,6 @@ cudaError_t launch_momentum_bicgstab(cgp_ctx_s* c, const double* u_in, double* x
 cudaError_t time_spmv_lanes(cgp_ctx_s* c, bool fine, int lanes, cudaStream_t s, float* ms);
 cudaError_t launch_spmv_fine(cgp_ctx_s* c, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_spmv_sell(cgp_ctx_s* c, const double* x, double* y, cudaStream_t s);
-// out[k] = in[src[k]] (src[k] >= 0) or 0, k < total
-cudaError_t gather_values(int total, const int* src, const double* in, double* out, cudaStream_t s);
 cudaError_t sell_fill(cgp_ctx_s* c, const double* csr_val, cudaStream_t s);
 cudaError_t ell_fill(int total, const int* src, const double* csr_val, double* val, float* val32, cudaStream_t s);
 

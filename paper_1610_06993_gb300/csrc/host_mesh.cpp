@@ -290,33 +290,4 @@ int build_host_mesh(const cgp_mesh_desc* d, int levels, HostMesh& out, bool renu
     return CGP_OK;
 }
 
-void csr_to_refinement_order(const HostCsr& in, const std::vector<int>& fperm, HostCsr& out, std::vector<int>& src) {
-    const int n = in.n;
-    std::vector<int> inv(n);
-    for (int i = 0; i < n; ++i) inv[fperm[i]] = i;
-    out = HostCsr();
-    out.n = n;
-    out.nnz = in.nnz;
-    out.rp.assign(n + 1, 0);
-    for (int q = 0; q < n; ++q) {
-        const int i = inv[q];
-        out.rp[q + 1] = out.rp[q] + (in.rp[i + 1] - in.rp[i]);
-    }
-    out.ci.assign(in.nnz, 0);
-    src.assign(in.nnz, 0);
-    out.diag.assign(n, 0);
-    std::vector<std::pair<int, int>> row;
-    for (int q = 0; q < n; ++q) {
-        const int i = inv[q];
-        row.clear();
-        for (int k = in.rp[i]; k < in.rp[i + 1]; ++k) row.push_back({fperm[in.ci[k]], k});
-        std::sort(row.begin(), row.end());
-        for (size_t e = 0; e < row.size(); ++e) {
-            out.ci[out.rp[q] + (int)e] = row[e].first;
-            src[out.rp[q] + (int)e] = row[e].second;
-            if (row[e].first == q) out.diag[q] = out.rp[q] + (int)e;
-        }
-    }
-}
-
 }  // namespace cgp

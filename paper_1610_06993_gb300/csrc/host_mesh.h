@@ -55,8 +55,5 @@ void build_sell(const HostCsr& c, int C, int sigma, HostSell& out);
 // CGP_ERR_MESH.
 int build_host_mesh(const cgp_mesh_desc* d, int levels, HostMesh& out, bool renumber_fine = false);
 
-// The CSR pattern `in` of the stored fine order, rows and columns mapped back to the refinement
-// order through fperm (columns sorted): out, and src[k] = the entry of `in` that entry k of out is.
-void csr_to_refinement_order(const HostCsr& in, const std::vector<int>& fperm, HostCsr& out, std::vector<int>& src);
 
 }  // namespace cgp

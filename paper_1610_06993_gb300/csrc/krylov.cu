@@ -360,11 +360,6 @@ cudaError_t ell_fill(int total, const int* src, const double* csr_val, double* v
     return cudaGetLastError();
 }
 
-cudaError_t gather_values(int total, const int* src, const double* in, double* out, cudaStream_t s) {
-    k_sell_fill<<<(total + 255) / 256, 256, 0, s>>>(total, src, in, out);
-    return cudaGetLastError();
-}
-
 cudaError_t sell_fill(cgp_ctx_s* c, const double* csr_val, cudaStream_t s) {
     k_sell_fill<<<(c->sell_total + 255) / 256, 256, 0, s>>>(c->sell_total, c->sell_src, csr_val, c->sell_val);
     return cudaGetLastError();
@@ -378,14 +373,14 @@ cudaError_t launch_spmv_sell(cgp_ctx_s* c, const double* x, double* y, cudaStrea
 }
 
 // y = A0 x on the fine mesh for two interleaved right-hand sides (A0 = rho M + dt mu K), x and y
-// in the refinement order (the pattern P and its SELL copy are in that order): the sliced-ELL
-// kernel when the autotuner chose it, else one row group of sh_f.lanes lanes per row.
+// in the stored fine order: the sliced-ELL kernel when the autotuner chose it, else one row group
+// of sh_f.lanes lanes per row.
 cudaError_t launch_spmv_fine(cgp_ctx_s* c, const double* x, double* y, cudaStream_t s) {
     if (c->spmv_sell) return launch_spmv_sell(c, x, y, s);
     const int n = c->nf, threads = 256, lanes = c->sh_f.lanes;
     const int rows_per_block = threads / lanes;
     const int blocks = (n + rows_per_block - 1) / rows_per_block;
-    k_spmv_probe<2><<<blocks, threads, 0, s>>>(n, c->P.rp, c->P.ci, c->P_A0, x, y, lanes, rows_per_block);
+    k_spmv_probe<2><<<blocks, threads, 0, s>>>(n, c->F.rp, c->F.ci, c->A0, x, y, lanes, rows_per_block);
     return cudaGetLastError();
 }
 
