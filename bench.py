@@ -276,6 +276,41 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def solver_spmv(L, f, flush, stream, reps: int = 10):
+    """The fine solvers' FP32 product (cgp_solver_spmv: their launch shape and layout, two
+    right-hand sides) on the headline's momentum matrix as assembled for its last timed step,
+    L2 cleaned before each product. Algorithmic bytes: 8 nnz (FP32 values, columns) + 4 (n + 1)
+    (row pointers) + 8 n (x) + 8 n (y)."""
+    import torch
+    info = L.cgp_mesh_info(f.ctx)
+    n, nnz = info.n_fine, info.nnz_fine
+    if f.params.precision != L.CGP_MIXED:
+        return None
+    x = torch.randn(n, 2, dtype=torch.float32, device=f.u.device)
+    y = torch.empty_like(x)
+    L.cgp_assemble(f.ctx, f.u, stream)
+    L.cgp_solver_spmv(f.ctx, x, y, stream)
+    ms = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.cgp_solver_spmv(f.ctx, x, y, stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    nbytes = 8 * nnz + 4 * (n + 1) + 16 * n
+    peak, kind = peaks()
+    gbs = nbytes / (t * 1e-3) / 1e9
+    layout = "sliced ELL" if info.solver_format == 1 else "CSR"
+    return {"kernel": f"k_solver_spmv<{'true' if info.solver_format == 1 else 'false'}> ({layout}, the fine solvers' "
+                      f"FP32 product, {info.grid_blocks} blocks x {info.block_threads} threads)",
+            "workload": f"the headline's momentum matrix: {n} rows, {nnz} nnz, 2 RHS, stored fine order",
+            "bytes": nbytes, "ms": t, "achieved": gbs, "unit": "GB/s", "peak": peak, "frac": gbs / peak,
+            "peak_kind": kind, "l2": "flushed before each product (512 MB write, then 256 MB read)"}
+
+
 def spmv_hbm(L, Flow, dev, flush, stream, reps: int = 10):
     """The Krylov SpMV (two right-hand sides, FP64) on a matrix larger than L2: the backward-facing
     step at h = 1/48 refined twice (~2.2M rows, ~15M nnz, ~265 MB per product). Algorithmic bytes
@@ -582,11 +617,14 @@ def run_gpu(args):
         line["errors_vs_oracle"] = errors
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    sv = solver_spmv(L, f, flush, stream) if not args.no_spmv else None
     f.close()
     if args.secondary and ws == 1:
         line["secondary"] = secondary_bfs33(L, Flow, dev, flush, stream, args)
     if not args.no_spmv:
         line["spmv_hbm"] = spmv_hbm(L, Flow, dev, flush, stream)
+        if sv is not None:
+            line["spmv_hbm"]["fine_solver_product"] = sv
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -309,6 +309,14 @@ int cgp_assemble_incremental(cgp_ctx ctx, const double* u_dev, const double* pc_
  * phi_dev, pc_dev: [n_coarse]. Stream-ordered. Errors: CGP_ERR_ARG, CGP_ERR_STATE (projection 0). */
 int cgp_pressure_update(cgp_ctx ctx, const double* bc_dev, const double* phi_dev, double* pc_dev, void* stream);
 
+/* y = A x with the FP32 copy of the momentum matrix of Eq. 19 assembled by the last cgp_assemble
+ * (the full operator rows, Dirichlet rows included), for two interleaved right-hand sides x_dev,
+ * y_dev [n_fine][2] (float) in the stored fine order: the product of the fine solvers' FP32
+ * iterations as a launch of its own, in their launch shape and layout (solver_format, lanes), for
+ * measuring it. Requires CGP_MIXED or momentum_degree >= 2 (else CGP_ERR_STATE) and a prior
+ * cgp_assemble. Stream-ordered. */
+int cgp_solver_spmv(cgp_ctx ctx, const float* x_dev, float* y_dev, void* stream);
+
 /* The library's storage order of the fine nodes: perm_host[n_fine] receives, for each stored node
  * i, its index in the refinement order of cgp_fine_mesh (the identity with fine_order = 1 or
  * levels = 0). Errors: CGP_ERR_ARG. */

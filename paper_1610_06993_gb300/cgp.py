@@ -101,6 +101,7 @@ _SIGNATURES = {
     "cgp_predict_pressure": (C.c_int, [_VP, _VP, _VP]),
     "cgp_spmv": (C.c_int, [_VP, _VP, _VP, _VP]),
     "cgp_fine_order": (C.c_int, [_VP, _VP]),
+    "cgp_solver_spmv": (C.c_int, [_VP, _VP, _VP, _VP]),
     "cgp_gemm_bf16": (C.c_int, [C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, _VP]),
     "cgp_ws_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(_VP)]),
     "cgp_ws_set_params": (C.c_int, [_VP] + [_VP] * 6),
@@ -371,6 +372,10 @@ def cgp_fine_order(ctx: int, n_fine: int) -> np.ndarray:
     perm = np.empty(n_fine, dtype=np.int32)
     _check(load().cgp_fine_order(ctx, _ptr(perm)), "cgp_fine_order")
     return perm
+
+
+def cgp_solver_spmv(ctx: int, x_dev, y_dev, stream=None) -> None:
+    _check(load().cgp_solver_spmv(ctx, _ptr(x_dev), _ptr(y_dev), _stream(stream)), "cgp_solver_spmv")
 
 
 def cgp_spmv(ctx: int, x_dev, y_dev, stream=None) -> None:

@@ -610,6 +610,13 @@ int cgp_step(cgp_ctx c, double* u_dev, double* pc_dev, void* stream) {
     return CGP_OK;
 }
 
+int cgp_solver_spmv(cgp_ctx c, const float* x_dev, float* y_dev, void* stream) {
+    if (!c || !x_dev || !y_dev) return CGP_ERR_ARG;
+    if (!c->fp32_A || !c->u_asm) return CGP_ERR_STATE;
+    CK(launch_solver_spmv(c, x_dev, y_dev, (cudaStream_t)stream));
+    return CGP_OK;
+}
+
 int cgp_fine_order(cgp_ctx c, int* perm_host) {
     if (!c || !perm_host) return CGP_ERR_ARG;
     for (int i = 0; i < c->nf; ++i) perm_host[i] = c->hm.fperm.empty() ? i : c->hm.fperm[i];

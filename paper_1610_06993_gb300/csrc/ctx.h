@@ -279,6 +279,8 @@ cudaError_t launch_momentum_bicgstab(cgp_ctx_s* c, const double* u_in, double* x
 cudaError_t time_spmv_lanes(cgp_ctx_s* c, bool fine, int lanes, cudaStream_t s, float* ms);
 cudaError_t launch_spmv_fine(cgp_ctx_s* c, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_spmv_sell(cgp_ctx_s* c, const double* x, double* y, cudaStream_t s);
+// y = A32 x, the fine solvers' FP32 product in their launch shape and layout (two RHS)
+cudaError_t launch_solver_spmv(cgp_ctx_s* c, const float* x, float* y, cudaStream_t s);
 cudaError_t sell_fill(cgp_ctx_s* c, const double* csr_val, cudaStream_t s);
 cudaError_t ell_fill(int total, const int* src, const double* csr_val, double* val, float* val32, cudaStream_t s);
 

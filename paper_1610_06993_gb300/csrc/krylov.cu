@@ -190,6 +190,17 @@ cudaError_t launch_momentum_bicgstab(cgp_ctx_s* c, const double* u_in, double* x
     return coop_launch(k_bicgstab<double>, B, T, L, s, bicg_smem(T));
 }
 
+cudaError_t launch_solver_spmv(cgp_ctx_s* c, const float* x, float* y, cudaStream_t s) {
+    const int B = c->sh_f.blocks, T = c->sh_f.threads;
+    if (c->ell_on)
+        k_solver_spmv<true><<<B, T, 0, s>>>(c->nf, c->F.rp, c->F.ci, c->A32, c->ell_ptr, c->ell_col, c->ell_A32, x, y,
+                                            c->sh_f.lanes);
+    else
+        k_solver_spmv<false><<<B, T, 0, s>>>(c->nf, c->F.rp, c->F.ci, c->A32, c->ell_ptr, c->ell_col, c->ell_A32, x,
+                                             y, c->sh_f.lanes);
+    return cudaGetLastError();
+}
+
 // ---- batched solver stages: one cooperative launch per stage for all instances ----------------
 namespace {
 

@@ -236,6 +236,19 @@ __device__ __forceinline__ RowRange solver_rows(int n, const Grp& g) {
 
 __device__ __forceinline__ bool bad(double v) { return !(fabs(v) <= 1.7976931348623157e308); }
 
+// The fine solvers' FP32 product as a launch of its own, in their shape (one block per SM, the
+// same row ranges, layout and rows in flight): y = A x for two interleaved right-hand sides.
+template <bool ELL>
+__global__ void __launch_bounds__(512, 1) k_solver_spmv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                       const float* __restrict__ val, const int* eptr, const int* ecol,
+                                                       const float* evalf, const float* x, float* __restrict__ y,
+                                                       int lanes) {
+    const Grp g{gridDim.x, blockIdx.x, 0};
+    const RowRange rr = solver_rows<ELL>(n, g);
+    spmv_sel<ELL, 2, float, float, CGP_ROWS_F32>(rr, eptr, ecol, evalf, rp, ci, val, x, lanes,
+                                                 [&](int i, float s0, float s1) { store2(y, i, s0, s1); });
+}
+
 // ------------------------------------------------------------------------------------------
 // CG (Chronopoulos-Gear) inside FP64 iterative refinement
 // ------------------------------------------------------------------------------------------

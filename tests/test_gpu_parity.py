@@ -318,6 +318,26 @@ def test_spmv_matches_oracle_operator(L, cavity_state, fmt):
     f.close()
 
 
+@pytest.mark.parametrize("fmt", [1, 2], ids=["sliced_ell", "csr"])
+def test_solver_product_matches_oracle_operator(L, cavity_state, fmt):
+    """cgp_solver_spmv: the fine solvers' FP32 product of the momentum matrix A = rho M + dt (rho
+    N(u^n) + mu K) (Eq. 19) assembled from the oracle's u^n, against the oracle's FP64 operator,
+    within FP32 rounding."""
+    coarse, prob, orc, res = cavity_state
+    f = flow(coarse, prob, precision=1, solver_format=fmt)
+    perm = L.cgp_fine_order(f.ctx, f.info.n_fine)
+    L.cgp_assemble(f.ctx, dev(res.u))
+    x = np.random.default_rng(5).standard_normal((f.info.n_fine, 2))
+    xs = torch.tensor(x[perm], dtype=torch.float32, device="cuda")
+    y = torch.empty_like(xs)
+    L.cgp_solver_spmv(f.ctx, xs, y)
+    A = prob.rho * orc.fine.M + prob.dt * (prob.rho * orc.fine.convection(res.u) + prob.mu * orc.fine.K)
+    y_ref = np.empty_like(x)
+    y_ref[perm] = y.cpu().numpy()
+    f.close()
+    assert rel(y_ref, A @ x) < 1e-6
+
+
 @pytest.fixture(scope="module")
 def bfs_full():
     coarse, prob, _ = ci.workload("bfs33")
