@@ -135,10 +135,11 @@ typedef struct {
                           cgp_set_bc, velocities, pf, gp) is in the refinement order either way; the
                           library permutes on the way in and out */
     double momentum_rtol; /* tolerance of the momentum solve (Eq. 19) alone: 0 (default) = rtol / 10
-                          (at least 1e-14, at most rtol). The momentum solve's error reaches the coarse
-                          right-hand side and the histories the extrapolated guesses of the later
-                          solves are built from; solving it ten times tighter saves more coarse and
-                          mass iterations than it costs */
+                          (at least 1e-14, at most rtol) with CGP_MIXED, rtol with CGP_FP64. The
+                          momentum solve's error reaches the coarse right-hand side and the histories
+                          the extrapolated guesses of the later solves are built from; with cheap FP32
+                          inner iterations a ten times tighter solve saves more coarse and mass
+                          iterations than it costs */
 } cgp_params;
 
 /* A coarse mesh: n_nodes points xy_host[n][2] and n_tris counter-clockwise triangles
@@ -179,7 +180,7 @@ typedef struct {
  * inner_rtol = 1e-4, max_iter = 20000, max_outer = 30, spmv_lanes = 0, block_threads = 0,
  * coarse_solver = 0, spmv_format = 0, precond_degree = 0, precond_ratio = 0, warm_start = 3, mass_degree = 0,
  * momentum_degree = 0, solver_format = 0, restrict_mode = 0, projection = 0, fine_order = 0,
- * momentum_rtol = 0 (rtol / 10). */
+ * momentum_rtol = 0 (rtol / 10 with CGP_MIXED, else rtol). */
 void cgp_default_params(cgp_params* p);
 
 /* Preprocessing (the paper's C_pre, Sect. 2.4): validates the coarse mesh, refines it

@@ -90,11 +90,14 @@ int create_impl(const cgp_mesh_desc* d, const cgp_params* prm, cgp_ctx_s* c) {
     if (P.projection < 0 || P.projection > 2) return CGP_ERR_ARG;
     if (P.fine_order < 0 || P.fine_order > 1) return CGP_ERR_ARG;
     if (!(P.momentum_rtol >= 0.0)) return CGP_ERR_ARG;
-    // default: ten times tighter than rtol (down to 1e-14, never looser than rtol); the momentum
-    // solve's error reaches the coarse right-hand side and the histories the later solves'
-    // guesses extrapolate, and on the cylinder and the channel the tighter solve saves more
-    // coarse and mass iterations than it costs (+3 % and +10 % steps/s)
-    if (P.momentum_rtol == 0.0) P.momentum_rtol = std::min(P.rtol, std::max(0.1 * P.rtol, 1e-14));
+    // default with FP32 inner iterations: ten times tighter than rtol (down to 1e-14, never looser
+    // than rtol). The momentum solve's error reaches the coarse right-hand side and the histories
+    // the later solves' guesses extrapolate; with cheap FP32 Jacobi iterations the tighter solve
+    // saves more coarse and mass iterations than it costs (cylinder +3 %, channel +10 % steps/s),
+    // while the FP64 path's polynomial-preconditioned iterations cost more than they save
+    // (cylinder -7 %, channel -10 %), so it keeps rtol.
+    if (P.momentum_rtol == 0.0)
+        P.momentum_rtol = P.precision == CGP_MIXED ? std::min(P.rtol, std::max(0.1 * P.rtol, 1e-14)) : P.rtol;
     if (P.inner_rtol <= 0.0) P.inner_rtol = 1e-4;
     if (P.max_iter <= 0) P.max_iter = 20000;
     if (P.max_outer <= 0) P.max_outer = 30;
