@@ -215,9 +215,9 @@ __device__ __forceinline__ void block_partials_lean(const double (&v)[K], double
     }
 }
 
-// Sum K floats over the block in FP32 (shuffle tree in every warp, then one warp over the warp
-// sums) and store the block's totals as doubles at part[k * nblocks + bid]. Written by thread 0;
-// needs s_scratch of 32 K floats.
+// Sum K floats over the block in FP32 (shuffle tree in every warp, then warp k over the warp sums
+// of value k) and store the block's totals as doubles at part[k * nblocks + bid]; needs s_scratch
+// of 32 K floats.
 template <int K>
 __device__ __forceinline__ void block_partials_f32(const float (&v0)[K], double* part, unsigned int nblocks,
                                                    unsigned int bid, float* s_scratch) {
@@ -235,14 +235,12 @@ __device__ __forceinline__ void block_partials_f32(const float (&v0)[K], double*
         for (int k = 0; k < K; ++k) s_scratch[k * 32 + warp] = v[k];
     }
     __syncthreads();
-    if (warp == 0) {
+    // second level: warp k sums value k over the warps (the same order whichever warp does it)
+    for (int k = warp; k < K; k += nwarps) {
+        float s = lane < nwarps ? s_scratch[k * 32 + lane] : 0.f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            float s = lane < nwarps ? s_scratch[k * 32 + lane] : 0.f;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) part[(size_t)k * nblocks + bid] = (double)s;
-        }
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) part[(size_t)k * nblocks + bid] = (double)s;
     }
 }
 

@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
     __shared__ double s_bc[8];
     __shared__ float s_f32[32 * 3 * NR];
     __shared__ double s_sc[2 * NR];
-    __shared__ int s_fl[2];
+    __shared__ int s_fl[2 * NR];
     const Grp g = group_of(L.map);
     const CgArgs<TI>& a = L.table ? L.table[g.inst] : L.single;
     const unsigned int nb = g.nb;
@@ -566,14 +566,15 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
             }
             iters += 1;
             first = false;
-            // scalar recurrences once per block (thread 0; FP64 division is slow on this GPU),
-            // broadcast through shared memory
-            if (threadIdx.x == 0) {
-                bool more = false, bad_any = false;
+            // scalar recurrences once per block, one thread per right-hand side (thread 32 c for
+            // component c, carrying its recurrence state; FP64 division is slow on this GPU, and
+            // the components' divisions run side by side), broadcast through shared memory
+            if ((threadIdx.x & 31) == 0 && threadIdx.x < 32 * NR) {
 #pragma unroll
                 for (int c = 0; c < NR; ++c) {
+                    if ((int)(threadIdx.x >> 5) != c) continue;
                     const double gnew = s_bc[c], rho = s_bc[NR + c], del = s_bc[2 * NR + c];
-                    bad_any |= bad(gnew) | bad(rho) | bad(del);
+                    s_fl[c] = (bad(gnew) | bad(rho) | bad(del)) ? 1 : 0;
                     if (act[c] && rho <= tgt[c]) act[c] = false;
                     if (act[c]) {
                         // beta = gnew / gam and alpha' = gnew gam alpha / (del gam alpha - gnew^2):
@@ -590,22 +591,21 @@ __global__ void __launch_bounds__(512, MINB) k_cg(Launch<CgArgs<TI>> L) {
                         }
                     }
                     if (!act[c]) alpha[c] = beta[c] = 0.0;
-                    more |= act[c];
+                    s_fl[NR + c] = act[c] ? 1 : 0;
                     s_sc[c] = alpha[c];
                     s_sc[NR + c] = beta[c];
                 }
-                s_fl[0] = more;
-                s_fl[1] = bad_any;
             }
             __syncthreads();
+            bool more = false;
 #pragma unroll
             for (int c = 0; c < NR; ++c) {
                 alpha[c] = s_sc[c];
                 beta[c] = s_sc[NR + c];
+                more |= s_fl[NR + c] != 0;
+                nan |= s_fl[c] != 0;
             }
-            const bool more = s_fl[0] != 0;
-            nan |= s_fl[1] != 0;
-            __syncthreads();   // s_sc / s_fl read by all before thread 0 writes them again
+            __syncthreads();   // s_sc / s_fl read by all before they are written again
             if (nan || !more || iters >= a.max_iter) break;
         }
         if (nan) { status = CGP_ERR_NAN; break; }
@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
     __shared__ double s_bc[10];
     __shared__ float s_f32[32 * 10];
     __shared__ double s_sc[4];
-    __shared__ int s_fl[2];
+    __shared__ int s_fl[4];
     const Grp g = group_of(L.map);
     const BicgArgs<TI>& a = L.table ? L.table[g.inst] : L.single;
     const unsigned int nb = g.nb;
@@ -922,21 +922,23 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
                 if (!grid_sync(a.sw, nb, epoch)) return record_failure(a.sw, a.st_barrier);
                 const int slot[2] = {BI_B2, BI_B2 + 1};
                 grid_totals_shared<2>(a.part, slot, nb, s_bc);
-                if (threadIdx.x == 0) {
-                    int fl = 0;
+                // one thread per right-hand side (thread 0: component 0, thread 32: component 1),
+                // each carrying its component's recurrence state, so the FP64 divisions of the
+                // two components run side by side
+                if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
+                        if ((int)(threadIdx.x >> 5) != c) continue;
                         const double ts = s_bc[c];
-                        fl |= bad(ts) ? 1 : 0;
+                        s_fl[c] = bad(ts) ? 1 : 0;
                         if (act[c] && ts != 0.0) alpha[c] = rho[c] / ts;
                         else { act[c] = false; alpha[c] = 0.0; }
                         s_sc[c] = alpha[c];
                     }
-                    s_fl[1] = fl;
                 }
                 __syncthreads();
                 for (int c = 0; c < 2; ++c) al[c] = (TI)s_sc[c];
-                nan |= s_fl[1] != 0;
+                nan |= (s_fl[0] | s_fl[1]) != 0;
             }
             // ---- s = r - alpha v, z = D^-1 s, d += alpha y (two rows per thread)
             for (int i0 = rr.r0 + threadIdx.x; i0 < rr.r1; i0 += 2 * tpb) {
@@ -1010,14 +1012,15 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
                 }
                 iters += 1;
                 first = false;
-                // omega, the next rho and beta, convergence: thread 0, broadcast
-                if (threadIdx.x == 0) {
-                    int more = 0, fl = 0;
+                // omega, the next rho and beta, convergence: one thread per component (as above),
+                // broadcast
+                if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
+                        if ((int)(threadIdx.x >> 5) != c) continue;
                         const double ts = s_bc[c], tt = s_bc[2 + c], ht = s_bc[4 + c], hs = s_bc[6 + c];
                         const double ss = s_bc[8 + c];
-                        fl |= (bad(ts) | bad(tt) | bad(ht) | bad(hs) | bad(ss)) ? 1 : 0;
+                        s_fl[c] = (bad(ts) | bad(tt) | bad(ht) | bad(hs) | bad(ss)) ? 1 : 0;
                         if (act[c] && ss <= tgt[c]) {          // converged at the half step
                             act[c] = false;
                             omega[c] = 0.0;
@@ -1043,12 +1046,10 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
                             }
                         }
                         if (!act[c]) beta[c] = 0.0;
-                        more |= act[c] ? 1 : 0;
+                        s_fl[2 + c] = act[c] ? 1 : 0;
                         s_sc[c] = omega[c];
                         s_sc[2 + c] = beta[c];
                     }
-                    s_fl[0] = more;
-                    s_fl[1] = fl;
                 }
                 __syncthreads();
                 for (int c = 0; c < 2; ++c) {
@@ -1056,9 +1057,9 @@ __global__ void __launch_bounds__(512, MINB) k_bicgstab(Launch<BicgArgs<TI>> L) 
                     beta[c] = s_sc[2 + c];
                     om[c] = (TI)omega[c];
                 }
-                const bool more = s_fl[0] != 0;
-                nan |= s_fl[1] != 0;
-                __syncthreads();   // s_sc / s_fl read by all before thread 0 writes them again
+                const bool more = (s_fl[2] | s_fl[3]) != 0;
+                nan |= (s_fl[0] | s_fl[1]) != 0;
+                __syncthreads();   // s_sc / s_fl read by all before they are written again
                 if (nan || !more || iters >= a.max_iter) {
                     // last update of this pass: d += omega z
                     for (int i = rr.r0 + threadIdx.x; i < rr.r1; i += tpb) {
