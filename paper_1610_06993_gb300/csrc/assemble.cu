@@ -211,14 +211,21 @@ __global__ void k_conv_elements(int t, const int* __restrict__ tri, const double
 #pragma unroll
     for (int q = 0; q < 3; ++q) load2(u, tri[3 * e + q], ux[q], uy[q]);
     const double sx = ux[0] + ux[1] + ux[2], sy = uy[0] + uy[1] + uy[2];
-    double S[3];
+    // the gradients of the three P1 basis functions sum to zero, so the third column of the
+    // element matrix is minus the sum of the first two (24 FP64 operations per element instead of
+    // 28; this GPU issues FP64 at a small fraction of its FP32 rate, and this kernel is bound by it)
+    double S[2];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) S[q] = fma(sy, gy[q], sx * gx[q]);
+    for (int q = 0; q < 2; ++q) S[q] = fma(sy, gy[q], sx * gx[q]);
     double* o = ev + 9 * (size_t)e;
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) o[r * 3 + q] = fma(ux[r], gx[q], fma(uy[r], gy[q], S[q]));
+    for (int r = 0; r < 3; ++r) {
+        const double o0 = fma(ux[r], gx[0], fma(uy[r], gy[0], S[0]));
+        const double o1 = fma(ux[r], gx[1], fma(uy[r], gy[1], S[1]));
+        o[r * 3] = o0;
+        o[r * 3 + 1] = o1;
+        o[r * 3 + 2] = -(o0 + o1);
+    }
 }
 
 // A[k] = A0[k] + the element contributions of entry k (and its FP32 copy); with `pos`, the same
@@ -255,10 +262,16 @@ __global__ void k_rows(int nf, const int* __restrict__ rp, const int* __restrict
     if (i < nf) {
         const unsigned char m = mask[i];
         const int kd = diag[i];
-        const double di = 1.0 / A[kd];
-        const double dx = (m & CGP_BC_U) ? 1.0 : di, dy = (m & CGP_BC_V) ? 1.0 : di;
-        store2(dinv, i, dx, dy);
-        if (dinv32) store2(dinv32, i, (float)dx, (float)dy);
+        if (dinv) {
+            const double di = 1.0 / A[kd];
+            const double dx = (m & CGP_BC_U) ? 1.0 : di, dy = (m & CGP_BC_V) ? 1.0 : di;
+            store2(dinv, i, dx, dy);
+            if (dinv32) store2(dinv32, i, (float)dx, (float)dy);
+        } else {
+            // FP32 inner iterations only: the FP32 inverse diagonal, without an FP64 division
+            const float di = 1.f / (float)A[kd];
+            store2(dinv32, i, (m & CGP_BC_U) ? 1.f : di, (m & CGP_BC_V) ? 1.f : di);
+        }
         double mx = 0.0, my = 0.0;
         float off = 0.f;
         for (int k = rp[i]; k < rp[i + 1]; ++k) {
@@ -321,8 +334,10 @@ cudaError_t launch_assemble_step(cgp_ctx_s* c, const double* u, cudaStream_t s, 
     k_gather_entries<<<(nnz + 255) / 256, 256, 0, s>>>(nnz, c->asm_ip, c->asm_idx, c->asm_ev, c->A0, c->A,
                                                       c->fp32_A ? c->A32 : nullptr, c->ell_on ? c->ell_pos : nullptr,
                                                       c->ell_A, c->fp32_A ? c->ell_A32 : nullptr);
+    // with FP32 inner iterations nothing reads the FP64 inverse diagonal
+    double* dinv64 = c->prm.precision == CGP_MIXED ? nullptr : c->dinvA;
     k_rows<<<(nf + 255) / 256, 256, 0, s>>>(nf, c->F.rp, c->F.ci, c->F.diag, c->A, c->A32, c->M, u, c->vel_mask,
-                                          c->g, c->prm.rho, c->dinvA, c->fp32_A ? c->dinvA32 : nullptr, c->b_mom,
+                                          c->g, c->prm.rho, dinv64, c->fp32_A ? c->dinvA32 : nullptr, c->b_mom,
                                           bound, gpn, c->prm.dt);
     return cudaGetLastError();
 }
