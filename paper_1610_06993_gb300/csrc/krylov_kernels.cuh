@@ -16,7 +16,10 @@ namespace {
 
 // CNT consecutive entries (from k) of R rows (row q starts at ka[q] and has na[q] entries): all
 // column and value loads first, then the x gathers and products; entries past a row's end are
-// skipped per lane.
+// skipped per lane. The fine-mesh products (two right-hand sides) stream their matrix with the
+// evict-first hint, so that it does not push the Krylov vectors out of L2; the scalar coarse
+// products keep theirs cached, since a coarse CG re-reads it every iteration (the 64-cavity
+// batch's coarse matrices, 50 MB in FP32, ran 6 % slower when streamed).
 template <int R, int CNT, int NR, typename TV, typename TX>
 __device__ __forceinline__ void spmv_rows_chunk(int k, const int (&ka)[R], const int (&na)[R],
                                                 const int* __restrict__ ci, const TV* __restrict__ val, const TX* x,
@@ -28,8 +31,13 @@ __device__ __forceinline__ void spmv_rows_chunk(int k, const int (&ka)[R], const
 #pragma unroll
         for (int e = 0; e < CNT; ++e) {
             const bool in = k + e < na[q];
-            j[q][e] = in ? __ldcs(ci + ka[q] + k + e) : -1;
-            v[q][e] = in ? (TX)__ldcs(val + ka[q] + k + e) : (TX)0;
+            if (NR == 2) {
+                j[q][e] = in ? __ldcs(ci + ka[q] + k + e) : -1;
+                v[q][e] = in ? (TX)__ldcs(val + ka[q] + k + e) : (TX)0;
+            } else {
+                j[q][e] = in ? __ldg(ci + ka[q] + k + e) : -1;
+                v[q][e] = in ? (TX)__ldg(val + ka[q] + k + e) : (TX)0;
+            }
         }
 #pragma unroll
     for (int q = 0; q < R; ++q)
@@ -57,10 +65,10 @@ __device__ __forceinline__ void spmv_rows_chunk(int k, const int (&ka)[R], const
 // number by R (measured on the 1M-row cylinder mesh: four rows per thread were no faster than two;
 // with perfectly coalesced x reads a product was only a fifth faster, so it is bound by the
 // matrix stream at this occupancy rather than by the gathers). x is written by other blocks during
-// the launch, so it is read with ordinary (coherent) loads; the matrix is streamed with the
-// evict-first hint, so that it does not push the Krylov vectors out of L2 (on the 1M-row cylinder
-// mesh the momentum products fell from ~44 to ~35 us). CGP_ROWS_F32 sets R for the single-context
-// FP32 products, the rest take two (registers).
+// the launch, so it is read with ordinary (coherent) loads; the fine-mesh matrices are streamed
+// with the evict-first hint (on the 1M-row cylinder mesh the momentum products fell from ~44 to
+// ~35 us). CGP_ROWS_F32 sets R for the single-context FP32 products, the rest take two
+// (registers).
 template <int NR, typename TV, typename TX, int R = 2, typename Emit>
 __device__ __forceinline__ void spmv_rows(RowRange rr, const int* __restrict__ rp, const int* __restrict__ ci,
                                           const TV* __restrict__ val, const TX* x, Emit emit) {
