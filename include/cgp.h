@@ -245,7 +245,8 @@ int cgp_assemble(cgp_ctx ctx, const double* u_dev, void* stream);
  * polynomial of cgp_params.momentum_degree (CGP_MIXED: FP32 BiCGStab inside FP64 iterative
  * refinement). Requires cgp_assemble() on the same u^n first. u_dev: u^n, the initial
  * guess, plus the previous converged increment when warm_start >= 1, or NULL for the velocity of
- * the last cgp_assemble (no second copy into the library's fine order); ut_dev: [n_fine][2]
+ * the last assembly (cgp_assemble, cgp_assemble_incremental or cgp_step; no second copy into the
+ * library's fine order); ut_dev: [n_fine][2]
  * output u~^{n+1}, or NULL to keep u~^{n+1} inside the context for cgp_restrict and
  * cgp_prolong_correct (no copy out of the library's fine order). */
 int cgp_momentum_solve(cgp_ctx ctx, const double* u_dev, double* ut_dev, void* stream);
@@ -310,12 +311,13 @@ int cgp_assemble_incremental(cgp_ctx ctx, const double* u_dev, const double* pc_
  * phi_dev, pc_dev: [n_coarse]. Stream-ordered. Errors: CGP_ERR_ARG, CGP_ERR_STATE (projection 0). */
 int cgp_pressure_update(cgp_ctx ctx, const double* bc_dev, const double* phi_dev, double* pc_dev, void* stream);
 
-/* y = A x with the FP32 copy of the momentum matrix of Eq. 19 assembled by the last cgp_assemble
+/* y = A x with the FP32 copy of the momentum matrix of Eq. 19 of the last assembly (cgp_assemble,
+ * cgp_assemble_incremental or cgp_step)
  * (the full operator rows, Dirichlet rows included), for two interleaved right-hand sides x_dev,
  * y_dev [n_fine][2] (float) in the stored fine order: the product of the fine solvers' FP32
  * iterations as a launch of its own, in their launch shape and layout (solver_format, lanes), for
  * measuring it. Requires CGP_MIXED or momentum_degree >= 2 (else CGP_ERR_STATE) and a prior
- * cgp_assemble. Stream-ordered. */
+ * assembly. Stream-ordered. */
 int cgp_solver_spmv(cgp_ctx ctx, const float* x_dev, float* y_dev, void* stream);
 
 /* The library's storage order of the fine nodes: perm_host[n_fine] receives, for each stored node

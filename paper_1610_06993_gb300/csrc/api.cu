@@ -565,6 +565,7 @@ int cgp_assemble_incremental(cgp_ctx c, const double* u_dev, const double* pc_de
     }
     CK(launch_pressure_term(c, pc_dev, s));
     CK(launch_assemble_step(c, u, s, c->grad_n));
+    c->u_asm = u;
     return CGP_OK;
 }
 
@@ -585,6 +586,7 @@ int cgp_step(cgp_ctx c, double* u_dev, double* pc_dev, void* stream) {
         CK(fine_to_stored(c, u_dev, c->u_int, 2, s));
         u = c->u_int;
     }
+    c->u_asm = u;
     if (c->prm.projection != 0) {
         // incremental forms: pressure term of p^n, momentum, restriction, Poisson for the
         // increment (its own extrapolated history), correction by the increment, p += phi (- mu chi)

@@ -151,7 +151,7 @@ struct cgp_ctx_s {
     // stored node i (nullptr: the two orders coincide). u_int: the velocity in the stored order.
     int* fperm = nullptr;
     double* u_int = nullptr;
-    const double* u_asm = nullptr;   // the stored-order velocity of the last cgp_assemble
+    const double* u_asm = nullptr;   // the stored-order velocity of the last assembly
 
     // sliced-ELL (SELL-32-256) copy of the fine pattern for the stand-alone SpMV
     int sell_nslices = 0, sell_total = 0;
