@@ -724,6 +724,18 @@ def secondary_bfs33(L, Flow, dev, flush, stream, args):
     return out
 
 
+def batch_launches_per_step(flows) -> int:
+    """Kernels of one batched step of one-level instances with the injection restriction (the
+    batch64 workload): the gather of u^n into the stored fine order (when the instances renumber),
+    the colour-scheduled assembly, the two predictor launches, the momentum solve, the batched
+    restriction, the batched two-level coarse CG, the prolongation per level and the gradient, the
+    mass solve and the correction: one launch each for all instances."""
+    lv = max(f.info.levels for f in flows)
+    renumber = any(f.info.fine_order == 0 for f in flows)
+    predict = any(f.params.warm_start >= 1 for f in flows)
+    return (1 if renumber else 0) + 1 + (2 if predict else 0) + 1 + 1 + 1 + lv + 1 + 1 + 1
+
+
 def run_batch(args):
     """64 independent cavities (coarse sizes log-uniform in [2k, 50k], Re in [100, 1000], dt =
     0.005, one refinement), advanced together by the batched step replayed as a CUDA graph.
@@ -844,7 +856,7 @@ def run_batch(args):
                                 "iters_batched_mean": statistics.mean(it_batch),
                                 "iters_plain_jacobi_mean": statistics.mean(plain[5][1]),
                                 "iters_plain_schwarz_mean": statistics.mean(plain[0][1])},
-        "gpu_launches": None, "clocks": clk.summary(),
+        "gpu_launches": batch_launches_per_step(flows) * args.steps, "clocks": clk.summary(),
     }
     if errs is not None:
         line["errors_vs_oracle"] = errs
