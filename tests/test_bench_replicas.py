@@ -88,3 +88,25 @@ def test_reference_arm_other_ranks_exit_quietly():
     code, lines = _run_bench(["--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "1"],
                              {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert code == 0 and lines == []
+
+
+def test_bench_accounting_helpers():
+    """The byte and launch counts behind the bench line's roofline and gpu_launches keys: the
+    momentum solve's algorithmic bytes (two products of (v + 4) nnz + 4 n + 4 v n bytes and 90 v / 8
+    bytes of vector passes per row per iteration, 12 nnz + 52 n per FP64 refinement pass) and the
+    batched step's one launch per stage for all instances."""
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    nnz, n = 7, 1
+    # one FP32 iteration (v = 4) and one refinement pass (outer 0 -> one residual)
+    assert bench.momentum_alg_bytes(nnz, n, 4, 1.0, 0.0) == 2 * (8 * 7 + 4 + 16) + 45 + (12 * 7 + 52)
+    # FP64 iterations: ~330 bytes per row at 7 entries per row
+    per_iter = bench.momentum_alg_bytes(nnz, n, 8, 1.0, -1.0)
+    assert 320 <= per_iter <= 340
+    flow = lambda lv, fo, ws: types.SimpleNamespace(info=types.SimpleNamespace(levels=lv, fine_order=fo),
+                                                    params=types.SimpleNamespace(warm_start=ws))
+    # permute, assembly, 2 predictor launches, momentum, restriction, coarse CG, 1 prolongation,
+    # gradient, mass, correction
+    assert bench.batch_launches_per_step([flow(1, 0, 3)] * 3) == 11
+    assert bench.batch_launches_per_step([flow(1, 1, 0)]) == 8
