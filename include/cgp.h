@@ -245,8 +245,11 @@ int cgp_assemble(cgp_ctx ctx, const double* u_dev, void* stream);
  * polynomial of cgp_params.momentum_degree (CGP_MIXED: FP32 BiCGStab inside FP64 iterative
  * refinement). Requires cgp_assemble() on the same u^n first. u_dev: u^n, the initial
  * guess, plus the previous converged increment when warm_start >= 1, or NULL for the velocity of
- * the last assembly (cgp_assemble, cgp_assemble_incremental or cgp_step; no second copy into the
- * library's fine order); ut_dev: [n_fine][2]
+ * the last assembly (cgp_assemble, cgp_assemble_incremental, cgp_step or a batched step; no second
+ * copy into the library's fine order) while a buffer still holds it: with fine_order = 1 or
+ * levels = 0 that buffer is the caller's, and once cgp_step, a batched step or cgp_prolong_correct
+ * has written u^{n+1} into it (with fine_order = 0: once cgp_body_force or cgp_reattachment has
+ * reused the library's copy), NULL returns CGP_ERR_STATE; ut_dev: [n_fine][2]
  * output u~^{n+1}, or NULL to keep u~^{n+1} inside the context for cgp_restrict and
  * cgp_prolong_correct (no copy out of the library's fine order). */
 int cgp_momentum_solve(cgp_ctx ctx, const double* u_dev, double* ut_dev, void* stream);
@@ -312,7 +315,7 @@ int cgp_assemble_incremental(cgp_ctx ctx, const double* u_dev, const double* pc_
 int cgp_pressure_update(cgp_ctx ctx, const double* bc_dev, const double* phi_dev, double* pc_dev, void* stream);
 
 /* y = A x with the FP32 copy of the momentum matrix of Eq. 19 of the last assembly (cgp_assemble,
- * cgp_assemble_incremental or cgp_step)
+ * cgp_assemble_incremental, cgp_step or a batched step)
  * (the full operator rows, Dirichlet rows included), for two interleaved right-hand sides x_dev,
  * y_dev [n_fine][2] (float) in the stored fine order: the product of the fine solvers' FP32
  * iterations as a launch of its own, in their launch shape and layout (solver_format, lanes), for

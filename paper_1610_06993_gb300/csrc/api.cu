@@ -486,6 +486,7 @@ int cgp_assemble(cgp_ctx c, const double* u_dev, void* stream) {
     }
     CK(launch_assemble_step(c, u, s));
     c->u_asm = u;
+    c->assembled = true;
     return CGP_OK;
 }
 
@@ -493,7 +494,7 @@ int cgp_momentum_solve(cgp_ctx c, const double* u_dev, double* ut_dev, void* str
     if (!c) return CGP_ERR_ARG;
     if (!c->bc_set) return CGP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
-    const double* u = c->u_asm;   // NULL u_dev: the velocity of the last cgp_assemble
+    const double* u = c->u_asm;   // NULL u_dev: the velocity of the last assembly
     if (u_dev) {
         u = u_dev;
         if (c->fperm) {
@@ -551,6 +552,7 @@ int cgp_prolong_correct(cgp_ctx c, const double* pc_dev, const double* ut_dev, d
     CK(launch_gradient(c, pf, c->grad, s));
     CK(mass_stage(c, s));
     CK(launch_correct(c, ut, c->w, u_dev, gp_dev, s, true));
+    if (u_dev == c->u_asm) c->u_asm = nullptr;   // the caller's u^n buffer now holds u^(n+1)
     return CGP_OK;
 }
 
@@ -566,6 +568,7 @@ int cgp_assemble_incremental(cgp_ctx c, const double* u_dev, const double* pc_de
     CK(launch_pressure_term(c, pc_dev, s));
     CK(launch_assemble_step(c, u, s, c->grad_n));
     c->u_asm = u;
+    c->assembled = true;
     return CGP_OK;
 }
 
@@ -586,7 +589,9 @@ int cgp_step(cgp_ctx c, double* u_dev, double* pc_dev, void* stream) {
         CK(fine_to_stored(c, u_dev, c->u_int, 2, s));
         u = c->u_int;
     }
-    c->u_asm = u;
+    // in the identity order u_dev receives u^(n+1) below, so no buffer keeps the assembly's u^n
+    c->u_asm = c->fperm ? u : nullptr;
+    c->assembled = true;
     if (c->prm.projection != 0) {
         // incremental forms: pressure term of p^n, momentum, restriction, Poisson for the
         // increment (its own extrapolated history), correction by the increment, p += phi (- mu chi)
@@ -617,7 +622,7 @@ int cgp_step(cgp_ctx c, double* u_dev, double* pc_dev, void* stream) {
 
 int cgp_solver_spmv(cgp_ctx c, const float* x_dev, float* y_dev, void* stream) {
     if (!c || !x_dev || !y_dev) return CGP_ERR_ARG;
-    if (!c->fp32_A || !c->u_asm) return CGP_ERR_STATE;
+    if (!c->fp32_A || !c->assembled) return CGP_ERR_STATE;
     CK(launch_solver_spmv(c, x_dev, y_dev, (cudaStream_t)stream));
     return CGP_OK;
 }

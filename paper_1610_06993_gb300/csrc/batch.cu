@@ -132,6 +132,13 @@ int create_impl(cgp_ctx* ctxs, int n, double* const* u, double* const* pc, cgp_b
 }
 
 cudaError_t enqueue_step(cgp_batch_s* b, cudaStream_t s) {
+    for (int i = 0; i < b->n; ++i) {
+        // each instance's A is assembled from u^n in its stored order: u_int, or (identity order)
+        // the caller's buffer, which the correction overwrites with u^(n+1)
+        cgp_ctx_s* c = b->ctx[i];
+        c->u_asm = c->fperm ? c->u_int : nullptr;
+        c->assembled = true;
+    }
     cudaError_t e = cudaMemsetAsync(b->sync, 0, sizeof(SyncWords) * (size_t)b->n * SYNC_COUNT, s);
     if (e == cudaSuccess) e = batch_perm_launch(b, s);   // u^n into the instances' stored fine order
     if (e == cudaSuccess) e = batch_asm_launch(b, s);

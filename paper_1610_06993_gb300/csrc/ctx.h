@@ -151,7 +151,11 @@ struct cgp_ctx_s {
     // stored node i (nullptr: the two orders coincide). u_int: the velocity in the stored order.
     int* fperm = nullptr;
     double* u_int = nullptr;
-    const double* u_asm = nullptr;   // the stored-order velocity of the last assembly
+    // u_asm: the stored-order u^n of the last assembly while some buffer still holds it (nullptr
+    // once a correction wrote u^(n+1) over the caller's buffer in the identity order, or a
+    // diagnostic reused u_int); assembled: A of Eq. 19 holds an assembly
+    const double* u_asm = nullptr;
+    bool assembled = false;
 
     // sliced-ELL (SELL-32-256) copy of the fine pattern for the stand-alone SpMV
     int sell_nslices = 0, sell_total = 0;

@@ -172,6 +172,7 @@ int cgp_body_force(cgp_ctx c, const double* u_dev, const double* pc_dev, double*
     cudaStream_t s = (cudaStream_t)stream;
     const double* u = u_dev;
     if (c->fperm) {
+        if (c->u_asm == c->u_int) c->u_asm = nullptr;   // the copy no longer holds the assembly's u^n
         if (fine_to_stored(c, u_dev, c->u_int, 2, s) != cudaSuccess) return CGP_ERR_CUDA;
         u = c->u_int;
     }
@@ -191,6 +192,7 @@ int cgp_reattachment(cgp_ctx c, const double* u_dev, double x_start, double* xr_
     double* tau = tau_dev ? tau_dev : S.xs + S.n;
     const double* u = u_dev;
     if (c->fperm) {
+        if (c->u_asm == c->u_int) c->u_asm = nullptr;   // the copy no longer holds the assembly's u^n
         if (fine_to_stored(c, u_dev, c->u_int, 2, s) != cudaSuccess) return CGP_ERR_CUDA;
         u = c->u_int;
     }

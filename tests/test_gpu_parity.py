@@ -253,6 +253,44 @@ def test_deterministic_and_host_entry(L):
     assert np.array_equal(us, outs[0])
 
 
+@pytest.mark.parametrize("order", [0, 1], ids=["hilbert", "refinement"])
+def test_null_velocity_follows_the_assembly(L, order):
+    """NULL u^n in cgp_momentum_solve means the velocity of the last assembly while a buffer still
+    holds it. In the refinement order that buffer is the caller's, which cgp_step and
+    cgp_prolong_correct overwrite with u^(n+1): NULL is then refused. In the Hilbert order the
+    library's copy keeps u^n until a diagnostic reuses it. The FP32 solver product only needs an
+    assembly."""
+    coarse, prob, _ = ci.workload("cavity33")
+    f = flow(coarse, prob, precision=L.CGP_MIXED, rtol=1e-10, fine_order=order)
+    x = torch.ones(f.info.n_fine, 2, dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    with pytest.raises(L.CGPError):
+        L.cgp_momentum_solve(f.ctx, None, None)   # nothing assembled yet
+    with pytest.raises(L.CGPError):
+        L.cgp_solver_spmv(f.ctx, x, y)
+    f.step(2)
+    L.cgp_solver_spmv(f.ctx, x, y)
+    if order == 1:
+        with pytest.raises(L.CGPError):
+            L.cgp_momentum_solve(f.ctx, None, None)
+    else:
+        L.cgp_momentum_solve(f.ctx, None, None)
+    # a stage-by-stage step: NULL is valid from the assembly up to the correction
+    bc = torch.empty_like(f.pc)
+    L.cgp_assemble(f.ctx, f.u)
+    L.cgp_momentum_solve(f.ctx, None, None)
+    L.cgp_restrict(f.ctx, None, bc)
+    L.cgp_poisson_solve(f.ctx, bc, f.pc)
+    L.cgp_prolong_correct(f.ctx, f.pc, None, f.u)
+    if order == 1:
+        with pytest.raises(L.CGPError):
+            L.cgp_momentum_solve(f.ctx, None, None)
+    else:
+        L.cgp_momentum_solve(f.ctx, None, None)
+    f.stats(check=True)
+    f.close()
+
+
 def test_zero_flow_stays_zero(L):
     """All-zero data: every right-hand side is zero and every solve returns exactly zero."""
     coarse = ci.cavity_mesh(9, 2)
