@@ -691,7 +691,7 @@ def coarse_throughput(L, Flow, make, f, other, B_log, P_log, stream, args):
 
 
 def secondary_bfs33(L, Flow, dev, flush, stream, args):
-    """The backward-facing-step channel (config 1: 65,308 / 259,117 nodes, l = 1) in FP64 and in
+    """The backward-facing-step channel (65,308 / 259,117 nodes, l = 1) in FP64 and in
     FP32+IR side by side, each after 100 developing steps: steps/s, coarse solves/s, and the relative
     L2 error of one more step of each from the FP64 state against one oracle step."""
     import torch

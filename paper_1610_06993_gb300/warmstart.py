@@ -5,7 +5,7 @@ Reynolds numbers are advanced together by the batched step, and every step's coa
 side b_c and pressure p_c (and the previous step's pressure) are logged on the device. The network
 works in residual form: it corrects a base guess (the previous step's pressure or its
 extrapolation in time) from that guess's residual b - K x_base, trained by
-``cgp_ws_train_step_residual`` (tcgen05 kernels). It is judged by the iteration count of the
+``cgp_ws_train_step_residual`` (tcgen05 kernels). Its gain is measured by the iteration count of the
 coarse CG, which always runs to the same tolerance whatever its initial guess; the held-out
 right-hand sides are solved together by ``cgp_poisson_solve_many``. All arithmetic runs in the
 CUDA library; this module only orchestrates calls and keeps torch device tensors.

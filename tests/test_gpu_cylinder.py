@@ -38,7 +38,7 @@ def L():
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
 def test_cylinder_small_parity(L, precision):
-    """988 coarse nodes, l = 2: 100 steps at the parity tolerance rtol = 1e-13, then the north-star
+    """988 coarse nodes, l = 2: 100 steps at the parity tolerance rtol = 1e-13, then the parity
     bar of 1e-10 relative L2 in u and in w = M^-1 G p_f (observed: u 3e-12, w 2e-11 in FP64;
     9e-12, 5e-11 with FP32 inner iterations)."""
     from paper_1610_06993_gb300.flow import Flow

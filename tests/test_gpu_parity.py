@@ -205,7 +205,7 @@ def _steps_with_gradient(L, f, n):
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
 def test_backward_facing_step_small(L, precision):
     """Open outflow (natural velocity, p = 0, Eq. 14), parabolic inflow, several grid blocks: the
-    spec bar, 1e-10 relative L2 in u and in w = M^-1 G p_f after 100 steps (Eqs. 19-23).
+    parity bar, 1e-10 relative L2 in u and in w = M^-1 G p_f after 100 steps (Eqs. 19-23).
     The 30:2 channel makes the coarse Poisson matrix ill-conditioned (kappa ~ 1e5 at h = 1/4); at
     the parity tolerance rtol = 1e-13 the per-step energy-norm error is <= sqrt(kappa) 1e-13 ~ 3e-11
     (observed after 100 steps: u 4e-12, w 6e-12 in FP64; 5e-12, 1e-11 with FP32 inner iterations)."""
@@ -575,8 +575,8 @@ def cavity129_ref():
 
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
 def test_cavity129_100_steps(L, cavity129_ref, precision):
-    """Config 4's mesh (129x129-node cavity, 16,641 coarse / 66,049 fine nodes, dt = 0.005): the
-    spec bar, 1e-10 relative L2 in u and in w = M^-1 G p_f after 100 steps at rtol 1e-13."""
+    """The 129x129-node cavity (16,641 coarse / 66,049 fine nodes, dt = 0.005): the
+    parity bar, 1e-10 relative L2 in u and in w = M^-1 G p_f after 100 steps at rtol 1e-13."""
     coarse, prob, ref = cavity129_ref
     f = flow(coarse, prob, rtol=1e-13, precision=precision)
     gp = _steps_with_gradient(L, f, 100)

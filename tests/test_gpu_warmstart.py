@@ -1,7 +1,7 @@
 """The learned warm start, end to end on a small case: pairs logged by the batched solver, the
 network trained in residual form (it corrects the previous step's pressure from that guess's
 residual b - K p^{n-1}) by the tcgen05 kernels, and its gain on held-out runs. Every start is
-solved by the batched multi-right-hand-side CG to the same tolerance, which is the judge."""
+solved by the batched multi-right-hand-side CG to the same tolerance, which decides each error."""
 import os
 
 import numpy as np
