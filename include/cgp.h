@@ -226,7 +226,9 @@ int cgp_fine_mesh(cgp_ctx ctx, double* xy_host, int* tri_host, unsigned char* on
  * p_mask_host[n_coarse]: 1 where the coarse pressure is held at 0 (Eq. 14 on the open boundary,
  * plus one pinned node for enclosed flows whose pure-Neumann problem of Eq. 13 is singular);
  * those rows and columns are eliminated symmetrically. g_host[n_fine][2]: prescribed velocity
- * values (read only where a bit is set). Synchronous. Errors: CGP_ERR_ARG. */
+ * values (read only where a bit is set). Synchronous. The momentum system must be assembled
+ * again afterwards (cgp_momentum_solve and cgp_solver_spmv return CGP_ERR_STATE until then).
+ * Errors: CGP_ERR_ARG. */
 int cgp_set_bc(cgp_ctx ctx, const unsigned char* vel_mask_host, const unsigned char* p_mask_host,
                const double* g_host);
 
@@ -243,7 +245,7 @@ int cgp_assemble(cgp_ctx ctx, const double* u_dev, void* stream);
 /* Step 1, Eq. 19: solve A u~ = b (per component, Dirichlet rows replaced by identity rows) by
  * BiCGStab on both components at once, preconditioned by Jacobi or by the FP32 Chebyshev
  * polynomial of cgp_params.momentum_degree (CGP_MIXED: FP32 BiCGStab inside FP64 iterative
- * refinement). Requires cgp_assemble() on the same u^n first. u_dev: u^n, the initial
+ * refinement). Requires an assembly on the same u^n first (else CGP_ERR_STATE). u_dev: u^n, the initial
  * guess, plus the previous converged increment when warm_start >= 1, or NULL for the velocity of
  * the last assembly (cgp_assemble, cgp_assemble_incremental, cgp_step or a batched step; no second
  * copy into the library's fine order) while a buffer still holds it: with fine_order = 1 or
@@ -439,7 +441,8 @@ int cgp_extrapolate(long long n, int order, const double* v0_dev, const double* 
  * persistent kernels (the default or 256, i.e. rows per thread), by timing the consistent-mass CG
  * on a fixed right-hand side and, after cgp_set_bc, the momentum BiCGStab on the matrix of a fluid
  * at rest (the default is left only for a 5 % gain). Overwrites the statistics, the momentum
- * matrix and right-hand side (rebuilt by the next cgp_assemble) and the context's intermediate-
+ * matrix and right-hand side (after cgp_set_bc they count as not assembled: rebuilt by the next
+ * assembly) and the context's intermediate-
  * velocity, staging and gradient buffers (not the solution histories). Synchronous. */
 int cgp_autotune(cgp_ctx ctx, void* stream);
 

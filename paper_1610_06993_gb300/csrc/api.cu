@@ -460,6 +460,8 @@ int cgp_set_bc(cgp_ctx c, const unsigned char* vel_mask, const unsigned char* p_
     CK(cudaMemcpy(c->p_mask, p_mask, (size_t)c->nc, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->g, g, 2 * sizeof(double) * (size_t)c->nf, cudaMemcpyHostToDevice));
     CK(launch_apply_pressure_bc(c, 0));
+    c->u_asm = nullptr;   // A and b of Eq. 19 carry the old boundary classes until assembled again
+    c->assembled = false;
     CK(cudaMemset(c->pc_flag, 0, sizeof(int)));   // the predictors start over
     CK(cudaMemset(c->w_flag, 0, sizeof(int)));
     CK(cudaMemset(c->mom_flag, 0, sizeof(int)));
@@ -492,7 +494,7 @@ int cgp_assemble(cgp_ctx c, const double* u_dev, void* stream) {
 
 int cgp_momentum_solve(cgp_ctx c, const double* u_dev, double* ut_dev, void* stream) {
     if (!c) return CGP_ERR_ARG;
-    if (!c->bc_set) return CGP_ERR_STATE;
+    if (!c->bc_set || !c->assembled) return CGP_ERR_STATE;
     cudaStream_t s = (cudaStream_t)stream;
     const double* u = c->u_asm;   // NULL u_dev: the velocity of the last assembly
     if (u_dev) {
@@ -796,6 +798,10 @@ int cgp_autotune(cgp_ctx c, void* stream) {
         c->sh_f.lanes = win.lanes;
         c->ell_on = win.ell;
         c->prm.warm_start = ws_keep;
+        if (mom) {   // A now holds the fluid at rest: the caller's assembly is gone
+            c->u_asm = nullptr;
+            c->assembled = false;
+        }
         CK(cudaMemset(c->stats, 0, sizeof(DevStats)));
     }
     return CGP_OK;

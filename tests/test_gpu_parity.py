@@ -267,6 +267,8 @@ def test_null_velocity_follows_the_assembly(L, order):
     with pytest.raises(L.CGPError):
         L.cgp_momentum_solve(f.ctx, None, None)   # nothing assembled yet
     with pytest.raises(L.CGPError):
+        L.cgp_momentum_solve(f.ctx, f.u, torch.empty_like(f.u))
+    with pytest.raises(L.CGPError):
         L.cgp_solver_spmv(f.ctx, x, y)
     f.step(2)
     L.cgp_solver_spmv(f.ctx, x, y)
@@ -288,6 +290,10 @@ def test_null_velocity_follows_the_assembly(L, order):
     else:
         L.cgp_momentum_solve(f.ctx, None, None)
     f.stats(check=True)
+    # new boundary classes: nothing is assembled with them yet
+    L.cgp_set_bc(f.ctx, f.vel_mask, f.p_mask, f.g_dev.cpu().numpy())
+    with pytest.raises(L.CGPError):
+        L.cgp_solver_spmv(f.ctx, x, y)
     f.close()
 
 
