@@ -204,6 +204,14 @@ int cgp_mesh_create(const cgp_mesh_desc* coarse, const cgp_params* prm, cgp_ctx*
 int cgp_refine(const cgp_mesh_desc* coarse, int levels, int* n_fine, int* n_tris_fine, double* xy_host,
                int* tri_host, int* sp_host, int* colour_host);
 
+/* Host-only query (no device calls): the order in which cgp_mesh_create() stores the fine nodes
+ * with fine_order = 0 (a data layout of this library, not a step of the paper): the nodes sorted
+ * by their position along a Hilbert curve of 2^16 x 2^16 cells spanning the larger side of the
+ * mesh's bounding box (ties in the refinement order). perm_host[n_fine] receives, for each stored
+ * node i, its index in the refinement order of cgp_refine (the identity when levels = 0): the
+ * permutation cgp_fine_order() reports for such a context. Errors: CGP_ERR_ARG, CGP_ERR_MESH. */
+int cgp_refine_order(const cgp_mesh_desc* coarse, int levels, int* perm_host);
+
 /* Coarse-pressure predictor for time stepping: pc <- 2 pc - pc_prev (warm_start = 1, or the second
  * call), pc <- 3 pc - 3 pc_prev + pc_prev2 (warm_start = 2, or the third call) or
  * pc <- 4 pc - 6 pc_prev + 4 pc_prev2 - pc_prev3 (warm_start = 3, from the fourth call on), where

@@ -68,6 +68,7 @@ _SIGNATURES = {
     "cgp_mesh_create": (C.c_int, [C.POINTER(cgp_mesh_desc), C.POINTER(cgp_params), C.POINTER(_VP)]),
     "cgp_refine": (C.c_int, [C.POINTER(cgp_mesh_desc), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                              _VP, _VP, _VP, _VP]),
+    "cgp_refine_order": (C.c_int, [C.POINTER(cgp_mesh_desc), C.c_int, _VP]),
     "cgp_mesh_info": (C.c_int, [_VP, C.POINTER(cgp_info)]),
     "cgp_fine_mesh": (C.c_int, [_VP, _VP, _VP, _VP]),
     "cgp_set_bc": (C.c_int, [_VP, _VP, _VP, _VP]),
@@ -205,6 +206,20 @@ def cgp_refine(xy: np.ndarray, tri: np.ndarray, levels: int):
     _check(load().cgp_refine(C.byref(d), levels, C.byref(nf), C.byref(tf), xf.ctypes.data, tr.ctypes.data,
                              sp.ctypes.data, col.ctypes.data), "cgp_refine")
     return xf, tr, sp, col
+
+
+def cgp_refine_order(xy: np.ndarray, tri: np.ndarray, levels: int) -> np.ndarray:
+    """Host-only query of the stored fine-node order (fine_order = 0): perm[i] is the refinement-
+    order index of stored node i."""
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    d = cgp_mesh_desc(int(xy.shape[0]), int(tri.shape[0]), xy.ctypes.data_as(C.POINTER(C.c_double)),
+                      tri.ctypes.data_as(C.POINTER(C.c_int)))
+    nf, tf = C.c_int(), C.c_int()
+    _check(load().cgp_refine(C.byref(d), levels, C.byref(nf), C.byref(tf), None, None, None, None), "cgp_refine")
+    perm = np.empty(nf.value, dtype=np.int32)
+    _check(load().cgp_refine_order(C.byref(d), levels, perm.ctypes.data), "cgp_refine_order")
+    return perm
 
 
 def cgp_mesh_info(ctx: int) -> cgp_info:

@@ -393,6 +393,16 @@ int cgp_refine(const cgp_mesh_desc* coarse, int levels, int* n_fine, int* n_tris
     return CGP_OK;
 }
 
+int cgp_refine_order(const cgp_mesh_desc* coarse, int levels, int* perm_host) {
+    if (!coarse || !perm_host) return CGP_ERR_ARG;
+    HostMesh H;
+    int s = build_host_mesh(coarse, levels, H, true);
+    if (s != CGP_OK) return s;
+    const int n = H.lv[levels].n;
+    for (int i = 0; i < n; ++i) perm_host[i] = H.fperm.empty() ? i : H.fperm[i];
+    return CGP_OK;
+}
+
 int cgp_mesh_info(cgp_ctx c, cgp_info* info) {
     if (!c || !info) return CGP_ERR_ARG;
     info->n_fine = c->nf;

@@ -187,6 +187,18 @@ def test_fine_storage_orders_agree(L, name):
         assert rel(out[0][k], out[1][k]) < 1e-10, k
 
 
+@pytest.mark.parametrize("order", [0, 1], ids=["hilbert", "refinement"])
+def test_context_order_is_the_host_query(L, order):
+    """cgp_fine_order on a context reports the permutation that the host-only cgp_refine_order
+    computes without a GPU (fine_order = 0), or the identity (fine_order = 1)."""
+    coarse, prob, _ = ci.workload("cavity33")
+    f = flow(coarse, prob, fine_order=order)
+    perm = L.cgp_fine_order(f.ctx, f.info.n_fine)
+    f.close()
+    want = L.cgp_refine_order(coarse.xy, coarse.tri, prob.levels) if order == 0 else np.arange(len(perm))
+    assert np.array_equal(perm, want)
+
+
 def _steps_with_gradient(L, f, n):
     """n steps; the last one through the stage entry points, returning w = M^-1 G p_f (the
     pressure gradient the correction applies) on the host."""

@@ -102,6 +102,70 @@ def test_refinement_at_workload_size(L):
     assert np.array_equal(xf, h.fine.xy) and np.array_equal(tf, h.fine.tri)
 
 
+def _hilbert_position(x, y, bits):
+    """Position of the integer cells (x, y), 0 <= x, y < 2^bits, along the Hilbert curve, from its
+    recursive construction: at each scale, coarsest first, the quadrant (rx, ry) gives the base-4
+    digit (3 rx) xor ry, and the coordinates are mapped into that quadrant's sub-curve (the lower
+    quadrants are transposed, the lower-right one also reflected)."""
+    n = 1 << bits
+    x, y = np.asarray(x, dtype=np.int64).copy(), np.asarray(y, dtype=np.int64).copy()
+    d = np.zeros_like(x)
+    s = n // 2
+    while s > 0:
+        rx, ry = (x & s) > 0, (y & s) > 0
+        d += s * s * ((3 * rx.astype(np.int64)) ^ ry.astype(np.int64))
+        flip = ~ry & rx
+        x, y = np.where(flip, n - 1 - x, x), np.where(flip, n - 1 - y, y)
+        x, y = np.where(~ry, y, x), np.where(~ry, x, y)
+        s //= 2
+    return d
+
+
+@pytest.mark.parametrize("bits", [1, 2, 3, 5])
+def test_hilbert_position_visits_every_cell_by_unit_steps(bits):
+    """The test's curve is a Hilbert curve: a bijection onto 0..4^bits - 1 starting at (0, 0) and
+    ending at (2^bits - 1, 0), whose consecutive cells are edge neighbours."""
+    n = 1 << bits
+    gx, gy = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    d = _hilbert_position(gx.ravel(), gy.ravel(), bits)
+    assert np.array_equal(np.sort(d), np.arange(n * n))
+    order = np.argsort(d)
+    px, py = gx.ravel()[order], gy.ravel()[order]
+    assert (px[0], py[0]) == (0, 0) and (px[-1], py[-1]) == (n - 1, 0)
+    assert np.all(np.abs(np.diff(px)) + np.abs(np.diff(py)) == 1)
+    if bits == 1:
+        assert [(a, b) for a, b in zip(px, py)] == [(0, 0), (0, 1), (1, 1), (1, 0)]
+
+
+@pytest.mark.parametrize("name", ["cavity", "bfs", "cylinder_small"])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_stored_fine_order_is_the_hilbert_order(L, name, levels):
+    """The fine-node storage order (fine_order = 0) is the refinement-order nodes sorted by their
+    Hilbert position on 2^16 x 2^16 cells over the larger side of the bounding box, ties kept in
+    refinement order; the identity at levels = 0. It makes the matrix graph local: the median index
+    distance of the fine edges falls to a few rows (observed 3, against 168-3,237 in the refinement
+    order on these meshes)."""
+    mesh = {"cavity": lambda: ci.cavity_mesh(17, 3), "bfs": lambda: ci.bfs_mesh(4, 1001),
+            "cylinder_small": lambda: ci.workload("cylinder_small")[0]}[name]()
+    xf, tf, _, _ = L.cgp_refine(mesh.xy, mesh.tri, levels)
+    perm = L.cgp_refine_order(mesh.xy, mesh.tri, levels)
+    assert np.array_equal(perm, L.cgp_refine_order(mesh.xy, mesh.tri, levels))
+    if levels == 0:
+        assert np.array_equal(perm, np.arange(len(xf)))
+        return
+    lo = xf.min(axis=0)
+    ext = float((xf.max(axis=0) - lo).max())
+    cells = np.minimum(65535.0, np.maximum(0.0, (xf - lo) * (65535.0 / ext))).astype(np.int64)
+    key = _hilbert_position(cells[:, 0], cells[:, 1], 16)
+    assert np.array_equal(perm, np.argsort(key, kind="stable"))
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+    e = np.concatenate([tf[:, [0, 1]], tf[:, [1, 2]], tf[:, [2, 0]]])
+    stored = np.median(np.abs(inv[e[:, 0]] - inv[e[:, 1]]))
+    natural = np.median(np.abs(e[:, 0] - e[:, 1]))
+    assert stored <= 8 and stored * 8 < natural, (stored, natural)
+
+
 def test_mesh_validation_errors(L):
     xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])
     good = np.array([[0, 1, 2], [1, 3, 2]])
@@ -119,6 +183,9 @@ def test_mesh_validation_errors(L):
     with pytest.raises(L.CGPError) as e:
         L.cgp_refine(xy, good, 7)
     assert e.value.code == L.CGP_ERR_ARG
+    with pytest.raises(L.CGPError) as e:
+        L.cgp_refine_order(xy, np.array([[0, 2, 1], [1, 3, 2]]), 1)
+    assert e.value.code == L.CGP_ERR_MESH
 
 
 def test_status_strings(L):
