@@ -151,6 +151,25 @@ def bfs_mesh(cells_per_unit: int = 33, seed: int = 1001) -> CoarseMesh:
     return m
 
 
+def centroid_split(m: CoarseMesh, n_split: int) -> CoarseMesh:
+    """``m`` with its first ``n_split`` even-numbered triangles each divided at its centroid into
+    three counter-clockwise triangles: one node and two triangles more per split, the boundary
+    unchanged. Reaches a prescribed node and triangle count (a jittered grid fixes the boundary
+    node count, the splits the rest)."""
+    tri = np.asarray(m.tri, dtype=np.int64)
+    sel = np.arange(0, 2 * n_split, 2)
+    if n_split < 0 or (n_split > 0 and sel[-1] >= len(tri)):
+        raise ValueError("not enough triangles to split")
+    g = m.xy[tri[sel]].mean(axis=1)
+    gi = m.n_nodes + np.arange(n_split)
+    a, b, c = tri[sel, 0], tri[sel, 1], tri[sel, 2]
+    keep = np.ones(len(tri), dtype=bool)
+    keep[sel] = False
+    new = np.concatenate([tri[keep], np.stack([a, b, gi], 1), np.stack([b, c, gi], 1), np.stack([c, a, gi], 1)])
+    return CoarseMesh(xy=np.ascontiguousarray(np.concatenate([m.xy, g]), dtype=np.float64),
+                      tri=np.ascontiguousarray(new.astype(np.int32)), name=f"{m.name}+{n_split}split")
+
+
 # --------------------------------------------------------------------------------------
 # Boundary conditions and problem definitions
 # --------------------------------------------------------------------------------------

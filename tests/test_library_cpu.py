@@ -166,6 +166,21 @@ def test_stored_fine_order_is_the_hilbert_order(L, name, levels):
     assert stored <= 8 and stored * 8 < natural, (stored, natural)
 
 
+def test_native_mapping_loop_counts_of_the_paper(L):
+    """The native refinement on the mesh of the paper's mapping count (Sect. 3.2, Table 5; l = 3,
+    1,600 coarse and 102,400 fine elements): the prolongation's levels 1-3 hold 68,659 nodes."""
+    from test_oracle_pins import load_mapping_loop_counts, mapping_loop_mesh
+    g = load_mapping_loop_counts()
+    m = mapping_loop_mesh()
+    sizes = []
+    for lv in range(1, g["levels"] + 1):
+        xf, tf, sp, _ = L.cgp_refine(m.xy, m.tri, lv)
+        sizes.append(len(xf))
+        assert len(sp) == len(xf)
+    assert len(tf) == g["fine_elements"]
+    assert sum(sizes) == g["prolongation_loops"]
+
+
 def test_mesh_validation_errors(L):
     xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])
     good = np.array([[0, 1, 2], [1, 3, 2]])

@@ -221,6 +221,34 @@ def test_refinement_topology(mesh, levels):
         np.testing.assert_allclose(area_f.reshape(-1, 4).sum(1), area_c, rtol=1e-13)
 
 
+def load_mapping_loop_counts():
+    """The mapping-operator loop counts the paper gives for l = 3 (tests/golden)."""
+    with open(os.path.join(GOLDEN, "mapping_loop_counts_bfs_l3.txt")) as f:
+        return {k: int(v) for k, v in (ln.split() for ln in f if ln.strip() and not ln.startswith("#"))}
+
+
+def mapping_loop_mesh():
+    """A simply connected coarse mesh of the quoted size: a 100 x 4-cell jittered channel (505
+    nodes, 800 triangles, 208 boundary nodes) with 400 triangles split at their centroids, 905
+    nodes and 1,600 triangles. The paper's grid is not available; the counts do not depend on it."""
+    return ci.centroid_split(ci.jittered_grid(0.0, 25.0, 0.0, 1.0, 100, 4, 1005), 400)
+
+
+def test_mapping_loop_counts_of_the_paper():
+    """Sect. 3.2, with Table 5: for l = 3 on a simply connected grid of 1,600 coarse and 102,400
+    fine elements the injection (Eqs. 20, 30) runs over the 905 coarse pressure nodes and the
+    prolongation (Eqs. 22, 29) over the 68,659 nodes of levels 1-3. A refinement that created a
+    midpoint per triangle side instead of per edge, or lost one, would miss both fine counts."""
+    g = load_mapping_loop_counts()
+    m = mapping_loop_mesh()
+    assert m.n_nodes == g["restriction_loops"] and m.n_tris == g["coarse_elements"]
+    h = refine.build_hierarchy(m.xy, m.tri, g["levels"])
+    assert len(h.fine.tri) == g["fine_elements"]
+    assert len(h.su) == g["restriction_loops"]
+    assert sum(len(sp) for sp in h.sp) == g["prolongation_loops"]
+    assert [len(lv.xy) for lv in h.levels[1:]] == [3409, 13217, 52033]
+
+
 def test_restrict_prolong_identity_and_linear_exactness():
     m = ci.cavity_mesh(9, 13)
     h = refine.build_hierarchy(m.xy, m.tri, 3)
