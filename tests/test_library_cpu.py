@@ -181,6 +181,18 @@ def test_native_mapping_loop_counts_of_the_paper(L):
     assert sum(sizes) == g["prolongation_loops"]
 
 
+@pytest.mark.parametrize("case", ["taylor_green", "cylinder"])
+def test_native_nested_mesh_counts_of_the_paper(L, case):
+    """The native refinement reproduces the nested-mesh counts of the paper's Taylor-Green and
+    cylinder meshes (Sects. 3.1, 3.3) from a mesh of the coarsest level's size."""
+    from test_oracle_pins import NESTED_GRIDS, holed_mesh_of_size, load_nested_mesh_counts
+    levels = load_nested_mesh_counts()[case]
+    m = holed_mesh_of_size(*levels[0], *NESTED_GRIDS[case])
+    for lv, (nodes, elems) in enumerate(levels[1:], start=1):
+        xf, tf, _, _ = L.cgp_refine(m.xy, m.tri, lv)
+        assert len(tf) == elems and (nodes < 0 or len(xf) == nodes)
+
+
 def test_mesh_validation_errors(L):
     xy = np.array([[0.0, 0.0], [1.0, 0.0], [0.0, 1.0], [1.0, 1.0]])
     good = np.array([[0, 1, 2], [1, 3, 2]])

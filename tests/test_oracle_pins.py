@@ -249,6 +249,47 @@ def test_mapping_loop_counts_of_the_paper():
     assert [len(lv.xy) for lv in h.levels[1:]] == [3409, 13217, 52033]
 
 
+def load_nested_mesh_counts():
+    """Per case, the (nodes, elements) of each level the paper gives (tests/golden)."""
+    out = {}
+    with open(os.path.join(GOLDEN, "nested_mesh_counts.txt")) as f:
+        for ln in f:
+            if ln.strip() and not ln.startswith("#"):
+                case, level, nodes, elems = ln.split()
+                out.setdefault(case, []).append((int(nodes), int(elems)))
+    return out
+
+
+def holed_mesh_of_size(n_nodes, n_tris, n, k):
+    """A mesh with one hole and the given counts: an n x n-cell jittered square with a centred
+    k x k-cell hole (boundary nodes 4 n + 4 k = 2 n_nodes - n_tris by Euler's formula) and as many
+    centroid splits as the remaining nodes. The paper's meshes are not available; the counts of the
+    refined levels depend only on these."""
+    c0 = (n - k) // 2
+    m = ci.jittered_grid(0.0, 1.0, 0.0, 1.0, n, n, 1006,
+                         removed_cell=lambda i, j: (i >= c0) & (i < c0 + k) & (j >= c0) & (j < c0 + k))
+    assert 4 * n + 4 * k == 2 * n_nodes - n_tris
+    return ci.centroid_split(m, n_nodes - m.n_nodes)
+
+
+NESTED_GRIDS = {"taylor_green": (40, 16), "cylinder": (30, 2)}
+
+
+@pytest.mark.parametrize("case", sorted(NESTED_GRIDS))
+def test_nested_mesh_counts_of_the_paper(case):
+    """The node and element counts the paper prints for its nested Taylor-Green (Sect. 3.1, Fig. 2,
+    Table 1) and cylinder (Sect. 3.3) meshes follow from the coarsest level by the refinement of
+    Sect. 2.2 on a domain with one hole: the oracle reproduces each level from a mesh of the
+    coarsest level's size."""
+    levels = load_nested_mesh_counts()[case]
+    m = holed_mesh_of_size(*levels[0], *NESTED_GRIDS[case])
+    assert (m.n_nodes, m.n_tris) == levels[0]
+    h = refine.build_hierarchy(m.xy, m.tri, len(levels) - 1)
+    for lv, (nodes, elems) in zip(h.levels, levels):
+        assert len(lv.tri) == elems
+        assert nodes < 0 or len(lv.xy) == nodes
+
+
 def test_restrict_prolong_identity_and_linear_exactness():
     m = ci.cavity_mesh(9, 13)
     h = refine.build_hierarchy(m.xy, m.tri, 3)
