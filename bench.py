@@ -311,7 +311,7 @@ def solver_spmv(L, f, flush, stream, reps: int = 10):
             "peak_kind": kind, "l2": "flushed before each product (512 MB write, then 256 MB read)"}
 
 
-def spmv_hbm(L, Flow, dev, flush, stream, reps: int = 10):
+def spmv_hbm(L, Flow, dev, flush, stream, reps: int = 10, fine_order: int = 0):
     """The Krylov SpMV (two right-hand sides, FP64) on a matrix larger than L2: the backward-facing
     step at h = 1/48 refined twice (~2.2M rows, ~15M nnz, ~265 MB per product). Algorithmic bytes
     per product: 12 nnz (values, columns) + 4 (n + 1) (row pointers) + 16 n (x) + 16 n (y)."""
@@ -321,7 +321,7 @@ def spmv_hbm(L, Flow, dev, flush, stream, reps: int = 10):
     peak, kind = peaks()
     best = None
     for fmt, kname in ((2, "k_spmv_probe<2> (CSR, autotuned lanes)"), (1, "k_spmv_sell2 (sliced ELL, 32-row slices)")):
-        f = Flow(coarse, prob, device=dev, spmv_format=fmt)
+        f = Flow(coarse, prob, device=dev, spmv_format=fmt, fine_order=fine_order)
         L.cgp_autotune(f.ctx, stream)
         info = L.cgp_mesh_info(f.ctx)
         n, nnz = info.n_fine, info.nnz_fine
@@ -341,8 +341,9 @@ def spmv_hbm(L, Flow, dev, flush, stream, reps: int = 10):
         t = statistics.median(ms)
         nbytes = 12 * nnz + 4 * (n + 1) + 32 * n
         gbs = nbytes / (t * 1e-3) / 1e9
+        order = "stored (Hilbert-curve)" if info.fine_order == 0 else "refinement"
         rec = {"kernel": kname, "workload": f"bfs48 l=2 fine A0: {n} rows, {nnz} nnz, 2 RHS, fine nodes in the "
-                                             f"library's stored (Hilbert-curve) order", "bytes": nbytes,
+                                             f"{order} order", "bytes": nbytes,
                "ms": t, "achieved": gbs, "unit": "GB/s", "peak": peak, "frac": gbs / peak, "peak_kind": kind,
                "lanes": info.spmv_lanes, "l2": "flushed before each product (512 MB write, then 256 MB read)"}
         if best is None or gbs > best["achieved"]:
@@ -625,7 +626,7 @@ def run_gpu(args):
     if args.secondary and ws == 1:
         line["secondary"] = secondary_bfs33(L, Flow, dev, flush, stream, args)
     if not args.no_spmv:
-        line["spmv_hbm"] = spmv_hbm(L, Flow, dev, flush, stream)
+        line["spmv_hbm"] = spmv_hbm(L, Flow, dev, flush, stream, fine_order=args.fine_order)
         if sv is not None:
             line["spmv_hbm"]["fine_solver_product"] = sv
     if rank == 0:
@@ -977,7 +978,8 @@ def main():
         from paper_1610_06993_gb300.flow import Flow
         torch.cuda.set_device(0)
         flush = L2Flush("cuda:0")
-        print(json.dumps(spmv_hbm(L, Flow, "cuda:0", flush, torch.cuda.current_stream(), reps=args.steps)), flush=True)
+        print(json.dumps(spmv_hbm(L, Flow, "cuda:0", flush, torch.cuda.current_stream(), reps=args.steps,
+                                  fine_order=args.fine_order)), flush=True)
     else:
         run_gpu(args)
 
