@@ -29,6 +29,17 @@ leave these open; each is defined here in plain terms and checked by the pins in
   chi = -(dt/rho) M_L^-1 b_c is the discrete divergence the coarse right-hand side was built
   from (D_c u~_c with injection, P^T D_f u~_f with the Galerkin restriction) divided by the
   lumped coarse mass M_L (chi = 0 where the pressure is held, as b_c is).
+
+Test device, not a scheme of the paper: ``exact_projection=True`` (levels = 0 only) keeps steps
+1-5 and their code but solves Eq. 23 with the lumped mass M_L and replaces K_c in Eq. 21 by
+E = -(Dx P_x M_L^-1 P_x Dx + Dy P_y M_L^-1 P_y Dy), where Dx, Dy give the correction's gradient
+G p = (Dx p, Dy p) and P_x, P_y keep the velocity components that are not Dirichlet. E p =
+-(rho/dt) D u~ is then exactly the condition D u^{n+1} = 0 on every row whose pressure is free,
+so the discrete divergence of the corrected velocity vanishes there up to rounding: an invariant
+against which the signs, factors and operator pairings of steps 2-5 are checked. Pressure nodes
+none of whose velocity neighbours is free (no row of D P) are held at 0 as well. The paper's own
+scheme (K_c, consistent M) does not have this property; equal-order P1 pairs can make E singular
+on some meshes (spurious pressure modes), which the sparse LU then reports.
 """
 from __future__ import annotations
 
@@ -63,11 +74,21 @@ class StepResult:
     gp: np.ndarray       # M^{-1} G p_f                  [N_f, 2]
 
 
+class _LumpedMass:
+    """M_L^-1 applied by a division (the exact-projection test device)."""
+
+    def __init__(self, ml: np.ndarray):
+        self.ml = ml
+
+    def solve(self, v: np.ndarray) -> np.ndarray:
+        return v / self.ml
+
+
 class CGPOracle:
     """The CGP method on one coarse mesh refined ``levels`` times (``levels = 0``: standard scheme)."""
 
     def __init__(self, coarse_xy, coarse_tri, rho, mu, dt, levels, vel_bc, p_bc, restrict_mode="injection",
-                 projection="standard"):
+                 projection="standard", exact_projection=False):
         if restrict_mode not in ("injection", "galerkin"):
             raise ValueError(restrict_mode)
         if projection not in ("standard", "incremental", "rotational"):
@@ -82,9 +103,24 @@ class CGPOracle:
         self.onb_c = refine.boundary_nodes(coarse.tri, coarse.xy.shape[0])
         self.vel_bc = vel_bc
         self.p_mask = np.asarray(p_bc(coarse.xy, self.onb_c)).astype(bool)
+        self.A0 = self.rho * self.fine.M + self.dt * self.mu * self.fine.K
+        if exact_projection:
+            if levels != 0:
+                raise ValueError("the exact projection is defined for levels = 0")
+            mask, _ = self.dirichlet(0.0)
+            ml = np.asarray(self.fine.M.sum(axis=1)).ravel()
+            E = sp.csr_matrix((self.fine.n, self.fine.n))
+            reach = np.zeros(self.fine.n)
+            for c, Dc in enumerate((self.fine.Dx, self.fine.Dy)):
+                free = ((mask & (1 << c)) == 0).astype(np.float64)
+                E = E - Dc @ sp.diags(free / ml) @ Dc
+                reach += abs(Dc) @ free
+            self.p_mask = self.p_mask | (reach == 0)
+            self.Kc_lu = spla.splu(_bc_sym(E.tocsr(), self.p_mask))
+            self.M_lu = _LumpedMass(ml)
+            return
         self.Kc_lu = spla.splu(_bc_sym(self.coarse.K, self.p_mask))
         self.M_lu = spla.splu(self.fine.M.tocsc())
-        self.A0 = self.rho * self.fine.M + self.dt * self.mu * self.fine.K
 
     @property
     def n_fine(self) -> int:
