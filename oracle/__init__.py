@@ -12,7 +12,9 @@ Modules
 ``refine``  nested 1:4 refinement and the s^p / s^u mapping tables (Sect. 2.2, Eqs. 29-30).
 ``fem``     closed-form P1 element matrices and global assembly (Eqs. 16-18).
 ``cgp``     the five-step IFE-CGP time step (Eqs. 19-23) with direct sparse solves, plus the
-            Galerkin restriction and the incremental / rotational forms (options, Sect. 4).
+            Galerkin restriction and the incremental / rotational forms (options, Sect. 4) and
+            an exact-projection test device (levels 0) that pins steps 2-5 by the discrete
+            divergence it must remove.
 ``diagnostics``  body forces (drag, lift), wall shear, reattachment length and Strouhal number
             of the benchmark flows (Sect. 3.2-3.3).
 
@@ -21,5 +23,6 @@ results carry only rounding error; the CUDA path's Krylov solvers are compared a
 their stated tolerance.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in ``tests/`` (closed
-forms, invariants, brute-force quadrature on tiny meshes, convergence rates). None is unpinned.
+forms, invariants, brute-force quadrature on tiny meshes, convergence rates, the mesh and mapping
+counts the paper prints). None is unpinned.
 """
