@@ -110,3 +110,25 @@ def test_bench_accounting_helpers():
     # gradient, mass, correction
     assert bench.batch_launches_per_step([flow(1, 0, 3)] * 3) == 11
     assert bench.batch_launches_per_step([flow(1, 1, 0)]) == 8
+
+
+def test_clock_record_from_sampled_lines():
+    """The `clocks` key: median SM clock under load, the maximum clock and every throttle reason
+    that was active in any sample (nvidia-smi's csv,noheader,nounits lines); lines that do not
+    parse are skipped."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    c.lines = [
+        "0, 2070, 2070, 900.50, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1965, 2070, 1399.12, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1100.00, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 1100.00, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "not a sample",
+    ]
+    assert c.summary() == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.lines.append("0, 1500, 2070, 1200.00, 0x0000000000000008, Active, Not Active, Not Active, Not Active")
+    s = c.summary()
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"] and s["samples"] == 4 and s["sm_mhz"] == 2017.5
+    c.lines = []
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
