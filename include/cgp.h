@@ -180,7 +180,7 @@ typedef struct {
  * inner_rtol = 1e-4, max_iter = 20000, max_outer = 30, spmv_lanes = 0, block_threads = 0,
  * coarse_solver = 0, spmv_format = 0, precond_degree = 0, precond_ratio = 0, warm_start = 3, mass_degree = 0,
  * momentum_degree = 0, solver_format = 0, restrict_mode = 0, projection = 0, fine_order = 0,
- * momentum_rtol = 0 (rtol / 10 with CGP_MIXED, else rtol). */
+ * momentum_rtol = 0 (rtol / 10 with CGP_MIXED, else rtol). p NULL: nothing is written. */
 void cgp_default_params(cgp_params* p);
 
 /* Preprocessing (the paper's C_pre, Sect. 2.4): validates the coarse mesh, refines it
@@ -221,12 +221,13 @@ int cgp_refine_order(const cgp_mesh_desc* coarse, int levels, int* perm_host);
  * cgp_step calls it when warm_start >= 1. Errors: CGP_ERR_ARG, CGP_ERR_STATE, CGP_ERR_CUDA. */
 int cgp_predict_pressure(cgp_ctx ctx, double* pc_dev, void* stream);
 
-/* Sizes and launch shapes of the context. */
+/* Sizes and launch shapes of the context. Host-side; errors: CGP_ERR_ARG (NULL). */
 int cgp_mesh_info(cgp_ctx ctx, cgp_info* info);
 
 /* Copy the fine (velocity) mesh out: xy_host[n_fine][2], tri_host[tris_fine][3] and
  * on_boundary_host[n_fine] (1 where the node lies on an edge with a single triangle). Any of
- * the three may be NULL. The coarse mesh is the caller's input. */
+ * the three may be NULL. The coarse mesh is the caller's input. Host-side, in the refinement
+ * numbering whatever fine_order is. Errors: CGP_ERR_ARG (NULL context). */
 int cgp_fine_mesh(cgp_ctx ctx, double* xy_host, int* tri_host, unsigned char* on_boundary_host);
 
 /* Boundary classes. vel_mask_host[n_fine]: CGP_BC_U / CGP_BC_V bits of velocity-Dirichlet
@@ -241,13 +242,17 @@ int cgp_set_bc(cgp_ctx ctx, const unsigned char* vel_mask_host, const unsigned c
                const double* g_host);
 
 /* Replace the prescribed velocity values (e.g. time-dependent data at t^{n+1}) from a device
- * array g_dev[n_fine][2]; stream-ordered copy. */
+ * array g_dev[n_fine][2] in the refinement numbering (read only where a mask bit is set);
+ * stream-ordered copy into the context. Errors: CGP_ERR_ARG (NULL), CGP_ERR_CUDA. */
 int cgp_set_dirichlet_values(cgp_ctx ctx, const double* g_dev, void* stream);
 
 /* Step 1 set-up, Eq. 19: A = rho M + dt (rho N(u^n) + mu K) written into the fixed fine CSR
  * pattern from per-element contributions gathered per entry (no atomics, deterministic), the Jacobi diagonal
  * per component, and the right-hand side b = rho M u^n with Dirichlet rows set to the prescribed
- * values. u_dev: [n_fine][2] velocity u^n. */
+ * values. u_dev: [n_fine][2] velocity u^n, read (with fine_order = 0 gathered into the library's
+ * stored order; with fine_order = 1 or levels = 0 this buffer is what a later NULL u^n in
+ * cgp_momentum_solve reads).
+ * Stream-ordered. Errors: CGP_ERR_ARG (NULL), CGP_ERR_STATE (before cgp_set_bc), CGP_ERR_CUDA. */
 int cgp_assemble(cgp_ctx ctx, const double* u_dev, void* stream);
 
 /* Step 1, Eq. 19: solve A u~ = b (per component, Dirichlet rows replaced by identity rows) by
@@ -269,7 +274,8 @@ int cgp_momentum_solve(cgp_ctx ctx, const double* u_dev, double* ut_dev, void* s
  * zero at p-masked nodes; with restrict_mode = 1, b_c = -(rho/dt) P^T (Dx_f u~_x + Dy_f u~_y)
  * instead (P^T level by level through inverse child lists of the s^p tables of Eq. 29).
  * ut_dev: [n_fine][2], or NULL for the context's u~ of the last cgp_momentum_solve; bc_dev:
- * [n_coarse] output. */
+ * [n_coarse] output. Stream-ordered. Errors: CGP_ERR_ARG (NULL context or bc_dev),
+ * CGP_ERR_STATE (before cgp_set_bc), CGP_ERR_CUDA. */
 int cgp_restrict(cgp_ctx ctx, const double* ut_dev, double* bc_dev, void* stream);
 
 /* Step 3, Eq. 21: solve K_c p_c = b_c (K_c = coarse stiffness, +(-Laplacian), after symmetric
@@ -277,7 +283,9 @@ int cgp_restrict(cgp_ctx ctx, const double* ut_dev, double* bc_dev, void* stream
  * as cgp_params.coarse_solver selects (default: two-level additive Schwarz; 5: Jacobi) (CGP_MIXED:
  * FP32 CG inside FP64 iterative refinement). pc_dev [n_coarse] is
  * the initial guess on entry (warm start) and the solution on exit. bc_dev [n_coarse], or NULL
- * for the context's own right-hand side of its latest cgp_step. */
+ * for the context's own right-hand side of its latest cgp_step. Stream-ordered. Errors:
+ * CGP_ERR_ARG (NULL context or pc_dev), CGP_ERR_STATE (before cgp_set_bc), CGP_ERR_CUDA; the
+ * solve's own outcome (CGP_ERR_NOT_CONVERGED, CGP_ERR_NAN, CGP_ERR_TIMEOUT) through cgp_get_stats. */
 int cgp_poisson_solve(cgp_ctx ctx, const double* bc_dev, double* pc_dev, void* stream);
 
 /* Steps 4-5, Eqs. 22-23 with Eq. 29: p_f = P p_c level by level, g = G p_f (G_ij = int phi_i
@@ -287,7 +295,10 @@ int cgp_poisson_solve(cgp_ctx ctx, const double* bc_dev, double* pc_dev, void* s
  * u = u~ - (dt/rho) w and Dirichlet nodes reset to their prescribed values.
  * pc_dev [n_coarse], ut_dev [n_fine][2] inputs (ut_dev NULL: the context's u~ of the last
  * cgp_momentum_solve); u_dev [n_fine][2] output (may equal ut_dev);
- * pf_dev [n_fine] and gp_dev [n_fine][2] optional outputs (NULL to skip): p_f and w. */
+ * pf_dev [n_fine] and gp_dev [n_fine][2] optional outputs (NULL to skip): p_f and w. All fine
+ * arrays in the refinement numbering. Stream-ordered. Errors: CGP_ERR_ARG (NULL context, pc_dev or
+ * u_dev), CGP_ERR_STATE (before cgp_set_bc), CGP_ERR_CUDA; the mass solve's outcome through
+ * cgp_get_stats. */
 int cgp_prolong_correct(cgp_ctx ctx, const double* pc_dev, const double* ut_dev, double* u_dev,
                         double* pf_dev, double* gp_dev, void* stream);
 
@@ -296,7 +307,9 @@ int cgp_prolong_correct(cgp_ctx ctx, const double* pc_dev, const double* ut_dev,
  * [n_coarse] holds p_c^n on entry and p_c^{n+1} on exit. With projection = 1 or 2 the step is
  * cgp_assemble_incremental with p_c^n, the momentum solve, the restriction, the Poisson solve for
  * the increment (warm-started from the extrapolated previous increments), prolong-correct with
- * the increment and cgp_pressure_update. Stream-ordered, no host sync. */
+ * the increment and cgp_pressure_update. Stream-ordered, no host sync. Errors: CGP_ERR_ARG (NULL),
+ * CGP_ERR_STATE (before cgp_set_bc), CGP_ERR_CUDA; the solves' outcomes (CGP_ERR_NOT_CONVERGED,
+ * CGP_ERR_NAN, CGP_ERR_TIMEOUT) through cgp_get_stats. */
 int cgp_step(cgp_ctx ctx, double* u_dev, double* pc_dev, void* stream);
 
 /* Many coarse Poisson solves (Eq. 21) with the context's matrix in one call: nrhs right-hand
@@ -315,7 +328,8 @@ int cgp_poisson_solve_many(cgp_ctx ctx, int nrhs, const double* b_dev, double* x
 /* Incremental forms, step 1: as cgp_assemble, with the momentum right-hand side
  * rho M u^n - dt G_f P p_c^n (the previous pressure prolonged by Eq. 29 and its fine gradient)
  * at rows that are not velocity-Dirichlet. pc_dev: [n_coarse] p_c^n. Stream-ordered. Not in the
- * paper (its Sect. 4 names the incremental form as future work). */
+ * paper (its Sect. 4 names the incremental form as future work). Errors: CGP_ERR_ARG (NULL),
+ * CGP_ERR_STATE (before cgp_set_bc), CGP_ERR_CUDA. */
 int cgp_assemble_incremental(cgp_ctx ctx, const double* u_dev, const double* pc_dev, void* stream);
 
 /* Incremental forms, last step: pc_dev += phi_dev (projection 1), and for projection 2 also
@@ -341,16 +355,19 @@ int cgp_fine_order(cgp_ctx ctx, int* perm_host);
 /* y = A0 x with A0 = rho M + dt mu K (the constant part of the momentum matrix of Eq. 19) on the
  * fine mesh, for two interleaved right-hand sides: x_dev, y_dev [n_fine][2] in the library's
  * stored fine order (cgp_fine_order), the layout the Krylov solvers multiply in. The sliced-ELL
- * or CSR SpMV kernel (cgp_autotune picks) as a stand-alone launch. Stream-ordered. */
+ * or CSR SpMV kernel (cgp_autotune picks) as a stand-alone launch. Stream-ordered. Errors:
+ * CGP_ERR_ARG (NULL), CGP_ERR_CUDA. */
 int cgp_spmv(cgp_ctx ctx, const double* x_dev, double* y_dev, void* stream);
 
 /* Copy the coarse right-hand side b_c of the context's latest cgp_step (or batched step) to
- * bc_dev [n_coarse] (e.g. to log (b_c, p_c) pairs). Stream-ordered. */
+ * bc_dev [n_coarse] (e.g. to log (b_c, p_c) pairs). Stream-ordered. Errors: CGP_ERR_ARG (NULL),
+ * CGP_ERR_CUDA. */
 int cgp_copy_coarse_rhs(cgp_ctx ctx, double* bc_dev, void* stream);
 
 /* The same step on host buffers: copies u_host [n_fine][2] and pc_host [n_coarse] to the
  * context's device staging buffers, runs cgp_step, copies both back and synchronises the
- * stream. For best copy speed the host buffers should be page-locked. */
+ * stream. For best copy speed the host buffers should be page-locked. Errors: CGP_ERR_ARG (NULL),
+ * the errors of cgp_step, CGP_ERR_CUDA (a copy). */
 int cgp_step_host(cgp_ctx ctx, double* u_host, double* pc_host, void* stream);
 
 /* Synchronise the stream and read the statistics of the latest solves. Returns the first
@@ -372,21 +389,26 @@ int cgp_get_stats(cgp_ctx ctx, void* stream, cgp_stats* st);
  * rejected (CGP_ERR_ARG). */
 typedef struct cgp_batch_s* cgp_batch;
 int cgp_batch_create(cgp_ctx* ctxs, int n, double* const* u_devs, double* const* pc_devs, cgp_batch* out);
-/* Launch shape: total blocks and each instance's group sizes (arrays of n, may be NULL). */
+/* Launch shape: total blocks and each instance's group sizes (arrays of n, may be NULL).
+ * Host-side; errors: CGP_ERR_ARG (NULL batch). */
 int cgp_batch_info(cgp_batch b, int* blocks, int* group_fine, int* group_coarse);
-/* One step of every instance, stream-ordered. */
+/* One step of every instance, stream-ordered. Errors: CGP_ERR_ARG (NULL), CGP_ERR_CUDA; the
+ * instances' solver outcomes through cgp_batch_get_stats. */
 int cgp_batch_step(cgp_batch b, void* stream);
 /* `steps` steps of every instance by replaying a CUDA graph of one step (captured on an internal
- * stream at the first call; make the first call outside any other stream capture). */
+ * stream at the first call; make the first call outside any other stream capture).
+ * Errors: CGP_ERR_ARG (NULL batch, steps < 0), CGP_ERR_CUDA (capture, instantiation or launch). */
 int cgp_batch_run(cgp_batch b, int steps, void* stream);
 /* Only the coarse Poisson stage (Eq. 21) of every instance, one batched launch: instance i solves
  * its context's last coarse right-hand side (from the latest step or cgp_restrict into the
- * context) into pc_devs[i], which is also the initial guess. */
+ * context) into pc_devs[i], which is also the initial guess. Stream-ordered. Errors:
+ * CGP_ERR_ARG (NULL), CGP_ERR_CUDA. */
 int cgp_batch_poisson_solve(cgp_batch b, void* stream);
 /* Synchronise and read every instance's statistics into per_instance[n]; returns the first
- * non-OK status. */
+ * non-OK status (an instance's solver or barrier status, or CGP_ERR_CUDA), CGP_ERR_ARG for NULL. */
 int cgp_batch_get_stats(cgp_batch b, void* stream, cgp_stats* per_instance);
-/* Free the batch (not the contexts). NULL is accepted. */
+/* Free the batch (not the contexts); synchronises the device first. NULL is accepted. Returns
+ * CGP_OK. */
 int cgp_batch_destroy(cgp_batch b);
 
 /* ---- learned warm start for the coarse solve (not in the paper) -----------------------------
@@ -401,22 +423,31 @@ typedef struct cgp_ws_s* cgp_ws;
  * (K contiguous, 16-byte aligned). Requires M % 128 == 0, N % 128 == 0, K % 64 == 0 (else
  * CGP_ERR_ARG). Stream-ordered. The tensor-core product the network is built from. */
 int cgp_gemm_bf16(int M, int N, int K, const void* A_dev, const void* B_dev, float* C_dev, void* stream);
-/* Network for n unknowns, hidden width H (H % 128 == 0), up to batch_max right-hand sides per call. */
+/* Network for n unknowns, hidden width H (H % 128 == 0), up to batch_max right-hand sides per call.
+ * Errors: CGP_ERR_ARG (NULL out, n, H or batch_max out of range), CGP_ERR_NOMEM, CGP_ERR_CUDA. */
 int cgp_ws_create(int n, int hidden, int batch_max, cgp_ws* out);
-/* Host float32 weights: W1 [H][n], b1 [H], W2 [H][H], b2 [H], W3 [n][H], b3 [n]; resets Adam. */
+/* Host float32 weights: W1 [H][n], b1 [H], W2 [H][H], b2 [H], W3 [n][H], b3 [n]; resets Adam.
+ * Synchronous. Errors: CGP_ERR_ARG (NULL), CGP_ERR_CUDA. */
 int cgp_ws_set_params(cgp_ws w, const float* W1, const float* b1, const float* W2, const float* b2, const float* W3,
                       const float* b3);
-/* Copy the FP32 master weights out (host arrays of the same shapes; NULL skips one). Synchronous. */
+/* Copy the FP32 master weights out (host arrays of the same shapes; NULL skips one). Synchronous.
+ * Errors: CGP_ERR_ARG (NULL network), CGP_ERR_CUDA. */
 int cgp_ws_get_params(cgp_ws w, float* W1, float* b1, float* W2, float* b2, float* W3, float* b3);
-/* Gradients of the latest cgp_ws_train_step (same shapes as the weights). Synchronous. */
+/* Gradients of the latest cgp_ws_train_step (same shapes as the weights; NULL skips one).
+ * Synchronous. Errors: CGP_ERR_ARG (NULL network), CGP_ERR_CUDA. */
 int cgp_ws_get_grads(cgp_ws w, float* dW1, float* db1, float* dW2, float* db2, float* dW3, float* db3);
-/* held_host[n]: 1 for pressure-held entries (output forced to 0, excluded from the loss). */
+/* held_host[n]: 1 for pressure-held entries (output forced to 0, excluded from the loss).
+ * Synchronous. Errors: CGP_ERR_ARG (NULL, or every entry held), CGP_ERR_CUDA. */
 int cgp_ws_set_mask(cgp_ws w, const unsigned char* held_host);
-/* Inference: p_dev [B][n] float64 = ||b|| NN(b / ||b||) for b_dev [B][n] float64, B <= batch_max. */
+/* Inference: p_dev [B][n] float64 = ||b|| NN(b / ||b||) for b_dev [B][n] float64, B <= batch_max.
+ * Stream-ordered. Errors: CGP_ERR_ARG (NULL, B outside 1..batch_max), CGP_ERR_CUDA; a device wait
+ * of the tensor-core pipeline that ran out through cgp_ws_status. */
 int cgp_ws_forward(cgp_ws w, const double* b_dev, int B, double* p_dev, void* stream);
 /* One training step on B pairs (b_dev, p_dev) [B][n] float64: loss L = 1/(B n_free) sum over
  * unmasked entries of (NN(b/s) - p/s)^2, gradients by back-propagation, then Adam with step size
- * lr (lr = 0: gradients only). loss_dev (device float, may be NULL) receives L. */
+ * lr (lr = 0: gradients only). loss_dev (device float, may be NULL) receives L. Stream-ordered.
+ * Errors: CGP_ERR_ARG (NULL, B outside 1..batch_max, lr negative or NaN), CGP_ERR_CUDA; a device
+ * wait that ran out through cgp_ws_status. */
 int cgp_ws_train_step(cgp_ws w, const double* b_dev, const double* p_dev, int B, float lr, float* loss_dev,
                       void* stream);
 /* Synchronise and return the network's device error word (CGP_ERR_TIMEOUT if a bounded
@@ -438,7 +469,8 @@ int cgp_ws_train_step_residual(cgp_ws w, cgp_ctx ctx, const double* b_dev, const
 
 /* out = the extrapolation in time of order 0..3 through the values v0 (newest) .. v3 of n doubles:
  * v0, 2 v0 - v1, 3 v0 - 3 v1 + v2, 4 v0 - 6 v1 + 4 v2 - v3 (the initial-guess predictors of
- * warm_start, without a history); unused inputs may be NULL. Stream-ordered. */
+ * warm_start, without a history); unused inputs may be NULL. Stream-ordered. Errors: CGP_ERR_ARG
+ * (n <= 0, order outside 0..3, a needed input NULL), CGP_ERR_CUDA. */
 int cgp_extrapolate(long long n, int order, const double* v0_dev, const double* v1_dev, const double* v2_dev,
                     const double* v3_dev, double* out_dev, void* stream);
 
@@ -451,7 +483,8 @@ int cgp_extrapolate(long long n, int order, const double* v0_dev, const double* 
  * at rest (the default is left only for a 5 % gain). Overwrites the statistics, the momentum
  * matrix and right-hand side (after cgp_set_bc they count as not assembled: rebuilt by the next
  * assembly) and the context's intermediate-
- * velocity, staging and gradient buffers (not the solution histories). Synchronous. */
+ * velocity, staging and gradient buffers (not the solution histories). Synchronous. Errors:
+ * CGP_ERR_ARG (NULL), CGP_ERR_CUDA. */
 int cgp_autotune(cgp_ctx ctx, void* stream);
 
 /* Allocation-free conjugate-gradient solve of one symmetric positive definite CSR system
@@ -518,10 +551,11 @@ int cgp_reattachment(cgp_ctx ctx, const double* u_dev, double x_start, double* x
  * device memory. Stream-ordered. Errors: CGP_ERR_ARG, CGP_ERR_CUDA. */
 int cgp_wait_probe(cgp_ctx ctx, int missing_blocks, double limit_ms, int* status_dev, void* stream);
 
-/* Free everything the context owns. NULL is accepted. */
+/* Free everything the context owns; synchronises the device first. NULL is accepted. Returns
+ * CGP_OK. */
 int cgp_mesh_destroy(cgp_ctx ctx);
 
-/* Name of a status code (static string). */
+/* Name of a status code (static string, never NULL; unknown codes get a generic name). */
 const char* cgp_status_str(int status);
 
 #ifdef __cplusplus
