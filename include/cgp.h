@@ -374,6 +374,7 @@ int cgp_step_host(cgp_ctx ctx, double* u_host, double* pc_host, void* stream);
  * non-OK status among them (CGP_ERR_NOT_CONVERGED, CGP_ERR_NAN, CGP_ERR_TIMEOUT) or CGP_OK. */
 int cgp_get_stats(cgp_ctx ctx, void* stream, cgp_stats* st);
 
+typedef struct cgp_batch_s* cgp_batch;
 /* ---- batched instances (many independent meshes advanced together) ------------------------
  * A batch advances n contexts (same precision and device, each after cgp_set_bc) by the step of
  * cgp_step, with one cooperative launch per persistent stage for all instances: the grid (up to
@@ -386,8 +387,8 @@ int cgp_get_stats(cgp_ctx ctx, void* stream, cgp_stats* st);
  * the paper: a systems pattern for many small problems.
  * u_devs[i] [n_fine_i][2] and pc_devs[i] [n_coarse_i] are the instances' state, caller-owned
  * device buffers that must stay valid until cgp_batch_destroy. Contexts with projection != 0 are
- * rejected (CGP_ERR_ARG). */
-typedef struct cgp_batch_s* cgp_batch;
+ * rejected (CGP_ERR_ARG). Errors: CGP_ERR_ARG (NULL, n <= 0, mixed precisions or devices, a context with
+ * projection != 0), CGP_ERR_STATE (a context before cgp_set_bc), CGP_ERR_NOMEM, CGP_ERR_CUDA. */
 int cgp_batch_create(cgp_ctx* ctxs, int n, double* const* u_devs, double* const* pc_devs, cgp_batch* out);
 /* Launch shape: total blocks and each instance's group sizes (arrays of n, may be NULL).
  * Host-side; errors: CGP_ERR_ARG (NULL batch). */
@@ -453,6 +454,7 @@ int cgp_ws_train_step(cgp_ws w, const double* b_dev, const double* p_dev, int B,
 /* Synchronise and return the network's device error word (CGP_ERR_TIMEOUT if a bounded
  * tensor-core pipeline wait gave up), else CGP_OK. */
 int cgp_ws_status(cgp_ws w, void* stream);
+/* Free the network and its device buffers. NULL is accepted. Returns CGP_OK. */
 int cgp_ws_destroy(cgp_ws w);
 
 /* Residual form of the learned warm start: the network corrects a base guess x_base (for example
@@ -461,9 +463,12 @@ int cgp_ws_destroy(cgp_ws w);
  * p = x_base + ||r|| NN(r / ||r||). Training on pairs (b, p): the same r as input and the
  * correction p - x_base as target (loss as in cgp_ws_train_step). b_dev, base_dev, p_dev: [B][n]
  * float64 with n = the context's n_coarse (else CGP_ERR_ARG). The first call allocates two
- * [batch_max][n] buffers. Stream-ordered. */
+ * [batch_max][n] buffers. Stream-ordered. Errors: CGP_ERR_ARG (NULL, B outside 1..batch_max,
+ * n mismatch), CGP_ERR_STATE (context before cgp_set_bc), CGP_ERR_NOMEM, CGP_ERR_CUDA. */
 int cgp_ws_forward_residual(cgp_ws w, cgp_ctx ctx, const double* b_dev, const double* base_dev, int B, double* p_dev,
                             void* stream);
+/* Training step of the residual form above, on pairs (b_dev, p_dev) with base guesses base_dev.
+ * Stream-ordered. Errors: as cgp_ws_forward_residual, plus CGP_ERR_ARG for a negative or NaN lr. */
 int cgp_ws_train_step_residual(cgp_ws w, cgp_ctx ctx, const double* b_dev, const double* p_dev, const double* base_dev,
                                int B, float lr, float* loss_dev, void* stream);
 

@@ -43,6 +43,20 @@ def test_binding_declares_every_entry_point(L):
     assert not missing, missing
 
 
+def test_every_entry_point_documents_its_errors():
+    """Each declaration of the boundary header carries a comment that states what it does and how
+    it fails (its CGP_ERR_* codes, or what it returns when it cannot fail)."""
+    decl = open(os.path.join(ROOT, "include", "cgp.h")).read()
+    names = re.findall(r"^\s*(?:int|void|const char\*)\s+(cgp_\w+)\(", decl, re.M)
+    documented = {m.group(2): m.group(1) for m in
+                  re.finditer(r"/\*((?:(?!\*/).)*)\*/\s*(?:int|void|const char\*)\s+(cgp_\w+)\(", decl, re.S)}
+    missing = [n for n in names if n not in documented]
+    assert not missing, missing
+    silent = [n for n, doc in documented.items()
+              if not re.search(r"Errors|CGP_ERR_|Returns|returns|nothing is written|never NULL", doc)]
+    assert not silent, silent
+
+
 def _header_structs():
     """Field lists (C type, name) of the header's typedef structs, comments removed."""
     text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "cgp.h")).read(), flags=re.S)
