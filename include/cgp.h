@@ -387,8 +387,9 @@ typedef struct cgp_batch_s* cgp_batch;
  * the paper: a systems pattern for many small problems.
  * u_devs[i] [n_fine_i][2] and pc_devs[i] [n_coarse_i] are the instances' state, caller-owned
  * device buffers that must stay valid until cgp_batch_destroy. Contexts with projection != 0 are
- * rejected (CGP_ERR_ARG). Errors: CGP_ERR_ARG (NULL, n <= 0, mixed precisions or devices, a context with
- * projection != 0), CGP_ERR_STATE (a context before cgp_set_bc), CGP_ERR_NOMEM, CGP_ERR_CUDA. */
+ * rejected (CGP_ERR_ARG). Errors: CGP_ERR_ARG (NULL, n <= 0, mixed precisions or devices, a
+ * context with projection != 0), CGP_ERR_STATE (a context before cgp_set_bc), CGP_ERR_NOMEM,
+ * CGP_ERR_CUDA. */
 int cgp_batch_create(cgp_ctx* ctxs, int n, double* const* u_devs, double* const* pc_devs, cgp_batch* out);
 /* Launch shape: total blocks and each instance's group sizes (arrays of n, may be NULL).
  * Host-side; errors: CGP_ERR_ARG (NULL batch). */
